@@ -1,0 +1,179 @@
+/*
+ * rcp.h -- C ABI of the GB300 (sm_103a) library for randomized complete pivoting (RCP):
+ * the block LDL^T factorization  Pi^T A Pi = L D L^T  of a dense symmetric indefinite A
+ * whose pivots come from a Gaussian sketch B = Omega A (Feng, Xiao and Gu,
+ * "Randomized complete pivoting for solving symmetric indefinite linear systems").
+ *
+ * Layout and conventions (all entry points):
+ *   - Matrices are column-major with a leading dimension (lda >= n).  Only the LOWER
+ *     triangle of a symmetric matrix is read or written.
+ *   - perm[i] (0-based) is the original index of the row/column that ends at position i:
+ *     A(perm[i], perm[j]) = (L D L^T)(i, j).
+ *   - L is unit lower triangular and is returned in the strictly lower triangle of the
+ *     factored array (its unit diagonal is implicit).  D is block diagonal with 1x1 and
+ *     2x2 blocks: Dd[i] = D(i, i), Ds[i] = D(i+1, i) (0 for a 1x1 block and for i = n-1).
+ *   - Device pointers are marked "device"; the caller owns every buffer it passes in.
+ *     A handle owns only its workspace (sketch, panels, status words), allocated with
+ *     cudaMalloc on first use and grown when a larger problem arrives; it is freed by
+ *     rcp_destroy.  One handle serves one stream at a time.
+ *   - Every call is asynchronous on the given stream unless it fills a host rcp_stats,
+ *     in which case it synchronizes that stream before returning.
+ *
+ * Errors: a negative rcp_status is returned before anything is launched when an argument
+ * is invalid.  Numerical faults found on the device (non-finite values, a bounded wait
+ * that ran out) are recorded in the handle's device status word and reported by the next
+ * call that synchronizes (any call given a non-NULL stats, or rcp_sync).  A positive
+ * value is LAPACK's info: 1 + position of the first 1x1 pivot that is exactly zero; the
+ * factorization still completes.  No kernel of this library traps or asserts.
+ */
+#ifndef RCP_GB300_H
+#define RCP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rcp_stream_t;   /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    RCP_OK = 0,
+    RCP_EINVAL = -1,        /* invalid argument                                    */
+    RCP_ENOMEM = -2,        /* workspace allocation failed                         */
+    RCP_ECUDA = -3,         /* a CUDA runtime call failed                          */
+    RCP_ENONFINITE = -4,    /* NaN or Inf met in a pivot or a norm                 */
+    RCP_ETIMEOUT = -5,      /* a bounded device-side wait ran out                  */
+    RCP_ENOCONV = -6,       /* refinement did not reach the tolerance in max_iter  */
+    RCP_EUNSUPPORTED = -7   /* size or option combination not supported            */
+} rcp_status;
+
+typedef enum {
+    RCP_FP64 = 0,           /* everything in FP64 (CUDA cores)                             */
+    RCP_FP32 = 1,           /* FP32 factor; FP32 trailing update on CUDA cores            */
+    RCP_TF32 = 2,           /* FP32 factor; trailing update on tensor cores, TF32 inputs   */
+    RCP_TF32X3 = 3          /* FP32 factor; trailing update with split-TF32 (3 products)   */
+} rcp_prec;
+
+typedef struct {
+    int b;              /* panel width (block size of Algorithm 1); 0 = default 64           */
+    int d;              /* sketch rows (the paper's p; >= 1); 0 = default b + 16             */
+    int q_mode;         /* 1: one sketch pivot per step (q = 1).  Only 1 is supported.       */
+    uint64_t seed;      /* Philox key of the sketch matrix Omega                             */
+    rcp_prec prec;      /* arithmetic of the factor                                          */
+    double alpha;       /* SBKP threshold; 0 = default sqrt(2)/2                             */
+    const void *omega;  /* optional device d x n Omega (ld = d) in the factor precision;     */
+                        /* NULL = draw it from Philox(seed)                                  */
+    int grid;           /* CTAs of the persistent panel kernel; 0 = automatic                */
+} rcp_opts;
+
+typedef struct {
+    double growth_D;          /* rho = max|D_ij| / max|A_ij|  (experiments section)         */
+    double max_abs_L;         /* max |L_ij|, i > j                                          */
+    double min_sketch_ratio;  /* min over steps of ||B(:, pi_k)|| / ||B^(1)||_{1,2}          */
+    int n_2x2;                /* number of 2x2 pivot blocks                                 */
+    int info;                 /* LAPACK-style zero-pivot position (1-based), 0 if none      */
+    int refine_iters;         /* refinement corrections applied (rcp_refine)                */
+    int device_flags;         /* raw device status bits                                     */
+    double berr;              /* final normwise backward error (rcp_refine)                 */
+    double anorm;             /* ||A||_inf of the original matrix (rcp_refine)              */
+} rcp_stats;
+
+typedef struct rcp_handle rcp_handle;
+
+/* Create / destroy a handle.  rcp_create allocates no device memory. */
+rcp_status rcp_create(rcp_handle **h);
+void rcp_destroy(rcp_handle *h);
+
+/* Human-readable name of a status code (static string). */
+const char *rcp_status_string(int status);
+
+/* Wait for the handle's stream work and report the device status word (0 = fine). */
+rcp_status rcp_sync(rcp_handle *h, rcp_stream_t stream);
+
+/* Size the workspace for order n and the given options without factoring, so that a
+ * later call makes no allocation (needed before capturing calls in a CUDA graph). */
+rcp_status rcp_reserve(rcp_handle *h, int n, int nrhs, const rcp_opts *opts);
+
+/*
+ * rcp_factor -- Algorithm 1 (blocked RCP, q = 1): draw Omega (d x n, Philox4x64-10 and
+ * Box-Muller), form B = Omega A, then per block of b columns: per pivot step the
+ * column-norm argmax on B, the symmetric interchange, the SBKP 1x1/2x2 choice
+ * (Figure SBKP, alpha = sqrt(2)/2), the multipliers L21 = A21 A11^{-1} (2x2 inverses in
+ * FP64), the sketch update B(:, k+s:n) -= B(:, k:k+s-1) L(k+s:n, k:k+s-1)^T
+ * (Eq. "Update matrix B"); after the block the deferred trailing update A22 -= W L21^T.
+ *
+ *   n            order (n >= 0; n = 0 is a no-op)
+ *   A, lda       device, n x n lower triangle; double* when opts->prec == RCP_FP64, float*
+ *                otherwise.  In: A.  Out: L in the strictly lower triangle (rows and columns
+ *                permuted), the diagonal overwritten by D's diagonal.
+ *   Dd, Ds       device double[n]: D's diagonal and sub-diagonal
+ *   perm         device int[n]: the permutation (see conventions)
+ *   opts         options (NULL = defaults: FP64, b = 64, d = 80, seed 0)
+ *   stream       CUDA stream
+ *   stats        host, filled after a stream synchronization; NULL = stay asynchronous
+ * Returns RCP_OK, a negative error, or info > 0 (only when stats != NULL).
+ */
+rcp_status rcp_factor(rcp_handle *h, int n, void *A, int lda, double *Dd, double *Ds, int *perm,
+                      const rcp_opts *opts, rcp_stream_t stream, rcp_stats *stats);
+
+/*
+ * rcp_solve -- solution phase (operation-count table, "solution phase"):
+ * X <- Pi L^{-T} D^{-1} L^{-1} Pi^T X for nrhs right-hand sides.
+ *   LA, lda      device factor from rcp_factor (double* for RCP_FP64, float* otherwise)
+ *   Dd, Ds, perm device, from rcp_factor
+ *   prec         the precision the factor was computed in
+ *   X, ldx       device double, n x nrhs: right-hand sides in, solutions out.  For an FP32
+ *                factor the solve runs in FP32 and X is rounded through FP32.
+ */
+rcp_status rcp_solve(rcp_handle *h, int n, int nrhs, const void *LA, int lda, const double *Dd,
+                     const double *Ds, const int *perm, rcp_prec prec, double *X, int ldx,
+                     rcp_stream_t stream);
+
+/*
+ * rcp_refine -- FP64 iterative refinement on top of a (possibly FP32) factor:
+ * x_0 = solve(b); repeat r = b - A x (FP64, original A), berr = ||r||_inf /
+ * (||A||_inf ||x||_inf) (the experiments section's backward error), stop when berr <= tol,
+ * else x += solve(r).  At most max_iter corrections.  The loop control stays on the device
+ * (no host round trip per iteration).
+ *   A64, lda     device double: the ORIGINAL matrix (lower triangle)
+ *   LA, ldla     device factor; Dd, Ds, perm from rcp_factor; prec its precision
+ *   Bv, ldb      device double n x nrhs right-hand sides
+ *   X, ldx       device double n x nrhs, output solutions
+ *   stats        host; when non-NULL: berr (max over columns), refine_iters, anorm; returns
+ *                RCP_ENOCONV if berr > tol after max_iter corrections
+ */
+rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda, const void *LA,
+                      int ldla, const double *Dd, const double *Ds, const int *perm, rcp_prec prec,
+                      const double *Bv, int ldb, double *X, int ldx, double tol, int max_iter,
+                      rcp_stream_t stream, rcp_stats *stats);
+
+/*
+ * rcp_sysv -- solve A X = B end to end: copy the lower triangle of A64 (rounding it to
+ * FP32 for the mixed precisions) into handle workspace, rcp_factor, rcp_refine.
+ *   A64, lda, Bv, ldb, X, ldx   device pointers, or host pointers when host_buffers != 0 (then
+ *                the copies in and out are part of the call; pinned host memory is fastest)
+ *   tol, max_iter               refinement control (max_iter = 0: plain solve, no refinement)
+ *   stats                       host, required (the call synchronizes)
+ */
+rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, const double *Bv,
+                    int ldb, double *X, int ldx, const rcp_opts *opts, double tol, int max_iter,
+                    int host_buffers, rcp_stream_t stream, rcp_stats *stats);
+
+/*
+ * Building blocks exposed for testing.
+ * rcp_omega:  Omega (d x n, ld d, FP64, device) from Philox4x64-10: entries (2t, 2t+1) of
+ *             column j come from counter (j, t, 0, 0) and key (seed, 0) through Box-Muller
+ *             (u1 = (w0 >> 11 + 1) 2^-53, u2 = (w1 >> 11) 2^-53).  Section 3, "draw Omega".
+ * rcp_sketch: B = Omega A (d x n, ld d, device, precision prec) for the lower-stored
+ *             symmetric A; Omega drawn from seed unless omega != NULL.  Section 3, B = Omega A.
+ */
+rcp_status rcp_omega(int d, int n, uint64_t seed, double *omega, rcp_stream_t stream);
+rcp_status rcp_sketch(int n, int d, const void *A, int lda, rcp_prec prec, uint64_t seed,
+                      const void *omega, void *B, rcp_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCP_GB300_H */

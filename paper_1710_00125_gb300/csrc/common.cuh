@@ -1,0 +1,108 @@
+// common.cuh -- device helpers shared by the RCP kernels: status bits, bounded grid
+// barrier, L2-coherent loads and stores, and the per-factorization device state.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rcpk {
+
+// Bits of the device status word.
+enum : int {
+    ST_TIMEOUT = 1,      // a bounded wait ran out
+    ST_NONFINITE = 2,    // NaN/Inf met in a pivot, a multiplier or a norm
+    ST_INTERNAL = 4      // an internal size check failed (the kernel skipped its work)
+};
+
+// Upper bound on a single device-side wait (nanoseconds of %globaltimer).
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
+
+// Device state of one factorization, kept in handle workspace.
+struct FactorState {
+    int next;        // first column of the next panel
+    int k0;          // first column of the current panel
+    int kend;        // one past its last column
+    int info;        // 1 + first zero pivot, 0 if none
+    int n2x2;        // 2x2 blocks so far
+    int n_moved;     // entries in the moved list of the current panel
+    int pad[2];
+    double beta2;           // ||B^(1)||_{1,2}^2 (largest initial sketch column norm^2)
+    double min_ratio;       // min over steps of ||B(:, pi)|| / sqrt(beta2)
+    unsigned long long maxD_bits;   // max |D_ij| as ordered bits of a non-negative double
+    unsigned long long maxL_bits;   // max |L_ij|
+    unsigned long long maxA_bits;   // max |A_ij| of the input
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_acquire_s32(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_s32(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Loads/stores of data exchanged between CTAs inside one kernel: cached in L2 only.
+template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+template <typename T> __device__ __forceinline__ void stcg(T *p, T v) { __stcg(p, v); }
+
+// Grid-wide barrier for a cooperative launch.  `bar` counts arrivals; the barrier with
+// sequence number `seq` (1, 2, ...) completes when bar >= base + seq * nblocks.  The wait is
+// bounded by kWaitLimitNs; on expiry ST_TIMEOUT is set and false is returned to every
+// thread of the CTA.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        red_release_add_u32(bar, 1u);
+        int ok = 1;
+        if (ld_acquire_u32(bar) < target) {
+            unsigned long long t0 = global_ns();
+            unsigned spins = 0;
+            while (ld_acquire_u32(bar) < target) {
+                if ((++spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+                    ok = 0;
+                    atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Base of the arrival counter at kernel entry: every launch completes all its barriers, so
+// the counter is a multiple of nblocks when no CTA of this launch has arrived yet, and at
+// most nblocks-1 arrivals of this launch can precede any CTA's read.
+__device__ __forceinline__ unsigned barrier_base(const unsigned *bar, unsigned nblocks) {
+    unsigned v = ld_acquire_u32(bar);
+    return (v / nblocks) * nblocks;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v) {
+    if (v > 0.0 || v == 0.0) atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
+
+}  // namespace rcpk

@@ -1,0 +1,276 @@
+// interchange.cu -- applies one panel's symmetric interchanges to the stored arrays and
+// performs the deferred trailing update of Algorithm 1 ("compute Schur complement").
+//
+// After a panel, position p >= k0 holds the block-start index phi(p); only a few indices
+// moved (at most twice the panel width).  For each moved index j with new position
+// p = lpos[j]:
+//   perm[p]              <- perm[j]
+//   L(p, 0:k0)           <- L(j, 0:k0)                (rows of the earlier L columns)
+//   A_sym(p, q), q >= kend <- A_sym(j, phi(q))         (only when p itself is >= kend)
+// done as a gather into scratch followed by a scatter (two launches, so no read sees a
+// half-written line).  Then the panel's multipliers go to A(:, k0:kend) in position order,
+// and the trailing update A22 -= W L21^T runs on the lower triangle of A(kend:n, kend:n).
+#include "kernels.h"
+
+namespace rcpk {
+
+template <typename T>
+__device__ __forceinline__ T a_sym_ld(const T *__restrict__ A, int lda, int i, int j) {
+    return i >= j ? A[(size_t)i + (size_t)j * lda] : A[(size_t)j + (size_t)i * lda];
+}
+
+template <typename T>
+__global__ void mark_kernel(FactorWork<T> w, int *phi) {
+    if (ldcg(w.status) != 0) return;
+    const int M = min(ldcg(&w.st->n_moved), w.maxmoved);
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        int j = w.moved[m];
+        phi[w.lpos[j]] = j;
+    }
+}
+
+template <typename T>
+__global__ void gather_kernel(FactorWork<T> w, const int *phi) {
+    if (ldcg(w.status) != 0) return;
+    const int M = min(ldcg(&w.st->n_moved), w.maxmoved);
+    const int m = blockIdx.y;
+    if (m >= M) return;
+    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
+    const int j = w.moved[m], p = w.lpos[j];
+    const T *__restrict__ A = w.A;
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.tmpP[m] = w.perm[j];
+    const int stride = gridDim.x * blockDim.x;
+    T *tl = w.tmpL + (size_t)m * n;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k0; t += stride) tl[t] = A[(size_t)j + (size_t)t * lda];
+    if (p >= kend) {
+        T *ta = w.tmpA + (size_t)m * n;
+        for (int q = kend + blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+            int src = phi[q];
+            ta[q] = a_sym_ld(A, lda, j, src >= 0 ? src : q);
+        }
+    }
+}
+
+template <typename T>
+__global__ void scatter_kernel(FactorWork<T> w) {
+    if (ldcg(w.status) != 0) return;
+    const int M = min(ldcg(&w.st->n_moved), w.maxmoved);
+    const int m = blockIdx.y;
+    if (m >= M) return;
+    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
+    const int j = w.moved[m], p = w.lpos[j];
+    T *__restrict__ A = w.A;
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.perm[p] = w.tmpP[m];
+    const int stride = gridDim.x * blockDim.x;
+    const T *tl = w.tmpL + (size_t)m * n;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k0; t += stride) A[(size_t)p + (size_t)t * lda] = tl[t];
+    if (p >= kend) {
+        const T *ta = w.tmpA + (size_t)m * n;
+        for (int q = kend + blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+            T v = ta[q];
+            if (p >= q) A[(size_t)p + (size_t)q * lda] = v;
+            else A[(size_t)q + (size_t)p * lda] = v;
+        }
+    }
+}
+
+// Panel multipliers into A(:, k0:kend) in position order; clears the position marks.
+template <typename T>
+__global__ void panel_store_kernel(FactorWork<T> w, int *phi) {
+    if (ldcg(w.status) != 0) return;
+    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend, bw = w.bw;
+    const int width = kend - k0;
+    T *__restrict__ A = w.A;
+    for (int j = k0 + blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int p = w.lpos[j];
+        const T *lrow = w.Lp + (size_t)j * bw;
+        const int tmax = min(width, p - k0);
+        for (int t = 0; t < tmax; ++t) A[(size_t)p + (size_t)(k0 + t) * lda] = lrow[t];
+    }
+    if (blockIdx.x == 0) {
+        const int M = min(w.st->n_moved, w.maxmoved);
+        for (int m = threadIdx.x; m < M; m += blockDim.x) phi[w.lpos[w.moved[m]]] = -1;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Trailing update: A(p, q) -= sum_t W(p, t) L(q, t), kend <= q <= p < n, over the lower
+// triangle in TM x TM tiles (persistent loop over the tiles); W rows come from Wbuf
+// (column-major, ld n), L21 from the panel columns A(:, k0:kend) just stored.
+// ------------------------------------------------------------------------------------------
+template <typename T, int TM, int TK, int RM>
+__global__ void __launch_bounds__((TM / RM) * (TM / RM))
+trailing_simt_kernel(FactorWork<T> w) {
+    constexpr int TPR = TM / RM;               // threads along a tile edge
+    constexpr int NT = TPR * TPR;
+    __shared__ T Wsm[TK][TM];
+    __shared__ T Lsm[TK][TM];
+    if (ldcg(w.status) != 0) return;
+    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
+    const int K = kend - k0, N = n - kend;
+    if (K <= 0 || N <= 0) return;
+    const int nt = (N + TM - 1) / TM;
+    const long long total = (long long)nt * (nt + 1) / 2;
+    const int tr = threadIdx.x % TPR, tc = threadIdx.x / TPR;
+    T *__restrict__ A = w.A;
+    const T *__restrict__ W = w.Wbuf;
+    for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        int I = (int)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+        while ((long long)I * (I + 1) / 2 > tile) --I;
+        while ((long long)(I + 1) * (I + 2) / 2 <= tile) ++I;
+        const int J = (int)(tile - (long long)I * (I + 1) / 2);
+        const int p0 = kend + I * TM, q0 = kend + J * TM;
+        T acc[RM][RM];
+#pragma unroll
+        for (int a = 0; a < RM; ++a)
+#pragma unroll
+            for (int b = 0; b < RM; ++b) acc[a][b] = T(0);
+        for (int t0 = 0; t0 < K; t0 += TK) {
+            for (int e = threadIdx.x; e < TK * TM; e += NT) {
+                int r = e % TM, tt = e / TM;
+                int p = p0 + r, q = q0 + r, t = t0 + tt;
+                bool okt = t < K;
+                Wsm[tt][r] = (okt && p < n) ? W[(size_t)p + (size_t)t * n] : T(0);
+                Lsm[tt][r] = (okt && q < n) ? A[(size_t)q + (size_t)(k0 + t) * lda] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int tt = 0; tt < TK; ++tt) {
+                T a[RM], b[RM];
+#pragma unroll
+                for (int x = 0; x < RM; ++x) a[x] = Wsm[tt][tr + TPR * x];
+#pragma unroll
+                for (int x = 0; x < RM; ++x) b[x] = Lsm[tt][tc + TPR * x];
+#pragma unroll
+                for (int x = 0; x < RM; ++x)
+#pragma unroll
+                    for (int y = 0; y < RM; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int y = 0; y < RM; ++y) {
+            const int q = q0 + tc + TPR * y;
+#pragma unroll
+            for (int x = 0; x < RM; ++x) {
+                const int p = p0 + tr + TPR * x;
+                if (p < n && q < n && p >= q) {
+                    T *c = A + (size_t)p + (size_t)q * lda;
+                    *c = *c - acc[x][y];
+                }
+            }
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s) {
+    int *phi = w.moved + w.n;   // second half of the moved buffer holds the position marks
+    mark_kernel<T><<<1, 256, 0, s>>>(w, phi);
+    dim3 g(8, w.maxmoved);
+    gather_kernel<T><<<g, 256, 0, s>>>(w, phi);
+    scatter_kernel<T><<<g, 256, 0, s>>>(w);
+    int blocks = (w.n + 255) / 256;
+    panel_store_kernel<T><<<blocks, 256, 0, s>>>(w, phi);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static int trailing_grid(const void *fn, int threads) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0);
+    return sms * (per > 0 ? per : 1);
+}
+
+template <>
+cudaError_t launch_trailing<double>(const FactorWork<double> &w, int kmin, int mode, cudaStream_t s) {
+    (void)mode;
+    constexpr int TM = 64, TK = 16, RM = 4;
+    static int grid = 0;
+    if (!grid) grid = trailing_grid<double>((const void *)trailing_simt_kernel<double, TM, TK, RM>, 256);
+    long long nt = (w.n - kmin + TM - 1) / TM;
+    long long total = nt * (nt + 1) / 2;
+    int g = (int)(total < grid ? (total > 0 ? total : 1) : grid);
+    trailing_simt_kernel<double, TM, TK, RM><<<g, (TM / RM) * (TM / RM), 0, s>>>(w);
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_trailing<float>(const FactorWork<float> &w, int kmin, int mode, cudaStream_t s) {
+    (void)mode;
+    constexpr int TM = 128, TK = 16, RM = 8;
+    static int grid = 0;
+    if (!grid) grid = trailing_grid<float>((const void *)trailing_simt_kernel<float, TM, TK, RM>, 256);
+    long long nt = (w.n - kmin + TM - 1) / TM;
+    long long total = nt * (nt + 1) / 2;
+    int g = (int)(total < grid ? (total > 0 ? total : 1) : grid);
+    trailing_simt_kernel<float, TM, TK, RM><<<g, (TM / RM) * (TM / RM), 0, s>>>(w);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Start and end of a factorization.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void factor_init_kernel(FactorWork<T> w) {
+    const int n = w.n;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        FactorState *st = w.st;
+        st->next = 0; st->k0 = 0; st->kend = 0; st->info = 0; st->n2x2 = 0; st->n_moved = 0;
+        st->beta2 = 0.0; st->min_ratio = 1.0;
+        st->maxD_bits = 0ull; st->maxL_bits = 0ull; st->maxA_bits = 0ull;
+    }
+    for (int i = tid; i < n; i += gridDim.x * blockDim.x) {
+        w.perm[i] = i;
+        w.moved[n + i] = -1;       // position marks
+        w.Dd[i] = 0.0;
+        w.Ds[i] = 0.0;
+    }
+}
+
+template <typename T>
+__global__ void maxabs_lower_kernel(FactorWork<T> w) {
+    const int n = w.n, lda = w.lda;
+    double m = 0.0;
+    for (int j = blockIdx.x; j < n; j += gridDim.x)
+        for (int i = j + threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs((double)w.A[(size_t)i + (size_t)j * lda]));
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_nonneg(&w.st->maxA_bits, m);
+}
+
+template <typename T>
+__global__ void factor_finish_kernel(FactorWork<T> w) {
+    const int n = w.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        w.A[(size_t)i + (size_t)i * w.lda] = (T)w.Dd[i];
+}
+
+template <typename T>
+cudaError_t launch_factor_init(const FactorWork<T> &w, cudaStream_t s) {
+    int blocks = (w.n + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 1024) blocks = 1024;
+    factor_init_kernel<T><<<blocks, 256, 0, s>>>(w);
+    maxabs_lower_kernel<T><<<w.n < 1024 ? (w.n > 0 ? w.n : 1) : 1024, 256, 0, s>>>(w);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_factor_finish(const FactorWork<T> &w, cudaStream_t s) {
+    int blocks = (w.n + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    factor_finish_kernel<T><<<blocks, 256, 0, s>>>(w);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_interchange<double>(const FactorWork<double> &, cudaStream_t);
+template cudaError_t launch_interchange<float>(const FactorWork<float> &, cudaStream_t);
+template cudaError_t launch_factor_init<double>(const FactorWork<double> &, cudaStream_t);
+template cudaError_t launch_factor_init<float>(const FactorWork<float> &, cudaStream_t);
+template cudaError_t launch_factor_finish<double>(const FactorWork<double> &, cudaStream_t);
+template cudaError_t launch_factor_finish<float>(const FactorWork<float> &, cudaStream_t);
+
+}  // namespace rcpk

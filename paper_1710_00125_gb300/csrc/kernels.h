@@ -1,0 +1,86 @@
+// kernels.h -- launchers of the RCP kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace rcpk {
+
+template <typename T>
+cudaError_t launch_omega(int d, int n, uint64_t seed, T *om, cudaStream_t s);
+
+template <typename TA, typename TC>
+cudaError_t launch_sketch(int n, int d, const TA *A, int lda, const TC *om, TC *B, float *A32, int lda32,
+                          cudaStream_t s);
+
+// Per-factorization workspace pointers used by the panel / interchange / trailing kernels.
+template <typename T>
+struct FactorWork {
+    int n, lda;
+    T *A;               // the matrix being factored (lower storage)
+    int d;
+    T *B;               // sketch, d x n, ld d
+    int bmax, bw;       // panel width target and row stride of the panel buffers (bmax + 1)
+    double alpha;
+    T *Wbuf;            // n x bw, column-major (ld n): W = L D rows of the panel, logical order
+    T *Lp;              // n x bw, row-major by block-start index: the panel's multipliers
+    double *Dd, *Ds;
+    int *perm;
+    int *lpos;          // [n]: final position in the panel of each block-start index
+    int *moved;         // [n]: block-start indices whose position changed
+    FactorState *st;
+    double *s1v, *s2v;  // reduction slots
+    int *s1i, *s2i;
+    T *pay;             // [2][grid][d] sketch columns of the candidates
+    unsigned *bar;
+    int *status;
+    int grid;           // CTAs of the cooperative panel kernel
+    int chunk_cap;      // max columns per CTA
+    // interchange scratch
+    T *tmpA;            // [maxmoved][n]
+    T *tmpL;            // [maxmoved][n]
+    int *tmpP;          // [maxmoved]
+    int maxmoved;
+};
+
+template <typename T>
+size_t panel_smem_bytes(int d, int bw, int chunk_cap);
+
+template <typename T>
+cudaError_t launch_panel(const FactorWork<T> &w, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_trailing(const FactorWork<T> &w, int kmin, int mode, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_factor_init(const FactorWork<T> &w, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_factor_finish(const FactorWork<T> &w, cudaStream_t s);
+
+template <typename T>
+int panel_max_grid(int d, int bw, int chunk_cap);
+
+// Solves and refinement.
+template <typename T>
+cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
+                         const int *perm, double *X, int ldx, T *work, int *flags, int *status,
+                         const int *skip, cudaStream_t s);
+
+size_t symv_part_doubles(int n, int nrhs);
+cudaError_t launch_symv_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx,
+                                 const double *Bv, int ldb, double *R, int ldr, double *part,
+                                 unsigned long long *mx, const int *skip, cudaStream_t s);
+cudaError_t launch_anorm(int n, const double *A, int lda, double *part, double *anorm, cudaStream_t s);
+cudaError_t launch_refine_check(int nrhs, const unsigned long long *mx, const double *anorm, double tol, int *conv,
+                                double *berr, int *iters, int count_iter, cudaStream_t s);
+cudaError_t launch_axpy_update(int n, int nrhs, double *X, int ldx, const double *D, int ldd,
+                               const int *skip, cudaStream_t s);
+cudaError_t launch_copy_lower_f64(int n, const double *src, int lds, void *dst, int ldd, int to_f32,
+                                  cudaStream_t s);
+
+}  // namespace rcpk

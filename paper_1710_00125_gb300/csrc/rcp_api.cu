@@ -1,0 +1,477 @@
+// rcp_api.cu -- the C ABI declared in include/rcp.h: handle, workspace and the host-side
+// orchestration of the kernels on one CUDA stream.  All loop control that depends on data
+// (panel widths, refinement convergence) stays on the device, so the launch sequence of a
+// call depends only on its arguments.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/rcp.h"
+#include "kernels.h"
+
+using namespace rcpk;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct rcp_handle {
+    int device = 0;
+    Buf status, state, bar, scal;                 // small persistent buffers
+    Buf om, B, Wbuf, Lp, lpos, moved, s1v, s2v, s1i, s2i, pay, tmpA, tmpL, tmpP;
+    Buf Y, flags, R, Dc, part;
+    Buf A64, F, Bh, Xh, Dd, Ds, perm;              // rcp_sysv buffers
+};
+
+namespace {
+
+rcp_status grow(Buf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return RCP_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return RCP_ENOMEM;
+    }
+    b.bytes = bytes;
+    return RCP_OK;
+}
+
+#define RCP_TRY(x)                          \
+    do {                                    \
+        rcp_status _s = (x);                \
+        if (_s != RCP_OK) return _s;        \
+    } while (0)
+#define CU_TRY(x)                           \
+    do {                                    \
+        if ((x) != cudaSuccess) {           \
+            cudaGetLastError();             \
+            return RCP_ECUDA;               \
+        }                                   \
+    } while (0)
+
+// Scalars of the refinement loop, laid out in h->scal.
+struct RefineScalars {
+    int conv;
+    int iters;
+    int pad[2];
+    double berr;
+    double anorm;
+    unsigned long long mx[2 * 1024];   // per right-hand side: max |r|, max |x|
+};
+constexpr int kMaxRhs = 1024;
+
+rcp_status ensure_small(rcp_handle *h) {
+    bool fresh = h->status.p == nullptr;
+    RCP_TRY(grow(h->status, 64));
+    RCP_TRY(grow(h->state, sizeof(FactorState)));
+    RCP_TRY(grow(h->bar, 64));
+    RCP_TRY(grow(h->scal, sizeof(RefineScalars)));
+    if (fresh) {
+        CU_TRY(cudaMemset(h->status.p, 0, 64));
+        CU_TRY(cudaMemset(h->bar.p, 0, 64));
+    }
+    return RCP_OK;
+}
+
+struct Resolved {
+    int b, d, grid, chunk_cap, bw, maxmoved;
+    double alpha;
+    rcp_prec prec;
+    uint64_t seed;
+    const void *omega;
+};
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
+    r.prec = o ? o->prec : RCP_FP64;
+    if (r.prec < RCP_FP64 || r.prec > RCP_TF32X3) return RCP_EINVAL;
+    r.b = (o && o->b > 0) ? o->b : 64;
+    r.d = (o && o->d > 0) ? o->d : r.b + 16;
+    if (o && o->q_mode != 0 && o->q_mode != 1) return RCP_EUNSUPPORTED;
+    if (r.b < 1 || r.b > 512 || r.d < 1 || r.d > 128) return RCP_EUNSUPPORTED;
+    r.alpha = (o && o->alpha > 0.0) ? o->alpha : std::sqrt(2.0) / 2.0;
+    if (!(r.alpha < 1.0)) return RCP_EINVAL;
+    r.seed = o ? o->seed : 0;
+    r.omega = o ? o->omega : nullptr;
+    r.bw = r.b + 1;
+    r.maxmoved = 2 * (r.b + 2);
+    const bool f64 = r.prec == RCP_FP64;
+    int maxg = 0;
+    int sms = sm_count();
+    int g = (o && o->grid > 0) ? o->grid : std::min(sms, std::max(1, (n + 31) / 32));
+    if (n > 0) g = std::min(g, n);
+    g = std::max(1, g);
+    r.chunk_cap = (n + g - 1) / g;
+    size_t smem = f64 ? panel_smem_bytes<double>(r.d, r.bw, r.chunk_cap) : panel_smem_bytes<float>(r.d, r.bw, r.chunk_cap);
+    (void)smem;
+    if (r.chunk_cap > 1024) return RCP_EUNSUPPORTED;
+    if (f64) maxg = panel_max_grid<double>(r.d, r.bw, r.chunk_cap);
+    else maxg = panel_max_grid<float>(r.d, r.bw, r.chunk_cap);
+    if (maxg <= 0 || g > maxg) return RCP_EUNSUPPORTED;
+    r.grid = g;
+    return RCP_OK;
+}
+
+template <typename T>
+rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
+    RCP_TRY(ensure_small(h));
+    const size_t N = n > 0 ? n : 1;
+    RCP_TRY(grow(h->om, N * r.d * sizeof(T)));
+    RCP_TRY(grow(h->B, N * r.d * sizeof(T)));
+    RCP_TRY(grow(h->Wbuf, N * r.bw * sizeof(T)));
+    RCP_TRY(grow(h->Lp, N * r.bw * sizeof(T)));
+    RCP_TRY(grow(h->lpos, N * sizeof(int)));
+    RCP_TRY(grow(h->moved, 2 * N * sizeof(int)));
+    RCP_TRY(grow(h->s1v, 2 * (size_t)r.grid * sizeof(double)));
+    RCP_TRY(grow(h->s2v, 3 * (size_t)r.grid * sizeof(double)));
+    RCP_TRY(grow(h->s1i, 2 * (size_t)r.grid * sizeof(int)));
+    RCP_TRY(grow(h->s2i, 2 * (size_t)r.grid * sizeof(int)));
+    RCP_TRY(grow(h->pay, 2 * (size_t)r.grid * r.d * sizeof(T)));
+    RCP_TRY(grow(h->tmpA, (size_t)r.maxmoved * N * sizeof(T)));
+    RCP_TRY(grow(h->tmpL, (size_t)r.maxmoved * N * sizeof(T)));
+    RCP_TRY(grow(h->tmpP, (size_t)r.maxmoved * sizeof(int)));
+    return RCP_OK;
+}
+
+template <typename T>
+FactorWork<T> make_work(rcp_handle *h, int n, T *A, int lda, double *Dd, double *Ds, int *perm, const Resolved &r) {
+    FactorWork<T> w;
+    w.n = n; w.lda = lda; w.A = A;
+    w.d = r.d; w.B = (T *)h->B.p;
+    w.bmax = r.b; w.bw = r.bw; w.alpha = r.alpha;
+    w.Wbuf = (T *)h->Wbuf.p; w.Lp = (T *)h->Lp.p;
+    w.Dd = Dd; w.Ds = Ds; w.perm = perm;
+    w.lpos = (int *)h->lpos.p; w.moved = (int *)h->moved.p;
+    w.st = (FactorState *)h->state.p;
+    w.s1v = (double *)h->s1v.p; w.s2v = (double *)h->s2v.p;
+    w.s1i = (int *)h->s1i.p; w.s2i = (int *)h->s2i.p;
+    w.pay = (T *)h->pay.p;
+    w.bar = (unsigned *)h->bar.p;
+    w.status = (int *)h->status.p;
+    w.grid = r.grid; w.chunk_cap = r.chunk_cap;
+    w.tmpA = (T *)h->tmpA.p; w.tmpL = (T *)h->tmpL.p; w.tmpP = (int *)h->tmpP.p;
+    w.maxmoved = r.maxmoved;
+    return w;
+}
+
+rcp_status status_from_bits(int bits) {
+    if (bits & ST_TIMEOUT) return RCP_ETIMEOUT;
+    if (bits & ST_NONFINITE) return RCP_ENONFINITE;
+    if (bits & ST_INTERNAL) return RCP_ECUDA;
+    return RCP_OK;
+}
+
+double bits_to_double(unsigned long long b) {
+    double v;
+    std::memcpy(&v, &b, sizeof v);
+    return v;
+}
+
+template <typename T>
+rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *Ds, int *perm, const Resolved &r,
+                       cudaStream_t s, rcp_stats *stats) {
+    RCP_TRY(ensure_factor_ws<T>(h, n, r));
+    FactorWork<T> w = make_work<T>(h, n, A, lda, Dd, Ds, perm, r);
+    CU_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
+    CU_TRY(cudaMemsetAsync(h->bar.p, 0, sizeof(unsigned), s));
+    CU_TRY(launch_factor_init<T>(w, s));
+    const T *om = (const T *)r.omega;
+    if (!om) {
+        CU_TRY(launch_omega<T>(r.d, n, r.seed, (T *)h->om.p, s));
+        om = (const T *)h->om.p;
+    }
+    CU_TRY((launch_sketch<T, T>(n, r.d, A, lda, om, w.B, nullptr, 0, s)));
+    const int nblk = (n + r.b - 1) / r.b;
+    for (int blk = 0; blk < nblk; ++blk) {
+        CU_TRY(launch_panel<T>(w, s));
+        CU_TRY(launch_interchange<T>(w, s));
+        CU_TRY(launch_trailing<T>(w, std::min(n, (blk + 1) * r.b), (int)r.prec, s));
+    }
+    CU_TRY(launch_factor_finish<T>(w, s));
+    if (!stats) return RCP_OK;
+    CU_TRY(cudaStreamSynchronize(s));
+    FactorState st;
+    int bits = 0;
+    CU_TRY(cudaMemcpy(&st, h->state.p, sizeof st, cudaMemcpyDeviceToHost));
+    CU_TRY(cudaMemcpy(&bits, h->status.p, sizeof bits, cudaMemcpyDeviceToHost));
+    double maxA = bits_to_double(st.maxA_bits);
+    stats->growth_D = maxA > 0.0 ? bits_to_double(st.maxD_bits) / maxA : 0.0;
+    stats->max_abs_L = bits_to_double(st.maxL_bits);
+    stats->min_sketch_ratio = st.min_ratio;
+    stats->n_2x2 = st.n2x2;
+    stats->info = st.info;
+    stats->device_flags = bits;
+    rcp_status e = status_from_bits(bits);
+    if (e != RCP_OK) return e;
+    return st.info > 0 ? (rcp_status)st.info : RCP_OK;
+}
+
+int solve_nb(int n) { return (n + 63) / 64; }
+
+template <typename T>
+rcp_status solve_impl(rcp_handle *h, int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
+                      const int *perm, double *X, int ldx, const int *skip, cudaStream_t s) {
+    RCP_TRY(ensure_small(h));
+    RCP_TRY(grow(h->Y, (size_t)n * nrhs * sizeof(T)));
+    const int nb = solve_nb(n);
+    bool fresh = h->flags.bytes < (size_t)(2 * nb + 2) * sizeof(int);
+    RCP_TRY(grow(h->flags, (size_t)(2 * nb + 2) * sizeof(int)));
+    if (fresh) CU_TRY(cudaMemsetAsync(h->flags.p, 0, h->flags.bytes, s));
+    CU_TRY(launch_solve<T>(n, nrhs, L, lda, Dd, Ds, perm, X, ldx, (T *)h->Y.p, (int *)h->flags.p,
+                           (int *)h->status.p, skip, s));
+    return RCP_OK;
+}
+
+bool valid_prec(rcp_prec p) { return p >= RCP_FP64 && p <= RCP_TF32X3; }
+
+}  // namespace
+
+extern "C" {
+
+rcp_status rcp_create(rcp_handle **h) {
+    if (!h) return RCP_EINVAL;
+    *h = new (std::nothrow) rcp_handle();
+    if (!*h) return RCP_ENOMEM;
+    cudaGetDevice(&(*h)->device);
+    return RCP_OK;
+}
+
+void rcp_destroy(rcp_handle *h) {
+    if (!h) return;
+    Buf *all[] = {&h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lp, &h->lpos, &h->moved,
+                  &h->s1v, &h->s2v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
+                  &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm};
+    for (Buf *b : all)
+        if (b->p) cudaFree(b->p);
+    delete h;
+}
+
+const char *rcp_status_string(int s) {
+    switch (s) {
+        case RCP_OK: return "ok";
+        case RCP_EINVAL: return "invalid argument";
+        case RCP_ENOMEM: return "device allocation failed";
+        case RCP_ECUDA: return "CUDA runtime error";
+        case RCP_ENONFINITE: return "non-finite value met during the factorization";
+        case RCP_ETIMEOUT: return "a bounded device-side wait ran out";
+        case RCP_ENOCONV: return "refinement did not reach the tolerance";
+        case RCP_EUNSUPPORTED: return "unsupported size or option";
+        default: return s > 0 ? "zero pivot (info > 0)" : "unknown status";
+    }
+}
+
+rcp_status rcp_sync(rcp_handle *h, rcp_stream_t stream) {
+    if (!h) return RCP_EINVAL;
+    CU_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (!h->status.p) return RCP_OK;
+    int bits = 0;
+    CU_TRY(cudaMemcpy(&bits, h->status.p, sizeof bits, cudaMemcpyDeviceToHost));
+    return status_from_bits(bits);
+}
+
+rcp_status rcp_reserve(rcp_handle *h, int n, int nrhs, const rcp_opts *opts) {
+    if (!h || n < 0 || nrhs < 0) return RCP_EINVAL;
+    Resolved r;
+    RCP_TRY(resolve(n, opts, r));
+    if (r.prec == RCP_FP64) RCP_TRY(ensure_factor_ws<double>(h, n, r));
+    else RCP_TRY(ensure_factor_ws<float>(h, n, r));
+    size_t tsz = r.prec == RCP_FP64 ? sizeof(double) : sizeof(float);
+    RCP_TRY(grow(h->Y, (size_t)n * std::max(nrhs, 1) * tsz));
+    RCP_TRY(grow(h->R, (size_t)n * std::max(nrhs, 1) * sizeof(double)));
+    RCP_TRY(grow(h->Dc, (size_t)n * std::max(nrhs, 1) * sizeof(double)));
+    RCP_TRY(grow(h->part, symv_part_doubles(n, std::max(nrhs, 1)) * sizeof(double)));
+    return RCP_OK;
+}
+
+rcp_status rcp_factor(rcp_handle *h, int n, void *A, int lda, double *Dd, double *Ds, int *perm, const rcp_opts *opts,
+                      rcp_stream_t stream, rcp_stats *stats) {
+    if (!h || n < 0 || (n > 0 && (!A || !Dd || !Ds || !perm)) || lda < (n > 0 ? n : 1)) return RCP_EINVAL;
+    if (stats) std::memset(stats, 0, sizeof *stats);
+    if (n == 0) return RCP_OK;
+    Resolved r;
+    RCP_TRY(resolve(n, opts, r));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (r.prec == RCP_FP64) return factor_impl<double>(h, n, (double *)A, lda, Dd, Ds, perm, r, s, stats);
+    return factor_impl<float>(h, n, (float *)A, lda, Dd, Ds, perm, r, s, stats);
+}
+
+rcp_status rcp_solve(rcp_handle *h, int n, int nrhs, const void *LA, int lda, const double *Dd, const double *Ds,
+                     const int *perm, rcp_prec prec, double *X, int ldx, rcp_stream_t stream) {
+    if (!h || n < 0 || nrhs < 0 || !valid_prec(prec)) return RCP_EINVAL;
+    if (n == 0 || nrhs == 0) return RCP_OK;
+    if (!LA || !Dd || !Ds || !perm || !X || lda < n || ldx < n) return RCP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == RCP_FP64) return solve_impl<double>(h, n, nrhs, (const double *)LA, lda, Dd, Ds, perm, X, ldx, nullptr, s);
+    return solve_impl<float>(h, n, nrhs, (const float *)LA, lda, Dd, Ds, perm, X, ldx, nullptr, s);
+}
+
+rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda, const void *LA, int ldla,
+                      const double *Dd, const double *Ds, const int *perm, rcp_prec prec, const double *Bv, int ldb,
+                      double *X, int ldx, double tol, int max_iter, rcp_stream_t stream, rcp_stats *stats) {
+    if (!h || n < 0 || nrhs < 0 || nrhs > kMaxRhs || !valid_prec(prec) || max_iter < 0) return RCP_EINVAL;
+    if (stats) std::memset(stats, 0, sizeof *stats);
+    if (n == 0 || nrhs == 0) return RCP_OK;
+    if (!A64 || !LA || !Dd || !Ds || !perm || !Bv || !X || lda < n || ldla < n || ldb < n || ldx < n) return RCP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    RCP_TRY(ensure_small(h));
+    RCP_TRY(grow(h->R, (size_t)n * nrhs * sizeof(double)));
+    RCP_TRY(grow(h->Dc, (size_t)n * nrhs * sizeof(double)));
+    RCP_TRY(grow(h->part, symv_part_doubles(n, nrhs) * sizeof(double)));
+    RefineScalars *sc = (RefineScalars *)h->scal.p;
+    double *R = (double *)h->R.p, *Dc = (double *)h->Dc.p, *part = (double *)h->part.p;
+    CU_TRY(cudaMemsetAsync(sc, 0, 2 * sizeof(int), s));
+    CU_TRY(launch_anorm(n, A64, lda, part, &sc->anorm, s));
+    CU_TRY(cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double), Bv, (size_t)ldb * sizeof(double), (size_t)n * sizeof(double),
+                             nrhs, cudaMemcpyDeviceToDevice, s));
+    auto do_solve = [&](double *rhs, const int *skip) -> rcp_status {
+        if (prec == RCP_FP64) return solve_impl<double>(h, n, nrhs, (const double *)LA, ldla, Dd, Ds, perm, rhs, rhs == X ? ldx : n, skip, s);
+        return solve_impl<float>(h, n, nrhs, (const float *)LA, ldla, Dd, Ds, perm, rhs, rhs == X ? ldx : n, skip, s);
+    };
+    RCP_TRY(do_solve(X, nullptr));
+    for (int it = 0; it <= max_iter; ++it) {
+        CU_TRY(launch_symv_residual(n, nrhs, A64, lda, X, ldx, Bv, ldb, R, n, part, sc->mx, &sc->conv, s));
+        CU_TRY(launch_refine_check(nrhs, sc->mx, &sc->anorm, tol, &sc->conv, &sc->berr, &sc->iters, it < max_iter, s));
+        if (it == max_iter) break;
+        CU_TRY(cudaMemcpyAsync(Dc, R, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        RCP_TRY(do_solve(Dc, &sc->conv));
+        CU_TRY(launch_axpy_update(n, nrhs, X, ldx, Dc, n, &sc->conv, s));
+    }
+    if (!stats) return RCP_OK;
+    CU_TRY(cudaStreamSynchronize(s));
+    RefineScalars host;
+    CU_TRY(cudaMemcpy(&host, sc, offsetof(RefineScalars, mx), cudaMemcpyDeviceToHost));
+    int bits = 0;
+    CU_TRY(cudaMemcpy(&bits, h->status.p, sizeof bits, cudaMemcpyDeviceToHost));
+    stats->berr = host.berr;
+    stats->anorm = host.anorm;
+    stats->refine_iters = host.iters;
+    stats->device_flags = bits;
+    rcp_status e = status_from_bits(bits);
+    if (e != RCP_OK) return e;
+    if (!(host.berr <= tol)) return RCP_ENOCONV;
+    return RCP_OK;
+}
+
+rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, const double *Bv, int ldb, double *X,
+                    int ldx, const rcp_opts *opts, double tol, int max_iter, int host_buffers, rcp_stream_t stream,
+                    rcp_stats *stats) {
+    if (!h || !stats || n < 0 || nrhs < 0 || nrhs > kMaxRhs || max_iter < 0) return RCP_EINVAL;
+    std::memset(stats, 0, sizeof *stats);
+    if (n == 0 || nrhs == 0) return RCP_OK;
+    if (!A64 || !Bv || !X || lda < n || ldb < n || ldx < n) return RCP_EINVAL;
+    Resolved r;
+    RCP_TRY(resolve(n, opts, r));
+    cudaStream_t s = (cudaStream_t)stream;
+    RCP_TRY(ensure_small(h));
+    const double *dA = A64, *dB = Bv;
+    double *dX = X;
+    int dlda = lda, dldb = ldb, dldx = ldx;
+    if (host_buffers) {
+        RCP_TRY(grow(h->A64, (size_t)n * n * sizeof(double)));
+        RCP_TRY(grow(h->Bh, (size_t)n * nrhs * sizeof(double)));
+        RCP_TRY(grow(h->Xh, (size_t)n * nrhs * sizeof(double)));
+        CU_TRY(cudaMemcpy2DAsync(h->A64.p, (size_t)n * sizeof(double), A64, (size_t)lda * sizeof(double),
+                                 (size_t)n * sizeof(double), n, cudaMemcpyHostToDevice, s));
+        CU_TRY(cudaMemcpy2DAsync(h->Bh.p, (size_t)n * sizeof(double), Bv, (size_t)ldb * sizeof(double),
+                                 (size_t)n * sizeof(double), nrhs, cudaMemcpyHostToDevice, s));
+        dA = (const double *)h->A64.p; dB = (const double *)h->Bh.p; dX = (double *)h->Xh.p;
+        dlda = dldb = dldx = n;
+    }
+    const bool f64 = r.prec == RCP_FP64;
+    RCP_TRY(grow(h->F, (size_t)n * n * (f64 ? sizeof(double) : sizeof(float))));
+    RCP_TRY(grow(h->Dd, (size_t)n * sizeof(double)));
+    RCP_TRY(grow(h->Ds, (size_t)n * sizeof(double)));
+    RCP_TRY(grow(h->perm, (size_t)n * sizeof(int)));
+    CU_TRY(launch_copy_lower_f64(n, dA, dlda, h->F.p, n, f64 ? 0 : 1, s));
+    rcp_stats fst;
+    rcp_status fs;
+    if (f64) fs = factor_impl<double>(h, n, (double *)h->F.p, n, (double *)h->Dd.p, (double *)h->Ds.p, (int *)h->perm.p, r, s, nullptr);
+    else fs = factor_impl<float>(h, n, (float *)h->F.p, n, (double *)h->Dd.p, (double *)h->Ds.p, (int *)h->perm.p, r, s, nullptr);
+    if (fs != RCP_OK) return fs;
+    (void)fst;
+    rcp_stats rst;
+    rcp_status rs = rcp_refine(h, n, nrhs, dA, dlda, h->F.p, n, (double *)h->Dd.p, (double *)h->Ds.p, (int *)h->perm.p, r.prec,
+                               dB, dldb, dX, dldx, tol, max_iter, stream, nullptr);
+    if (rs != RCP_OK) return rs;
+    if (host_buffers)
+        CU_TRY(cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double), dX, (size_t)n * sizeof(double), (size_t)n * sizeof(double),
+                                 nrhs, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    // statistics of both phases
+    FactorState st;
+    RefineScalars host;
+    int bits = 0;
+    CU_TRY(cudaMemcpy(&st, h->state.p, sizeof st, cudaMemcpyDeviceToHost));
+    CU_TRY(cudaMemcpy(&host, h->scal.p, offsetof(RefineScalars, mx), cudaMemcpyDeviceToHost));
+    CU_TRY(cudaMemcpy(&bits, h->status.p, sizeof bits, cudaMemcpyDeviceToHost));
+    double maxA = bits_to_double(st.maxA_bits);
+    stats->growth_D = maxA > 0.0 ? bits_to_double(st.maxD_bits) / maxA : 0.0;
+    stats->max_abs_L = bits_to_double(st.maxL_bits);
+    stats->min_sketch_ratio = st.min_ratio;
+    stats->n_2x2 = st.n2x2;
+    stats->info = st.info;
+    stats->device_flags = bits;
+    stats->berr = host.berr;
+    stats->anorm = host.anorm;
+    stats->refine_iters = host.iters;
+    (void)rst;
+    rcp_status e = status_from_bits(bits);
+    if (e != RCP_OK) return e;
+    if (st.info > 0) return (rcp_status)st.info;
+    if (max_iter > 0 && !(host.berr <= tol)) return RCP_ENOCONV;
+    return RCP_OK;
+}
+
+rcp_status rcp_omega(int d, int n, uint64_t seed, double *omega, rcp_stream_t stream) {
+    if (d < 1 || n < 0 || (n > 0 && !omega)) return RCP_EINVAL;
+    CU_TRY(launch_omega<double>(d, n, seed, omega, (cudaStream_t)stream));
+    return RCP_OK;
+}
+
+rcp_status rcp_sketch(int n, int d, const void *A, int lda, rcp_prec prec, uint64_t seed, const void *omega, void *B,
+                      rcp_stream_t stream) {
+    if (n < 0 || d < 1 || d > 128 || !valid_prec(prec) || (n > 0 && (!A || !B || lda < n))) return RCP_EINVAL;
+    if (n == 0) return RCP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == RCP_FP64) {
+        const double *om = (const double *)omega;
+        double *tmp = nullptr;
+        if (!om) {
+            CU_TRY(cudaMallocAsync((void **)&tmp, (size_t)d * n * sizeof(double), s));
+            CU_TRY(launch_omega<double>(d, n, seed, tmp, s));
+            om = tmp;
+        }
+        cudaError_t e = launch_sketch<double, double>(n, d, (const double *)A, lda, om, (double *)B, nullptr, 0, s);
+        if (tmp) cudaFreeAsync(tmp, s);
+        CU_TRY(e);
+    } else {
+        const float *om = (const float *)omega;
+        float *tmp = nullptr;
+        if (!om) {
+            CU_TRY(cudaMallocAsync((void **)&tmp, (size_t)d * n * sizeof(float), s));
+            CU_TRY(launch_omega<float>(d, n, seed, tmp, s));
+            om = tmp;
+        }
+        cudaError_t e = launch_sketch<float, float>(n, d, (const float *)A, lda, om, (float *)B, nullptr, 0, s);
+        if (tmp) cudaFreeAsync(tmp, s);
+        CU_TRY(e);
+    }
+    return RCP_OK;
+}
+
+}  // extern "C"

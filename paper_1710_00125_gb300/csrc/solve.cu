@@ -1,0 +1,444 @@
+// solve.cu -- the solution phase (x = Pi L^{-T} D^{-1} L^{-1} Pi^T b, the operation-count
+// table's "solution phase"), and the FP64 pieces of iterative refinement: the residual
+// r = b - A x with the lower-stored original A, ||A||_inf, and the normwise backward error
+// ||r||_inf / (||A||_inf ||x||_inf) of the experiments section.
+//
+// Triangular solves: one persistent launch per triangle.  Row blocks of SV_NB rows are
+// handed out in dependency order through an atomic ticket; a block waits (bounded) on the
+// "done" flags of the blocks it depends on, subtracts their contributions tile by tile,
+// solves its diagonal block one warp per right-hand side, and publishes its flag.
+#include "kernels.h"
+
+namespace rcpk {
+
+constexpr int SV_NB = 64, SV_THREADS = 256, SV_RC = 8;
+
+template <typename T>
+__device__ __forceinline__ bool wait_flag(const int *flag, int epoch, int *status) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (ld_acquire_s32(flag) != epoch) {
+            unsigned long long t0 = global_ns();
+            unsigned spins = 0;
+            while (ld_acquire_s32(flag) != epoch) {
+                if ((++spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+                    ok = 0;
+                    atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// acc[r][c] -= sum_jj M(r, jj) y[jj][c] with M given by (Ms, transposed?) in shared memory.
+template <typename T, bool TRANS>
+__device__ __forceinline__ void block_gemv_sub(T (*acc)[SV_RC], const T (*Ms)[SV_NB + 1], const T (*ys)[SV_RC],
+                                               int nr, int nj, int rc) {
+    const int pairs = SV_NB * rc;
+    const int g = pairs <= 64 ? 4 : (pairs <= 128 ? 2 : 1);
+    if (g == 1) {
+        for (int e = threadIdx.x; e < pairs; e += SV_THREADS) {
+            int r = e % SV_NB, c = e / SV_NB;
+            if (r >= nr) continue;
+            T s = T(0);
+            for (int jj = 0; jj < nj; ++jj) s += (TRANS ? Ms[jj][r] : Ms[r][jj]) * ys[jj][c];
+            acc[r][c] -= s;
+        }
+    } else {
+        // split the inner dimension over g threads of the same warp, then reduce
+        const int e = threadIdx.x / g, sl = threadIdx.x % g;
+        const int r = e % SV_NB, c = e / SV_NB;
+        T s = T(0);
+        if (r < nr)
+            for (int jj = sl; jj < nj; jj += g) s += (TRANS ? Ms[jj][r] : Ms[r][jj]) * ys[jj][c];
+        for (int off = g / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (sl == 0 && r < nr) acc[r][c] -= s;
+    }
+}
+
+// Forward: L y = Pi^T x (L unit lower).  Y (work, type T, n x nrhs, ld n) receives y.
+template <typename T>
+__global__ void __launch_bounds__(SV_THREADS)
+fwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const int *__restrict__ perm,
+           const double *__restrict__ X, int ldx, T *Y, int *flags, int epoch, int *ticket, int *status,
+           const int *skip) {
+    __shared__ T Ms[SV_NB][SV_NB + 1];
+    __shared__ T acc[SV_NB][SV_RC];
+    __shared__ T ys[SV_NB][SV_RC];
+    __shared__ int s_I;
+    if (skip && ldcg(skip)) return;
+    if (ldcg(status) != 0) return;
+    const int nb = (n + SV_NB - 1) / SV_NB;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_I = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int I = s_I;
+        __syncthreads();
+        if (I >= nb) return;
+        const int r0 = I * SV_NB, nr = min(SV_NB, n - r0);
+        for (int c0 = 0; c0 < nrhs; c0 += SV_RC) {
+            const int rc = min(SV_RC, nrhs - c0);
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                acc[r][c] = (r < nr && c < rc) ? (T)X[(size_t)perm[r0 + r] + (size_t)(c0 + c) * ldx] : T(0);
+            }
+            for (int J = 0; J < I; ++J) {
+                if (!wait_flag<T>(flags + J, epoch, status)) return;
+                const int j0 = J * SV_NB;
+                for (int e = threadIdx.x; e < SV_NB * SV_NB; e += SV_THREADS) {
+                    int r = e % SV_NB, jj = e / SV_NB;
+                    Ms[r][jj] = r < nr ? L[(size_t)(r0 + r) + (size_t)(j0 + jj) * lda] : T(0);
+                }
+                for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                    int jj = e % SV_NB, c = e / SV_NB;
+                    ys[jj][c] = c < rc ? ldcg(Y + (size_t)(j0 + jj) + (size_t)(c0 + c) * n) : T(0);
+                }
+                __syncthreads();
+                block_gemv_sub<T, false>(acc, Ms, ys, nr, SV_NB, rc);
+                __syncthreads();
+            }
+            // diagonal block
+            for (int e = threadIdx.x; e < SV_NB * SV_NB; e += SV_THREADS) {
+                int r = e % SV_NB, jj = e / SV_NB;
+                Ms[r][jj] = (r < nr && jj < nr) ? L[(size_t)(r0 + r) + (size_t)(r0 + jj) * lda] : T(0);
+            }
+            __syncthreads();
+            for (int c = warp; c < rc; c += SV_THREADS / 32) {
+                for (int jj = 0; jj < nr; ++jj) {
+                    T z = acc[jj][c];
+                    __syncwarp();
+                    for (int r = jj + 1 + lane; r < nr; r += 32) acc[r][c] -= Ms[r][jj] * z;
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                if (r < nr && c < rc) stcg(Y + (size_t)(r0 + r) + (size_t)(c0 + c) * n, acc[r][c]);
+            }
+            __syncthreads();
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) st_release_s32(flags + I, epoch);
+    }
+}
+
+// Block-diagonal solve D w = y in place (FP64 arithmetic for the 2x2 blocks).
+template <typename T>
+__global__ void dsolve_kernel(int n, int nrhs, const double *__restrict__ Dd, const double *__restrict__ Ds,
+                              T *Y, int *status, const int *skip) {
+    if (skip && ldcg(skip)) return;
+    if (ldcg(status) != 0) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i > 0 && Ds[i - 1] != 0.0) continue;       // second row of a 2x2 block
+        if (i + 1 < n && Ds[i] != 0.0) {
+            const double b = Ds[i], a = Dd[i] / b, c = Dd[i + 1] / b, den = a * c - 1.0;
+            for (int k = 0; k < nrhs; ++k) {
+                T *y = Y + (size_t)k * n;
+                double y1 = (double)y[i] / b, y2 = (double)y[i + 1] / b;
+                y[i] = (T)((c * y1 - y2) / den);
+                y[i + 1] = (T)((a * y2 - y1) / den);
+            }
+        } else {
+            const double dv = Dd[i];
+            for (int k = 0; k < nrhs; ++k) Y[(size_t)i + (size_t)k * n] = (T)((double)Y[(size_t)i + (size_t)k * n] / dv);
+        }
+    }
+}
+
+// Backward: L^T v = w, then X(perm[i], :) = v(i, :).  Blocks are taken last to first.
+template <typename T>
+__global__ void __launch_bounds__(SV_THREADS)
+bwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const int *__restrict__ perm, double *X,
+           int ldx, T *Y, int *flags, int epoch, int *ticket, int *status, const int *skip) {
+    __shared__ T Ms[SV_NB][SV_NB + 1];
+    __shared__ T acc[SV_NB][SV_RC];
+    __shared__ T ys[SV_NB][SV_RC];
+    __shared__ int s_I;
+    if (skip && ldcg(skip)) return;
+    if (ldcg(status) != 0) return;
+    const int nb = (n + SV_NB - 1) / SV_NB;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_I = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int It = s_I;
+        __syncthreads();
+        if (It >= nb) return;
+        const int I = nb - 1 - It;
+        const int r0 = I * SV_NB, nr = min(SV_NB, n - r0);
+        for (int c0 = 0; c0 < nrhs; c0 += SV_RC) {
+            const int rc = min(SV_RC, nrhs - c0);
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                acc[r][c] = (r < nr && c < rc) ? ldcg(Y + (size_t)(r0 + r) + (size_t)(c0 + c) * n) : T(0);
+            }
+            for (int J = nb - 1; J > I; --J) {
+                if (!wait_flag<T>(flags + J, epoch, status)) return;
+                const int j0 = J * SV_NB, nj = min(SV_NB, n - j0);
+                // Ms[jj][r] = L(j0 + jj, r0 + r)
+                for (int e = threadIdx.x; e < SV_NB * SV_NB; e += SV_THREADS) {
+                    int jj = e % SV_NB, r = e / SV_NB;
+                    Ms[jj][r] = (jj < nj && r < nr) ? L[(size_t)(j0 + jj) + (size_t)(r0 + r) * lda] : T(0);
+                }
+                for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                    int jj = e % SV_NB, c = e / SV_NB;
+                    ys[jj][c] = (jj < nj && c < rc) ? ldcg(Y + (size_t)(j0 + jj) + (size_t)(c0 + c) * n) : T(0);
+                }
+                __syncthreads();
+                block_gemv_sub<T, true>(acc, Ms, ys, nr, nj, rc);
+                __syncthreads();
+            }
+            for (int e = threadIdx.x; e < SV_NB * SV_NB; e += SV_THREADS) {
+                int jj = e % SV_NB, r = e / SV_NB;
+                Ms[jj][r] = (jj < nr && r < nr) ? L[(size_t)(r0 + jj) + (size_t)(r0 + r) * lda] : T(0);
+            }
+            __syncthreads();
+            // v_r = acc_r - sum_{jj > r} L(jj, r) v_jj, from the last row up
+            for (int c = warp; c < rc; c += SV_THREADS / 32) {
+                for (int jj = nr - 1; jj >= 0; --jj) {
+                    T z = acc[jj][c];
+                    __syncwarp();
+                    for (int r = lane; r < jj; r += 32) acc[r][c] -= Ms[jj][r] * z;
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                if (r < nr && c < rc) {
+                    stcg(Y + (size_t)(r0 + r) + (size_t)(c0 + c) * n, acc[r][c]);
+                    X[(size_t)perm[r0 + r] + (size_t)(c0 + c) * ldx] = (double)acc[r][c];
+                }
+            }
+            __syncthreads();
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) st_release_s32(flags + I, epoch);
+    }
+}
+
+// work layout: T Y[n * nrhs]; flags: int[2 * nb] (forward, backward); tickets: int[2] right after.
+template <typename T>
+cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
+                         const int *perm, double *X, int ldx, T *work, int *flags, int *status,
+                         const int *skip, cudaStream_t s) {
+    if (n == 0 || nrhs == 0) return cudaSuccess;
+    static int epoch = 0;
+    epoch = epoch % 1000000000 + 1;
+    const int nb = (n + SV_NB - 1) / SV_NB;
+    int *tickets = flags + 2 * nb;
+    cudaError_t e = cudaMemsetAsync(tickets, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = nb < sms ? nb : sms;
+    fwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, perm, X, ldx, work, flags, epoch, tickets, status, skip);
+    dsolve_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(n, nrhs, Dd, Ds, work, status, skip);
+    bwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, perm, X, ldx, work, flags + nb, epoch, tickets + 1,
+                                              status, skip);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_solve<double>(int, int, const double *, int, const double *, const double *, const int *,
+                                          double *, int, double *, int *, int *, const int *, cudaStream_t);
+template cudaError_t launch_solve<float>(int, int, const float *, int, const double *, const double *, const int *,
+                                         double *, int, float *, int *, int *, const int *, cudaStream_t);
+
+// ------------------------------------------------------------------------------------------
+// Refinement pieces (FP64).
+// ------------------------------------------------------------------------------------------
+constexpr int RV_ROWS = 64, RV_CW = 1024;   // row block and column chunk of the row pass
+
+// Row pass: part[ch][c][i] = sum_{j in chunk ch, j <= i} A(i, j) x_j   (ABS: |A(i, j)|, x = 1)
+template <bool ABS>
+__global__ void __launch_bounds__(256)
+symv_rows_kernel(int n, int nrhs, const double *__restrict__ A, int lda, const double *__restrict__ X, int ldx,
+                 double *part, const int *skip) {
+    if (skip && ldcg(skip)) return;
+    const int r0 = blockIdx.x * RV_ROWS, ch = blockIdx.y;
+    const int jlo = ch * RV_CW;
+    const int r = threadIdx.x % RV_ROWS, sl = threadIdx.x / RV_ROWS;   // 4 column slices
+    const int i = r0 + r;
+    const int jhi = min(min(n, jlo + RV_CW), r0 + RV_ROWS);
+    __shared__ double red[4][RV_ROWS];
+    for (int c = 0; c < (ABS ? 1 : nrhs); ++c) {
+        double s = 0.0;
+        if (i < n) {
+            const double *xc = X ? X + (size_t)c * ldx : nullptr;
+            for (int j = jlo + sl; j < jhi; j += 4) {
+                if (j > i) break;
+                double a = A[(size_t)i + (size_t)j * lda];
+                s += ABS ? fabs(a) : a * xc[j];
+            }
+        }
+        red[sl][r] = s;
+        __syncthreads();
+        if (sl == 0 && i < n)
+            part[((size_t)ch * (ABS ? 1 : nrhs) + c) * n + i] = red[0][r] + red[1][r] + red[2][r] + red[3][r];
+        __syncthreads();
+    }
+}
+
+// Column pass: y2[c][j] = sum_{i > j} A(i, j) x_i  (one warp per column)
+template <bool ABS>
+__global__ void symv_cols_kernel(int n, int nrhs, const double *__restrict__ A, int lda,
+                                 const double *__restrict__ X, int ldx, double *y2, const int *skip) {
+    if (skip && ldcg(skip)) return;
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const double *col = A + (size_t)j * lda;
+    for (int c = 0; c < (ABS ? 1 : nrhs); ++c) {
+        const double *xc = X ? X + (size_t)c * ldx : nullptr;
+        double s = 0.0;
+        for (int i = j + 1 + lane; i < n; i += 32) s += ABS ? fabs(col[i]) : col[i] * xc[i];
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) y2[(size_t)c * n + j] = s;
+    }
+}
+
+// R = B - (sum_ch part + y2); per-column max |r| and max |x| into mx[2*c], mx[2*c+1] (bits).
+__global__ void residual_combine_kernel(int n, int nrhs, int nch, const double *part, const double *y2,
+                                        const double *__restrict__ Bv, int ldb, const double *__restrict__ X,
+                                        int ldx, double *R, int ldr, unsigned long long *mx, const int *skip) {
+    if (skip && ldcg(skip)) return;
+    for (int c = 0; c < nrhs; ++c) {
+        double rm = 0.0, xm = 0.0;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            double y = y2[(size_t)c * n + i];
+            for (int ch = 0; ch < nch; ++ch) y += part[((size_t)ch * nrhs + c) * n + i];
+            double r = Bv[(size_t)i + (size_t)c * ldb] - y;
+            R[(size_t)i + (size_t)c * ldr] = r;
+            rm = fmax(rm, fabs(r));
+            xm = fmax(xm, fabs(X[(size_t)i + (size_t)c * ldx]));
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            rm = fmax(rm, __shfl_xor_sync(0xffffffffu, rm, off));
+            xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, off));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (rm > 0.0 || isnan(rm)) atomicMax(mx + 2 * c, (unsigned long long)__double_as_longlong(isnan(rm) ? INFINITY : rm));
+            if (xm > 0.0) atomicMax(mx + 2 * c + 1, (unsigned long long)__double_as_longlong(xm));
+        }
+    }
+}
+
+__global__ void anorm_finish_kernel(int n, int nch, const double *part, const double *y2, double *anorm) {
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double y = y2[i];
+        for (int ch = 0; ch < nch; ++ch) y += part[(size_t)ch * n + i];
+        m = fmax(m, y);
+    }
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) v = fmax(v, red[w]);
+        *anorm = v;
+    }
+}
+
+// berr = max_c ||r_c||_inf / (||A||_inf ||x_c||_inf); sets conv when berr <= tol.
+__global__ void refine_check_kernel(int nrhs, const unsigned long long *mx, const double *anorm, double tol,
+                                    int *conv, double *berr, int *iters, int count_iter) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (*conv) return;
+    double worst = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+        double rm = __longlong_as_double((long long)mx[2 * c]), xm = __longlong_as_double((long long)mx[2 * c + 1]);
+        double e = (*anorm > 0.0 && xm > 0.0) ? rm / (*anorm * xm) : (rm > 0.0 ? INFINITY : 0.0);
+        if (!(e <= worst)) worst = e;
+    }
+    *berr = worst;
+    if (worst <= tol) *conv = 1;
+    else if (count_iter) *iters += 1;
+}
+
+__global__ void axpy_kernel(int n, int nrhs, double *X, int ldx, const double *D, int ldd, const int *skip) {
+    if (skip && ldcg(skip)) return;
+    long long total = (long long)n * nrhs;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(e % n), c = (int)(e / n);
+        X[(size_t)i + (size_t)c * ldx] += D[(size_t)i + (size_t)c * ldd];
+    }
+}
+
+static int nchunks(int n) { return (n + RV_CW - 1) / RV_CW; }
+
+// part: >= symv_part_doubles(n, nrhs) doubles; mx: 2*nrhs u64 maxima
+size_t symv_part_doubles(int n, int nrhs) { return ((size_t)nchunks(n) + 1) * (size_t)nrhs * (size_t)n + 64; }
+
+cudaError_t launch_symv_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx,
+                                 const double *Bv, int ldb, double *R, int ldr, double *part,
+                                 unsigned long long *mx, const int *skip, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int nch = nchunks(n);
+    double *y2 = part + (size_t)nch * nrhs * n;
+    cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * 2 * nrhs, s);
+    if (e != cudaSuccess) return e;
+    dim3 g((n + RV_ROWS - 1) / RV_ROWS, nch);
+    symv_rows_kernel<false><<<g, 256, 0, s>>>(n, nrhs, A, lda, X, ldx, part, skip);
+    symv_cols_kernel<false><<<(n + 7) / 8, 256, 0, s>>>(n, nrhs, A, lda, X, ldx, y2, skip);
+    int blocks = (n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    residual_combine_kernel<<<blocks, 256, 0, s>>>(n, nrhs, nch, part, y2, Bv, ldb, X, ldx, R, ldr, mx, skip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_anorm(int n, const double *A, int lda, double *part, double *anorm, cudaStream_t s) {
+    if (n == 0) return cudaMemsetAsync(anorm, 0, sizeof(double), s);
+    const int nch = nchunks(n);
+    double *y2 = part + (size_t)nch * n;
+    dim3 g((n + RV_ROWS - 1) / RV_ROWS, nch);
+    symv_rows_kernel<true><<<g, 256, 0, s>>>(n, 1, A, lda, nullptr, 0, part, nullptr);
+    symv_cols_kernel<true><<<(n + 7) / 8, 256, 0, s>>>(n, 1, A, lda, nullptr, 0, y2, nullptr);
+    anorm_finish_kernel<<<1, 1024, 0, s>>>(n, nch, part, y2, anorm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_check(int nrhs, const unsigned long long *mx, const double *anorm, double tol, int *conv,
+                                double *berr, int *iters, int count_iter, cudaStream_t s) {
+    refine_check_kernel<<<1, 32, 0, s>>>(nrhs, mx, anorm, tol, conv, berr, iters, count_iter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_update(int n, int nrhs, double *X, int ldx, const double *D, int ldd, const int *skip,
+                               cudaStream_t s) {
+    long long total = (long long)n * nrhs;
+    if (total == 0) return cudaSuccess;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 2048) blocks = 2048;
+    axpy_kernel<<<blocks, 256, 0, s>>>(n, nrhs, X, ldx, D, ldd, skip);
+    return cudaGetLastError();
+}
+
+// Copy of the lower triangle of an FP64 matrix, optionally rounded to FP32.
+__global__ void copy_lower_kernel(int n, const double *__restrict__ src, int lds, void *dst, int ldd, int to_f32) {
+    for (int j = blockIdx.x; j < n; j += gridDim.x)
+        for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+            double v = src[(size_t)i + (size_t)j * lds];
+            if (to_f32) static_cast<float *>(dst)[(size_t)i + (size_t)j * ldd] = (float)v;
+            else static_cast<double *>(dst)[(size_t)i + (size_t)j * ldd] = v;
+        }
+}
+
+cudaError_t launch_copy_lower_f64(int n, const double *src, int lds, void *dst, int ldd, int to_f32, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    copy_lower_kernel<<<n < 4096 ? n : 4096, 256, 0, s>>>(n, src, lds, dst, ldd, to_f32);
+    return cudaGetLastError();
+}
+
+}  // namespace rcpk

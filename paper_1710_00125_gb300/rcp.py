@@ -1,0 +1,237 @@
+"""Thin ctypes binding of the C ABI in ``include/rcp.h`` (argument marshalling only).
+
+Every function here forwards torch tensors' device pointers to the CUDA library
+``_rcp_gb300.so``; no step of the method runs in Python.  Importing this module does not load
+the library; the first call does, and raises ``RuntimeError`` if it is missing or if no CUDA
+device is present (there is no CPU fallback).
+
+Layout: the library is column-major.  A symmetric matrix needs no transpose (a contiguous
+row-major ``n x n`` tensor is also its own column-major storage, ``lda = n``); after
+:func:`rcp_factor` the multipliers sit in the library's strictly lower triangle, i.e. in the
+tensor's strictly UPPER triangle (use :func:`unit_lower` to get L as a normal tensor).
+Right-hand sides are ``(nrhs, n)`` tensors (column-major ``n x nrhs``, ``ldx = n``) or 1-D.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_rcp_gb300.so")
+_lock = threading.Lock()
+_lib = None
+
+RCP_FP64, RCP_FP32, RCP_TF32, RCP_TF32X3 = 0, 1, 2, 3
+PREC_NAMES = {"fp64": RCP_FP64, "fp32": RCP_FP32, "tf32": RCP_TF32, "tf32x3": RCP_TF32X3}
+STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT", -6: "ENOCONV",
+          -7: "EUNSUPPORTED"}
+
+
+class RcpError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({code})")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_int), ("d", ctypes.c_int), ("q_mode", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("prec", ctypes.c_int), ("alpha", ctypes.c_double), ("omega", ctypes.c_void_p),
+                ("grid", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("growth_D", ctypes.c_double), ("max_abs_L", ctypes.c_double),
+                ("min_sketch_ratio", ctypes.c_double), ("n_2x2", ctypes.c_int), ("info", ctypes.c_int),
+                ("refine_iters", ctypes.c_int), ("device_flags", ctypes.c_int), ("berr", ctypes.c_double),
+                ("anorm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def lib():
+    """Load the CUDA library (raises if it is not built or no GPU is visible)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"RCP CUDA library not built ({_LIB_PATH}); run paper_1710_00125_gb300.build.build()")
+        if not torch.cuda.is_available():
+            raise RuntimeError("RCP needs a CUDA device; there is no CPU fallback")
+        torch.cuda.init()
+        L = ctypes.CDLL(_LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.rcp_create.argtypes = [ctypes.POINTER(P)]
+        L.rcp_destroy.argtypes = [P]
+        L.rcp_destroy.restype = None
+        L.rcp_status_string.argtypes = [I]
+        L.rcp_status_string.restype = ctypes.c_char_p
+        L.rcp_sync.argtypes = [P, P]
+        L.rcp_reserve.argtypes = [P, I, I, ctypes.POINTER(Opts)]
+        L.rcp_factor.argtypes = [P, I, P, I, P, P, P, ctypes.POINTER(Opts), P, ctypes.POINTER(Stats)]
+        L.rcp_solve.argtypes = [P, I, I, P, I, P, P, P, I, P, I, P]
+        L.rcp_refine.argtypes = [P, I, I, P, I, P, I, P, P, P, I, P, I, P, I, D, I, P, ctypes.POINTER(Stats)]
+        L.rcp_sysv.argtypes = [P, I, I, P, I, P, I, P, I, ctypes.POINTER(Opts), D, I, I, P, ctypes.POINTER(Stats)]
+        L.rcp_omega.argtypes = [I, I, ctypes.c_uint64, P, P]
+        L.rcp_sketch.argtypes = [I, I, P, I, I, ctypes.c_uint64, P, P, P]
+        for name in ("rcp_create", "rcp_sync", "rcp_reserve", "rcp_factor", "rcp_solve", "rcp_refine", "rcp_sysv",
+                     "rcp_omega", "rcp_sketch"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check(code, where, allow_info=False):
+    if code < 0 or (code > 0 and not allow_info):
+        raise RcpError(code, where)
+    return code
+
+
+def make_opts(b=64, d=None, seed=0, prec=RCP_FP64, alpha=None, omega=None, grid=0, q_mode=1) -> Opts:
+    if isinstance(prec, str):
+        prec = PREC_NAMES[prec]
+    return Opts(b=b, d=(b + 16 if d is None else d), q_mode=q_mode, seed=seed, prec=prec,
+                alpha=(math.sqrt(2.0) / 2.0 if alpha is None else alpha),
+                omega=(omega.data_ptr() if omega is not None else None), grid=grid)
+
+
+class Handle:
+    """Owns an ``rcp_handle`` (workspace); freed when garbage collected."""
+
+    def __init__(self):
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        _check(self._lib.rcp_create(ctypes.byref(h)), "rcp_create")
+        self.h = h
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) and self.h.value:
+                self._lib.rcp_destroy(self.h)
+                self.h = ctypes.c_void_p()
+        except Exception:
+            pass
+
+
+def rcp_create() -> Handle:
+    return Handle()
+
+
+def rcp_sync(h: Handle, stream=None) -> int:
+    return _check(lib().rcp_sync(h.h, _stream(stream)), "rcp_sync")
+
+
+def rcp_reserve(h: Handle, n: int, nrhs: int = 1, opts: Opts | None = None) -> None:
+    _check(lib().rcp_reserve(h.h, n, nrhs, ctypes.byref(opts) if opts else None), "rcp_reserve")
+
+
+def rcp_factor(h: Handle, A: torch.Tensor, Dd: torch.Tensor, Ds: torch.Tensor, perm: torch.Tensor,
+               opts: Opts | None = None, stream=None, stats: bool = True):
+    """Factor the symmetric ``A`` in place (n x n, contiguous, float64 for FP64 else float32).
+    Returns (status, Stats) when ``stats``; status > 0 is LAPACK's info."""
+    n = A.shape[0]
+    assert A.is_cuda and A.is_contiguous() and A.shape == (n, n)
+    st = Stats()
+    code = lib().rcp_factor(h.h, n, _ptr(A), n, _ptr(Dd), _ptr(Ds), _ptr(perm),
+                            ctypes.byref(opts) if opts else None, _stream(stream),
+                            ctypes.byref(st) if stats else None)
+    _check(code, "rcp_factor", allow_info=True)
+    return code, (st if stats else None)
+
+
+def _rhs_view(X, n):
+    if X.dim() == 1:
+        return 1, n
+    assert X.shape[1] == n and X.is_contiguous()
+    return X.shape[0], n
+
+
+def rcp_solve(h: Handle, LA: torch.Tensor, Dd, Ds, perm, prec, X: torch.Tensor, stream=None) -> None:
+    """In place: X <- A^{-1} X using the factor (X float64, (nrhs, n) or (n,))."""
+    n = LA.shape[0]
+    nrhs, ldx = _rhs_view(X, n)
+    if isinstance(prec, str):
+        prec = PREC_NAMES[prec]
+    _check(lib().rcp_solve(h.h, n, nrhs, _ptr(LA), n, _ptr(Dd), _ptr(Ds), _ptr(perm), prec, _ptr(X), ldx,
+                           _stream(stream)), "rcp_solve")
+
+
+def rcp_refine(h: Handle, A64, LA, Dd, Ds, perm, prec, Bv, X, tol=1e-12, max_iter=10, stream=None,
+               stats: bool = True, raise_noconv: bool = False):
+    n = A64.shape[0]
+    nrhs, ldb = _rhs_view(Bv, n)
+    if isinstance(prec, str):
+        prec = PREC_NAMES[prec]
+    st = Stats()
+    code = lib().rcp_refine(h.h, n, nrhs, _ptr(A64), n, _ptr(LA), n, _ptr(Dd), _ptr(Ds), _ptr(perm), prec,
+                            _ptr(Bv), ldb, _ptr(X), ldb, float(tol), int(max_iter), _stream(stream),
+                            ctypes.byref(st) if stats else None)
+    if code == -6 and not raise_noconv:
+        return code, st
+    _check(code, "rcp_refine")
+    return code, (st if stats else None)
+
+
+def rcp_sysv(h: Handle, A64, Bv, X, opts: Opts | None = None, tol=1e-12, max_iter=10, host_buffers=False,
+             stream=None):
+    """Solve A X = B end to end.  With host_buffers the tensors live in (pinned) host memory
+    and the copies are part of the call."""
+    n = A64.shape[0]
+    nrhs, ldb = _rhs_view(Bv, n)
+    st = Stats()
+    code = lib().rcp_sysv(h.h, n, nrhs, _ptr(A64), n, _ptr(Bv), ldb, _ptr(X), ldb,
+                          ctypes.byref(opts) if opts else None, float(tol), int(max_iter), int(bool(host_buffers)),
+                          _stream(stream), ctypes.byref(st))
+    if code != -6:
+        _check(code, "rcp_sysv", allow_info=True)
+    return code, st
+
+
+def rcp_omega(d: int, n: int, seed: int = 0, device="cuda", stream=None) -> torch.Tensor:
+    """Omega as a (d, n) float64 tensor view of the column-major d x n array."""
+    om = torch.empty((n, d), dtype=torch.float64, device=device)
+    _check(lib().rcp_omega(d, n, seed, _ptr(om), _stream(stream)), "rcp_omega")
+    return om.t()
+
+
+def rcp_sketch(A: torch.Tensor, d: int, seed: int = 0, prec=RCP_FP64, omega: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """B = Omega A as a (d, n) tensor view (dtype follows ``prec``)."""
+    n = A.shape[0]
+    if isinstance(prec, str):
+        prec = PREC_NAMES[prec]
+    dt = torch.float64 if prec == RCP_FP64 else torch.float32
+    B = torch.empty((n, d), dtype=dt, device=A.device)
+    om_ptr = None
+    if omega is not None:
+        om_cm = omega.t().contiguous()            # (n, d) row-major = d x n column-major
+        om_ptr = _ptr(om_cm)
+    _check(lib().rcp_sketch(n, d, _ptr(A), n, prec, seed, om_ptr, _ptr(B), _stream(stream)), "rcp_sketch")
+    return B.t()
+
+
+def unit_lower(LA: torch.Tensor) -> torch.Tensor:
+    """L (unit lower triangular) from a factored tensor."""
+    n = LA.shape[0]
+    return torch.tril(LA.t(), -1) + torch.eye(n, dtype=LA.dtype, device=LA.device)
+
+
+def block_d(Dd: torch.Tensor, Ds: torch.Tensor) -> torch.Tensor:
+    D = torch.diag(Dd)
+    off = Ds[:-1]
+    D += torch.diag(off, -1) + torch.diag(off, 1)
+    return D

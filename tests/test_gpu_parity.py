@@ -1,0 +1,235 @@
+"""GPU path vs the CPU oracle, through the C ABI.  Inputs come from the shared seeded
+generators; expected values only from ``oracle``."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1710_00125_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def rcp():
+    from paper_1710_00125_gb300 import rcp as r
+    return r
+
+
+@pytest.fixture(scope="module")
+def handle(rcp):
+    return rcp.rcp_create()
+
+
+def _factor(rcp, handle, a, b, d, seed, prec="fp64", grid=0):
+    n = a.shape[0]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    A = torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(dt)
+    Dd = torch.zeros(n, dtype=torch.float64, device=DEV)
+    Ds = torch.zeros(n, dtype=torch.float64, device=DEV)
+    perm = torch.zeros(n, dtype=torch.int32, device=DEV)
+    code, st = rcp.rcp_factor(handle, A, Dd, Ds, perm, rcp.make_opts(b=b, d=d, seed=seed, prec=prec, grid=grid))
+    return code, st, A, Dd, Ds, perm
+
+
+def _unit_lower(A):
+    n = A.shape[0]
+    return np.tril(A.cpu().double().numpy().T, -1) + np.eye(n)
+
+
+# ------------------------------------------------------------------------------------------
+# Omega and the sketch
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,n,seed", [(1, 5, 0), (7, 33, 1), (40, 256, 0), (80, 1000, 12345)])
+def test_omega_matches_oracle(rcp, d, n, seed):
+    got = rcp.rcp_omega(d, n, seed).cpu().numpy()
+    ref = oracle.omega(seed, d, n)
+    # same Philox words; Box-Muller through CUDA's and the C library's log/sin/cos
+    assert np.allclose(got, ref, rtol=4e-15, atol=4e-15)
+
+
+@pytest.mark.parametrize("n,d", [(1, 3), (63, 5), (130, 40), (257, 80)])
+def test_sketch_matches_oracle(rcp, n, d):
+    a = inputs.gaussian_sym(n, seed=n)
+    A = torch.from_numpy(a).to(DEV)
+    got = rcp.rcp_sketch(A, d, seed=9).cpu().numpy()
+    om = oracle.omega(9, d, n)
+    ref = oracle.sketch(om, a)
+    scale = np.abs(om).max() * np.abs(a).max() * n
+    assert np.max(np.abs(got - ref)) <= 1e-14 * scale
+    got32 = rcp.rcp_sketch(A.float(), d, seed=9, prec="fp32").cpu().double().numpy()
+    assert np.max(np.abs(got32 - ref)) <= 2e-6 * scale
+
+
+# ------------------------------------------------------------------------------------------
+# FP64 factorization: the same pivot sequence as the oracle
+# ------------------------------------------------------------------------------------------
+
+CASES = [
+    (1, 8, 3, 0), (2, 8, 3, 1), (3, 8, 4, 2), (37, 8, 6, 3), (100, 8, 12, 4),     # many panels, ragged
+    (256, 32, 40, 0),                                                               # the n = 256 workload
+    (300, 32, 40, 5), (513, 64, 80, 6),                                             # ragged tails
+]
+
+
+@pytest.mark.parametrize("n,b,d,seed", CASES)
+def test_fp64_factor_matches_oracle(rcp, handle, n, b, d, seed):
+    a = inputs.gaussian_sym(n, seed=seed)
+    ref = oracle.rcp(a, oracle.omega(seed, d, n), record=False)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, b, d, seed)
+    assert code == 0
+    assert np.array_equal(perm.cpu().numpy(), ref["perm"])
+    ds = Ds.cpu().numpy()
+    assert np.array_equal(ds != 0, ref["Ds"] != 0)
+    scale = np.abs(a).max()
+    assert np.allclose(Dd.cpu().numpy(), ref["Dd"], rtol=0, atol=1e-11 * scale * max(1, n / 64))
+    assert np.allclose(ds, ref["Ds"], rtol=0, atol=1e-11 * scale * max(1, n / 64))
+    L = _unit_lower(A)
+    assert np.allclose(L, ref["L"], rtol=0, atol=1e-10 * max(1, n / 64))
+    assert st.n_2x2 == ref["n_2x2"]
+    assert st.growth_D == pytest.approx(oracle.growth_d(ref["Dd"], ref["Ds"], a), rel=1e-10)
+    assert st.max_abs_L == pytest.approx(ref["max_abs_L"], rel=1e-9)
+
+
+@pytest.mark.parametrize("grid", [1, 3, 16])
+def test_fp64_factor_any_grid(rcp, handle, grid):
+    # the result must not depend on how the indices are split over CTAs
+    n, b, d, seed = 150, 16, 20, 8
+    a = inputs.gaussian_sym(n, seed=seed)
+    ref = oracle.rcp(a, oracle.omega(seed, d, n), record=False)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, b, d, seed, grid=grid)
+    assert code == 0
+    assert np.array_equal(perm.cpu().numpy(), ref["perm"])
+
+
+@pytest.mark.parametrize("name", ["bk_worst", "kkt", "dst", "dct", "hankel", "augmented", "spectrum"])
+def test_fp64_structured_families(rcp, handle, name):
+    n = 64
+    a = {"bk_worst": lambda: inputs.bk_worst(n), "kkt": lambda: inputs.kkt(40, 24, seed=1),
+         "dst": lambda: inputs.dst(n), "dct": lambda: inputs.dct(n), "hankel": lambda: inputs.hankel(n, 2),
+         "augmented": lambda: inputs.augmented(40, 24, 3), "spectrum": lambda: inputs.spectrum(n, 4, 4.0, 8)}[name]()
+    d = 12
+    ref = oracle.rcp(a, oracle.omega(2, d, n), record=False)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, 16, d, 2)
+    assert code == ref["info"]
+    D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
+    L = _unit_lower(A)
+    p = perm.cpu().numpy()
+    recon = np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() / np.abs(a).max()
+    assert recon < 1e-12
+    # growth within 1% of the oracle's (its pivot order may differ on exact ties)
+    assert st.growth_D == pytest.approx(oracle.growth_d(ref["Dd"], ref["Ds"], a), rel=0.01)
+    if name in ("bk_worst", "spectrum", "hankel"):
+        assert np.array_equal(p, ref["perm"])
+
+
+def test_degenerate_inputs(rcp, handle):
+    # zero matrix: every pivot is a zero 1x1 (SBKP case 0); info reports the first
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, np.zeros((5, 5)), 4, 3, 0)
+    assert code == 1 and st.info == 1
+    assert np.all(Dd.cpu().numpy() == 0)
+    # [[0, 1], [1, 0]] needs a 2x2 pivot
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, np.array([[0.0, 1.0], [1.0, 0.0]]), 4, 3, 0)
+    assert code == 0 and st.n_2x2 == 1 and Ds.cpu().numpy()[0] == 1.0
+    # NaN input is reported, never trapped
+    a = inputs.gaussian_sym(20, 1)
+    a[3, 3] = np.nan
+    code = None
+    try:
+        code, st, *_ = _factor(rcp, handle, a, 8, 4, 0)
+    except rcp.RcpError as e:
+        code = e.code
+    assert code == -4
+    # the handle stays usable afterwards
+    a = inputs.gaussian_sym(20, 1)
+    code, st, *_ = _factor(rcp, handle, a, 8, 4, 0)
+    assert code == 0
+
+
+def test_invalid_arguments(rcp, handle):
+    lib = rcp.lib()
+    assert lib.rcp_factor(handle.h, -1, None, 1, None, None, None, None, None, None) == -1
+    assert lib.rcp_solve(handle.h, 4, 1, None, 4, None, None, None, 0, None, 4, None) == -1
+
+
+# ------------------------------------------------------------------------------------------
+# Solve and refinement
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,nrhs", [(1, 1), (65, 3), (256, 1), (300, 32)])
+def test_solve_with_oracle_factor(rcp, handle, n, nrhs):
+    # feed the oracle's factorization to the GPU solve and compare with the oracle's solve
+    a = inputs.gaussian_sym(n, seed=n)
+    ref = oracle.rcp(a, oracle.omega(1, 10, n), record=False)
+    LA = torch.from_numpy(np.ascontiguousarray(ref["L"].T)).to(DEV)   # column-major L
+    Dd = torch.from_numpy(ref["Dd"]).to(DEV)
+    Ds = torch.from_numpy(ref["Ds"]).to(DEV)
+    perm = torch.from_numpy(ref["perm"].astype(np.int32)).to(DEV)
+    rhs = inputs.x_true(n, nrhs, seed=3)
+    X = torch.from_numpy(rhs.copy()).to(DEV)
+    rcp.rcp_solve(handle, LA, Dd, Ds, perm, "fp64", X)
+    want = oracle.ldlt_solve(ref["L"], ref["Dd"], ref["Ds"], ref["perm"], rhs.T).T
+    cond = np.linalg.cond(a)
+    assert np.allclose(X.cpu().numpy(), want, rtol=0, atol=1e-13 * cond * np.abs(want).max())
+
+
+def test_fp64_solve_backward_error(rcp, handle):
+    n = 256
+    a = inputs.gaussian_sym(n, seed=0)
+    x = inputs.x_true(n, 1, seed=0)
+    rhs = inputs.rhs_for(a, x)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, 32, 40, 0)
+    X = torch.from_numpy(rhs.copy()).to(DEV)
+    rcp.rcp_solve(handle, A, Dd, Ds, perm, "fp64", X)
+    be = oracle.berr(a, X.cpu().numpy().T, rhs.T)
+    ref = oracle.rcp(a, oracle.omega(0, 40, n), record=False)
+    be_ref = oracle.berr(a, oracle.ldlt_solve(ref["L"], ref["Dd"], ref["Ds"], ref["perm"], rhs.T), rhs.T)
+    assert be <= max(1e-15, 10 * be_ref)
+
+
+@pytest.mark.parametrize("prec", ["fp32"])
+@pytest.mark.parametrize("kexp", [2.0, 4.0, 6.0])
+def test_mixed_refine_reaches_fp64_backward_error(rcp, handle, prec, kexp):
+    n = 384
+    a = inputs.spectrum(n, seed=7, kexp=kexp, nrefl=16)
+    x = inputs.x_true(n, 2, seed=7)
+    rhs = inputs.rhs_for(a, x)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, 32, 48, 1, prec=prec)
+    assert code == 0
+    A64 = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    Bv = torch.from_numpy(rhs.copy()).to(DEV)
+    X = torch.zeros_like(Bv)
+    code, rst = rcp.rcp_refine(handle, A64, A, Dd, Ds, perm, prec, Bv, X, tol=1e-12, max_iter=30)
+    assert code == 0, rst.as_dict()
+    xs = X.cpu().numpy()
+    be = oracle.berr(a, xs.T, rhs.T)
+    assert be <= 1e-12 and rst.berr <= 1e-12
+    assert be == pytest.approx(rst.berr, rel=0.5, abs=1e-16)
+    cond = np.linalg.cond(a)
+    assert np.abs(xs - x).max() / np.abs(x).max() <= 50 * cond * 1e-12
+
+
+def test_sysv_device_and_host_buffers(rcp, handle):
+    n = 200
+    a = inputs.gaussian_sym(n, seed=11)
+    x = inputs.x_true(n, 4, seed=11)
+    rhs = inputs.rhs_for(a, x)
+    for prec in ("fp64", "fp32"):
+        A64 = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+        Bv = torch.from_numpy(rhs.copy()).to(DEV)
+        X = torch.zeros_like(Bv)
+        code, st = rcp.rcp_sysv(handle, A64, Bv, X, rcp.make_opts(b=32, d=40, prec=prec), tol=1e-12, max_iter=10)
+        assert code == 0
+        assert oracle.berr(a, X.cpu().numpy().T, rhs.T) <= 1e-12
+        Ah = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        Bh = torch.from_numpy(rhs.copy()).pin_memory()
+        Xh = torch.zeros_like(Bh).pin_memory()
+        code, st2 = rcp.rcp_sysv(handle, Ah, Bh, Xh, rcp.make_opts(b=32, d=40, prec=prec), tol=1e-12, max_iter=10,
+                                 host_buffers=True)
+        assert code == 0
+        assert np.array_equal(Xh.numpy(), X.cpu().numpy())
