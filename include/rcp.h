@@ -58,7 +58,7 @@ typedef enum {
 
 typedef struct {
     int b;              /* panel width (block size of Algorithm 1); 0 = default 64           */
-    int d;              /* sketch rows (the paper's p; >= 1); 0 = default b + 16             */
+    int d;              /* sketch rows (the paper's p; 1..128); 0 = default min(b + 16, 128) */
     int q_mode;         /* 1: one sketch pivot per step (q = 1).  Only 1 is supported.       */
     uint64_t seed;      /* Philox key of the sketch matrix Omega                             */
     rcp_prec prec;      /* arithmetic of the factor                                          */
@@ -160,6 +160,20 @@ rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda
 rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, const double *Bv,
                     int ldb, double *X, int ldx, const rcp_opts *opts, double tol, int max_iter,
                     int host_buffers, rcp_stream_t stream, rcp_stats *stats);
+
+/*
+ * Phase timing (off by default).  With profiling on, every call brackets each phase's
+ * launches with two CUDA events on its stream; rcp_profile_read waits for them and returns,
+ * per phase, the summed milliseconds and the number of bracketed stretches since the last
+ * read.  Phases: 0 sketch (Omega + B = Omega A), 1 panel, 2 interchange, 3 trailing update,
+ * 4 solve (forward, D, backward), 5 residual (refinement).  Profiling adds event records
+ * between launches, so time calls with it off.
+ */
+rcp_status rcp_profile(rcp_handle *h, int enable);
+
+/* Number of kernels this library has launched in the process so far (all handles). */
+long long rcp_kernel_launches(void);
+rcp_status rcp_profile_read(rcp_handle *h, double *ms, int *launches, int nphase);
 
 /*
  * Building blocks exposed for testing.

@@ -6,6 +6,9 @@
 
 namespace rcpk {
 
+// Host-side count of kernel launches issued by this library (for benchmark reporting).
+void count_launches(long long k);
+
 // Bits of the device status word.
 enum : int {
     ST_TIMEOUT = 1,      // a bounded wait ran out
@@ -70,7 +73,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
+        // the CTA's writes are ordered before this release by the __syncthreads above
         red_release_add_u32(bar, 1u);
         int ok = 1;
         if (ld_acquire_u32(bar) < target) {
@@ -84,7 +87,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int
                 }
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

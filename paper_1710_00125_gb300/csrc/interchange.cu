@@ -167,11 +167,15 @@ template <typename T>
 cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s) {
     int *phi = w.moved + w.n;   // second half of the moved buffer holds the position marks
     mark_kernel<T><<<1, 256, 0, s>>>(w, phi);
+    count_launches(1);
     dim3 g(8, w.maxmoved);
     gather_kernel<T><<<g, 256, 0, s>>>(w, phi);
+    count_launches(1);
     scatter_kernel<T><<<g, 256, 0, s>>>(w);
+    count_launches(1);
     int blocks = (w.n + 255) / 256;
     panel_store_kernel<T><<<blocks, 256, 0, s>>>(w, phi);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -194,6 +198,7 @@ cudaError_t launch_trailing<double>(const FactorWork<double> &w, int kmin, int m
     long long total = nt * (nt + 1) / 2;
     int g = (int)(total < grid ? (total > 0 ? total : 1) : grid);
     trailing_simt_kernel<double, TM, TK, RM><<<g, (TM / RM) * (TM / RM), 0, s>>>(w);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -207,6 +212,7 @@ cudaError_t launch_trailing<float>(const FactorWork<float> &w, int kmin, int mod
     long long total = nt * (nt + 1) / 2;
     int g = (int)(total < grid ? (total > 0 ? total : 1) : grid);
     trailing_simt_kernel<float, TM, TK, RM><<<g, (TM / RM) * (TM / RM), 0, s>>>(w);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -254,7 +260,9 @@ cudaError_t launch_factor_init(const FactorWork<T> &w, cudaStream_t s) {
     if (blocks < 1) blocks = 1;
     if (blocks > 1024) blocks = 1024;
     factor_init_kernel<T><<<blocks, 256, 0, s>>>(w);
+    count_launches(1);
     maxabs_lower_kernel<T><<<w.n < 1024 ? (w.n > 0 ? w.n : 1) : 1024, 256, 0, s>>>(w);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -263,6 +271,7 @@ cudaError_t launch_factor_finish(const FactorWork<T> &w, cudaStream_t s) {
     int blocks = (w.n + 255) / 256;
     if (blocks < 1) blocks = 1;
     factor_finish_kernel<T><<<blocks, 256, 0, s>>>(w);
+    count_launches(1);
     return cudaGetLastError();
 }
 

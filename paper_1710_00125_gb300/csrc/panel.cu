@@ -22,6 +22,7 @@
 //       Schur diagonal update, and the rank-s sketch update fused with the next norms.
 // So one pivot step (1x1 or 2x2) costs two grid-wide barriers.
 #include <climits>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -34,7 +35,7 @@ constexpr unsigned FULL = 0xffffffffu;
 template <typename T>
 size_t panel_smem_bytes(int d, int bw, int chunk_cap) {
     size_t s = 0;
-    s += (size_t)chunk_cap * sizeof(double);           // nrm
+    s += (size_t)chunk_cap * sizeof(double);           // nrm (T, padded to 8 bytes)
     s += (size_t)chunk_cap * d * sizeof(T);            // Bs
     s += (size_t)chunk_cap * bw * sizeof(T);           // Ws
     s += (size_t)chunk_cap * 5 * sizeof(T);            // dg, c1, c2, l1s, l2s
@@ -45,20 +46,24 @@ size_t panel_smem_bytes(int d, int bw, int chunk_cap) {
     return s + 64;
 }
 
-struct Cand {
-    double v;
+template <typename V>
+struct CandT {
+    V v;
     int lpos;
     int phys;
 };
+using Cand = CandT<double>;
 
-__device__ __forceinline__ bool better(double v1, int l1, double v2, int l2) {
+template <typename V>
+__device__ __forceinline__ bool better(V v1, int l1, V v2, int l2) {
     return v1 > v2 || (v1 == v2 && l1 < l2);
 }
 
-__device__ __forceinline__ Cand warp_argmax(Cand c) {
+template <typename V>
+__device__ __forceinline__ CandT<V> warp_argmax(CandT<V> c) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        double v = __shfl_down_sync(FULL, c.v, off);
+        V v = __shfl_down_sync(FULL, c.v, off);
         int l = __shfl_down_sync(FULL, c.lpos, off);
         int p = __shfl_down_sync(FULL, c.phys, off);
         if (better(v, l, c.v, c.lpos)) { c.v = v; c.lpos = l; c.phys = p; }
@@ -67,23 +72,25 @@ __device__ __forceinline__ Cand warp_argmax(Cand c) {
 }
 
 // Block-wide argmax; the result is returned to every thread.
-__device__ __forceinline__ Cand block_argmax(Cand c, Cand *red) {
+template <typename V>
+__device__ __forceinline__ CandT<V> block_argmax(CandT<V> c, CandT<V> *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     c = warp_argmax(c);
     if (lane == 0) red[warp] = c;
     __syncthreads();
     if (warp == 0) {
-        Cand x = lane < PANEL_WARPS ? red[lane] : Cand{-1.0, INT_MAX, -1};
+        CandT<V> x = lane < PANEL_WARPS ? red[lane] : CandT<V>{V(-1), INT_MAX, -1};
         x = warp_argmax(x);
         if (lane == 0) red[PANEL_WARPS] = x;
     }
     __syncthreads();
-    Cand r = red[PANEL_WARPS];
+    CandT<V> r = red[PANEL_WARPS];
     __syncthreads();
     return r;
 }
 
-__device__ __forceinline__ double warp_sum(double s) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T s) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(FULL, s, off);
     return s;
@@ -94,36 +101,65 @@ __device__ __forceinline__ T a_sym(const T *__restrict__ A, int lda, int i, int 
     return i >= j ? A[(size_t)i + (size_t)j * lda] : A[(size_t)j + (size_t)i * lda];
 }
 
-// Reads G slots (value, position, index) and returns the winning CTA (warp 0 only).
-__device__ __forceinline__ int slot_winner(const double *sv, int vstride, const int *si, int G) {
-    const int lane = threadIdx.x & 31;
-    Cand c{-1.0, INT_MAX, lane};
-    for (int g = lane; g < G; g += 32) {
-        double v = ldcg(sv + (size_t)g * vstride);
-        int l = ldcg(si + 2 * (size_t)g);
-        if (better(v, l, c.v, c.lpos)) { c.v = v; c.lpos = l; c.phys = g; }
-    }
-    c = warp_argmax(c);
-    return __shfl_sync(FULL, c.phys, 0);
+// Reduction slots: one 32-byte record per CTA {value, aux1, aux2, (position, index)}.
+__device__ __forceinline__ void slot_write(double *slots, int cta, double v, double a1, double a2, int lpos, int phys) {
+    double2 *p = reinterpret_cast<double2 *>(slots + 4 * (size_t)cta);
+    unsigned long long packed = ((unsigned long long)(unsigned)phys << 32) | (unsigned)lpos;
+    __stcg(p, make_double2(v, a1));
+    __stcg(p + 1, make_double2(a2, __longlong_as_double((long long)packed)));
 }
 
-// c[jl] = A(j, X) - sum_{t < i} Ws[jl][t] lX[t] for the alive owned rows.
+struct SlotWin {
+    double v, a1, a2;
+    int lpos, phys, cta;
+};
+
+// Warp 0: reads all G records in one pass and returns the best (value desc, position asc).
+__device__ __forceinline__ SlotWin slot_reduce(const double *slots, int G) {
+    const int lane = threadIdx.x & 31;
+    SlotWin b{-1.0, 0.0, 0.0, INT_MAX, -1, -1};
+    for (int g = lane; g < G; g += 32) {
+        const double2 *p = reinterpret_cast<const double2 *>(slots + 4 * (size_t)g);
+        double2 x = __ldcg(p), y = __ldcg(p + 1);
+        unsigned long long packed = (unsigned long long)__double_as_longlong(y.y);
+        int lpos = (int)(unsigned)(packed & 0xffffffffull), phys = (int)(unsigned)(packed >> 32);
+        if (better(x.x, lpos, b.v, b.lpos)) b = SlotWin{x.x, x.y, y.x, lpos, phys, g};
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        SlotWin o;
+        o.v = __shfl_down_sync(FULL, b.v, off);
+        o.a1 = __shfl_down_sync(FULL, b.a1, off);
+        o.a2 = __shfl_down_sync(FULL, b.a2, off);
+        o.lpos = __shfl_down_sync(FULL, b.lpos, off);
+        o.phys = __shfl_down_sync(FULL, b.phys, off);
+        o.cta = __shfl_down_sync(FULL, b.cta, off);
+        if (better(o.v, o.lpos, b.v, b.lpos)) b = o;
+    }
+    return b;   // valid in lane 0
+}
+
+// c[jl] = A(j, X) - sum_{t < i} Ws[jl][t] L(X, t) for the alive owned rows.  The loads of
+// the column of A, of L(X, 0:i) (into lX) and of the candidate's sketch column (into bX) are
+// all issued before the first barrier so that their latencies overlap.
 template <typename T>
 __device__ void schur_column(const T *__restrict__ A, int lda, int j_lo, int cnt, int X, int i, int bw,
-                             const T *Ws, const T *lX, const int *alive, T *c) {
+                             const T *Ws, const T *lXg, T *lX, const T *bXg, T *bX, int d, const int *alive, T *c) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // issue the column loads first (at most two rows per thread)
     T a0 = T(0), a1 = T(0);
     const int r0 = threadIdx.x, r1 = threadIdx.x + PANEL_THREADS;
     if (r0 < cnt && alive[r0]) a0 = a_sym(A, lda, j_lo + r0, X);
     if (r1 < cnt && alive[r1]) a1 = a_sym(A, lda, j_lo + r1, X);
+    for (int t = threadIdx.x; t < i; t += PANEL_THREADS) lX[t] = ldcg(lXg + t);
+    for (int r = threadIdx.x; r < d; r += PANEL_THREADS) bX[r] = ldcg(bXg + r);
+    __syncthreads();
     if (i > 0) {
         for (int jl = warp; jl < cnt; jl += PANEL_WARPS) {
             if (!alive[jl]) continue;
-            double s = 0.0;
-            for (int t = lane; t < i; t += 32) s += (double)(Ws[(size_t)jl * bw + t] * lX[t]);
+            T s = T(0);
+            for (int t = lane; t < i; t += 32) s = fma(Ws[(size_t)jl * bw + t], lX[t], s);
             s = warp_sum(s);
-            if (lane == 0) c[jl] = (T)s;
+            if (lane == 0) c[jl] = s;
         }
     } else {
         for (int jl = threadIdx.x; jl < cnt; jl += PANEL_THREADS) c[jl] = T(0);
@@ -137,9 +173,10 @@ __device__ void schur_column(const T *__restrict__ A, int lda, int j_lo, int cnt
 template <typename T>
 __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ Cand s_red[PANEL_WARPS + 1];
+    __shared__ CandT<T> s_red[PANEL_WARPS + 1];
     __shared__ int s_i[16];
     __shared__ double s_d[16];
+    __shared__ T s_t[8];
 
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ldcg(w.status) != 0) return;
@@ -165,8 +202,8 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     const int cnt = max(0, min(n, j_lo + chunk) - j_lo);
     const int cap = w.chunk_cap;
 
-    double *nrm = reinterpret_cast<double *>(smem);
-    T *Bs = reinterpret_cast<T *>(nrm + cap);
+    T *nrm = reinterpret_cast<T *>(smem);
+    T *Bs = reinterpret_cast<T *>(reinterpret_cast<double *>(smem) + cap);
     T *Ws = Bs + (size_t)cap * d;
     T *dg = Ws + (size_t)cap * bw;
     T *c1 = dg + cap;
@@ -203,8 +240,8 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     __syncthreads();
     // initial column norms
     for (int jl = warp; jl < cnt; jl += PANEL_WARPS) {
-        double s = 0.0;
-        for (int r = lane; r < d; r += 32) { double b = (double)Bs[(size_t)jl * d + r]; s += b * b; }
+        T s = T(0);
+        for (int r = lane; r < d; r += 32) { T b = Bs[(size_t)jl * d + r]; s = fma(b, b, s); }
         s = warp_sum(s);
         if (lane == 0) nrm[jl] = s;
     }
@@ -219,97 +256,104 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
 
     while (i < w.bmax && k < n) {
         // ---------------- (1) sketch column-norm argmax ----------------
-        Cand c{-1.0, INT_MAX, -1};
+        CandT<T> c{T(-1), INT_MAX, -1};
         for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
-            if (alive[jl] && better(nrm[jl], lp[jl], c.v, c.lpos)) c = Cand{nrm[jl], lp[jl], j_lo + jl};
+            if (alive[jl] && better(nrm[jl], lp[jl], c.v, c.lpos)) c = CandT<T>{nrm[jl], lp[jl], j_lo + jl};
         c = block_argmax(c, s_red);
         if (c.phys >= 0)
             for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay1 + (size_t)cta * d + r, Bs[(size_t)(c.phys - j_lo) * d + r]);
-        if (tid == 0) {
-            stcg(w.s1v + 2 * (size_t)cta, c.v);
-            stcg(w.s1v + 2 * (size_t)cta + 1, c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0);
-            stcg(w.s1i + 2 * (size_t)cta, c.lpos);
-            stcg(w.s1i + 2 * (size_t)cta + 1, c.phys);
-        }
+        if (tid == 0)
+            slot_write(w.s1v, cta, (double)c.v, c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0, 0.0, c.lpos, c.phys);
         if (!grid_barrier(w.bar, base + (++nbar) * (unsigned)G, w.status)) return;
         if (warp == 0) {
-            int g = slot_winner(w.s1v, 2, w.s1i, G);
+            SlotWin b = slot_reduce(w.s1v, G);
             if (lane == 0) {
-                s_i[1] = ldcg(w.s1i + 2 * (size_t)g + 1);   // P
-                s_i[2] = ldcg(w.s1i + 2 * (size_t)g);       // position of P
-                s_i[3] = g;
-                s_d[0] = ldcg(w.s1v + 2 * (size_t)g);       // ||B(:, P)||^2
-                s_d[1] = ldcg(w.s1v + 2 * (size_t)g + 1);   // a_kk
+                s_i[1] = b.phys;   // P
+                s_i[2] = b.lpos;   // position of P
+                s_i[3] = b.cta;
+                s_d[0] = b.v;      // ||B(:, P)||^2
+                s_d[1] = b.a1;     // a_kk
+                const int P = b.phys, LP = b.lpos;
+                if (P >= 0) {
+                    // interchange k <-> LP (positions); Q is the index now at position k
+                    int Q = win[k - k0];
+                    if (LP - k0 < wsz) win[LP - k0] = Q;
+                    win[k - k0] = P;
+                    if (P >= j_lo && P < j_lo + cnt) lp[P - j_lo] = k;
+                    if (Q != P && Q >= j_lo && Q < j_lo + cnt) lp[Q - j_lo] = LP;
+                }
+                if (cta == 0 && P >= 0) {
+                    if (k == 0) w.st->beta2 = b.v;
+                    double b2 = (k == 0) ? b.v : ldcg(&w.st->beta2);
+                    if (b2 > 0.0) minratio = fmin(minratio, sqrt(b.v / b2));
+                }
             }
         }
         __syncthreads();
-        const int P = s_i[1], LP = s_i[2], gP = s_i[3];
-        const double norm2 = s_d[0], akk = s_d[1];
-        if (P < 0 || !isfinite(norm2) || !isfinite(akk)) { fail = ST_NONFINITE; break; }
-        for (int r = tid; r < d; r += PANEL_THREADS) bP[r] = ldcg(pay1 + (size_t)gP * d + r);
-        for (int t = tid; t < i; t += PANEL_THREADS) lP[t] = ldcg(w.Lp + (size_t)P * bw + t);
-        if (tid == 0) {
-            // interchange k <-> LP (positions); Q is the index now at position k
-            int Q = win[k - k0];
-            if (LP - k0 < wsz) win[LP - k0] = Q;
-            win[k - k0] = P;
-            if (P >= j_lo && P < j_lo + cnt) lp[P - j_lo] = k;
-            if (Q != P && Q >= j_lo && Q < j_lo + cnt) lp[Q - j_lo] = LP;
-            if (cta == 0) {
-                if (k == 0) w.st->beta2 = norm2;
-                double b2 = (k == 0) ? norm2 : ldcg(&w.st->beta2);
-                if (b2 > 0.0) minratio = fmin(minratio, sqrt(norm2 / b2));
-            }
-        }
-        __syncthreads();
+        const int P = s_i[1], gP = s_i[3];
+        const double akk = s_d[1];
+        if (P < 0 || !isfinite(s_d[0]) || !isfinite(akk)) { fail = ST_NONFINITE; break; }
 
         // ---------------- (2) column P of the Schur complement, lambda and r ----------------
-        schur_column<T>(A, lda, j_lo, cnt, P, i, bw, Ws, lP, alive, c1);
-        c = Cand{-1.0, INT_MAX, -1};
+        schur_column<T>(A, lda, j_lo, cnt, P, i, bw, Ws, w.Lp + (size_t)P * bw, lP, pay1 + (size_t)gP * d, bP, d,
+                        alive, c1);
+        c = CandT<T>{T(-1), INT_MAX, -1};
         for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
             if (!alive[jl] || j_lo + jl == P) continue;
-            double v = fabs((double)c1[jl]);
-            if (better(v, lp[jl], c.v, c.lpos)) c = Cand{v, lp[jl], j_lo + jl};
+            T v = fabs(c1[jl]);
+            if (better(v, lp[jl], c.v, c.lpos)) c = CandT<T>{v, lp[jl], j_lo + jl};
         }
         c = block_argmax(c, s_red);
         if (c.phys >= 0)
             for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay2 + (size_t)cta * d + r, Bs[(size_t)(c.phys - j_lo) * d + r]);
-        if (tid == 0) {
-            stcg(w.s2v + 3 * (size_t)cta, c.v);
-            stcg(w.s2v + 3 * (size_t)cta + 1, c.phys >= 0 ? (double)c1[c.phys - j_lo] : 0.0);
-            stcg(w.s2v + 3 * (size_t)cta + 2, c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0);
-            stcg(w.s2i + 2 * (size_t)cta, c.lpos);
-            stcg(w.s2i + 2 * (size_t)cta + 1, c.phys);
-        }
+        if (tid == 0)
+            slot_write(w.s2v, cta, (double)c.v, c.phys >= 0 ? (double)c1[c.phys - j_lo] : 0.0,
+                       c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0, c.lpos, c.phys);
         if (!grid_barrier(w.bar, base + (++nbar) * (unsigned)G, w.status)) return;
         if (warp == 0) {
-            int g = slot_winner(w.s2v, 3, w.s2i, G);
+            SlotWin b = slot_reduce(w.s2v, G);
             if (lane == 0) {
-                s_i[4] = ldcg(w.s2i + 2 * (size_t)g + 1);   // R (or -1)
-                s_i[5] = ldcg(w.s2i + 2 * (size_t)g);       // position of R
+                // one thread takes the SBKP decision (FP64 scalars); everything the other
+                // threads need goes through shared memory
+                const int R = b.phys;   // r (or -1)
+                const double lam = R >= 0 ? b.v : 0.0;
+                const double ark = R >= 0 ? b.a1 : 0.0;
+                const double arr = R >= 0 ? b.a2 : 0.0;
+                const int g = b.cta;
+                int kase;
+                if (!isfinite(lam) || !isfinite(ark) || !isfinite(arr)) kase = -1;
+                else if (lam == 0.0) kase = 0;
+                else if (fabs(akk) >= alpha * lam) kase = 1;
+                else if (fabs(arr) >= alpha * lam) kase = 2;
+                else kase = 3;
+                s_i[4] = R;
+                s_i[5] = R >= 0 ? b.lpos : -1;   // position of r
                 s_i[6] = g;
-                s_d[2] = ldcg(w.s2v + 3 * (size_t)g);       // lambda
-                s_d[3] = ldcg(w.s2v + 3 * (size_t)g + 1);   // a_rk
-                s_d[4] = ldcg(w.s2v + 3 * (size_t)g + 2);   // a_rr
+                s_i[7] = kase;
+                s_d[2] = lam; s_d[3] = ark; s_d[4] = arr;
+                const double dpiv = kase == 2 ? arr : akk;
+                s_d[5] = dpiv;
+                if (kase == 3) {
+                    const double aa = akk / ark, cc = arr / ark, tinv = 1.0 / (aa * cc - 1.0);
+                    s_t[0] = (T)aa; s_t[1] = (T)cc; s_t[2] = (T)tinv; s_t[3] = (T)ark; s_t[4] = (T)(1.0 / ark);
+                } else {
+                    s_t[0] = s_t[1] = s_t[2] = T(0);
+                    s_t[3] = T(1); s_t[4] = T(1);
+                }
+                s_t[5] = (T)dpiv;
+                s_t[6] = dpiv != 0.0 ? (T)(1.0 / dpiv) : T(0);
+                s_i[8] = dpiv != 0.0;
             }
         }
         __syncthreads();
-        const int R = s_i[4], LR = s_i[5], gR = s_i[6];
-        const double lam = R >= 0 ? s_d[2] : 0.0, ark = s_d[3], arr = s_d[4];
-        if (!isfinite(lam) || (R >= 0 && (!isfinite(ark) || !isfinite(arr)))) { fail = ST_NONFINITE; break; }
-
-        // ---------------- (3) SBKP ----------------
-        int kase;
-        if (lam == 0.0) kase = 0;
-        else if (fabs(akk) >= alpha * lam) kase = 1;
-        else if (fabs(arr) >= alpha * lam) kase = 2;
-        else kase = 3;
+        const int R = s_i[4], LR = s_i[5], gR = s_i[6], kase = s_i[7];
+        if (kase < 0) { fail = ST_NONFINITE; break; }
+        const double lam = s_d[2], ark = s_d[3], arr = s_d[4];
+        (void)lam;
         const int s = kase == 3 ? 2 : 1;
         if (kase >= 2) {
-            for (int r = tid; r < d; r += PANEL_THREADS) bR[r] = ldcg(pay2 + (size_t)gR * d + r);
-            for (int t = tid; t < i; t += PANEL_THREADS) lR[t] = ldcg(w.Lp + (size_t)R * bw + t);
-            __syncthreads();
-            schur_column<T>(A, lda, j_lo, cnt, R, i, bw, Ws, lR, alive, c2);
+            schur_column<T>(A, lda, j_lo, cnt, R, i, bw, Ws, w.Lp + (size_t)R * bw, lR, pay2 + (size_t)gR * d, bR, d,
+                            alive, c2);
             if (tid == 0) {
                 if (kase == 2) {
                     // interchange k <-> LR: R to position k, P to LR
@@ -331,10 +375,11 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         // ---------------- (4) multipliers, W, diagonal, sketch update ----------------
         const int piv1 = kase == 2 ? R : P;
         const int piv2 = kase == 3 ? R : -1;
-        // 2x2 inverse in FP64, scaled by the off-diagonal entry
-        const double aa = kase == 3 ? akk / ark : 0.0, cc = kase == 3 ? arr / ark : 0.0;
-        const double tinv = kase == 3 ? 1.0 / (aa * cc - 1.0) : 0.0;
-        const double dpiv = kase == 2 ? arr : akk;
+        const double dpiv = s_d[5];
+        const bool nonzero_piv = s_i[8] != 0;
+        const T t_aa = s_t[0], t_cc = s_t[1], t_tinv = s_t[2], t_ark = s_t[3], t_rark = s_t[4];
+        const T t_dpiv = s_t[5], t_rdpiv = s_t[6];
+        T tmaxL = T(0);
         for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
             if (!alive[jl]) continue;
             const int j = j_lo + jl;
@@ -347,32 +392,34 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 alive[jl] = 0;
                 continue;
             }
-            double l1 = 0.0, l2 = 0.0;
+            T l1 = T(0), l2 = T(0);
             if (kase <= 1) {
-                double cv = (double)c1[jl];
-                l1 = dpiv != 0.0 ? cv / dpiv : 0.0;
-                wrow[i] = c1[jl];
-                dg[jl] = (T)((double)dg[jl] - cv * l1);
+                const T cv = c1[jl];
+                if (nonzero_piv) l1 = std::is_same<T, double>::value ? cv / t_dpiv : cv * t_rdpiv;
+                wrow[i] = cv;
+                dg[jl] = fma(-cv, l1, dg[jl]);
             } else if (kase == 2) {
-                double cv = (double)c2[jl];
-                l1 = cv / dpiv;
-                wrow[i] = c2[jl];
-                dg[jl] = (T)((double)dg[jl] - cv * l1);
+                const T cv = c2[jl];
+                l1 = std::is_same<T, double>::value ? cv / t_dpiv : cv * t_rdpiv;
+                wrow[i] = cv;
+                dg[jl] = fma(-cv, l1, dg[jl]);
             } else {
-                double x1 = (double)c1[jl] / ark, x2 = (double)c2[jl] / ark;
-                l1 = tinv * (cc * x1 - x2);
-                l2 = tinv * (aa * x2 - x1);
-                wrow[i] = c1[jl];
-                wrow[i + 1] = c2[jl];
-                dg[jl] = (T)((double)dg[jl] - (double)c1[jl] * l1 - (double)c2[jl] * l2);
+                const T v1 = c1[jl], v2 = c2[jl];
+                const T x1 = std::is_same<T, double>::value ? v1 / t_ark : v1 * t_rark;
+                const T x2 = std::is_same<T, double>::value ? v2 / t_ark : v2 * t_rark;
+                l1 = t_tinv * (t_cc * x1 - x2);
+                l2 = t_tinv * (t_aa * x2 - x1);
+                wrow[i] = v1;
+                wrow[i + 1] = v2;
+                dg[jl] = dg[jl] - v1 * l1 - v2 * l2;
             }
-            T tl1 = (T)l1, tl2 = (T)l2;
-            stcg(lrow + i, tl1);
-            if (s == 2) stcg(lrow + i + 1, tl2);
-            l1s[jl] = tl1;
-            l2s[jl] = tl2;
-            maxL = fmax(maxL, fmax(fabs(l1), fabs(l2)));
+            stcg(lrow + i, l1);
+            if (s == 2) stcg(lrow + i + 1, l2);
+            l1s[jl] = l1;
+            l2s[jl] = l2;
+            tmaxL = fmax(tmaxL, fmax(fabs(l1), fabs(l2)));
         }
+        maxL = fmax(maxL, (double)tmaxL);
         __syncthreads();
         // rank-s sketch update fused with the next column norms
         const T *b1 = kase == 2 ? bR : bP;
@@ -380,18 +427,18 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             if (!alive[jl]) continue;
             const T f1 = l1s[jl], f2 = l2s[jl];
             T *col = Bs + (size_t)jl * d;
-            double sacc = 0.0;
+            T sacc = T(0);
             if (s == 2) {
                 for (int r = lane; r < d; r += 32) {
                     T v = col[r] - b1[r] * f1 - bR[r] * f2;
                     col[r] = v;
-                    sacc += (double)v * (double)v;
+                    sacc = fma(v, v, sacc);
                 }
             } else {
                 for (int r = lane; r < d; r += 32) {
                     T v = col[r] - b1[r] * f1;
                     col[r] = v;
-                    sacc += (double)v * (double)v;
+                    sacc = fma(v, v, sacc);
                 }
             }
             sacc = warp_sum(sacc);
@@ -479,6 +526,7 @@ cudaError_t launch_panel(const FactorWork<T> &w, cudaStream_t s) {
     if (smem > panel_dyn_limit<T>()) return cudaErrorInvalidValue;
     FactorWork<T> arg = w;
     void *args[] = {&arg};
+    count_launches(1);
     return cudaLaunchCooperativeKernel((const void *)panel_kernel<T>, dim3(w.grid), dim3(PANEL_THREADS), args, smem, s);
 }
 

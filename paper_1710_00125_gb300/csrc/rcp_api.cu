@@ -5,12 +5,19 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "../../include/rcp.h"
 #include "kernels.h"
 
 using namespace rcpk;
+
+namespace rcpk {
+static std::atomic<long long> g_launches{0};
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace rcpk
 
 namespace {
 
@@ -21,8 +28,19 @@ struct Buf {
 
 }  // namespace
 
+enum Phase { PH_SKETCH = 0, PH_PANEL, PH_INTERCHANGE, PH_TRAILING, PH_SOLVE, PH_RESIDUAL, PH_OTHER, PH_COUNT };
+
+struct EventPair {
+    int phase;
+    cudaEvent_t a, b;
+};
+
 struct rcp_handle {
     int device = 0;
+    int profiling = 0;
+    std::vector<EventPair> events;      // recorded pairs of the calls since the last read
+    std::vector<cudaEvent_t> pool;      // free events
+    int launches[PH_COUNT] = {0};
     Buf status, state, bar, scal;                 // small persistent buffers
     Buf om, B, Wbuf, Lp, lpos, moved, s1v, s2v, s1i, s2i, pay, tmpA, tmpL, tmpP;
     Buf Y, flags, R, Dc, part;
@@ -101,7 +119,7 @@ rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
     r.prec = o ? o->prec : RCP_FP64;
     if (r.prec < RCP_FP64 || r.prec > RCP_TF32X3) return RCP_EINVAL;
     r.b = (o && o->b > 0) ? o->b : 64;
-    r.d = (o && o->d > 0) ? o->d : r.b + 16;
+    r.d = (o && o->d > 0) ? o->d : std::min(r.b + 16, 128);
     if (o && o->q_mode != 0 && o->q_mode != 1) return RCP_EUNSUPPORTED;
     if (r.b < 1 || r.b > 512 || r.d < 1 || r.d > 128) return RCP_EUNSUPPORTED;
     r.alpha = (o && o->alpha > 0.0) ? o->alpha : std::sqrt(2.0) / 2.0;
@@ -109,7 +127,8 @@ rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
     r.seed = o ? o->seed : 0;
     r.omega = o ? o->omega : nullptr;
     r.bw = r.b + 1;
-    r.maxmoved = 2 * (r.b + 2);
+    // each pivot column costs at most two transpositions, and each moves two indices
+    r.maxmoved = 4 * (r.b + 2);
     const bool f64 = r.prec == RCP_FP64;
     int maxg = 0;
     int sms = sm_count();
@@ -176,6 +195,39 @@ rcp_status status_from_bits(int bits) {
     return RCP_OK;
 }
 
+cudaEvent_t take_event(rcp_handle *h) {
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets a stretch of launches of one phase with two events when profiling is on.
+struct PhaseScope {
+    rcp_handle *h;
+    cudaStream_t s;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseScope(rcp_handle *h_, cudaStream_t s_, int ph) : h(h_), s(s_), phase(ph) {
+        if (h->profiling) {
+            a = take_event(h);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~PhaseScope() {
+        if (h->profiling && a) {
+            cudaEvent_t b = take_event(h);
+            cudaEventRecord(b, s);
+            h->events.push_back({phase, a, b});
+            h->launches[phase] += 1;
+        }
+    }
+};
+
 double bits_to_double(unsigned long long b) {
     double v;
     std::memcpy(&v, &b, sizeof v);
@@ -191,16 +243,28 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
     CU_TRY(cudaMemsetAsync(h->bar.p, 0, sizeof(unsigned), s));
     CU_TRY(launch_factor_init<T>(w, s));
     const T *om = (const T *)r.omega;
-    if (!om) {
-        CU_TRY(launch_omega<T>(r.d, n, r.seed, (T *)h->om.p, s));
-        om = (const T *)h->om.p;
+    {
+        PhaseScope ps(h, s, PH_SKETCH);
+        if (!om) {
+            CU_TRY(launch_omega<T>(r.d, n, r.seed, (T *)h->om.p, s));
+            om = (const T *)h->om.p;
+        }
+        CU_TRY((launch_sketch<T, T>(n, r.d, A, lda, om, w.B, nullptr, 0, s)));
     }
-    CU_TRY((launch_sketch<T, T>(n, r.d, A, lda, om, w.B, nullptr, 0, s)));
     const int nblk = (n + r.b - 1) / r.b;
     for (int blk = 0; blk < nblk; ++blk) {
-        CU_TRY(launch_panel<T>(w, s));
-        CU_TRY(launch_interchange<T>(w, s));
-        CU_TRY(launch_trailing<T>(w, std::min(n, (blk + 1) * r.b), (int)r.prec, s));
+        {
+            PhaseScope ps(h, s, PH_PANEL);
+            CU_TRY(launch_panel<T>(w, s));
+        }
+        {
+            PhaseScope ps(h, s, PH_INTERCHANGE);
+            CU_TRY(launch_interchange<T>(w, s));
+        }
+        {
+            PhaseScope ps(h, s, PH_TRAILING);
+            CU_TRY(launch_trailing<T>(w, std::min(n, (blk + 1) * r.b), (int)r.prec, s));
+        }
     }
     CU_TRY(launch_factor_finish<T>(w, s));
     if (!stats) return RCP_OK;
@@ -232,6 +296,7 @@ rcp_status solve_impl(rcp_handle *h, int n, int nrhs, const T *L, int lda, const
     bool fresh = h->flags.bytes < (size_t)(2 * nb + 2) * sizeof(int);
     RCP_TRY(grow(h->flags, (size_t)(2 * nb + 2) * sizeof(int)));
     if (fresh) CU_TRY(cudaMemsetAsync(h->flags.p, 0, h->flags.bytes, s));
+    PhaseScope ps(h, s, PH_SOLVE);
     CU_TRY(launch_solve<T>(n, nrhs, L, lda, Dd, Ds, perm, X, ldx, (T *)h->Y.p, (int *)h->flags.p,
                            (int *)h->status.p, skip, s));
     return RCP_OK;
@@ -258,6 +323,8 @@ void rcp_destroy(rcp_handle *h) {
                   &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm};
     for (Buf *b : all)
         if (b->p) cudaFree(b->p);
+    for (auto &e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    for (auto e : h->pool) cudaEventDestroy(e);
     delete h;
 }
 
@@ -344,7 +411,10 @@ rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda
     };
     RCP_TRY(do_solve(X, nullptr));
     for (int it = 0; it <= max_iter; ++it) {
-        CU_TRY(launch_symv_residual(n, nrhs, A64, lda, X, ldx, Bv, ldb, R, n, part, sc->mx, &sc->conv, s));
+        {
+            PhaseScope ps(h, s, PH_RESIDUAL);
+            CU_TRY(launch_symv_residual(n, nrhs, A64, lda, X, ldx, Bv, ldb, R, n, part, sc->mx, &sc->conv, s));
+        }
         CU_TRY(launch_refine_check(nrhs, sc->mx, &sc->anorm, tol, &sc->conv, &sc->berr, &sc->iters, it < max_iter, s));
         if (it == max_iter) break;
         CU_TRY(cudaMemcpyAsync(Dc, R, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -436,6 +506,36 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
     if (max_iter > 0 && !(host.berr <= tol)) return RCP_ENOCONV;
     return RCP_OK;
 }
+
+rcp_status rcp_profile(rcp_handle *h, int enable) {
+    if (!h) return RCP_EINVAL;
+    h->profiling = enable ? 1 : 0;
+    return RCP_OK;
+}
+
+rcp_status rcp_profile_read(rcp_handle *h, double *ms, int *launches, int nphase) {
+    if (!h || !ms || nphase < 1) return RCP_EINVAL;
+    for (int i = 0; i < nphase; ++i) {
+        ms[i] = 0.0;
+        if (launches) launches[i] = 0;
+    }
+    for (auto &e : h->events) {
+        CU_TRY(cudaEventSynchronize(e.b));
+        float t = 0.f;
+        CU_TRY(cudaEventElapsedTime(&t, e.a, e.b));
+        if (e.phase < nphase) ms[e.phase] += t;
+        h->pool.push_back(e.a);
+        h->pool.push_back(e.b);
+    }
+    h->events.clear();
+    for (int i = 0; i < nphase && i < PH_COUNT; ++i) {
+        if (launches) launches[i] = h->launches[i];
+        h->launches[i] = 0;
+    }
+    return RCP_OK;
+}
+
+long long rcp_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 rcp_status rcp_omega(int d, int n, uint64_t seed, double *omega, rcp_stream_t stream) {
     if (d < 1 || n < 0 || (n > 0 && !omega)) return RCP_EINVAL;

@@ -135,6 +135,7 @@ cudaError_t launch_omega(int d, int n, uint64_t seed, T *om, cudaStream_t s) {
     if (total == 0) return cudaSuccess;
     int blocks = (int)((total + 255) / 256);
     omega_kernel<T><<<blocks, 256, 0, s>>>(d, n, seed, om);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -149,6 +150,7 @@ static cudaError_t launch_sketch_rpt(int n, int d, const TA *A, int lda, const T
 #undef SK_CASE
         default: return cudaErrorInvalidValue;
     }
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -243,9 +243,12 @@ cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = nb < sms ? nb : sms;
     fwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, perm, X, ldx, work, flags, epoch, tickets, status, skip);
+    count_launches(1);
     dsolve_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(n, nrhs, Dd, Ds, work, status, skip);
+    count_launches(1);
     bwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, perm, X, ldx, work, flags + nb, epoch, tickets + 1,
                                               status, skip);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -391,10 +394,13 @@ cudaError_t launch_symv_residual(int n, int nrhs, const double *A, int lda, cons
     if (e != cudaSuccess) return e;
     dim3 g((n + RV_ROWS - 1) / RV_ROWS, nch);
     symv_rows_kernel<false><<<g, 256, 0, s>>>(n, nrhs, A, lda, X, ldx, part, skip);
+    count_launches(1);
     symv_cols_kernel<false><<<(n + 7) / 8, 256, 0, s>>>(n, nrhs, A, lda, X, ldx, y2, skip);
+    count_launches(1);
     int blocks = (n + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     residual_combine_kernel<<<blocks, 256, 0, s>>>(n, nrhs, nch, part, y2, Bv, ldb, X, ldx, R, ldr, mx, skip);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -404,14 +410,18 @@ cudaError_t launch_anorm(int n, const double *A, int lda, double *part, double *
     double *y2 = part + (size_t)nch * n;
     dim3 g((n + RV_ROWS - 1) / RV_ROWS, nch);
     symv_rows_kernel<true><<<g, 256, 0, s>>>(n, 1, A, lda, nullptr, 0, part, nullptr);
+    count_launches(1);
     symv_cols_kernel<true><<<(n + 7) / 8, 256, 0, s>>>(n, 1, A, lda, nullptr, 0, y2, nullptr);
+    count_launches(1);
     anorm_finish_kernel<<<1, 1024, 0, s>>>(n, nch, part, y2, anorm);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_refine_check(int nrhs, const unsigned long long *mx, const double *anorm, double tol, int *conv,
                                 double *berr, int *iters, int count_iter, cudaStream_t s) {
     refine_check_kernel<<<1, 32, 0, s>>>(nrhs, mx, anorm, tol, conv, berr, iters, count_iter);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -422,6 +432,7 @@ cudaError_t launch_axpy_update(int n, int nrhs, double *X, int ldx, const double
     int blocks = (int)((total + 255) / 256);
     if (blocks > 2048) blocks = 2048;
     axpy_kernel<<<blocks, 256, 0, s>>>(n, nrhs, X, ldx, D, ldd, skip);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -438,6 +449,7 @@ __global__ void copy_lower_kernel(int n, const double *__restrict__ src, int lds
 cudaError_t launch_copy_lower_f64(int n, const double *src, int lds, void *dst, int ldd, int to_f32, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     copy_lower_kernel<<<n < 4096 ? n : 4096, 256, 0, s>>>(n, src, lds, dst, ldd, to_f32);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -79,7 +79,11 @@ def lib():
         L.rcp_sysv.argtypes = [P, I, I, P, I, P, I, P, I, ctypes.POINTER(Opts), D, I, I, P, ctypes.POINTER(Stats)]
         L.rcp_omega.argtypes = [I, I, ctypes.c_uint64, P, P]
         L.rcp_sketch.argtypes = [I, I, P, I, I, ctypes.c_uint64, P, P, P]
-        for name in ("rcp_create", "rcp_sync", "rcp_reserve", "rcp_factor", "rcp_solve", "rcp_refine", "rcp_sysv",
+        L.rcp_profile.argtypes = [P, I]
+        L.rcp_profile_read.argtypes = [P, P, P, I]
+        L.rcp_kernel_launches.argtypes = []
+        L.rcp_kernel_launches.restype = ctypes.c_longlong
+        for name in ("rcp_profile", "rcp_profile_read", "rcp_create", "rcp_sync", "rcp_reserve", "rcp_factor", "rcp_solve", "rcp_refine", "rcp_sysv",
                      "rcp_omega", "rcp_sketch"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -104,7 +108,7 @@ def _check(code, where, allow_info=False):
 def make_opts(b=64, d=None, seed=0, prec=RCP_FP64, alpha=None, omega=None, grid=0, q_mode=1) -> Opts:
     if isinstance(prec, str):
         prec = PREC_NAMES[prec]
-    return Opts(b=b, d=(b + 16 if d is None else d), q_mode=q_mode, seed=seed, prec=prec,
+    return Opts(b=b, d=(min(b + 16, 128) if d is None else d), q_mode=q_mode, seed=seed, prec=prec,
                 alpha=(math.sqrt(2.0) / 2.0 if alpha is None else alpha),
                 omega=(omega.data_ptr() if omega is not None else None), grid=grid)
 
@@ -201,6 +205,23 @@ def rcp_sysv(h: Handle, A64, Bv, X, opts: Opts | None = None, tol=1e-12, max_ite
     return code, st
 
 
+PHASES = ("sketch", "panel", "interchange", "trailing", "solve", "residual")
+
+
+def rcp_profile(h: Handle, enable: bool = True) -> None:
+    _check(lib().rcp_profile(h.h, int(bool(enable))), "rcp_profile")
+
+
+def rcp_profile_read(h: Handle) -> dict:
+    """Per-phase milliseconds and bracketed-stretch counts since the last read."""
+    k = len(PHASES)
+    ms = (ctypes.c_double * k)()
+    cnt = (ctypes.c_int * k)()
+    _check(lib().rcp_profile_read(h.h, ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(cnt, ctypes.c_void_p), k),
+           "rcp_profile_read")
+    return {name: (ms[i], cnt[i]) for i, name in enumerate(PHASES)}
+
+
 def rcp_omega(d: int, n: int, seed: int = 0, device="cuda", stream=None) -> torch.Tensor:
     """Omega as a (d, n) float64 tensor view of the column-major d x n array."""
     om = torch.empty((n, d), dtype=torch.float64, device=device)
@@ -235,3 +256,8 @@ def block_d(Dd: torch.Tensor, Ds: torch.Tensor) -> torch.Tensor:
     off = Ds[:-1]
     D += torch.diag(off, -1) + torch.diag(off, 1)
     return D
+
+
+def rcp_kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().rcp_kernel_launches())
