@@ -187,6 +187,27 @@ rcp_status rcp_omega(int d, int n, uint64_t seed, double *omega, rcp_stream_t st
 rcp_status rcp_sketch(int n, int d, const void *A, int lda, rcp_prec prec, uint64_t seed,
                       const void *omega, void *B, rcp_stream_t stream);
 
+/*
+ * rcp_solve_noalloc -- the same solve as rcp_solve for callers that cannot allocate device
+ * memory when they solve: code running while a stream is captured into a CUDA graph (where
+ * cudaMalloc is not allowed), real-time loops that must never block in the allocator, or
+ * programs whose device memory belongs to another allocator.  It takes no handle and calls no
+ * cudaMalloc, cudaFree or allocating library routine; its scratch is one 8 MiB array in
+ * device memory that every GPU loading this library keeps until the process exits.
+ * (The paper has no counterpart to this entry point; it is a deployment convenience.)
+ *   Arguments, layout and results are those of rcp_solve.
+ *   Limit: n * nrhs * (8 for RCP_FP64, 4 otherwise) + 4 * (2 * ceil(n / 64) + 3) bytes must fit
+ *          in 8 MiB (about n * nrhs <= 1.04e6 for an FP64 factor, 2.09e6 for an FP32 one);
+ *          larger problems return RCP_EUNSUPPORTED before anything is launched.
+ *   The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ *   not stream-ordered): make that first call before any stream capture.
+ *   All calls share the array: calls whose kernels can overlap on the GPU (different streams,
+ *   or unsynchronized host threads) race and give wrong results.  Each call clears the parts
+ *   that must start at zero.  The call is asynchronous and reports only argument errors.
+ */
+rcp_status rcp_solve_noalloc(int n, int nrhs, const void *LA, int lda, const double *Dd, const double *Ds,
+                             const int *perm, rcp_prec prec, double *X, int ldx, rcp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

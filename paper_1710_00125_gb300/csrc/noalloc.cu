@@ -1,0 +1,95 @@
+// noalloc.cu -- rcp_solve_noalloc: the solution phase without any device allocation.
+//
+// Some callers cannot allocate device memory at the moment they need a solve: code that runs
+// while a stream is being captured into a CUDA graph (cudaMalloc is not allowed there), hard
+// real-time loops that must never block in the allocator, and programs whose device memory is
+// entirely owned by another allocator (a framework's pool).  For them this entry point runs the
+// same forward / block-diagonal / backward kernels as rcp_solve, but takes its scratch (the
+// work vector, the row-block flags, the tickets and a status word) from one statically sized
+// __device__ array instead of a handle's cudaMalloc'ed workspace.
+//
+// That array lives in every GPU that loads this library until the process exits.  All calls
+// share it: two calls whose kernels overlap on the GPU (different streams, or different host
+// threads on one stream without ordering) race on it and give wrong results.
+#include <mutex>
+
+#include "../../include/rcp.h"
+#include "kernels.h"
+
+namespace {
+
+// 8 MiB of scratch: the work vector n * nrhs * sizeof(factor type), then 2 * ceil(n / 64) + 2
+// flag/ticket words and one status word.
+constexpr size_t kScratchBytes = 8u << 20;
+static __device__ __align__(256) unsigned char g_solve_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once per device.  In
+// host code the symbol is only a host-side stand-in; its device address must come from the
+// runtime with the device current.
+void *scratch_address(rcp_status *err) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        *err = RCP_ECUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_solve_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            *err = RCP_ECUDA;
+            return nullptr;
+        }
+        g_scratch_ptr[dev] = p;
+    }
+    return g_scratch_ptr[dev];
+}
+
+size_t scratch_needed(int n, int nrhs, size_t tsz) {
+    const size_t nb = ((size_t)n + 63) / 64;
+    size_t work = ((size_t)n * (size_t)nrhs * tsz + 255) / 256 * 256;
+    return work + (2 * nb + 2 + 1) * sizeof(int);
+}
+
+}  // namespace
+
+extern "C" rcp_status rcp_solve_noalloc(int n, int nrhs, const void *LA, int lda, const double *Dd,
+                                        const double *Ds, const int *perm, rcp_prec prec, double *X,
+                                        int ldx, rcp_stream_t stream) {
+    if (n < 0 || nrhs < 0 || prec < RCP_FP64 || prec > RCP_TF32X3) return RCP_EINVAL;
+    if (n == 0 || nrhs == 0) return RCP_OK;
+    if (!LA || !Dd || !Ds || !perm || !X || lda < n || ldx < n) return RCP_EINVAL;
+    const size_t tsz = prec == RCP_FP64 ? sizeof(double) : sizeof(float);
+    if (scratch_needed(n, nrhs, tsz) > kScratchBytes) return RCP_EUNSUPPORTED;
+    rcp_status err = RCP_OK;
+    unsigned char *base = static_cast<unsigned char *>(scratch_address(&err));
+    if (!base) return err;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nb = ((size_t)n + 63) / 64;
+    const size_t work = ((size_t)n * (size_t)nrhs * tsz + 255) / 256 * 256;
+    int *flags = reinterpret_cast<int *>(base + work);        // 2*nb flags, then 2 tickets
+    int *status = flags + 2 * nb + 2;
+    // The flags, tickets and status word must start at zero for this call: earlier calls left
+    // their epochs and tickets behind.
+    if (cudaMemsetAsync(flags, 0, (2 * nb + 3) * sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return RCP_ECUDA;
+    }
+    cudaError_t e;
+    if (prec == RCP_FP64)
+        e = rcpk::launch_solve<double>(n, nrhs, (const double *)LA, lda, Dd, Ds, perm, X, ldx,
+                                       reinterpret_cast<double *>(base), flags, status, nullptr, s);
+    else
+        e = rcpk::launch_solve<float>(n, nrhs, (const float *)LA, lda, Dd, Ds, perm, X, ldx,
+                                      reinterpret_cast<float *>(base), flags, status, nullptr, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return RCP_ECUDA;
+    }
+    return RCP_OK;
+}

@@ -81,6 +81,8 @@ def lib():
         L.rcp_sketch.argtypes = [I, I, P, I, I, ctypes.c_uint64, P, P, P]
         L.rcp_profile.argtypes = [P, I]
         L.rcp_profile_read.argtypes = [P, P, P, I]
+        L.rcp_solve_noalloc.argtypes = [I, I, P, I, P, P, P, I, P, I, P]
+        L.rcp_solve_noalloc.restype = ctypes.c_int
         L.rcp_kernel_launches.argtypes = []
         L.rcp_kernel_launches.restype = ctypes.c_longlong
         for name in ("rcp_profile", "rcp_profile_read", "rcp_create", "rcp_sync", "rcp_reserve", "rcp_factor", "rcp_solve", "rcp_refine", "rcp_sysv",
@@ -172,6 +174,17 @@ def rcp_solve(h: Handle, LA: torch.Tensor, Dd, Ds, perm, prec, X: torch.Tensor, 
         prec = PREC_NAMES[prec]
     _check(lib().rcp_solve(h.h, n, nrhs, _ptr(LA), n, _ptr(Dd), _ptr(Ds), _ptr(perm), prec, _ptr(X), ldx,
                            _stream(stream)), "rcp_solve")
+
+
+def rcp_solve_noalloc(LA: torch.Tensor, Dd, Ds, perm, prec, X: torch.Tensor, stream=None) -> None:
+    """rcp_solve without any device allocation (for callers that cannot allocate, e.g. inside
+    stream capture): scratch comes from a fixed 8 MiB device array shared by all calls."""
+    n = LA.shape[0]
+    nrhs, ldx = _rhs_view(X, n)
+    if isinstance(prec, str):
+        prec = PREC_NAMES[prec]
+    _check(lib().rcp_solve_noalloc(n, nrhs, _ptr(LA), n, _ptr(Dd), _ptr(Ds), _ptr(perm), prec, _ptr(X), ldx,
+                                   _stream(stream)), "rcp_solve_noalloc")
 
 
 def rcp_refine(h: Handle, A64, LA, Dd, Ds, perm, prec, Bv, X, tol=1e-12, max_iter=10, stream=None,
