@@ -171,6 +171,13 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
  */
 rcp_status rcp_profile(rcp_handle *h, int enable);
 
+/* With rcp_profile(h, 2), the next factorizations also record, for every pivot position k, ten
+ * SM clock stamps (clock64 of one thread of the first CTA) at fixed points of the panel step
+ * (top, before/after barrier 1, Schur column P, before/after barrier 2, decision, column r,
+ * multipliers, sketch update).  rcp_panel_trace copies up to cap stamps (10 per position, zero
+ * where a step started at another position) of the last such factorization. */
+rcp_status rcp_panel_trace(rcp_handle *h, unsigned long long *out, int cap);
+
 /* Number of kernels this library has launched in the process so far (all handles). */
 long long rcp_kernel_launches(void);
 rcp_status rcp_profile_read(rcp_handle *h, double *ms, int *launches, int nphase);
@@ -192,13 +199,14 @@ rcp_status rcp_sketch(int n, int d, const void *A, int lda, rcp_prec prec, uint6
  * memory when they solve: code running while a stream is captured into a CUDA graph (where
  * cudaMalloc is not allowed), real-time loops that must never block in the allocator, or
  * programs whose device memory belongs to another allocator.  It takes no handle and calls no
- * cudaMalloc, cudaFree or allocating library routine; its scratch is one 8 MiB array in
+ * cudaMalloc, cudaFree or allocating library routine; its scratch is one 16 MiB array in
  * device memory that every GPU loading this library keeps until the process exits.
  * (The paper has no counterpart to this entry point; it is a deployment convenience.)
  *   Arguments, layout and results are those of rcp_solve.
- *   Limit: n * nrhs * (8 for RCP_FP64, 4 otherwise) + 4 * (2 * ceil(n / 64) + 3) bytes must fit
- *          in 8 MiB (about n * nrhs <= 1.04e6 for an FP64 factor, 2.09e6 for an FP32 one);
- *          larger problems return RCP_EUNSUPPORTED before anything is launched.
+ *   Limit: w * (n * nrhs + 64 * 64 * ceil(n / 64)) + 4 * (2 * ceil(n / 64) + 3) bytes (plus
+ *          alignment padding), w = 8 for RCP_FP64 and 4 otherwise, must fit in 16 MiB (for
+ *          example n = 16384 with nrhs <= 64 for an FP64 factor); larger problems return
+ *          RCP_EUNSUPPORTED before anything is launched.
  *   The first call on each device looks up the array's device address (cudaGetSymbolAddress,
  *   not stream-ordered): make that first call before any stream capture.
  *   All calls share the array: calls whose kernels can overlap on the GPU (different streams,

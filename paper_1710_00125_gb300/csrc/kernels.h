@@ -42,6 +42,8 @@ struct FactorWork {
     T *tmpL;            // [maxmoved][n]
     int *tmpP;          // [maxmoved]
     int maxmoved;
+    unsigned long long *trace;   // optional per-step timestamps (profiling), 10 per position
+    unsigned long long *keys;    // ring of packed argmax keys (FP32 path), zeroed per factorization
 };
 
 template <typename T>
@@ -65,7 +67,9 @@ cudaError_t launch_factor_finish(const FactorWork<T> &w, cudaStream_t s);
 template <typename T>
 int panel_max_grid(int d, int bw, int chunk_cap);
 
-// Solves and refinement.
+// Solves and refinement.  `work` holds solve_work_bytes<T>(n, nrhs) bytes.
+template <typename T>
+size_t solve_work_bytes(int n, int nrhs);
 template <typename T>
 cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
                          const int *perm, double *X, int ldx, T *work, int *flags, int *status,

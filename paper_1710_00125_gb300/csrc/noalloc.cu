@@ -18,9 +18,10 @@
 
 namespace {
 
-// 8 MiB of scratch: the work vector n * nrhs * sizeof(factor type), then 2 * ceil(n / 64) + 2
+// 16 MiB of scratch: the solve's work area (the work vector, n * nrhs entries of the factor
+// type, and the inverses of the 64 x 64 diagonal blocks of L), then 2 * ceil(n / 64) + 2
 // flag/ticket words and one status word.
-constexpr size_t kScratchBytes = 8u << 20;
+constexpr size_t kScratchBytes = 16u << 20;
 static __device__ __align__(256) unsigned char g_solve_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -50,10 +51,14 @@ void *scratch_address(rcp_status *err) {
     return g_scratch_ptr[dev];
 }
 
-size_t scratch_needed(int n, int nrhs, size_t tsz) {
+size_t work_bytes(int n, int nrhs, bool f64) {
+    const size_t w = f64 ? rcpk::solve_work_bytes<double>(n, nrhs) : rcpk::solve_work_bytes<float>(n, nrhs);
+    return (w + 255) / 256 * 256;
+}
+
+size_t scratch_needed(int n, int nrhs, bool f64) {
     const size_t nb = ((size_t)n + 63) / 64;
-    size_t work = ((size_t)n * (size_t)nrhs * tsz + 255) / 256 * 256;
-    return work + (2 * nb + 2 + 1) * sizeof(int);
+    return work_bytes(n, nrhs, f64) + (2 * nb + 2 + 1) * sizeof(int);
 }
 
 }  // namespace
@@ -64,15 +69,14 @@ extern "C" rcp_status rcp_solve_noalloc(int n, int nrhs, const void *LA, int lda
     if (n < 0 || nrhs < 0 || prec < RCP_FP64 || prec > RCP_TF32X3) return RCP_EINVAL;
     if (n == 0 || nrhs == 0) return RCP_OK;
     if (!LA || !Dd || !Ds || !perm || !X || lda < n || ldx < n) return RCP_EINVAL;
-    const size_t tsz = prec == RCP_FP64 ? sizeof(double) : sizeof(float);
-    if (scratch_needed(n, nrhs, tsz) > kScratchBytes) return RCP_EUNSUPPORTED;
+    const bool f64 = prec == RCP_FP64;
+    if (scratch_needed(n, nrhs, f64) > kScratchBytes) return RCP_EUNSUPPORTED;
     rcp_status err = RCP_OK;
     unsigned char *base = static_cast<unsigned char *>(scratch_address(&err));
     if (!base) return err;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nb = ((size_t)n + 63) / 64;
-    const size_t work = ((size_t)n * (size_t)nrhs * tsz + 255) / 256 * 256;
-    int *flags = reinterpret_cast<int *>(base + work);        // 2*nb flags, then 2 tickets
+    int *flags = reinterpret_cast<int *>(base + work_bytes(n, nrhs, f64));   // 2*nb flags, then 2 tickets
     int *status = flags + 2 * nb + 2;
     // The flags, tickets and status word must start at zero for this call: earlier calls left
     // their epochs and tickets behind.

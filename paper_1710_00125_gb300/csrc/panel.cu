@@ -12,15 +12,19 @@
 //
 // Per pivot step (Section 3, Figure SBKP, Eq. "Update matrix B"):
 //   (1) argmax of ||B(:, j)||^2 over the remaining indices (ties: smallest position)  -> P
-//       grid barrier #1 (each CTA publishes its best candidate and that candidate's B column)
+//       grid barrier #1
 //   (2) the interchange k <-> position(P); column P of the Schur complement,
 //       c_j = A(j, P) - sum_t W(j, t) L(P, t) (a GEMV over the panel built so far);
 //       lambda = max_{j != P} |c_j| at r (ties: smallest position)
-//       grid barrier #2 (best candidate, its c value, its current diagonal, its B column)
+//       grid barrier #2
 //   (3) SBKP case (0)-(3) with alpha; for cases (2)/(3) column r of the Schur complement
-//   (4) multipliers (1x1: c / a_kk; 2x2: [c_j c'_j] D_k^{-1} in FP64), W = L D, the
-//       Schur diagonal update, and the rank-s sketch update fused with the next norms.
-// So one pivot step (1x1 or 2x2) costs two grid-wide barriers.
+//   (4) multipliers (1x1: c / a_kk; 2x2: [c_j c'_j] D_k^{-1}, its scalars in FP64), W = L D,
+//       the Schur diagonal update, and the rank-s sketch update fused with the next norms.
+// Grid-wide argmax: in FP32 every CTA folds its candidate into one 64-bit word with red.max
+// (value bits | inverted position | index), so a reader needs a single L2 load; in FP64 the
+// value does not fit beside the position, so every CTA publishes a record and the readers
+// reduce all records.  The winner's scalars and sketch column are fetched together with the
+// column of A they select, so each barrier is followed by one dependent L2 and one HBM trip.
 #include <climits>
 #include <type_traits>
 
@@ -32,12 +36,17 @@ constexpr int PANEL_THREADS = 512;
 constexpr int PANEL_WARPS = PANEL_THREADS / 32;
 constexpr unsigned FULL = 0xffffffffu;
 
+// Row strides of the per-row shared arrays: a quad of threads works on one row and walks the
+// row with stride 4, so a stride of 4 (mod 32) words puts the 8 rows x 4 threads of a warp on
+// 32 different banks.
+__host__ __device__ constexpr int quad_stride(int x) { return x + ((36 - (x % 32)) % 32); }
+
 template <typename T>
 size_t panel_smem_bytes(int d, int bw, int chunk_cap) {
     size_t s = 0;
     s += (size_t)chunk_cap * sizeof(double);           // nrm (T, padded to 8 bytes)
-    s += (size_t)chunk_cap * d * sizeof(T);            // Bs
-    s += (size_t)chunk_cap * bw * sizeof(T);           // Ws
+    s += (size_t)chunk_cap * quad_stride(d) * sizeof(T);    // Bs
+    s += (size_t)chunk_cap * quad_stride(bw) * sizeof(T);   // Ws
     s += (size_t)chunk_cap * 5 * sizeof(T);            // dg, c1, c2, l1s, l2s
     s += (size_t)2 * d * sizeof(T);                    // bP, bR
     s += (size_t)2 * bw * sizeof(T);                   // lP, lR
@@ -139,30 +148,53 @@ __device__ __forceinline__ SlotWin slot_reduce(const double *slots, int G) {
     return b;   // valid in lane 0
 }
 
+// FP32 argmax key: larger key = larger value, then smaller position.  Needs n <= 65535.
+__device__ __forceinline__ unsigned long long make_key(float v, int lpos, int phys) {
+    return ((unsigned long long)__float_as_uint(v) << 32) | ((unsigned long long)(0xFFFFu - (unsigned)lpos) << 16) |
+           (unsigned long long)(unsigned)phys;
+}
+
+__device__ __forceinline__ void red_max_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr int KEY_RING = 16;
+
 // c[jl] = A(j, X) - sum_{t < i} Ws[jl][t] L(X, t) for the alive owned rows.  The loads of
-// the column of A, of L(X, 0:i) (into lX) and of the candidate's sketch column (into bX) are
-// all issued before the first barrier so that their latencies overlap.
-template <typename T>
+// the column of A, of L(X, 0:i) (into lX), of the candidate's sketch column (into bX) and of
+// `nx` scalars of the candidate's record (into xs, thread 0) are all issued before the first
+// barrier so that their latencies overlap.  `hook` runs on thread 0 right after that barrier.
+template <typename T, typename Hook>
 __device__ void schur_column(const T *__restrict__ A, int lda, int j_lo, int cnt, int X, int i, int bw,
-                             const T *Ws, const T *lXg, T *lX, const T *bXg, T *bX, int d, const int *alive, T *c) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                             const T *Ws, const T *lXg, T *lX, const T *bXg, T *bX, int d, const int *alive, T *c,
+                             const double *xsrc, double *xs, int nx, Hook hook) {
     T a0 = T(0), a1 = T(0);
     const int r0 = threadIdx.x, r1 = threadIdx.x + PANEL_THREADS;
     if (r0 < cnt && alive[r0]) a0 = a_sym(A, lda, j_lo + r0, X);
     if (r1 < cnt && alive[r1]) a1 = a_sym(A, lda, j_lo + r1, X);
     for (int t = threadIdx.x; t < i; t += PANEL_THREADS) lX[t] = ldcg(lXg + t);
     for (int r = threadIdx.x; r < d; r += PANEL_THREADS) bX[r] = ldcg(bXg + r);
+    if (threadIdx.x < nx) xs[threadIdx.x] = ldcg(xsrc + threadIdx.x);
     __syncthreads();
-    if (i > 0) {
-        for (int jl = warp; jl < cnt; jl += PANEL_WARPS) {
-            if (!alive[jl]) continue;
-            T s = T(0);
-            for (int t = lane; t < i; t += 32) s = fma(Ws[(size_t)jl * bw + t], lX[t], s);
-            s = warp_sum(s);
-            if (lane == 0) c[jl] = s;
+    if (threadIdx.x == 0) hook();
+    // four threads per row, each summing every fourth term, combined by two shuffles
+    const int sub = threadIdx.x & 3;
+    for (int jl0 = 0; jl0 < cnt; jl0 += PANEL_THREADS / 4) {
+        const int jl = jl0 + (threadIdx.x >> 2);
+        T s = T(0);
+        if (jl < cnt && alive[jl] && i > 0) {
+            const T *wr = Ws + (size_t)jl * bw;
+            for (int t = sub; t < i; t += 4) s = fma(wr[t], lX[t], s);
         }
-    } else {
-        for (int jl = threadIdx.x; jl < cnt; jl += PANEL_THREADS) c[jl] = T(0);
+        s += __shfl_xor_sync(FULL, s, 1);
+        s += __shfl_xor_sync(FULL, s, 2);
+        if (sub == 0 && jl < cnt) c[jl] = s;
     }
     __syncthreads();
     if (r0 < cnt) c[r0] = alive[r0] ? (T)(a0 - c[r0]) : T(0);
@@ -170,8 +202,44 @@ __device__ void schur_column(const T *__restrict__ A, int lda, int j_lo, int cnt
     __syncthreads();
 }
 
+struct NoHook {
+    __device__ void operator()() const {}
+};
+
+constexpr int CASE_PENDING = 4;   // lambda > 0 and |a_kk| < alpha lambda: case 2 or 3, a_rr needed
+
+// SBKP decision and the per-step scalars (thread 0).  FP64 arithmetic; the FP32 path uses
+// one reciprocal of the off-diagonal entry instead of two divisions.
+template <typename T>
+__device__ void sbkp_scalars(int kase, double akk, double lam, double ark, double arr, double alpha, int *s_i,
+                             double *s_d, T *s_t) {
+    if (kase == CASE_PENDING) {
+        if (!isfinite(ark) || !isfinite(arr)) kase = -1;
+        else kase = fabs(arr) >= alpha * lam ? 2 : 3;
+    }
+    s_i[7] = kase;
+    const double dpiv = kase == 2 ? arr : akk;
+    s_d[3] = ark;
+    s_d[4] = arr;
+    s_d[5] = dpiv;
+    if (kase == 3) {
+        double aa, cc, r;
+        if (std::is_same<T, double>::value) { aa = akk / ark; cc = arr / ark; r = 1.0 / ark; }
+        else { r = 1.0 / ark; aa = akk * r; cc = arr * r; }
+        const double tinv = 1.0 / (aa * cc - 1.0);
+        s_t[0] = (T)aa; s_t[1] = (T)cc; s_t[2] = (T)tinv; s_t[3] = (T)ark; s_t[4] = (T)r;
+    } else {
+        s_t[0] = s_t[1] = s_t[2] = T(0);
+        s_t[3] = T(1); s_t[4] = T(1);
+    }
+    s_t[5] = (T)dpiv;
+    s_t[6] = (kase == 1 || kase == 2) ? (T)(1.0 / dpiv) : T(0);
+    s_i[8] = dpiv != 0.0;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w) {
+    constexpr bool KEYS = std::is_same<T, float>::value;   // packed-key argmax (FP32 values)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ CandT<T> s_red[PANEL_WARPS + 1];
     __shared__ int s_i[16];
@@ -202,15 +270,14 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     const int cnt = max(0, min(n, j_lo + chunk) - j_lo);
     const int cap = w.chunk_cap;
 
+    const int ds = quad_stride(d), ws = quad_stride(bw);   // shared-memory row strides
     T *nrm = reinterpret_cast<T *>(smem);
     T *Bs = reinterpret_cast<T *>(reinterpret_cast<double *>(smem) + cap);
-    T *Ws = Bs + (size_t)cap * d;
-    T *dg = Ws + (size_t)cap * bw;
+    T *Ws = Bs + (size_t)cap * ds;
+    T *dg = Ws + (size_t)cap * ws;
     T *c1 = dg + cap;
     T *c2 = c1 + cap;
-    T *l1s = c2 + cap;
-    T *l2s = l1s + cap;
-    T *bP = l2s + cap;
+    T *bP = c2 + 3 * (size_t)cap;      // (two spare rows kept for alignment of the layout)
     T *bR = bP + d;
     T *lP = bR + d;
     T *lR = lP + bw;
@@ -220,12 +287,16 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     const int wsz = bw + 3;
 
     const T *__restrict__ A = w.A;
+    // optional per-step timestamps of CTA 0 (profiling only)
+    unsigned long long *const trace = (cta == 0 && tid == 0) ? w.trace : nullptr;
+#define PANEL_MARK(slot) \
+    do { if (trace) trace[(size_t)k * 10 + (slot)] = clock64(); } while (0)
     // ---- load the owned state ----
     for (int e = tid; e < cnt * d; e += PANEL_THREADS) {
         int jl = e / d, r = e - jl * d;
-        Bs[e] = w.B[(size_t)r + (size_t)(j_lo + jl) * d];
+        Bs[(size_t)jl * ds + r] = w.B[(size_t)r + (size_t)(j_lo + jl) * d];
     }
-    for (int e = tid; e < cnt * bw; e += PANEL_THREADS) Ws[e] = T(0);
+    for (int e = tid; e < cnt * ws; e += PANEL_THREADS) Ws[e] = T(0);
     for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
         int j = j_lo + jl;
         dg[jl] = A[(size_t)j + (size_t)j * lda];
@@ -233,70 +304,103 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         alive[jl] = 1;
     }
     for (int x = tid; x < wsz; x += PANEL_THREADS) win[x] = k0 + x;
+    double beta2 = 0.0;   // thread 0 of CTA 0: ||B^(1)||_{1,2}^2
     if (tid == 0) {
         s_i[0] = (int)barrier_base(w.bar, (unsigned)G);
-        if (cta == 0) w.st->n_moved = 0;
+        if (cta == 0) {
+            w.st->n_moved = 0;
+            beta2 = ldcg(&w.st->beta2);
+        }
     }
     __syncthreads();
     // initial column norms
     for (int jl = warp; jl < cnt; jl += PANEL_WARPS) {
         T s = T(0);
-        for (int r = lane; r < d; r += 32) { T b = Bs[(size_t)jl * d + r]; s = fma(b, b, s); }
+        for (int r = lane; r < d; r += 32) { T b = Bs[(size_t)jl * ds + r]; s = fma(b, b, s); }
         s = warp_sum(s);
         if (lane == 0) nrm[jl] = s;
     }
     const unsigned base = (unsigned)s_i[0];
+    const unsigned gbase = base / (unsigned)G;   // barriers completed before this launch
     unsigned nbar = 0;
     int k = k0, i = 0, n2 = 0;
-    double maxL = 0.0, maxD = 0.0, minratio = 2.0;
+    double maxD = 0.0, minnorm2 = INFINITY;
+    T tmaxL = T(0);
     int info = 0, fail = 0;
     const double alpha = w.alpha;
     T *pay1 = w.pay, *pay2 = w.pay + (size_t)G * d;
+    double *rec1 = w.s1v, *rec2 = w.s2v;   // per-CTA records (4 doubles each)
+    unsigned long long *keys = w.keys;
     __syncthreads();
 
     while (i < w.bmax && k < n) {
+        PANEL_MARK(0);
         // ---------------- (1) sketch column-norm argmax ----------------
         CandT<T> c{T(-1), INT_MAX, -1};
         for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
             if (alive[jl] && better(nrm[jl], lp[jl], c.v, c.lpos)) c = CandT<T>{nrm[jl], lp[jl], j_lo + jl};
         c = block_argmax(c, s_red);
         if (c.phys >= 0)
-            for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay1 + (size_t)cta * d + r, Bs[(size_t)(c.phys - j_lo) * d + r]);
-        if (tid == 0)
-            slot_write(w.s1v, cta, (double)c.v, c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0, 0.0, c.lpos, c.phys);
+            for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay1 + (size_t)cta * d + r, Bs[(size_t)(c.phys - j_lo) * ds + r]);
+        const unsigned g1 = gbase + nbar + 1;
+        if (tid == 0) {
+            const double dgc = c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0;
+            if (KEYS) {
+                if (c.phys >= 0) {
+                    stcg(rec1 + 4 * (size_t)cta, dgc);
+                    red_max_u64(keys + (g1 % KEY_RING), make_key((float)c.v, c.lpos, c.phys));
+                }
+            } else {
+                slot_write(rec1, cta, (double)c.v, dgc, 0.0, c.lpos, c.phys);
+            }
+        }
+        PANEL_MARK(1);
         if (!grid_barrier(w.bar, base + (++nbar) * (unsigned)G, w.status)) return;
-        if (warp == 0) {
-            SlotWin b = slot_reduce(w.s1v, G);
+        PANEL_MARK(2);
+        if (KEYS) {
+            if (tid == 0) {
+                const unsigned long long key = ld_acquire_u64(keys + (g1 % KEY_RING));
+                if (cta == 0) keys[(g1 + KEY_RING / 2) % KEY_RING] = 0ull;
+                if (key != 0ull) {
+                    s_i[1] = (int)(key & 0xFFFFull);
+                    s_i[2] = 0xFFFF - (int)((key >> 16) & 0xFFFFull);
+                    s_i[3] = (s_i[1] - k0) / chunk;
+                    s_d[0] = (double)__uint_as_float((unsigned)(key >> 32));
+                } else {
+                    s_i[1] = -1;
+                }
+            }
+        } else if (warp == 0) {
+            SlotWin b = slot_reduce(rec1, G);
             if (lane == 0) {
-                s_i[1] = b.phys;   // P
-                s_i[2] = b.lpos;   // position of P
-                s_i[3] = b.cta;
-                s_d[0] = b.v;      // ||B(:, P)||^2
-                s_d[1] = b.a1;     // a_kk
-                const int P = b.phys, LP = b.lpos;
-                if (P >= 0) {
-                    // interchange k <-> LP (positions); Q is the index now at position k
-                    int Q = win[k - k0];
-                    if (LP - k0 < wsz) win[LP - k0] = Q;
-                    win[k - k0] = P;
-                    if (P >= j_lo && P < j_lo + cnt) lp[P - j_lo] = k;
-                    if (Q != P && Q >= j_lo && Q < j_lo + cnt) lp[Q - j_lo] = LP;
-                }
-                if (cta == 0 && P >= 0) {
-                    if (k == 0) w.st->beta2 = b.v;
-                    double b2 = (k == 0) ? b.v : ldcg(&w.st->beta2);
-                    if (b2 > 0.0) minratio = fmin(minratio, sqrt(b.v / b2));
-                }
+                s_i[1] = b.phys; s_i[2] = b.lpos; s_i[3] = b.cta;
+                s_d[0] = b.v; s_d[1] = b.a1;
+            }
+        }
+        if (tid == 0 && s_i[1] >= 0) {
+            // interchange k <-> LP (positions); Q is the index now at position k
+            const int P = s_i[1], LP = s_i[2];
+            const int Q = win[k - k0];
+            if (LP - k0 < wsz) win[LP - k0] = Q;
+            win[k - k0] = P;
+            if (P >= j_lo && P < j_lo + cnt) lp[P - j_lo] = k;
+            if (Q != P && Q >= j_lo && Q < j_lo + cnt) lp[Q - j_lo] = LP;
+            if (cta == 0) {
+                if (k == 0) { beta2 = s_d[0]; w.st->beta2 = beta2; }
+                minnorm2 = fmin(minnorm2, s_d[0]);
             }
         }
         __syncthreads();
         const int P = s_i[1], gP = s_i[3];
-        const double akk = s_d[1];
-        if (P < 0 || !isfinite(s_d[0]) || !isfinite(akk)) { fail = ST_NONFINITE; break; }
+        if (P < 0 || !isfinite(s_d[0])) { fail = ST_NONFINITE; break; }
 
         // ---------------- (2) column P of the Schur complement, lambda and r ----------------
-        schur_column<T>(A, lda, j_lo, cnt, P, i, bw, Ws, w.Lp + (size_t)P * bw, lP, pay1 + (size_t)gP * d, bP, d,
-                        alive, c1);
+        PANEL_MARK(3);
+        schur_column<T>(A, lda, j_lo, cnt, P, i, ws, Ws, w.Lp + (size_t)P * bw, lP, pay1 + (size_t)gP * d, bP, d,
+                        alive, c1, rec1 + 4 * (size_t)gP, s_d + 8, KEYS ? 1 : 0, NoHook());
+        const double akk = KEYS ? s_d[8] : s_d[1];
+        if (!isfinite(akk)) { fail = ST_NONFINITE; break; }
+        PANEL_MARK(4);
         c = CandT<T>{T(-1), INT_MAX, -1};
         for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
             if (!alive[jl] || j_lo + jl == P) continue;
@@ -305,55 +409,75 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         }
         c = block_argmax(c, s_red);
         if (c.phys >= 0)
-            for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay2 + (size_t)cta * d + r, Bs[(size_t)(c.phys - j_lo) * d + r]);
-        if (tid == 0)
-            slot_write(w.s2v, cta, (double)c.v, c.phys >= 0 ? (double)c1[c.phys - j_lo] : 0.0,
-                       c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0, c.lpos, c.phys);
+            for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay2 + (size_t)cta * d + r, Bs[(size_t)(c.phys - j_lo) * ds + r]);
+        const unsigned g2 = gbase + nbar + 1;
+        if (tid == 0) {
+            const double cv = c.phys >= 0 ? (double)c1[c.phys - j_lo] : 0.0;
+            const double dgc = c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0;
+            if (KEYS) {
+                if (c.phys >= 0) {
+                    stcg(reinterpret_cast<double2 *>(rec2 + 4 * (size_t)cta), make_double2(cv, dgc));
+                    red_max_u64(keys + (g2 % KEY_RING), make_key((float)c.v, c.lpos, c.phys));
+                }
+            } else {
+                slot_write(rec2, cta, (double)c.v, cv, dgc, c.lpos, c.phys);
+            }
+        }
+        PANEL_MARK(5);
         if (!grid_barrier(w.bar, base + (++nbar) * (unsigned)G, w.status)) return;
-        if (warp == 0) {
-            SlotWin b = slot_reduce(w.s2v, G);
+        PANEL_MARK(6);
+        if (KEYS) {
+            if (tid == 0) {
+                const unsigned long long key = ld_acquire_u64(keys + (g2 % KEY_RING));
+                if (cta == 0) keys[(g2 + KEY_RING / 2) % KEY_RING] = 0ull;
+                int R = -1, LR = -1;
+                double lam = 0.0;
+                if (key != 0ull) {
+                    R = (int)(key & 0xFFFFull);
+                    LR = 0xFFFF - (int)((key >> 16) & 0xFFFFull);
+                    lam = (double)__uint_as_float((unsigned)(key >> 32));
+                }
+                s_i[4] = R; s_i[5] = LR; s_i[6] = R >= 0 ? (R - k0) / chunk : 0;
+                s_d[2] = lam;
+                int kase;
+                if (!isfinite(lam)) kase = -1;
+                else if (lam == 0.0) kase = 0;
+                else if (fabs(akk) >= alpha * lam) kase = 1;
+                else kase = CASE_PENDING;
+                if (kase == CASE_PENDING) s_i[7] = CASE_PENDING;
+                else sbkp_scalars<T>(kase, akk, lam, 0.0, 0.0, alpha, s_i, s_d, s_t);
+            }
+        } else if (warp == 0) {
+            SlotWin b = slot_reduce(rec2, G);
             if (lane == 0) {
-                // one thread takes the SBKP decision (FP64 scalars); everything the other
-                // threads need goes through shared memory
-                const int R = b.phys;   // r (or -1)
-                const double lam = R >= 0 ? b.v : 0.0;
-                const double ark = R >= 0 ? b.a1 : 0.0;
-                const double arr = R >= 0 ? b.a2 : 0.0;
-                const int g = b.cta;
+                const int R = b.phys;
+                const double lam = R >= 0 ? b.v : 0.0, ark = R >= 0 ? b.a1 : 0.0, arr = R >= 0 ? b.a2 : 0.0;
+                s_i[4] = R; s_i[5] = R >= 0 ? b.lpos : -1; s_i[6] = b.cta;
+                s_d[2] = lam;
                 int kase;
                 if (!isfinite(lam) || !isfinite(ark) || !isfinite(arr)) kase = -1;
                 else if (lam == 0.0) kase = 0;
                 else if (fabs(akk) >= alpha * lam) kase = 1;
-                else if (fabs(arr) >= alpha * lam) kase = 2;
-                else kase = 3;
-                s_i[4] = R;
-                s_i[5] = R >= 0 ? b.lpos : -1;   // position of r
-                s_i[6] = g;
-                s_i[7] = kase;
-                s_d[2] = lam; s_d[3] = ark; s_d[4] = arr;
-                const double dpiv = kase == 2 ? arr : akk;
-                s_d[5] = dpiv;
-                if (kase == 3) {
-                    const double aa = akk / ark, cc = arr / ark, tinv = 1.0 / (aa * cc - 1.0);
-                    s_t[0] = (T)aa; s_t[1] = (T)cc; s_t[2] = (T)tinv; s_t[3] = (T)ark; s_t[4] = (T)(1.0 / ark);
-                } else {
-                    s_t[0] = s_t[1] = s_t[2] = T(0);
-                    s_t[3] = T(1); s_t[4] = T(1);
-                }
-                s_t[5] = (T)dpiv;
-                s_t[6] = dpiv != 0.0 ? (T)(1.0 / dpiv) : T(0);
-                s_i[8] = dpiv != 0.0;
+                else kase = fabs(arr) >= alpha * lam ? 2 : 3;
+                sbkp_scalars<T>(kase, akk, lam, ark, arr, alpha, s_i, s_d, s_t);
             }
         }
         __syncthreads();
-        const int R = s_i[4], LR = s_i[5], gR = s_i[6], kase = s_i[7];
+        const int R = s_i[4], LR = s_i[5], gR = s_i[6];
+        int kase = s_i[7];
         if (kase < 0) { fail = ST_NONFINITE; break; }
-        const double lam = s_d[2], ark = s_d[3], arr = s_d[4];
-        (void)lam;
-        const int s = kase == 3 ? 2 : 1;
+        PANEL_MARK(7);
         if (kase >= 2) {
-            schur_column<T>(A, lda, j_lo, cnt, R, i, bw, Ws, w.Lp + (size_t)R * bw, lR, pay2 + (size_t)gR * d, bR, d,
-                            alive, c2);
+            // column r of the Schur complement; in FP32 its record (a_rk, a_rr) arrives with the
+            // column loads and thread 0 settles case 2 versus 3 right after them
+            const double lam = s_d[2];
+            auto hook = [&]() {
+                if (KEYS) sbkp_scalars<T>(CASE_PENDING, akk, lam, s_d[10], s_d[11], alpha, s_i, s_d, s_t);
+            };
+            schur_column<T>(A, lda, j_lo, cnt, R, i, ws, Ws, w.Lp + (size_t)R * bw, lR, pay2 + (size_t)gR * d, bR, d,
+                            alive, c2, rec2 + 4 * (size_t)gR, s_d + 10, KEYS ? 2 : 0, hook);
+            kase = s_i[7];
+            if (kase < 0) { fail = ST_NONFINITE; break; }
             if (tid == 0) {
                 if (kase == 2) {
                     // interchange k <-> LR: R to position k, P to LR
@@ -373,77 +497,83 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             }
         }
         // ---------------- (4) multipliers, W, diagonal, sketch update ----------------
+        PANEL_MARK(8);
+        const int s = kase == 3 ? 2 : 1;
         const int piv1 = kase == 2 ? R : P;
         const int piv2 = kase == 3 ? R : -1;
-        const double dpiv = s_d[5];
+        const double ark = s_d[3], arr = s_d[4], dpiv = s_d[5];
         const bool nonzero_piv = s_i[8] != 0;
         const T t_aa = s_t[0], t_cc = s_t[1], t_tinv = s_t[2], t_ark = s_t[3], t_rark = s_t[4];
         const T t_dpiv = s_t[5], t_rdpiv = s_t[6];
-        T tmaxL = T(0);
-        for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
-            if (!alive[jl]) continue;
-            const int j = j_lo + jl;
-            T *wrow = Ws + (size_t)jl * bw;
-            T *lrow = w.Lp + (size_t)j * bw;
-            if (j == piv1 || j == piv2) {
-                wrow[i] = T(0);
-                stcg(lrow + i, T(0));
-                if (s == 2) { wrow[i + 1] = T(0); stcg(lrow + i + 1, T(0)); }
-                alive[jl] = 0;
-                continue;
-            }
-            T l1 = T(0), l2 = T(0);
-            if (kase <= 1) {
-                const T cv = c1[jl];
-                if (nonzero_piv) l1 = std::is_same<T, double>::value ? cv / t_dpiv : cv * t_rdpiv;
-                wrow[i] = cv;
-                dg[jl] = fma(-cv, l1, dg[jl]);
-            } else if (kase == 2) {
-                const T cv = c2[jl];
-                l1 = std::is_same<T, double>::value ? cv / t_dpiv : cv * t_rdpiv;
-                wrow[i] = cv;
-                dg[jl] = fma(-cv, l1, dg[jl]);
-            } else {
-                const T v1 = c1[jl], v2 = c2[jl];
-                const T x1 = std::is_same<T, double>::value ? v1 / t_ark : v1 * t_rark;
-                const T x2 = std::is_same<T, double>::value ? v2 / t_ark : v2 * t_rark;
-                l1 = t_tinv * (t_cc * x1 - x2);
-                l2 = t_tinv * (t_aa * x2 - x1);
-                wrow[i] = v1;
-                wrow[i + 1] = v2;
-                dg[jl] = dg[jl] - v1 * l1 - v2 * l2;
-            }
-            stcg(lrow + i, l1);
-            if (s == 2) stcg(lrow + i + 1, l2);
-            l1s[jl] = l1;
-            l2s[jl] = l2;
-            tmaxL = fmax(tmaxL, fmax(fabs(l1), fabs(l2)));
-        }
-        maxL = fmax(maxL, (double)tmaxL);
-        __syncthreads();
-        // rank-s sketch update fused with the next column norms
         const T *b1 = kase == 2 ? bR : bP;
-        for (int jl = warp; jl < cnt; jl += PANEL_WARPS) {
-            if (!alive[jl]) continue;
-            const T f1 = l1s[jl], f2 = l2s[jl];
-            T *col = Bs + (size_t)jl * d;
+        // four threads per owned row: multipliers (each of the four computes them), then the
+        // row's sketch column with every fourth entry per thread
+        const int sub = tid & 3;
+        for (int jl0 = 0; jl0 < cnt; jl0 += PANEL_THREADS / 4) {
+            const int jl = jl0 + (tid >> 2);
+            bool live = jl < cnt && alive[jl];
             T sacc = T(0);
-            if (s == 2) {
-                for (int r = lane; r < d; r += 32) {
-                    T v = col[r] - b1[r] * f1 - bR[r] * f2;
-                    col[r] = v;
-                    sacc = fma(v, v, sacc);
-                }
-            } else {
-                for (int r = lane; r < d; r += 32) {
-                    T v = col[r] - b1[r] * f1;
-                    col[r] = v;
-                    sacc = fma(v, v, sacc);
+            if (live) {
+                const int j = j_lo + jl;
+                T *wrow = Ws + (size_t)jl * ws;
+                T *lrow = w.Lp + (size_t)j * bw;
+                if (j == piv1 || j == piv2) {
+                    if (sub == 0) {
+                        wrow[i] = T(0);
+                        stcg(lrow + i, T(0));
+                        if (s == 2) { wrow[i + 1] = T(0); stcg(lrow + i + 1, T(0)); }
+                    }
+                    live = false;
+                } else {
+                    T l1 = T(0), l2 = T(0);
+                    if (kase <= 1) {
+                        const T cv = c1[jl];
+                        if (nonzero_piv) l1 = std::is_same<T, double>::value ? cv / t_dpiv : cv * t_rdpiv;
+                        if (sub == 0) { wrow[i] = cv; dg[jl] = fma(-cv, l1, dg[jl]); }
+                    } else if (kase == 2) {
+                        const T cv = c2[jl];
+                        l1 = std::is_same<T, double>::value ? cv / t_dpiv : cv * t_rdpiv;
+                        if (sub == 0) { wrow[i] = cv; dg[jl] = fma(-cv, l1, dg[jl]); }
+                    } else {
+                        const T v1 = c1[jl], v2 = c2[jl];
+                        const T x1 = std::is_same<T, double>::value ? v1 / t_ark : v1 * t_rark;
+                        const T x2 = std::is_same<T, double>::value ? v2 / t_ark : v2 * t_rark;
+                        l1 = t_tinv * (t_cc * x1 - x2);
+                        l2 = t_tinv * (t_aa * x2 - x1);
+                        if (sub == 0) { wrow[i] = v1; wrow[i + 1] = v2; dg[jl] = dg[jl] - v1 * l1 - v2 * l2; }
+                    }
+                    if (sub == 0) {
+                        stcg(lrow + i, l1);
+                        if (s == 2) stcg(lrow + i + 1, l2);
+                    }
+                    tmaxL = fmax(tmaxL, fmax(fabs(l1), fabs(l2)));
+                    T *col = Bs + (size_t)jl * ds;
+                    if (s == 2) {
+                        for (int r = sub; r < d; r += 4) {
+                            T v = col[r] - b1[r] * l1 - bR[r] * l2;
+                            col[r] = v;
+                            sacc = fma(v, v, sacc);
+                        }
+                    } else {
+                        for (int r = sub; r < d; r += 4) {
+                            T v = col[r] - b1[r] * l1;
+                            col[r] = v;
+                            sacc = fma(v, v, sacc);
+                        }
+                    }
                 }
             }
-            sacc = warp_sum(sacc);
-            if (lane == 0) nrm[jl] = sacc;
+            sacc += __shfl_xor_sync(FULL, sacc, 1);
+            sacc += __shfl_xor_sync(FULL, sacc, 2);
+            if (live && sub == 0) nrm[jl] = sacc;
         }
+        __syncthreads();
+        // pivots leave the active set only after every quad has read alive[]
+        for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
+            const int j = j_lo + jl;
+            if (alive[jl] && (j == piv1 || j == piv2)) alive[jl] = 0;
+        }
+        PANEL_MARK(9);
         if (cta == 0 && tid == 0) {
             if (kase == 3) {
                 w.Dd[k] = akk; w.Ds[k] = ark; w.Dd[k + 1] = arr; w.Ds[k + 1] = 0.0;
@@ -452,23 +582,24 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             } else {
                 w.Dd[k] = dpiv; w.Ds[k] = 0.0;
                 maxD = fmax(maxD, fabs(dpiv));
-                if (dpiv == 0.0 && info == 0) info = k + 1;
+                if (!nonzero_piv && info == 0) info = k + 1;
             }
         }
         k += s;
         i += s;
         __syncthreads();
     }
+#undef PANEL_MARK
 
     // ---------------- epilogue: publish the panel in logical order ----------------
     __syncthreads();
     for (int e = tid; e < cnt * i; e += PANEL_THREADS) {
         int t = e / cnt, jl = e - t * cnt;
-        if (alive[jl]) w.Wbuf[(size_t)lp[jl] + (size_t)t * n] = Ws[(size_t)jl * bw + t];
+        if (alive[jl]) w.Wbuf[(size_t)lp[jl] + (size_t)t * n] = Ws[(size_t)jl * ws + t];
     }
     for (int e = tid; e < cnt * d; e += PANEL_THREADS) {
         int jl = e / d, r = e - jl * d;
-        if (alive[jl]) w.B[(size_t)r + (size_t)lp[jl] * d] = Bs[e];
+        if (alive[jl]) w.B[(size_t)r + (size_t)lp[jl] * d] = Bs[(size_t)jl * ds + r];
     }
     for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
         int j = j_lo + jl;
@@ -481,7 +612,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     }
     // per-CTA statistics
     {
-        double v = maxL;
+        double v = (double)tmaxL;
         for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, off));
         if (lane == 0 && v > 0.0) atomic_max_nonneg(&w.st->maxL_bits, v);
     }
@@ -496,7 +627,10 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         w.st->kend = k;
         w.st->n2x2 += n2;
         if (info && w.st->info == 0) w.st->info = info;
-        if (minratio < w.st->min_ratio) w.st->min_ratio = minratio;
+        if (beta2 > 0.0 && minnorm2 < INFINITY) {
+            const double ratio = sqrt(minnorm2 / beta2);
+            if (ratio < w.st->min_ratio) w.st->min_ratio = ratio;
+        }
         atomic_max_nonneg(&w.st->maxD_bits, maxD);
     }
 }

@@ -45,6 +45,9 @@ struct rcp_handle {
     Buf om, B, Wbuf, Lp, lpos, moved, s1v, s2v, s1i, s2i, pay, tmpA, tmpL, tmpP;
     Buf Y, flags, R, Dc, part;
     Buf A64, F, Bh, Xh, Dd, Ds, perm;              // rcp_sysv buffers
+    Buf trace;                                     // per-step panel timestamps (profiling level 2)
+    Buf keys;                                      // packed argmax keys of the FP32 panel
+    int trace_n = 0;
 };
 
 namespace {
@@ -130,6 +133,7 @@ rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
     // each pivot column costs at most two transpositions, and each moves two indices
     r.maxmoved = 4 * (r.b + 2);
     const bool f64 = r.prec == RCP_FP64;
+    if (!f64 && n > 65535) return RCP_EUNSUPPORTED;   // positions and indices are packed in 16 bits
     int maxg = 0;
     int sms = sm_count();
     int g = (o && o->grid > 0) ? o->grid : std::min(sms, std::max(1, (n + 31) / 32));
@@ -156,8 +160,9 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->Lp, N * r.bw * sizeof(T)));
     RCP_TRY(grow(h->lpos, N * sizeof(int)));
     RCP_TRY(grow(h->moved, 2 * N * sizeof(int)));
-    RCP_TRY(grow(h->s1v, 2 * (size_t)r.grid * sizeof(double)));
-    RCP_TRY(grow(h->s2v, 3 * (size_t)r.grid * sizeof(double)));
+    RCP_TRY(grow(h->s1v, 4 * (size_t)r.grid * sizeof(double)));
+    RCP_TRY(grow(h->s2v, 4 * (size_t)r.grid * sizeof(double)));
+    RCP_TRY(grow(h->keys, 16 * sizeof(unsigned long long)));
     RCP_TRY(grow(h->s1i, 2 * (size_t)r.grid * sizeof(int)));
     RCP_TRY(grow(h->s2i, 2 * (size_t)r.grid * sizeof(int)));
     RCP_TRY(grow(h->pay, 2 * (size_t)r.grid * r.d * sizeof(T)));
@@ -185,6 +190,13 @@ FactorWork<T> make_work(rcp_handle *h, int n, T *A, int lda, double *Dd, double 
     w.grid = r.grid; w.chunk_cap = r.chunk_cap;
     w.tmpA = (T *)h->tmpA.p; w.tmpL = (T *)h->tmpL.p; w.tmpP = (int *)h->tmpP.p;
     w.maxmoved = r.maxmoved;
+    w.keys = (unsigned long long *)h->keys.p;
+    w.trace = nullptr;
+    if (h->profiling >= 2 && grow(h->trace, (size_t)n * 10 * sizeof(unsigned long long)) == RCP_OK) {
+        w.trace = (unsigned long long *)h->trace.p;
+        cudaMemset(h->trace.p, 0, (size_t)n * 10 * sizeof(unsigned long long));
+        h->trace_n = n;
+    }
     return w;
 }
 
@@ -241,6 +253,7 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
     FactorWork<T> w = make_work<T>(h, n, A, lda, Dd, Ds, perm, r);
     CU_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
     CU_TRY(cudaMemsetAsync(h->bar.p, 0, sizeof(unsigned), s));
+    CU_TRY(cudaMemsetAsync(h->keys.p, 0, 16 * sizeof(unsigned long long), s));
     CU_TRY(launch_factor_init<T>(w, s));
     const T *om = (const T *)r.omega;
     {
@@ -291,7 +304,7 @@ template <typename T>
 rcp_status solve_impl(rcp_handle *h, int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
                       const int *perm, double *X, int ldx, const int *skip, cudaStream_t s) {
     RCP_TRY(ensure_small(h));
-    RCP_TRY(grow(h->Y, (size_t)n * nrhs * sizeof(T)));
+    RCP_TRY(grow(h->Y, solve_work_bytes<T>(n, nrhs)));
     const int nb = solve_nb(n);
     bool fresh = h->flags.bytes < (size_t)(2 * nb + 2) * sizeof(int);
     RCP_TRY(grow(h->flags, (size_t)(2 * nb + 2) * sizeof(int)));
@@ -318,7 +331,7 @@ rcp_status rcp_create(rcp_handle **h) {
 
 void rcp_destroy(rcp_handle *h) {
     if (!h) return;
-    Buf *all[] = {&h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lp, &h->lpos, &h->moved,
+    Buf *all[] = {&h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lp, &h->lpos, &h->moved,
                   &h->s1v, &h->s2v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
                   &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm};
     for (Buf *b : all)
@@ -357,8 +370,8 @@ rcp_status rcp_reserve(rcp_handle *h, int n, int nrhs, const rcp_opts *opts) {
     RCP_TRY(resolve(n, opts, r));
     if (r.prec == RCP_FP64) RCP_TRY(ensure_factor_ws<double>(h, n, r));
     else RCP_TRY(ensure_factor_ws<float>(h, n, r));
-    size_t tsz = r.prec == RCP_FP64 ? sizeof(double) : sizeof(float);
-    RCP_TRY(grow(h->Y, (size_t)n * std::max(nrhs, 1) * tsz));
+    RCP_TRY(grow(h->Y, r.prec == RCP_FP64 ? solve_work_bytes<double>(n, std::max(nrhs, 1))
+                                          : solve_work_bytes<float>(n, std::max(nrhs, 1))));
     RCP_TRY(grow(h->R, (size_t)n * std::max(nrhs, 1) * sizeof(double)));
     RCP_TRY(grow(h->Dc, (size_t)n * std::max(nrhs, 1) * sizeof(double)));
     RCP_TRY(grow(h->part, symv_part_doubles(n, std::max(nrhs, 1)) * sizeof(double)));
@@ -509,7 +522,7 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
 
 rcp_status rcp_profile(rcp_handle *h, int enable) {
     if (!h) return RCP_EINVAL;
-    h->profiling = enable ? 1 : 0;
+    h->profiling = enable < 0 ? 0 : (enable > 2 ? 2 : enable);
     return RCP_OK;
 }
 
@@ -532,6 +545,15 @@ rcp_status rcp_profile_read(rcp_handle *h, double *ms, int *launches, int nphase
         if (launches) launches[i] = h->launches[i];
         h->launches[i] = 0;
     }
+    return RCP_OK;
+}
+
+rcp_status rcp_panel_trace(rcp_handle *h, unsigned long long *out, int cap) {
+    if (!h || !out || cap < 0) return RCP_EINVAL;
+    if (!h->trace.p) return RCP_EINVAL;
+    size_t m = std::min((size_t)cap, (size_t)h->trace_n * 10);
+    CU_TRY(cudaDeviceSynchronize());
+    CU_TRY(cudaMemcpy(out, h->trace.p, m * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     return RCP_OK;
 }
 

@@ -61,12 +61,64 @@ __device__ __forceinline__ void block_gemv_sub(T (*acc)[SV_RC], const T (*Ms)[SV
     }
 }
 
-// Forward: L y = Pi^T x (L unit lower).  Y (work, type T, n x nrhs, ld n) receives y.
+// Inverses of the unit lower triangular diagonal blocks L(I, I) (SV_NB x SV_NB, column-major
+// at Linv + I * SV_NB * SV_NB; the last block is padded with the identity).  One CTA per block,
+// one thread per column: x = L_II^{-1} e_c by forward substitution.
+template <typename T>
+__global__ void __launch_bounds__(SV_NB)
+inv_diag_kernel(int n, const T *__restrict__ L, int lda, T *Linv, int *status, const int *skip) {
+    __shared__ T Ls[SV_NB][SV_NB + 1];
+    __shared__ T Xs[SV_NB][SV_NB + 1];
+    if (skip && ldcg(skip)) return;
+    if (ldcg(status) != 0) return;
+    const int I = blockIdx.x, r0 = I * SV_NB, nr = min(SV_NB, n - r0);
+    const int c = threadIdx.x;
+    for (int r = 0; r < SV_NB; ++r)
+        Ls[r][c] = (r < nr && c < nr && r > c) ? L[(size_t)(r0 + r) + (size_t)(r0 + c) * lda] : T(0);
+    __syncthreads();
+    for (int r = 0; r < SV_NB; ++r) Xs[r][c] = r == c ? T(1) : T(0);
+    for (int r = c + 1; r < SV_NB; ++r) {
+        T s = T(0);
+        for (int k = c; k < r; ++k) s = fma(Ls[r][k], Xs[k][c], s);
+        Xs[r][c] = -s;
+    }
+    __syncthreads();
+    T *out = Linv + (size_t)I * SV_NB * SV_NB;
+    for (int r = 0; r < SV_NB; ++r) out[(size_t)r + (size_t)c * SV_NB] = Xs[r][c];
+}
+
+// A SV_NB x SV_NB tile of L, column-major with leading dimension lda, staged through registers:
+// every thread holds TILE_PER_THREAD entries (issued as independent loads).
+constexpr int TILE_PER_THREAD = SV_NB * SV_NB / SV_THREADS;
+
+template <typename T>
+__device__ __forceinline__ void tile_load(T (&reg)[TILE_PER_THREAD], const T *__restrict__ L, int lda, int r0, int c0,
+                                          int nr, int nc) {
+#pragma unroll
+    for (int u = 0; u < TILE_PER_THREAD; ++u) {
+        const int e = threadIdx.x + u * SV_THREADS;
+        const int r = e % SV_NB, cc = e / SV_NB;
+        reg[u] = (r < nr && cc < nc) ? L[(size_t)(r0 + r) + (size_t)(c0 + cc) * lda] : T(0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_store(const T (&reg)[TILE_PER_THREAD], T (*Ms)[SV_NB + 1]) {
+#pragma unroll
+    for (int u = 0; u < TILE_PER_THREAD; ++u) {
+        const int e = threadIdx.x + u * SV_THREADS;
+        Ms[e % SV_NB][e / SV_NB] = reg[u];
+    }
+}
+
+// Forward: L y = Pi^T x (L unit lower).  Y (work, type T, n x nrhs, ld n) receives y.  The next
+// tile of L is loaded into registers before the flag of the block it multiplies is awaited, and
+// the diagonal block is applied through its precomputed inverse (a GEMV, not a sequential sweep).
 template <typename T>
 __global__ void __launch_bounds__(SV_THREADS)
-fwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const int *__restrict__ perm,
-           const double *__restrict__ X, int ldx, T *Y, int *flags, int epoch, int *ticket, int *status,
-           const int *skip) {
+fwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const T *__restrict__ Linv,
+           const int *__restrict__ perm, const double *__restrict__ X, int ldx, T *Y, int *flags, int epoch,
+           int *ticket, int *status, const int *skip) {
     __shared__ T Ms[SV_NB][SV_NB + 1];
     __shared__ T acc[SV_NB][SV_RC];
     __shared__ T ys[SV_NB][SV_RC];
@@ -74,7 +126,6 @@ fwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const int *__restr
     if (skip && ldcg(skip)) return;
     if (ldcg(status) != 0) return;
     const int nb = (n + SV_NB - 1) / SV_NB;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_I = atomicAdd(ticket, 1);
         __syncthreads();
@@ -88,13 +139,13 @@ fwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const int *__restr
                 int r = e % SV_NB, c = e / SV_NB;
                 acc[r][c] = (r < nr && c < rc) ? (T)X[(size_t)perm[r0 + r] + (size_t)(c0 + c) * ldx] : T(0);
             }
+            T cur[TILE_PER_THREAD], nxt[TILE_PER_THREAD];
+            if (I > 0) tile_load(cur, L, lda, r0, 0, nr, SV_NB);
             for (int J = 0; J < I; ++J) {
+                if (J + 1 < I) tile_load(nxt, L, lda, r0, (J + 1) * SV_NB, nr, SV_NB);
+                tile_store(cur, Ms);
                 if (!wait_flag<T>(flags + J, epoch, status)) return;
                 const int j0 = J * SV_NB;
-                for (int e = threadIdx.x; e < SV_NB * SV_NB; e += SV_THREADS) {
-                    int r = e % SV_NB, jj = e / SV_NB;
-                    Ms[r][jj] = r < nr ? L[(size_t)(r0 + r) + (size_t)(j0 + jj) * lda] : T(0);
-                }
                 for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
                     int jj = e % SV_NB, c = e / SV_NB;
                     ys[jj][c] = c < rc ? ldcg(Y + (size_t)(j0 + jj) + (size_t)(c0 + c) * n) : T(0);
@@ -102,25 +153,26 @@ fwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const int *__restr
                 __syncthreads();
                 block_gemv_sub<T, false>(acc, Ms, ys, nr, SV_NB, rc);
                 __syncthreads();
+#pragma unroll
+                for (int u = 0; u < TILE_PER_THREAD; ++u) cur[u] = nxt[u];
             }
-            // diagonal block
-            for (int e = threadIdx.x; e < SV_NB * SV_NB; e += SV_THREADS) {
-                int r = e % SV_NB, jj = e / SV_NB;
-                Ms[r][jj] = (r < nr && jj < nr) ? L[(size_t)(r0 + r) + (size_t)(r0 + jj) * lda] : T(0);
+            // y_I = L_II^{-1} acc
+            {
+                T reg[TILE_PER_THREAD];
+                tile_load(reg, Linv + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
+                tile_store(reg, Ms);
+            }
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                ys[r][c] = acc[r][c];
+                acc[r][c] = T(0);
             }
             __syncthreads();
-            for (int c = warp; c < rc; c += SV_THREADS / 32) {
-                for (int jj = 0; jj < nr; ++jj) {
-                    T z = acc[jj][c];
-                    __syncwarp();
-                    for (int r = jj + 1 + lane; r < nr; r += 32) acc[r][c] -= Ms[r][jj] * z;
-                    __syncwarp();
-                }
-            }
+            block_gemv_sub<T, false>(acc, Ms, ys, nr, nr, rc);   // acc = -Linv * y
             __syncthreads();
             for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
                 int r = e % SV_NB, c = e / SV_NB;
-                if (r < nr && c < rc) stcg(Y + (size_t)(r0 + r) + (size_t)(c0 + c) * n, acc[r][c]);
+                if (r < nr && c < rc) stcg(Y + (size_t)(r0 + r) + (size_t)(c0 + c) * n, -acc[r][c]);
             }
             __syncthreads();
         }
@@ -153,11 +205,13 @@ __global__ void dsolve_kernel(int n, int nrhs, const double *__restrict__ Dd, co
     }
 }
 
-// Backward: L^T v = w, then X(perm[i], :) = v(i, :).  Blocks are taken last to first.
+// Backward: L^T v = w, then X(perm[i], :) = v(i, :).  Blocks are taken last to first; the
+// diagonal block goes through the transpose of its precomputed inverse.
 template <typename T>
 __global__ void __launch_bounds__(SV_THREADS)
-bwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const int *__restrict__ perm, double *X,
-           int ldx, T *Y, int *flags, int epoch, int *ticket, int *status, const int *skip) {
+bwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const T *__restrict__ Linv,
+           const int *__restrict__ perm, double *X, int ldx, T *Y, int *flags, int epoch, int *ticket, int *status,
+           const int *skip) {
     __shared__ T Ms[SV_NB][SV_NB + 1];
     __shared__ T acc[SV_NB][SV_RC];
     __shared__ T ys[SV_NB][SV_RC];
@@ -165,7 +219,6 @@ bwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const int *__restr
     if (skip && ldcg(skip)) return;
     if (ldcg(status) != 0) return;
     const int nb = (n + SV_NB - 1) / SV_NB;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_I = atomicAdd(ticket, 1);
         __syncthreads();
@@ -180,14 +233,14 @@ bwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const int *__restr
                 int r = e % SV_NB, c = e / SV_NB;
                 acc[r][c] = (r < nr && c < rc) ? ldcg(Y + (size_t)(r0 + r) + (size_t)(c0 + c) * n) : T(0);
             }
+            // tiles L(J, I) for J = nb-1 down to I+1, Ms[jj][r] = L(j0 + jj, r0 + r)
+            T cur[TILE_PER_THREAD], nxt[TILE_PER_THREAD];
+            if (I + 1 < nb) tile_load(cur, L, lda, (nb - 1) * SV_NB, r0, min(SV_NB, n - (nb - 1) * SV_NB), nr);
             for (int J = nb - 1; J > I; --J) {
+                if (J - 1 > I) tile_load(nxt, L, lda, (J - 1) * SV_NB, r0, min(SV_NB, n - (J - 1) * SV_NB), nr);
+                tile_store(cur, Ms);
                 if (!wait_flag<T>(flags + J, epoch, status)) return;
                 const int j0 = J * SV_NB, nj = min(SV_NB, n - j0);
-                // Ms[jj][r] = L(j0 + jj, r0 + r)
-                for (int e = threadIdx.x; e < SV_NB * SV_NB; e += SV_THREADS) {
-                    int jj = e % SV_NB, r = e / SV_NB;
-                    Ms[jj][r] = (jj < nj && r < nr) ? L[(size_t)(j0 + jj) + (size_t)(r0 + r) * lda] : T(0);
-                }
                 for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
                     int jj = e % SV_NB, c = e / SV_NB;
                     ys[jj][c] = (jj < nj && c < rc) ? ldcg(Y + (size_t)(j0 + jj) + (size_t)(c0 + c) * n) : T(0);
@@ -195,27 +248,29 @@ bwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const int *__restr
                 __syncthreads();
                 block_gemv_sub<T, true>(acc, Ms, ys, nr, nj, rc);
                 __syncthreads();
+#pragma unroll
+                for (int u = 0; u < TILE_PER_THREAD; ++u) cur[u] = nxt[u];
             }
-            for (int e = threadIdx.x; e < SV_NB * SV_NB; e += SV_THREADS) {
-                int jj = e % SV_NB, r = e / SV_NB;
-                Ms[jj][r] = (jj < nr && r < nr) ? L[(size_t)(r0 + jj) + (size_t)(r0 + r) * lda] : T(0);
+            // v_I = (L_II^{-1})^T acc: Ms[jj][r] = Linv(jj, r) used transposed
+            {
+                T reg[TILE_PER_THREAD];
+                tile_load(reg, Linv + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
+                tile_store(reg, Ms);
+            }
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                ys[r][c] = acc[r][c];
+                acc[r][c] = T(0);
             }
             __syncthreads();
-            // v_r = acc_r - sum_{jj > r} L(jj, r) v_jj, from the last row up
-            for (int c = warp; c < rc; c += SV_THREADS / 32) {
-                for (int jj = nr - 1; jj >= 0; --jj) {
-                    T z = acc[jj][c];
-                    __syncwarp();
-                    for (int r = lane; r < jj; r += 32) acc[r][c] -= Ms[jj][r] * z;
-                    __syncwarp();
-                }
-            }
+            block_gemv_sub<T, true>(acc, Ms, ys, nr, nr, rc);   // acc = -Linv^T * w
             __syncthreads();
             for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
                 int r = e % SV_NB, c = e / SV_NB;
                 if (r < nr && c < rc) {
-                    stcg(Y + (size_t)(r0 + r) + (size_t)(c0 + c) * n, acc[r][c]);
-                    X[(size_t)perm[r0 + r] + (size_t)(c0 + c) * ldx] = (double)acc[r][c];
+                    const T v = -acc[r][c];
+                    stcg(Y + (size_t)(r0 + r) + (size_t)(c0 + c) * n, v);
+                    X[(size_t)perm[r0 + r] + (size_t)(c0 + c) * ldx] = (double)v;
                 }
             }
             __syncthreads();
@@ -226,7 +281,15 @@ bwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const int *__restr
     }
 }
 
-// work layout: T Y[n * nrhs]; flags: int[2 * nb] (forward, backward); tickets: int[2] right after.
+// Work layout (solve_work_bytes): T Y[n * nrhs] (rounded up to 256 bytes), then T Linv[nb * NB * NB].
+// flags: int[2 * nb] (forward, backward), then the two tickets.
+template <typename T>
+size_t solve_work_bytes(int n, int nrhs) {
+    const size_t nb = ((size_t)n + SV_NB - 1) / SV_NB;
+    const size_t y = ((size_t)n * nrhs * sizeof(T) + 255) / 256 * 256;
+    return y + nb * SV_NB * SV_NB * sizeof(T);
+}
+
 template <typename T>
 cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
                          const int *perm, double *X, int ldx, T *work, int *flags, int *status,
@@ -236,22 +299,30 @@ cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd,
     epoch = epoch % 1000000000 + 1;
     const int nb = (n + SV_NB - 1) / SV_NB;
     int *tickets = flags + 2 * nb;
+    T *Y = work;
+    T *Linv = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(work) +
+                                    ((size_t)n * nrhs * sizeof(T) + 255) / 256 * 256);
     cudaError_t e = cudaMemsetAsync(tickets, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = nb < sms ? nb : sms;
-    fwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, perm, X, ldx, work, flags, epoch, tickets, status, skip);
+    inv_diag_kernel<T><<<nb, SV_NB, 0, s>>>(n, L, lda, Linv, status, skip);
     count_launches(1);
-    dsolve_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(n, nrhs, Dd, Ds, work, status, skip);
+    fwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, Y, flags, epoch, tickets, status,
+                                              skip);
     count_launches(1);
-    bwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, perm, X, ldx, work, flags + nb, epoch, tickets + 1,
+    dsolve_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(n, nrhs, Dd, Ds, Y, status, skip);
+    count_launches(1);
+    bwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, Y, flags + nb, epoch, tickets + 1,
                                               status, skip);
     count_launches(1);
     return cudaGetLastError();
 }
 
+template size_t solve_work_bytes<double>(int, int);
+template size_t solve_work_bytes<float>(int, int);
 template cudaError_t launch_solve<double>(int, int, const double *, int, const double *, const double *, const int *,
                                           double *, int, double *, int *, int *, const int *, cudaStream_t);
 template cudaError_t launch_solve<float>(int, int, const float *, int, const double *, const double *, const int *,

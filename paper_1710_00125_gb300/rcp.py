@@ -83,6 +83,8 @@ def lib():
         L.rcp_profile_read.argtypes = [P, P, P, I]
         L.rcp_solve_noalloc.argtypes = [I, I, P, I, P, P, P, I, P, I, P]
         L.rcp_solve_noalloc.restype = ctypes.c_int
+        L.rcp_panel_trace.argtypes = [P, P, I]
+        L.rcp_panel_trace.restype = ctypes.c_int
         L.rcp_kernel_launches.argtypes = []
         L.rcp_kernel_launches.restype = ctypes.c_longlong
         for name in ("rcp_profile", "rcp_profile_read", "rcp_create", "rcp_sync", "rcp_reserve", "rcp_factor", "rcp_solve", "rcp_refine", "rcp_sysv",
@@ -178,7 +180,7 @@ def rcp_solve(h: Handle, LA: torch.Tensor, Dd, Ds, perm, prec, X: torch.Tensor, 
 
 def rcp_solve_noalloc(LA: torch.Tensor, Dd, Ds, perm, prec, X: torch.Tensor, stream=None) -> None:
     """rcp_solve without any device allocation (for callers that cannot allocate, e.g. inside
-    stream capture): scratch comes from a fixed 8 MiB device array shared by all calls."""
+    stream capture): scratch comes from a fixed 16 MiB device array shared by all calls."""
     n = LA.shape[0]
     nrhs, ldx = _rhs_view(X, n)
     if isinstance(prec, str):
@@ -221,8 +223,17 @@ def rcp_sysv(h: Handle, A64, Bv, X, opts: Opts | None = None, tol=1e-12, max_ite
 PHASES = ("sketch", "panel", "interchange", "trailing", "solve", "residual")
 
 
-def rcp_profile(h: Handle, enable: bool = True) -> None:
-    _check(lib().rcp_profile(h.h, int(bool(enable))), "rcp_profile")
+def rcp_profile(h: Handle, enable=True) -> None:
+    """0/False: off; 1/True: per-phase events; 2: events plus per-step panel timestamps."""
+    _check(lib().rcp_profile(h.h, int(enable)), "rcp_profile")
+
+
+def rcp_panel_trace(h: Handle, n: int):
+    """(n, 10) uint64 SM clock stamps of the panel steps of the last traced factorization."""
+    import numpy as np
+    out = np.zeros(n * 10, dtype=np.uint64)
+    _check(lib().rcp_panel_trace(h.h, ctypes.c_void_p(out.ctypes.data), out.size), "rcp_panel_trace")
+    return out.reshape(n, 10)
 
 
 def rcp_profile_read(h: Handle) -> dict:

@@ -36,6 +36,6 @@ def test_noalloc_solve_matches_rcp_solve(prec, n, nrhs):
 def test_noalloc_solve_rejects_sizes_beyond_its_scratch():
     from paper_1710_00125_gb300 import rcp
     lib = rcp.lib()
-    # n * nrhs * 8 bytes beyond 8 MiB: refused before touching any pointer
+    # n * nrhs * 8 bytes beyond 16 MiB: refused before touching any pointer
     fake = 1 << 20
-    assert lib.rcp_solve_noalloc(4096, 300, fake, 4096, fake, fake, fake, 0, fake, 4096, None) == -7
+    assert lib.rcp_solve_noalloc(4096, 600, fake, 4096, fake, fake, fake, 0, fake, 4096, None) == -7
