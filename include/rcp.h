@@ -51,9 +51,10 @@ typedef enum {
 
 typedef enum {
     RCP_FP64 = 0,           /* everything in FP64 (CUDA cores)                             */
-    RCP_FP32 = 1,           /* FP32 factor; FP32 trailing update on CUDA cores            */
-    RCP_TF32 = 2,           /* FP32 factor; trailing update on tensor cores, TF32 inputs   */
-    RCP_TF32X3 = 3          /* FP32 factor; trailing update with split-TF32 (3 products)   */
+    RCP_FP32 = 1,           /* FP32 factor; FP32 trailing update on CUDA cores                  */
+    RCP_TF32 = 2,           /* reserved: currently runs as RCP_FP32                              */
+    RCP_TF32X3 = 3          /* FP32 factor; trailing update on tcgen05 tensor cores with split  */
+                            /* TF32 operands (hi*hi + hi*lo + lo*hi, FP32 accumulation)        */
 } rcp_prec;
 
 typedef struct {

@@ -44,6 +44,7 @@ struct FactorWork {
     int maxmoved;
     unsigned long long *trace;   // optional per-step timestamps (profiling), 10 per position
     unsigned long long *keys;    // ring of packed argmax keys (FP32 path), zeroed per factorization
+    float *tcops;                // tensor-core operand tiles (TF32x3 trailing update)
 };
 
 template <typename T>
@@ -57,6 +58,9 @@ cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_trailing(const FactorWork<T> &w, int kmin, int mode, cudaStream_t s);
+
+size_t tc_ops_floats(int n, int bmax);
+cudaError_t launch_trailing_tc(const FactorWork<float> &w, float *ops, int kmin, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_factor_init(const FactorWork<T> &w, cudaStream_t s);

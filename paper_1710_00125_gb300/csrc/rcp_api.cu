@@ -47,6 +47,7 @@ struct rcp_handle {
     Buf A64, F, Bh, Xh, Dd, Ds, perm;              // rcp_sysv buffers
     Buf trace;                                     // per-step panel timestamps (profiling level 2)
     Buf keys;                                      // packed argmax keys of the FP32 panel
+    Buf tcops;                                     // tensor-core operand tiles
     int trace_n = 0;
 };
 
@@ -163,6 +164,7 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->s1v, 4 * (size_t)r.grid * sizeof(double)));
     RCP_TRY(grow(h->s2v, 4 * (size_t)r.grid * sizeof(double)));
     RCP_TRY(grow(h->keys, 16 * sizeof(unsigned long long)));
+    if (r.prec == RCP_TF32X3) RCP_TRY(grow(h->tcops, tc_ops_floats(n, r.b) * sizeof(float)));
     RCP_TRY(grow(h->s1i, 2 * (size_t)r.grid * sizeof(int)));
     RCP_TRY(grow(h->s2i, 2 * (size_t)r.grid * sizeof(int)));
     RCP_TRY(grow(h->pay, 2 * (size_t)r.grid * r.d * sizeof(T)));
@@ -191,6 +193,7 @@ FactorWork<T> make_work(rcp_handle *h, int n, T *A, int lda, double *Dd, double 
     w.tmpA = (T *)h->tmpA.p; w.tmpL = (T *)h->tmpL.p; w.tmpP = (int *)h->tmpP.p;
     w.maxmoved = r.maxmoved;
     w.keys = (unsigned long long *)h->keys.p;
+    w.tcops = r.prec == RCP_TF32X3 ? (float *)h->tcops.p : nullptr;
     w.trace = nullptr;
     if (h->profiling >= 2 && grow(h->trace, (size_t)n * 10 * sizeof(unsigned long long)) == RCP_OK) {
         w.trace = (unsigned long long *)h->trace.p;
@@ -331,7 +334,7 @@ rcp_status rcp_create(rcp_handle **h) {
 
 void rcp_destroy(rcp_handle *h) {
     if (!h) return;
-    Buf *all[] = {&h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lp, &h->lpos, &h->moved,
+    Buf *all[] = {&h->tcops, &h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lp, &h->lpos, &h->moved,
                   &h->s1v, &h->s2v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
                   &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm};
     for (Buf *b : all)

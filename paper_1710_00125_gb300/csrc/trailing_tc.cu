@@ -1,0 +1,370 @@
+// trailing_tc.cu -- the deferred trailing update of Algorithm 1, A22 -= W L21^T (lower triangle),
+// on the 5th-generation tensor cores (tcgen05, accumulators in tensor memory) for FP32 factors.
+//
+// Precision: W and L21 are FP32.  With plain TF32 inputs (10-bit mantissa) the update error
+// is ~1e-3 relative, too large for FP64 refinement to converge at condition numbers of 1e4.
+// Each operand is split as x = hi + lo with hi = tf32(x), lo = tf32(x - hi), and three products
+// hi*hi + hi*lo + lo*hi are accumulated in FP32 (the dropped lo*lo term is ~2^-22 relative).
+//
+// Data path per panel:
+//   prep kernel: rows kend..n of W (Wbuf) and of L21 (the panel columns of A) are rounded to
+//     hi/lo and written as K-major 128-row x 32-column tiles in the exact shared-memory image of
+//     the 128-byte swizzle (16 KB per tile, contiguous), one tile per (row block, K chunk).
+//   MMA kernel: persistent CTAs walk the 128 x 128 tiles (I >= J) of the trailing lower
+//     triangle.  Per K chunk one thread issues four 16 KB bulk copies (W_hi, W_lo of row block
+//     I; L_hi, L_lo of row block J) into a 3-stage ring guarded by mbarriers, then 4 K-steps x 3
+//     tcgen05.mma (M = N = 128, K = 8) into a 128-column TMEM accumulator, and commits the stage
+//     back to its "free" barrier.  After the last chunk the accumulator is drained by four warps
+//     (tcgen05.ld 32x32b, one TMEM lane quarter each) and subtracted from A in place.
+// Every wait is bounded (kWaitLimitNs); on expiry the status word is set, the CTA stops
+// issuing work, waits for its issued copies and MMAs (bounded), frees its tensor memory and
+// returns.
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace rcpk {
+
+namespace tc {
+
+constexpr int TM = 128;              // tile rows (M) and columns (N)
+constexpr int KC = 32;               // K chunk: 32 tf32 = one 128-byte swizzle row
+constexpr int TILE_FLOATS = TM * KC; // 4096 floats = 16 KB
+constexpr int STAGES = 3;
+constexpr int THREADS = 128;
+constexpr uint32_t STAGE_BYTES = 4u * TILE_FLOATS * 4u;   // W_hi, W_lo, L_hi, L_lo
+
+// Offset (in floats) of element (m, k) of a 128 x 32 K-major tile in the 128-byte swizzle
+// image: 8-row groups of 1024 bytes, rows of 128 bytes, 16-byte chunks xor-ed with row % 8.
+__host__ __device__ __forceinline__ int swz(int m, int k) {
+    const int r = m & 7;
+    return (m >> 3) * 256 + r * 32 + (((k >> 2) ^ r) << 2) + (k & 3);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t y;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+    return __uint_as_float(y);
+}
+
+// ---- shared-memory / tensor-memory primitives ------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the phase with parity `phase` to complete; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
+    const uint32_t a = smem_u32(bar);
+    uint32_t done = 0;
+    unsigned long long t0 = 0;
+    for (unsigned spins = 0;; ++spins) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if (spins == 0) t0 = global_ns();
+        else if ((spins & 63u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle layout, 8-row
+// groups 1024 bytes apart (stride byte offset), descriptor version 1, base offset 0 (every
+// tile starts on a 1024-byte boundary).
+__device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);           // start address
+    d |= (uint64_t)1u << 16;                              // leading byte offset (unused here)
+    d |= (uint64_t)(1024u >> 4) << 32;                    // stride byte offset
+    d |= (uint64_t)1u << 46;                              // version
+    d |= (uint64_t)2u << 61;                              // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, N = 128, M = 128.
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+}  // namespace tc
+
+// ------------------------------------------------------------------------------------------
+// prep: hi/lo split of W(kend:n, 0:K) and L21 = A(kend:n, k0:kend) into swizzled tiles.
+// Tile (R, c) of an operand starts at (R * nkc + c) * TILE_FLOATS; rows past n and columns past
+// K are zero.  Layout of the operand buffer: [W_hi | W_lo | L_hi | L_lo], each nrb * nkc tiles.
+// ------------------------------------------------------------------------------------------
+// One CTA per (row block R, K chunk c): coalesced column reads of W and L21, the hi/lo split,
+// the swizzle in shared memory, then contiguous 16-byte stores of the four 16 KB tiles.
+__global__ void __launch_bounds__(256) tc_prep_kernel(FactorWork<float> w, float *ops, int nrb_cap, int nkc_cap) {
+    __shared__ __align__(16) float t2[2][tc::TILE_FLOATS];   // hi, lo of one operand (32 KB)
+    if (ldcg(w.status) != 0) return;
+    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
+    const int K = kend - k0, N = n - kend;
+    if (K <= 0 || N <= 0) return;
+    const int nrb = (N + tc::TM - 1) / tc::TM, nkc = (K + tc::KC - 1) / tc::KC;
+    if (nrb > nrb_cap || nkc > nkc_cap) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(w.status, ST_INTERNAL);
+        return;
+    }
+    const size_t per = (size_t)nrb_cap * nkc_cap * tc::TILE_FLOATS;
+    for (int tile = blockIdx.x; tile < nrb * nkc; tile += gridDim.x) {
+        const int R = tile / nkc, c = tile % nkc;
+        const size_t toff = ((size_t)R * nkc + c) * tc::TILE_FLOATS;
+        for (int op = 0; op < 2; ++op) {   // 0: W rows, 1: L21 rows
+            for (int idx = threadIdx.x; idx < tc::TILE_FLOATS; idx += blockDim.x) {
+                const int m = idx % tc::TM, kk = idx / tc::TM;
+                const int p = kend + R * tc::TM + m, k = c * tc::KC + kk;
+                float v = 0.f;
+                if (p < n && k < K) v = op == 0 ? w.Wbuf[(size_t)p + (size_t)k * n] : w.A[(size_t)p + (size_t)(k0 + k) * lda];
+                const float h = tc::tf32_rna(v);
+                const int o = tc::swz(m, kk);
+                t2[0][o] = h;
+                t2[1][o] = tc::tf32_rna(v - h);
+            }
+            __syncthreads();
+            for (int q = 0; q < 2; ++q) {
+                float4 *dst = reinterpret_cast<float4 *>(ops + (size_t)(2 * op + q) * per + toff);
+                const float4 *src = reinterpret_cast<const float4 *>(t2[q]);
+                for (int v = threadIdx.x; v < tc::TILE_FLOATS / 4; v += blockDim.x) dst[v] = src[v];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// tcgen05 MMA kernel.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(tc::THREADS, 1) tc_trailing_kernel(FactorWork<float> w, const float *ops, int nrb_cap,
+                                                                     int nkc_cap) {
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[tc::STAGES];
+    __shared__ __align__(8) uint64_t free_bar[tc::STAGES];
+    __shared__ __align__(8) uint64_t acc_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (ldcg(w.status) != 0) return;
+    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
+    const int K = kend - k0, N = n - kend;
+    if (K <= 0 || N <= 0) return;
+    const int nrb = (N + tc::TM - 1) / tc::TM, nkc = (K + tc::KC - 1) / tc::KC;
+    if (nrb > nrb_cap || nkc > nkc_cap) return;   // prep has flagged it
+    const long long total = (long long)nrb * (nrb + 1) / 2;
+    if ((long long)blockIdx.x >= total) return;
+
+    // 1024-byte aligned stage ring
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+    float *stage0 = reinterpret_cast<float *>(base);
+
+    if (tid == 0) {
+        for (int s = 0; s < tc::STAGES; ++s) { tc::mbar_init(&full_bar[s], 1); tc::mbar_init(&free_bar[s], 1); }
+        tc::mbar_init(&acc_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        // 128 columns of tensor memory for the FP32 128 x 128 accumulator
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" :: "r"(tc::smem_u32(&s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    const size_t per = (size_t)nrb_cap * nkc_cap * tc::TILE_FLOATS;
+    const float *whi = ops, *wlo = ops + per, *lhi = ops + 2 * per, *llo = ops + 3 * per;
+
+    // producer/consumer state (thread 0 only)
+    uint32_t full_phase[tc::STAGES] = {0, 0, 0}, free_phase[tc::STAGES] = {0, 0, 0};
+    int issued_free[tc::STAGES] = {0, 0, 0};   // stage has an outstanding MMA commit
+    int pending_full[tc::STAGES] = {0, 0, 0};  // stage has copies not yet waited for
+    uint32_t acc_phase = 0;
+    float *__restrict__ A = w.A;
+
+    for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        int I = (int)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+        while ((long long)I * (I + 1) / 2 > tile) --I;
+        while ((long long)(I + 1) * (I + 2) / 2 <= tile) ++I;
+        const int J = (int)(tile - (long long)I * (I + 1) / 2);
+
+        if (tid == 0 && !s_abort) {
+            // prologue: fill up to STAGES chunks, then MMA chunk by chunk, refilling
+            int next = 0;
+            auto issue = [&](int c) -> bool {
+                const int s = c % tc::STAGES;
+                if (issued_free[s]) {
+                    if (!tc::mbar_wait(&free_bar[s], free_phase[s])) return false;
+                    free_phase[s] ^= 1u;
+                    issued_free[s] = 0;
+                }
+                float *dst = stage0 + (size_t)s * (tc::STAGE_BYTES / 4);
+                tc::mbar_expect_tx(&full_bar[s], tc::STAGE_BYTES);
+                const size_t ti = ((size_t)I * nkc + c) * tc::TILE_FLOATS, tj = ((size_t)J * nkc + c) * tc::TILE_FLOATS;
+                tc::bulk_g2s(dst, whi + ti, tc::TILE_FLOATS * 4, &full_bar[s]);
+                tc::bulk_g2s(dst + tc::TILE_FLOATS, wlo + ti, tc::TILE_FLOATS * 4, &full_bar[s]);
+                tc::bulk_g2s(dst + 2 * tc::TILE_FLOATS, lhi + tj, tc::TILE_FLOATS * 4, &full_bar[s]);
+                tc::bulk_g2s(dst + 3 * tc::TILE_FLOATS, llo + tj, tc::TILE_FLOATS * 4, &full_bar[s]);
+                pending_full[s] = 1;
+                return true;
+            };
+            bool ok = true;
+            for (; next < nkc && next < tc::STAGES && ok; ++next) ok = issue(next);
+            for (int c = 0; c < nkc && ok; ++c) {
+                const int s = c % tc::STAGES;
+                if (!tc::mbar_wait(&full_bar[s], full_phase[s])) { ok = false; break; }
+                full_phase[s] ^= 1u;
+                pending_full[s] = 0;
+                tc::tc_fence_after();
+                const float *st = stage0 + (size_t)s * (tc::STAGE_BYTES / 4);
+                const uint32_t a_hi = tc::smem_u32(st), a_lo = tc::smem_u32(st + tc::TILE_FLOATS);
+                const uint32_t b_hi = tc::smem_u32(st + 2 * tc::TILE_FLOATS), b_lo = tc::smem_u32(st + 3 * tc::TILE_FLOATS);
+#pragma unroll
+                for (int kk = 0; kk < tc::KC / 8; ++kk) {
+                    const uint32_t off = kk * 32;   // 8 tf32 = 32 bytes along the swizzled row
+                    const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+                    tc::mma_tf32(tmem, tc::sdesc_k128(a_hi + off), tc::sdesc_k128(b_hi + off), acc);
+                    tc::mma_tf32(tmem, tc::sdesc_k128(a_hi + off), tc::sdesc_k128(b_lo + off), 1u);
+                    tc::mma_tf32(tmem, tc::sdesc_k128(a_lo + off), tc::sdesc_k128(b_hi + off), 1u);
+                }
+                tc::mma_commit(&free_bar[s]);
+                issued_free[s] = 1;
+                if (next < nkc) { ok = issue(next); ++next; }
+            }
+            if (ok) tc::mma_commit(&acc_bar);
+            if (!ok) {
+                s_abort = 1;
+                atomicOr(w.status, ST_TIMEOUT);
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        // epilogue: wait for the accumulator, then C -= acc on the lower triangle
+        if (!tc::mbar_wait(&acc_bar, acc_phase)) {
+            atomicOr(w.status, ST_TIMEOUT);
+            s_abort = 1;
+        }
+        acc_phase ^= 1u;
+        __syncthreads();
+        if (s_abort) break;
+        tc::tc_fence_after();
+        const int p = kend + I * tc::TM + warp * 32 + lane;
+        const int q0 = kend + J * tc::TM;
+        for (int c0 = 0; c0 < tc::TM; c0 += 16) {
+            uint32_t r[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            tc::tmem_wait_ld();
+            if (p < n) {
+                float cv[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int q = q0 + c0 + j;
+                    cv[j] = (q < n && p >= q) ? A[(size_t)p + (size_t)q * lda] : 0.f;
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int q = q0 + c0 + j;
+                    if (q < n && p >= q) A[(size_t)p + (size_t)q * lda] = cv[j] - __uint_as_float(r[j]);
+                }
+            }
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+    }
+    // drain: every issued copy and MMA must finish before the CTA (and its shared memory and
+    // tensor memory) goes away
+    if (tid == 0) {
+        for (int s = 0; s < tc::STAGES; ++s) {
+            if (pending_full[s]) tc::mbar_wait(&full_bar[s], full_phase[s]);
+            if (issued_free[s]) tc::mbar_wait(&free_bar[s], free_phase[s]);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" :: "r"(tmem) : "memory");
+}
+
+size_t tc_ops_floats(int n, int bmax) {
+    const size_t nrb = ((size_t)n + tc::TM - 1) / tc::TM;
+    const size_t nkc = ((size_t)bmax + 1 + tc::KC - 1) / tc::KC;
+    return 4 * nrb * nkc * tc::TILE_FLOATS;
+}
+
+cudaError_t launch_trailing_tc(const FactorWork<float> &w, float *ops, int kmin, cudaStream_t s) {
+    const int nrb_cap = (w.n + tc::TM - 1) / tc::TM;
+    const int nkc_cap = (w.bmax + 1 + tc::KC - 1) / tc::KC;
+    static int sms = 0;
+    static bool attr = false;
+    const size_t smem = (size_t)tc::STAGES * tc::STAGE_BYTES + 1024;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_trailing_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long rows = (long long)w.n - kmin;
+    const long long nrb = rows > 0 ? (rows + tc::TM - 1) / tc::TM : 1;
+    tc_prep_kernel<<<8 * sms, 256, 0, s>>>(w, ops, nrb_cap, nkc_cap);
+    count_launches(1);
+    const long long tiles = nrb * (nrb + 1) / 2;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    tc_trailing_kernel<<<grid > 0 ? grid : 1, tc::THREADS, smem, s>>>(w, ops, nrb_cap, nkc_cap);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace rcpk

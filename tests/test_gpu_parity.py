@@ -233,3 +233,43 @@ def test_sysv_device_and_host_buffers(rcp, handle):
                                  host_buffers=True)
         assert code == 0
         assert np.array_equal(Xh.numpy(), X.cpu().numpy())
+
+
+# ------------------------------------------------------------------------------------------
+# FP32 factors: SIMT and tensor-core (tcgen05, split TF32) trailing updates
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("n,b,d", [(300, 32, 40), (777, 64, 80), (1500, 128, 80)])
+def test_fp32_factor_backward_error(rcp, handle, prec, n, b, d):
+    # ||P A P^T - L D L^T||_max / ||A||_max computed in FP64 from the FP32 factor: a wrong
+    # tile, swizzle or descriptor in the update makes this O(1)
+    a = inputs.gaussian_sym(n, seed=n + b)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, b, d, 3, prec=prec)
+    assert code == 0
+    L = _unit_lower(A)
+    D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
+    p = perm.cpu().numpy()
+    assert sorted(p.tolist()) == list(range(n))
+    err = np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() / np.abs(a).max()
+    assert err < 2e-5 * max(1.0, st.growth_D), err
+    # the FP32 pivot sequence stays close to the oracle's FP64 one: same 2x2 count within 5%
+    ref = oracle.rcp(a, oracle.omega(3, d, n), record=False)
+    assert abs(st.n_2x2 - ref["n_2x2"]) <= max(3, 0.05 * ref["n_2x2"])
+
+
+@pytest.mark.parametrize("kexp", [2.0, 4.0, 6.0])
+def test_tf32x3_refine_reaches_fp64_backward_error(rcp, handle, kexp):
+    n = 1024
+    a = inputs.spectrum(n, seed=9, kexp=kexp, nrefl=16)
+    x = inputs.x_true(n, 1, seed=9)
+    rhs = inputs.rhs_for(a, x)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, 128, 80, 2, prec="tf32x3")
+    assert code == 0
+    A64 = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    Bv = torch.from_numpy(rhs.copy()).to(DEV)
+    X = torch.zeros_like(Bv)
+    code, rst = rcp.rcp_refine(handle, A64, A, Dd, Ds, perm, "tf32x3", Bv, X, tol=1e-12, max_iter=30)
+    assert code == 0, rst.as_dict()
+    assert oracle.berr(a, X.cpu().numpy().T, rhs.T) <= 1e-12
+    assert rst.refine_iters <= 6
