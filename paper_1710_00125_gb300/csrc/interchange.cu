@@ -26,27 +26,45 @@ __global__ void mark_kernel(FactorWork<T> w, int *phi) {
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
         int j = w.moved[m];
         phi[w.lpos[j]] = j;
+        w.tmpP[m] = w.perm[j];
     }
+}
+
+// Work items of the gather and scatter: for every moved index m, segments of SEG entries of its
+// L row (t < k0) and, when its new position is in the trailing block, of its trailing line.
+constexpr int SEG = 1024;
+
+__device__ __forceinline__ bool moved_item(long long item, int M, int nl, int nt, int *m, int *part, int *seg) {
+    const int per = nl + nt;
+    if (item >= (long long)M * per) return false;
+    *m = (int)(item / per);
+    const int r = (int)(item % per);
+    *part = r < nl ? 0 : 1;
+    *seg = r < nl ? r : r - nl;
+    return true;
 }
 
 template <typename T>
 __global__ void gather_kernel(FactorWork<T> w, const int *phi) {
     if (ldcg(w.status) != 0) return;
     const int M = min(ldcg(&w.st->n_moved), w.maxmoved);
-    const int m = blockIdx.y;
-    if (m >= M) return;
     const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
-    const int j = w.moved[m], p = w.lpos[j];
+    const int nl = (k0 + SEG - 1) / SEG, nt = (n - kend + SEG - 1) / SEG;
     const T *__restrict__ A = w.A;
-    if (blockIdx.x == 0 && threadIdx.x == 0) w.tmpP[m] = w.perm[j];
-    const int stride = gridDim.x * blockDim.x;
-    T *tl = w.tmpL + (size_t)m * n;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k0; t += stride) tl[t] = A[(size_t)j + (size_t)t * lda];
-    if (p >= kend) {
-        T *ta = w.tmpA + (size_t)m * n;
-        for (int q = kend + blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-            int src = phi[q];
-            ta[q] = a_sym_ld(A, lda, j, src >= 0 ? src : q);
+    int m, part, seg;
+    for (long long item = blockIdx.x; moved_item(item, M, nl, nt, &m, &part, &seg); item += gridDim.x) {
+        const int j = w.moved[m], p = w.lpos[j];
+        if (part == 0) {
+            T *tl = w.tmpL + (size_t)m * n;
+            const int hi = min(k0, (seg + 1) * SEG);
+            for (int t = seg * SEG + threadIdx.x; t < hi; t += blockDim.x) tl[t] = A[(size_t)j + (size_t)t * lda];
+        } else if (p >= kend) {
+            T *ta = w.tmpA + (size_t)m * n;
+            const int hi = min(n, kend + (seg + 1) * SEG);
+            for (int q = kend + seg * SEG + threadIdx.x; q < hi; q += blockDim.x) {
+                const int src = phi[q];
+                ta[q] = a_sym_ld(A, lda, j, src >= 0 ? src : q);
+            }
         }
     }
 }
@@ -55,41 +73,48 @@ template <typename T>
 __global__ void scatter_kernel(FactorWork<T> w) {
     if (ldcg(w.status) != 0) return;
     const int M = min(ldcg(&w.st->n_moved), w.maxmoved);
-    const int m = blockIdx.y;
-    if (m >= M) return;
     const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
-    const int j = w.moved[m], p = w.lpos[j];
+    const int nl = (k0 + SEG - 1) / SEG, nt = (n - kend + SEG - 1) / SEG;
     T *__restrict__ A = w.A;
-    if (blockIdx.x == 0 && threadIdx.x == 0) w.perm[p] = w.tmpP[m];
-    const int stride = gridDim.x * blockDim.x;
-    const T *tl = w.tmpL + (size_t)m * n;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < k0; t += stride) A[(size_t)p + (size_t)t * lda] = tl[t];
-    if (p >= kend) {
-        const T *ta = w.tmpA + (size_t)m * n;
-        for (int q = kend + blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-            T v = ta[q];
-            if (p >= q) A[(size_t)p + (size_t)q * lda] = v;
-            else A[(size_t)q + (size_t)p * lda] = v;
+    int m, part, seg;
+    for (long long item = blockIdx.x; moved_item(item, M, nl, nt, &m, &part, &seg); item += gridDim.x) {
+        const int j = w.moved[m], p = w.lpos[j];
+        if (part == 0) {
+            const T *tl = w.tmpL + (size_t)m * n;
+            const int hi = min(k0, (seg + 1) * SEG);
+            for (int t = seg * SEG + threadIdx.x; t < hi; t += blockDim.x) A[(size_t)p + (size_t)t * lda] = tl[t];
+        } else if (p >= kend) {
+            const T *ta = w.tmpA + (size_t)m * n;
+            const int hi = min(n, kend + (seg + 1) * SEG);
+            for (int q = kend + seg * SEG + threadIdx.x; q < hi; q += blockDim.x) {
+                const T v = ta[q];
+                if (p >= q) A[(size_t)p + (size_t)q * lda] = v;
+                else A[(size_t)q + (size_t)p * lda] = v;
+            }
         }
     }
 }
 
-// Panel multipliers into A(:, k0:kend) in position order; clears the position marks.
+// Panel multipliers (already in position order, column-major) into A(:, k0:kend); clears the
+// position marks.
 template <typename T>
 __global__ void panel_store_kernel(FactorWork<T> w, int *phi) {
     if (ldcg(w.status) != 0) return;
-    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend, bw = w.bw;
+    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
     const int width = kend - k0;
     T *__restrict__ A = w.A;
-    for (int j = k0 + blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const int p = w.lpos[j];
-        const T *lrow = w.Lp + (size_t)j * bw;
-        const int tmax = min(width, p - k0);
-        for (int t = 0; t < tmax; ++t) A[(size_t)p + (size_t)(k0 + t) * lda] = lrow[t];
+    const long long total = (long long)width * (n - k0);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(e / (n - k0)), p = k0 + (int)(e % (n - k0));
+        if (p > k0 + t) A[(size_t)p + (size_t)(k0 + t) * lda] = w.Lc[(size_t)p + (size_t)t * n];
     }
     if (blockIdx.x == 0) {
         const int M = min(w.st->n_moved, w.maxmoved);
-        for (int m = threadIdx.x; m < M; m += blockDim.x) phi[w.lpos[w.moved[m]]] = -1;
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            const int j = w.moved[m];
+            phi[w.lpos[j]] = -1;
+            w.perm[w.lpos[j]] = w.tmpP[m];
+        }
     }
 }
 
@@ -168,7 +193,10 @@ cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s) {
     int *phi = w.moved + w.n;   // second half of the moved buffer holds the position marks
     mark_kernel<T><<<1, 256, 0, s>>>(w, phi);
     count_launches(1);
-    dim3 g(8, w.maxmoved);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int g = 4 * sms;
     gather_kernel<T><<<g, 256, 0, s>>>(w, phi);
     count_launches(1);
     scatter_kernel<T><<<g, 256, 0, s>>>(w);

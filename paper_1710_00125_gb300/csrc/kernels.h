@@ -24,7 +24,8 @@ struct FactorWork {
     int bmax, bw;       // panel width target and row stride of the panel buffers (bmax + 1)
     double alpha;
     T *Wbuf;            // n x bw, column-major (ld n): W = L D rows of the panel, logical order
-    T *Lp;              // n x bw, row-major by block-start index: the panel's multipliers
+    T *Lc;              // n x bw, column-major (ld n), position order: the panel's multipliers
+    T *Lg;              // n x bw, row-major by block-start index: multipliers as they are made
     double *Dd, *Ds;
     int *perm;
     int *lpos;          // [n]: final position in the panel of each block-start index
@@ -32,7 +33,7 @@ struct FactorWork {
     FactorState *st;
     double *s1v, *s2v;  // reduction slots
     int *s1i, *s2i;
-    T *pay;             // [2][grid][d] sketch columns of the candidates
+    T *pay;             // [2][grid][d] sketch column of each CTA's candidate
     unsigned *bar;
     int *status;
     int grid;           // CTAs of the cooperative panel kernel

@@ -50,8 +50,9 @@ size_t panel_smem_bytes(int d, int bw, int chunk_cap) {
     s += (size_t)chunk_cap * 5 * sizeof(T);            // dg, c1, c2, l1s, l2s
     s += (size_t)2 * d * sizeof(T);                    // bP, bR
     s += (size_t)2 * bw * sizeof(T);                   // lP, lR
+    s += (size_t)4 * bw * sizeof(T) + (size_t)bw * sizeof(int);   // per-column D scalars and kinds
     s += (size_t)chunk_cap * 2 * sizeof(int);          // lp, alive
-    s += (size_t)(bw + 3) * sizeof(int);               // window
+    s += (size_t)(bw + 3) * sizeof(int);               // window (kinds counted above)
     return s + 64;
 }
 
@@ -166,20 +167,40 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 
 constexpr int KEY_RING = 16;
 
+// The multiplier L(j, t) of a row from its W = L D row and the panel's per-column D scalars,
+// with the same operations the elimination used (so the result is bitwise the same): kind 0
+// (zero column), 1 (1x1: w / d, or w * (1/d) in FP32), 3 / 4 (first / second column of a 2x2
+// block: scaled inverse).
+template <typename T>
+__device__ __forceinline__ T l_entry(const T *wr, int t, const int *kind, const T *cs0, const T *cs1, const T *cs2,
+                                     const T *cs3) {
+    constexpr bool F64 = std::is_same<T, double>::value;
+    const int k = kind[t];
+    if (k == 1) return F64 ? wr[t] / cs0[t] : wr[t] * cs0[t];
+    if (k == 3 || k == 4) {
+        const int t0 = k == 3 ? t : t - 1;
+        const T r = cs3[t0];
+        const T x1 = F64 ? wr[t0] / r : wr[t0] * r, x2 = F64 ? wr[t0 + 1] / r : wr[t0 + 1] * r;
+        return k == 3 ? cs2[t0] * (cs1[t0] * x1 - x2) : cs2[t0] * (cs0[t0] * x2 - x1);
+    }
+    return T(0);
+}
+
 // c[jl] = A(j, X) - sum_{t < i} Ws[jl][t] L(X, t) for the alive owned rows.  The loads of
-// the column of A, of L(X, 0:i) (into lX), of the candidate's sketch column (into bX) and of
-// `nx` scalars of the candidate's record (into xs, thread 0) are all issued before the first
-// barrier so that their latencies overlap.  `hook` runs on thread 0 right after that barrier.
+// the column of A, of the candidate's sketch column (into bX), of its multiplier row L(X, 0:i)
+// (into lX) and of `nx` scalars of the candidate's slot (into xs, thread 0) are all issued
+// before the first barrier so that their latencies overlap.  `hook` runs on thread 0 right
+// after that barrier.
 template <typename T, typename Hook>
 __device__ void schur_column(const T *__restrict__ A, int lda, int j_lo, int cnt, int X, int i, int bw,
-                             const T *Ws, const T *lXg, T *lX, const T *bXg, T *bX, int d, const int *alive, T *c,
-                             const double *xsrc, double *xs, int nx, Hook hook) {
+                             const T *Ws, const T *payg, T *bX, const T *lXg, T *lX, int d,
+                             const int *alive, T *c, const double *xsrc, double *xs, int nx, Hook hook) {
     T a0 = T(0), a1 = T(0);
     const int r0 = threadIdx.x, r1 = threadIdx.x + PANEL_THREADS;
     if (r0 < cnt && alive[r0]) a0 = a_sym(A, lda, j_lo + r0, X);
     if (r1 < cnt && alive[r1]) a1 = a_sym(A, lda, j_lo + r1, X);
+    for (int r = threadIdx.x; r < d; r += PANEL_THREADS) bX[r] = ldcg(payg + r);
     for (int t = threadIdx.x; t < i; t += PANEL_THREADS) lX[t] = ldcg(lXg + t);
-    for (int r = threadIdx.x; r < d; r += PANEL_THREADS) bX[r] = ldcg(bXg + r);
     if (threadIdx.x < nx) xs[threadIdx.x] = ldcg(xsrc + threadIdx.x);
     __syncthreads();
     if (threadIdx.x == 0) hook();
@@ -281,9 +302,11 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     T *bR = bP + d;
     T *lP = bR + d;
     T *lR = lP + bw;
-    int *lp = reinterpret_cast<int *>(lR + bw);
+    T *cs0 = lR + bw, *cs1 = cs0 + bw, *cs2 = cs1 + bw, *cs3 = cs2 + bw;   // per-column D scalars
+    int *lp = reinterpret_cast<int *>(cs3 + bw);
     int *alive = lp + cap;
     int *win = alive + cap;           // positions k0 .. k0 + bw + 2
+    int *ckind = win + (bw + 3);      // per panel column: 0 zero, 1 scalar, 3/4 first/second of 2x2
     const int wsz = bw + 3;
 
     const T *__restrict__ A = w.A;
@@ -328,7 +351,8 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     T tmaxL = T(0);
     int info = 0, fail = 0;
     const double alpha = w.alpha;
-    T *pay1 = w.pay, *pay2 = w.pay + (size_t)G * d;
+    const int ps = d;        // payload record: the candidate's sketch column
+    T *pay1 = w.pay, *pay2 = w.pay + (size_t)G * ps;
     double *rec1 = w.s1v, *rec2 = w.s2v;   // per-CTA records (4 doubles each)
     unsigned long long *keys = w.keys;
     __syncthreads();
@@ -340,8 +364,10 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
             if (alive[jl] && better(nrm[jl], lp[jl], c.v, c.lpos)) c = CandT<T>{nrm[jl], lp[jl], j_lo + jl};
         c = block_argmax(c, s_red);
-        if (c.phys >= 0)
-            for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay1 + (size_t)cta * d + r, Bs[(size_t)(c.phys - j_lo) * ds + r]);
+        if (c.phys >= 0) {
+            const int jc = c.phys - j_lo;
+            for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay1 + (size_t)cta * ps + r, Bs[(size_t)jc * ds + r]);
+        }
         const unsigned g1 = gbase + nbar + 1;
         if (tid == 0) {
             const double dgc = c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0;
@@ -396,7 +422,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
 
         // ---------------- (2) column P of the Schur complement, lambda and r ----------------
         PANEL_MARK(3);
-        schur_column<T>(A, lda, j_lo, cnt, P, i, ws, Ws, w.Lp + (size_t)P * bw, lP, pay1 + (size_t)gP * d, bP, d,
+        schur_column<T>(A, lda, j_lo, cnt, P, i, ws, Ws, pay1 + (size_t)gP * ps, bP, w.Lg + (size_t)P * bw, lP, d,
                         alive, c1, rec1 + 4 * (size_t)gP, s_d + 8, KEYS ? 1 : 0, NoHook());
         const double akk = KEYS ? s_d[8] : s_d[1];
         if (!isfinite(akk)) { fail = ST_NONFINITE; break; }
@@ -408,8 +434,10 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             if (better(v, lp[jl], c.v, c.lpos)) c = CandT<T>{v, lp[jl], j_lo + jl};
         }
         c = block_argmax(c, s_red);
-        if (c.phys >= 0)
-            for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay2 + (size_t)cta * d + r, Bs[(size_t)(c.phys - j_lo) * ds + r]);
+        if (c.phys >= 0) {
+            const int jc = c.phys - j_lo;
+            for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay2 + (size_t)cta * ps + r, Bs[(size_t)jc * ds + r]);
+        }
         const unsigned g2 = gbase + nbar + 1;
         if (tid == 0) {
             const double cv = c.phys >= 0 ? (double)c1[c.phys - j_lo] : 0.0;
@@ -474,7 +502,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             auto hook = [&]() {
                 if (KEYS) sbkp_scalars<T>(CASE_PENDING, akk, lam, s_d[10], s_d[11], alpha, s_i, s_d, s_t);
             };
-            schur_column<T>(A, lda, j_lo, cnt, R, i, ws, Ws, w.Lp + (size_t)R * bw, lR, pay2 + (size_t)gR * d, bR, d,
+            schur_column<T>(A, lda, j_lo, cnt, R, i, ws, Ws, pay2 + (size_t)gR * ps, bR, w.Lg + (size_t)R * bw, lR, d,
                             alive, c2, rec2 + 4 * (size_t)gR, s_d + 10, KEYS ? 2 : 0, hook);
             kase = s_i[7];
             if (kase < 0) { fail = ST_NONFINITE; break; }
@@ -516,7 +544,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             if (live) {
                 const int j = j_lo + jl;
                 T *wrow = Ws + (size_t)jl * ws;
-                T *lrow = w.Lp + (size_t)j * bw;
+                T *lrow = w.Lg + (size_t)j * bw;
                 if (j == piv1 || j == piv2) {
                     if (sub == 0) {
                         wrow[i] = T(0);
@@ -542,7 +570,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                         l2 = t_tinv * (t_aa * x2 - x1);
                         if (sub == 0) { wrow[i] = v1; wrow[i + 1] = v2; dg[jl] = dg[jl] - v1 * l1 - v2 * l2; }
                     }
-                    if (sub == 0) {
+                    if (sub == 1) {
                         stcg(lrow + i, l1);
                         if (s == 2) stcg(lrow + i + 1, l2);
                     }
@@ -574,6 +602,17 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             if (alive[jl] && (j == piv1 || j == piv2)) alive[jl] = 0;
         }
         PANEL_MARK(9);
+        if (tid == 0) {
+            // the D scalars of this step, so that any row's L entries can be rebuilt from W
+            if (kase == 3) {
+                ckind[i] = 3; ckind[i + 1] = 4;
+                cs0[i] = t_aa; cs1[i] = t_cc; cs2[i] = t_tinv;
+                cs3[i] = std::is_same<T, double>::value ? t_ark : t_rark;
+            } else {
+                ckind[i] = (kase == 0 || !nonzero_piv) ? 0 : 1;
+                cs0[i] = std::is_same<T, double>::value ? t_dpiv : t_rdpiv;
+            }
+        }
         if (cta == 0 && tid == 0) {
             if (kase == 3) {
                 w.Dd[k] = akk; w.Ds[k] = ark; w.Dd[k + 1] = arr; w.Ds[k + 1] = 0.0;
@@ -595,7 +634,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     __syncthreads();
     for (int e = tid; e < cnt * i; e += PANEL_THREADS) {
         int t = e / cnt, jl = e - t * cnt;
-        if (alive[jl]) w.Wbuf[(size_t)lp[jl] + (size_t)t * n] = Ws[(size_t)jl * ws + t];
+        const T *wrow = Ws + (size_t)jl * ws;
+        if (alive[jl]) w.Wbuf[(size_t)lp[jl] + (size_t)t * n] = wrow[t];
+        w.Lc[(size_t)lp[jl] + (size_t)t * n] = l_entry<T>(wrow, t, ckind, cs0, cs1, cs2, cs3);
     }
     for (int e = tid; e < cnt * d; e += PANEL_THREADS) {
         int jl = e / d, r = e - jl * d;

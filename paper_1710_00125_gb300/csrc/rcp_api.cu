@@ -42,7 +42,7 @@ struct rcp_handle {
     std::vector<cudaEvent_t> pool;      // free events
     int launches[PH_COUNT] = {0};
     Buf status, state, bar, scal;                 // small persistent buffers
-    Buf om, B, Wbuf, Lp, lpos, moved, s1v, s2v, s1i, s2i, pay, tmpA, tmpL, tmpP;
+    Buf om, B, Wbuf, Lc, Lg, lpos, moved, s1v, s2v, s1i, s2i, pay, tmpA, tmpL, tmpP;
     Buf Y, flags, R, Dc, part;
     Buf A64, F, Bh, Xh, Dd, Ds, perm;              // rcp_sysv buffers
     Buf trace;                                     // per-step panel timestamps (profiling level 2)
@@ -158,7 +158,8 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->om, N * r.d * sizeof(T)));
     RCP_TRY(grow(h->B, N * r.d * sizeof(T)));
     RCP_TRY(grow(h->Wbuf, N * r.bw * sizeof(T)));
-    RCP_TRY(grow(h->Lp, N * r.bw * sizeof(T)));
+    RCP_TRY(grow(h->Lc, N * r.bw * sizeof(T)));
+    RCP_TRY(grow(h->Lg, N * r.bw * sizeof(T)));
     RCP_TRY(grow(h->lpos, N * sizeof(int)));
     RCP_TRY(grow(h->moved, 2 * N * sizeof(int)));
     RCP_TRY(grow(h->s1v, 4 * (size_t)r.grid * sizeof(double)));
@@ -180,7 +181,7 @@ FactorWork<T> make_work(rcp_handle *h, int n, T *A, int lda, double *Dd, double 
     w.n = n; w.lda = lda; w.A = A;
     w.d = r.d; w.B = (T *)h->B.p;
     w.bmax = r.b; w.bw = r.bw; w.alpha = r.alpha;
-    w.Wbuf = (T *)h->Wbuf.p; w.Lp = (T *)h->Lp.p;
+    w.Wbuf = (T *)h->Wbuf.p; w.Lc = (T *)h->Lc.p; w.Lg = (T *)h->Lg.p;
     w.Dd = Dd; w.Ds = Ds; w.perm = perm;
     w.lpos = (int *)h->lpos.p; w.moved = (int *)h->moved.p;
     w.st = (FactorState *)h->state.p;
@@ -334,7 +335,7 @@ rcp_status rcp_create(rcp_handle **h) {
 
 void rcp_destroy(rcp_handle *h) {
     if (!h) return;
-    Buf *all[] = {&h->tcops, &h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lp, &h->lpos, &h->moved,
+    Buf *all[] = {&h->tcops, &h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
                   &h->s1v, &h->s2v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
                   &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm};
     for (Buf *b : all)
