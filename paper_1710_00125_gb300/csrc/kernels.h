@@ -46,10 +46,12 @@ struct FactorWork {
     unsigned long long *trace;   // optional per-step timestamps (profiling), 10 per position
     unsigned long long *keys;    // ring of packed argmax keys (FP32 path), zeroed per factorization
     float *tcops;                // tensor-core operand tiles (TF32x3 trailing update)
+    int spec;                    // FP32 panel: speculative case-(1) path enabled (shadow sketch fits)
+    double *s3v;                 // [2][grid][4] records of the speculative candidates
 };
 
 template <typename T>
-size_t panel_smem_bytes(int d, int bw, int chunk_cap);
+size_t panel_smem_bytes(int d, int bw, int chunk_cap, int spec);
 
 template <typename T>
 cudaError_t launch_panel(const FactorWork<T> &w, cudaStream_t s);
@@ -70,7 +72,7 @@ template <typename T>
 cudaError_t launch_factor_finish(const FactorWork<T> &w, cudaStream_t s);
 
 template <typename T>
-int panel_max_grid(int d, int bw, int chunk_cap);
+int panel_max_grid(int d, int bw, int chunk_cap, int spec);
 
 // Solves and refinement.  `work` holds solve_work_bytes<T>(n, nrhs) bytes.
 template <typename T>

@@ -42,8 +42,9 @@ constexpr unsigned FULL = 0xffffffffu;
 __host__ __device__ constexpr int quad_stride(int x) { return x + ((36 - (x % 32)) % 32); }
 
 template <typename T>
-size_t panel_smem_bytes(int d, int bw, int chunk_cap) {
+size_t panel_smem_bytes(int d, int bw, int chunk_cap, int spec) {
     size_t s = 0;
+    if (spec) s += (size_t)chunk_cap * (quad_stride(d) + 1) * sizeof(T) + 16;   // shadow sketch + norms
     s += (size_t)chunk_cap * sizeof(double);           // nrm (T, padded to 8 bytes)
     s += (size_t)chunk_cap * quad_stride(d) * sizeof(T);    // Bs
     s += (size_t)chunk_cap * quad_stride(bw) * sizeof(T);   // Ws
@@ -159,13 +160,40 @@ __device__ __forceinline__ void red_max_u64(unsigned long long *p, unsigned long
     asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+// Keys are read right after the grid barrier, whose acquire already orders these loads after
+// every CTA's red.max; a relaxed load suffices and lets independent key loads overlap.
+__device__ __forceinline__ unsigned long long ld_key(const unsigned long long *p) {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
 constexpr int KEY_RING = 16;
+
+// Block-wide maximum of two packed keys per thread (the result to every thread).
+__device__ __forceinline__ void block_max2_u64(unsigned long long &a, unsigned long long &b, unsigned long long *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a = max(a, __shfl_xor_sync(FULL, a, off));
+        b = max(b, __shfl_xor_sync(FULL, b, off));
+    }
+    if (lane == 0) { red[warp] = a; red[PANEL_WARPS + warp] = b; }
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long x = lane < PANEL_WARPS ? red[lane] : 0ull, y = lane < PANEL_WARPS ? red[PANEL_WARPS + lane] : 0ull;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            x = max(x, __shfl_xor_sync(FULL, x, off));
+            y = max(y, __shfl_xor_sync(FULL, y, off));
+        }
+        if (lane == 0) { red[2 * PANEL_WARPS] = x; red[2 * PANEL_WARPS + 1] = y; }
+    }
+    __syncthreads();
+    a = red[2 * PANEL_WARPS];
+    b = red[2 * PANEL_WARPS + 1];
+    __syncthreads();
+}
 
 // The multiplier L(j, t) of a row from its W = L D row and the panel's per-column D scalars,
 // with the same operations the elimination used (so the result is bitwise the same): kind 0
@@ -194,14 +222,17 @@ __device__ __forceinline__ T l_entry(const T *wr, int t, const int *kind, const 
 template <typename T, typename Hook>
 __device__ void schur_column(const T *__restrict__ A, int lda, int j_lo, int cnt, int X, int i, int bw,
                              const T *Ws, const T *payg, T *bX, const T *lXg, T *lX, int d,
-                             const int *alive, T *c, const double *xsrc, double *xs, int nx, Hook hook) {
-    T a0 = T(0), a1 = T(0);
+                             const int *alive, T *c, const double *xsrc, double *xs, int nx, Hook hook,
+                             bool preloaded = false, T pa0 = T(0), T pa1 = T(0)) {
+    T a0 = pa0, a1 = pa1;
     const int r0 = threadIdx.x, r1 = threadIdx.x + PANEL_THREADS;
-    if (r0 < cnt && alive[r0]) a0 = a_sym(A, lda, j_lo + r0, X);
-    if (r1 < cnt && alive[r1]) a1 = a_sym(A, lda, j_lo + r1, X);
-    for (int r = threadIdx.x; r < d; r += PANEL_THREADS) bX[r] = ldcg(payg + r);
-    for (int t = threadIdx.x; t < i; t += PANEL_THREADS) lX[t] = ldcg(lXg + t);
-    if (threadIdx.x < nx) xs[threadIdx.x] = ldcg(xsrc + threadIdx.x);
+    if (!preloaded) {   // else the caller already has the column in (pa0, pa1) and bX, lX, xs filled
+        if (r0 < cnt && alive[r0]) a0 = a_sym(A, lda, j_lo + r0, X);
+        if (r1 < cnt && alive[r1]) a1 = a_sym(A, lda, j_lo + r1, X);
+        for (int r = threadIdx.x; r < d; r += PANEL_THREADS) bX[r] = ldcg(payg + r);
+        for (int t = threadIdx.x; t < i; t += PANEL_THREADS) lX[t] = ldcg(lXg + t);
+        if (threadIdx.x < nx) xs[threadIdx.x] = ldcg(xsrc + threadIdx.x);
+    }
     __syncthreads();
     if (threadIdx.x == 0) hook();
     // four threads per row, each summing every fourth term, combined by two shuffles
@@ -233,7 +264,7 @@ constexpr int CASE_PENDING = 4;   // lambda > 0 and |a_kk| < alpha lambda: case 
 // one reciprocal of the off-diagonal entry instead of two divisions.
 template <typename T>
 __device__ void sbkp_scalars(int kase, double akk, double lam, double ark, double arr, double alpha, int *s_i,
-                             double *s_d, T *s_t) {
+                             double *s_d, T *s_t, T rkk) {
     if (kase == CASE_PENDING) {
         if (!isfinite(ark) || !isfinite(arr)) kase = -1;
         else kase = fabs(arr) >= alpha * lam ? 2 : 3;
@@ -254,7 +285,7 @@ __device__ void sbkp_scalars(int kase, double akk, double lam, double ark, doubl
         s_t[3] = T(1); s_t[4] = T(1);
     }
     s_t[5] = (T)dpiv;
-    s_t[6] = (kase == 1 || kase == 2) ? (T)(1.0 / dpiv) : T(0);
+    s_t[6] = kase == 1 ? rkk : (kase == 2 ? (T)(1.0 / dpiv) : T(0));
     s_i[8] = dpiv != 0.0;
 }
 
@@ -266,6 +297,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     __shared__ int s_i[16];
     __shared__ double s_d[16];
     __shared__ T s_t[8];
+    __shared__ unsigned long long s_red2[2 * PANEL_WARPS + 2];
 
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ldcg(w.status) != 0) return;
@@ -293,7 +325,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
 
     const int ds = quad_stride(d), ws = quad_stride(bw);   // shared-memory row strides
     T *nrm = reinterpret_cast<T *>(smem);
-    T *Bs = reinterpret_cast<T *>(reinterpret_cast<double *>(smem) + cap);
+    T *Bs = reinterpret_cast<T *>(reinterpret_cast<double *>(smem) + cap);   // swapped with Bs2 on a committed speculation
     T *Ws = Bs + (size_t)cap * ds;
     T *dg = Ws + (size_t)cap * ws;
     T *c1 = dg + cap;
@@ -307,6 +339,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     int *alive = lp + cap;
     int *win = alive + cap;           // positions k0 .. k0 + bw + 2
     int *ckind = win + (bw + 3);      // per panel column: 0 zero, 1 scalar, 3/4 first/second of 2x2
+    // shadow sketch columns and norms for the speculative case-(1) update (when w.spec)
+    T *Bs2 = reinterpret_cast<T *>(ckind + bw);
+    T *nrm2 = Bs2 + (w.spec ? (size_t)cap * ds : 0);
     const int wsz = bw + 3;
 
     const T *__restrict__ A = w.A;
@@ -355,11 +390,21 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     T *pay1 = w.pay, *pay2 = w.pay + (size_t)G * ps;
     double *rec1 = w.s1v, *rec2 = w.s2v;   // per-CTA records (4 doubles each)
     unsigned long long *keys = w.keys;
+    // speculative case-(1) state (FP32 path with room for the shadow sketch)
+    unsigned long long *spec_keys = (KEYS && w.spec) ? w.keys + KEY_RING : nullptr;
+    T *spec_pay = w.pay + (size_t)2 * G * ps;                 // [2][G][d], by barrier parity
+    double *spec_rec = w.s3v;                                  // [2][G][4]
+    bool have_next = false;
+    int run1 = 2;   // consecutive case-(0)/(1) steps; speculate when >= 2
+    T preA0 = T(0), preA1 = T(0);   // next pivot's column of A, loaded during a commit
+    int spec_par = 0;
     __syncthreads();
 
     while (i < w.bmax && k < n) {
         PANEL_MARK(0);
         // ---------------- (1) sketch column-norm argmax ----------------
+        // (skipped when the previous step's speculation already found this step's pivot)
+        if (!have_next) {
         CandT<T> c{T(-1), INT_MAX, -1};
         for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
             if (alive[jl] && better(nrm[jl], lp[jl], c.v, c.lpos)) c = CandT<T>{nrm[jl], lp[jl], j_lo + jl};
@@ -385,8 +430,11 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         PANEL_MARK(2);
         if (KEYS) {
             if (tid == 0) {
-                const unsigned long long key = ld_acquire_u64(keys + (g1 % KEY_RING));
-                if (cta == 0) keys[(g1 + KEY_RING / 2) % KEY_RING] = 0ull;
+                const unsigned long long key = ld_key(keys + (g1 % KEY_RING));
+                if (cta == 0) {
+                    keys[(g1 + KEY_RING / 2) % KEY_RING] = 0ull;
+                    if (spec_keys) spec_keys[(g1 + KEY_RING / 2) % KEY_RING] = 0ull;
+                }
                 if (key != 0ull) {
                     s_i[1] = (int)(key & 0xFFFFull);
                     s_i[2] = 0xFFFF - (int)((key >> 16) & 0xFFFFull);
@@ -416,38 +464,97 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 minnorm2 = fmin(minnorm2, s_d[0]);
             }
         }
+        }   // !have_next (a committed speculation did this step's interchange bookkeeping)
         __syncthreads();
         const int P = s_i[1], gP = s_i[3];
         if (P < 0 || !isfinite(s_d[0])) { fail = ST_NONFINITE; break; }
+        // where P's sketch column and a_kk were published: by step (1), or by the speculation
+        const T *payP = have_next ? spec_pay + (size_t)(spec_par * G + gP) * ps : pay1 + (size_t)gP * ps;
+        const double *recP = have_next ? spec_rec + (size_t)(spec_par * G + gP) * 4 : rec1 + 4 * (size_t)gP;
 
         // ---------------- (2) column P of the Schur complement, lambda and r ----------------
         PANEL_MARK(3);
-        schur_column<T>(A, lda, j_lo, cnt, P, i, ws, Ws, pay1 + (size_t)gP * ps, bP, w.Lg + (size_t)P * bw, lP, d,
-                        alive, c1, rec1 + 4 * (size_t)gP, s_d + 8, KEYS ? 1 : 0, NoHook());
+        schur_column<T>(A, lda, j_lo, cnt, P, i, ws, Ws, payP, bP, w.Lg + (size_t)P * bw, lP, d,
+                        alive, c1, recP, s_d + 8, KEYS ? 1 : 0, [&]() {
+                            // reciprocal of a_kk, used by case (1) and by the speculation
+                            if (KEYS) s_t[7] = s_d[8] != 0.0 ? (T)(1.0 / s_d[8]) : T(0);
+                        }, have_next, preA0, preA1);
         const double akk = KEYS ? s_d[8] : s_d[1];
         if (!isfinite(akk)) { fail = ST_NONFINITE; break; }
         PANEL_MARK(4);
-        c = CandT<T>{T(-1), INT_MAX, -1};
-        for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
-            if (!alive[jl] || j_lo + jl == P) continue;
-            T v = fabs(c1[jl]);
-            if (better(v, lp[jl], c.v, c.lpos)) c = CandT<T>{v, lp[jl], j_lo + jl};
-        }
-        c = block_argmax(c, s_red);
-        if (c.phys >= 0) {
-            const int jc = c.phys - j_lo;
-            for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay2 + (size_t)cta * ps + r, Bs[(size_t)jc * ds + r]);
-        }
         const unsigned g2 = gbase + nbar + 1;
-        if (tid == 0) {
-            const double cv = c.phys >= 0 ? (double)c1[c.phys - j_lo] : 0.0;
-            const double dgc = c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0;
-            if (KEYS) {
-                if (c.phys >= 0) {
-                    stcg(reinterpret_cast<double2 *>(rec2 + 4 * (size_t)cta), make_double2(cv, dgc));
-                    red_max_u64(keys + (g2 % KEY_RING), make_key((float)c.v, c.lpos, c.phys));
+        // speculation (FP32): assume case (1) (multipliers c / a_kk), update the sketch into the
+        // shadow buffer and find the next step's pivot candidate before the barrier
+        const bool spec = KEYS && spec_keys && run1 >= 2 && i + 1 < w.bmax && k + 1 < n;
+        const int par = (int)(g2 & 1u);
+        if (KEYS) {
+            unsigned long long kl = 0ull, ks = 0ull;   // best lambda key, best speculative sketch key
+            if (spec) {
+                const T f = s_t[7];
+                const int sub = tid & 3;
+                for (int jl0 = 0; jl0 < cnt; jl0 += PANEL_THREADS / 4) {
+                    const int jl = jl0 + (tid >> 2);
+                    const bool live = jl < cnt && alive[jl] && j_lo + jl != P;
+                    T sacc = T(0);
+                    if (live) {
+                        const T l1 = c1[jl] * f;
+                        const T *col = Bs + (size_t)jl * ds;
+                        T *col2 = Bs2 + (size_t)jl * ds;
+                        for (int r = sub; r < d; r += 4) {
+                            T v = col[r] - bP[r] * l1;
+                            col2[r] = v;
+                            sacc = fma(v, v, sacc);
+                        }
+                    }
+                    sacc += __shfl_xor_sync(FULL, sacc, 1);
+                    sacc += __shfl_xor_sync(FULL, sacc, 2);
+                    if (live && sub == 0) {
+                        nrm2[jl] = sacc;
+                        kl = max(kl, make_key((float)fabs(c1[jl]), lp[jl], j_lo + jl));
+                        ks = max(ks, make_key((float)sacc, lp[jl], j_lo + jl));
+                    }
                 }
             } else {
+                for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
+                    if (alive[jl] && j_lo + jl != P) kl = max(kl, make_key((float)fabs(c1[jl]), lp[jl], j_lo + jl));
+            }
+            block_max2_u64(kl, ks, s_red2);
+            if (kl != 0ull) {
+                const int jc = (int)(kl & 0xFFFFull) - j_lo;
+                for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay2 + (size_t)cta * ps + r, Bs[(size_t)jc * ds + r]);
+                if (tid == 0) {
+                    stcg(reinterpret_cast<double2 *>(rec2 + 4 * (size_t)cta), make_double2((double)c1[jc], (double)dg[jc]));
+                    red_max_u64(keys + (g2 % KEY_RING), kl);
+                }
+            }
+            if (ks != 0ull) {
+                const int jc = (int)(ks & 0xFFFFull) - j_lo;
+                T *dst = spec_pay + (size_t)(par * G + cta) * ps;
+                for (int r = tid; r < d; r += PANEL_THREADS) stcg(dst + r, Bs2[(size_t)jc * ds + r]);
+                if (tid == 0) {
+                    const T cv = c1[jc], l1 = cv * s_t[7];
+                    const T dnew = fma(-cv, l1, dg[jc]);
+                    stcg(reinterpret_cast<double2 *>(spec_rec + (size_t)(par * G + cta) * 4),
+                         make_double2((double)dnew, (double)l1));
+                    red_max_u64(spec_keys + (g2 % KEY_RING), ks);
+                }
+            }
+        } else {
+            CandT<T> c{T(-1), INT_MAX, -1};
+            for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
+                if (!alive[jl] || j_lo + jl == P) continue;
+                T v = fabs(c1[jl]);
+                if (better(v, lp[jl], c.v, c.lpos)) c = CandT<T>{v, lp[jl], j_lo + jl};
+            }
+            c = block_argmax(c, s_red);
+            if (c.phys >= 0) {
+                const int jc = c.phys - j_lo;
+                for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay2 + (size_t)cta * ps + r, Bs[(size_t)jc * ds + r]);
+            }
+            if (tid == 0) {
+                s_i[9] = 0;
+                const double cv = c.phys >= 0 ? (double)c1[c.phys - j_lo] : 0.0;
+                const double dgc = c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0;
                 slot_write(rec2, cta, (double)c.v, cv, dgc, c.lpos, c.phys);
             }
         }
@@ -456,7 +563,8 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         PANEL_MARK(6);
         if (KEYS) {
             if (tid == 0) {
-                const unsigned long long key = ld_acquire_u64(keys + (g2 % KEY_RING));
+                const unsigned long long key = ld_key(keys + (g2 % KEY_RING));
+                const unsigned long long key3 = spec ? ld_key(spec_keys + (g2 % KEY_RING)) : 0ull;
                 if (cta == 0) keys[(g2 + KEY_RING / 2) % KEY_RING] = 0ull;
                 int R = -1, LR = -1;
                 double lam = 0.0;
@@ -473,7 +581,18 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 else if (fabs(akk) >= alpha * lam) kase = 1;
                 else kase = CASE_PENDING;
                 if (kase == CASE_PENDING) s_i[7] = CASE_PENDING;
-                else sbkp_scalars<T>(kase, akk, lam, 0.0, 0.0, alpha, s_i, s_d, s_t);
+                else sbkp_scalars<T>(kase, akk, lam, 0.0, 0.0, alpha, s_i, s_d, s_t, s_t[7]);
+                s_i[9] = 0;
+                if (spec_keys && cta == 0) spec_keys[(g2 + KEY_RING / 2) % KEY_RING] = 0ull;
+                if (spec) {
+                    if ((kase == 0 || kase == 1) && key3 != 0ull) {
+                        s_i[9] = 1;   // commit the speculation
+                        s_i[10] = (int)(key3 & 0xFFFFull);
+                        s_i[11] = 0xFFFF - (int)((key3 >> 16) & 0xFFFFull);
+                        s_i[12] = (s_i[10] - k0) / chunk;
+                        s_d[6] = (double)__uint_as_float((unsigned)(key3 >> 32));
+                    }
+                }
             }
         } else if (warp == 0) {
             SlotWin b = slot_reduce(rec2, G);
@@ -487,20 +606,90 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 else if (lam == 0.0) kase = 0;
                 else if (fabs(akk) >= alpha * lam) kase = 1;
                 else kase = fabs(arr) >= alpha * lam ? 2 : 3;
-                sbkp_scalars<T>(kase, akk, lam, ark, arr, alpha, s_i, s_d, s_t);
+                sbkp_scalars<T>(kase, akk, lam, ark, arr, alpha, s_i, s_d, s_t, akk != 0.0 ? (T)(1.0 / akk) : T(0));
             }
         }
         __syncthreads();
         const int R = s_i[4], LR = s_i[5], gR = s_i[6];
         int kase = s_i[7];
         if (kase < 0) { fail = ST_NONFINITE; break; }
+        if (s_i[9]) {
+            PANEL_MARK(7);
+            // case (0)/(1) confirmed: the speculative sketch update stands.  Issue the loads of
+            // the next step first (its pivot's column of A, sketch column, multipliers and a_kk,
+            // the last multiplier coming with the speculation record), then finish this step's
+            // elimination (W, L, diagonal) with the same multipliers while they are in flight.
+            const T f = s_t[7];
+            const int P2 = s_i[10], LP2 = s_i[11], gc2 = s_i[12];
+            {
+                const int r0 = tid, r1 = tid + PANEL_THREADS;
+                preA0 = (r0 < cnt && alive[r0] && j_lo + r0 != P) ? a_sym(A, lda, j_lo + r0, P2) : T(0);
+                preA1 = (r1 < cnt && alive[r1] && j_lo + r1 != P) ? a_sym(A, lda, j_lo + r1, P2) : T(0);
+            }
+            const T pb = tid < d ? ldcg(spec_pay + (size_t)(par * G + gc2) * ps + tid) : T(0);
+            const T pl = tid < i ? ldcg(w.Lg + (size_t)P2 * bw + tid) : T(0);
+            double2 prec = make_double2(0.0, 0.0);
+            if (tid == 0) prec = __ldcg(reinterpret_cast<const double2 *>(spec_rec + (size_t)(par * G + gc2) * 4));
+            for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
+                if (!alive[jl]) continue;
+                const int j = j_lo + jl;
+                T *wrow = Ws + (size_t)jl * ws;
+                T *lrow = w.Lg + (size_t)j * bw;
+                if (j == P) {
+                    wrow[i] = T(0);
+                    stcg(lrow + i, T(0));
+                    continue;
+                }
+                const T cv = c1[jl];
+                const T l1 = cv * f;
+                wrow[i] = cv;
+                dg[jl] = fma(-cv, l1, dg[jl]);
+                stcg(lrow + i, l1);
+                tmaxL = fmax(tmaxL, fabs(l1));
+            }
+            __syncthreads();
+            for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
+                if (j_lo + jl == P) alive[jl] = 0;
+            { T *t = Bs; Bs = Bs2; Bs2 = t; t = nrm; nrm = nrm2; nrm2 = t; }
+            if (tid == 0) {
+                ckind[i] = (kase == 0 || !s_i[8]) ? 0 : 1;
+                cs0[i] = s_t[6];
+                if (cta == 0) {
+                    w.Dd[k] = akk; w.Ds[k] = 0.0;
+                    maxD = fmax(maxD, fabs(akk));
+                    if (!s_i[8] && info == 0) info = k + 1;
+                    minnorm2 = fmin(minnorm2, s_d[6]);
+                }
+                // the next step: pivot P2 to position k + 1
+                const int kn = k + 1;
+                const int Q = win[kn - k0];
+                if (LP2 - k0 < wsz) win[LP2 - k0] = Q;
+                win[kn - k0] = P2;
+                if (P2 >= j_lo && P2 < j_lo + cnt) lp[P2 - j_lo] = kn;
+                if (Q != P2 && Q >= j_lo && Q < j_lo + cnt) lp[Q - j_lo] = LP2;
+                s_i[1] = P2; s_i[2] = LP2; s_i[3] = gc2;
+                s_d[0] = s_d[6];
+                s_d[8] = prec.x;            // a_kk of P2 after this step
+                lP[i] = (T)prec.y;          // L(P2, k)
+            }
+            if (tid < d) bP[tid] = pb;
+            if (tid < i) lP[tid] = pl;
+            have_next = true;
+            ++run1;
+            k += 1;
+            i += 1;
+            __syncthreads();
+            continue;
+        }
+        have_next = false;
+        run1 = kase <= 1 ? run1 + 1 : 0;
         PANEL_MARK(7);
         if (kase >= 2) {
             // column r of the Schur complement; in FP32 its record (a_rk, a_rr) arrives with the
             // column loads and thread 0 settles case 2 versus 3 right after them
             const double lam = s_d[2];
             auto hook = [&]() {
-                if (KEYS) sbkp_scalars<T>(CASE_PENDING, akk, lam, s_d[10], s_d[11], alpha, s_i, s_d, s_t);
+                if (KEYS) sbkp_scalars<T>(CASE_PENDING, akk, lam, s_d[10], s_d[11], alpha, s_i, s_d, s_t, s_t[7]);
             };
             schur_column<T>(A, lda, j_lo, cnt, R, i, ws, Ws, pay2 + (size_t)gR * ps, bR, w.Lg + (size_t)R * bw, lR, d,
                             alive, c2, rec2 + 4 * (size_t)gR, s_d + 10, KEYS ? 2 : 0, hook);
@@ -697,7 +886,7 @@ static size_t panel_dyn_limit() {
 
 template <typename T>
 cudaError_t launch_panel(const FactorWork<T> &w, cudaStream_t s) {
-    size_t smem = panel_smem_bytes<T>(w.d, w.bw, w.chunk_cap);
+    size_t smem = panel_smem_bytes<T>(w.d, w.bw, w.chunk_cap, w.spec);
     if (smem > panel_dyn_limit<T>()) return cudaErrorInvalidValue;
     FactorWork<T> arg = w;
     void *args[] = {&arg};
@@ -707,21 +896,21 @@ cudaError_t launch_panel(const FactorWork<T> &w, cudaStream_t s) {
 
 // Largest cooperative grid for the given per-CTA workspace (0 if it does not fit).
 template <typename T>
-int panel_max_grid(int d, int bw, int chunk_cap) {
+int panel_max_grid(int d, int bw, int chunk_cap, int spec) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    size_t smem = panel_smem_bytes<T>(d, bw, chunk_cap);
+    size_t smem = panel_smem_bytes<T>(d, bw, chunk_cap, spec);
     if (smem > panel_dyn_limit<T>()) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_kernel<T>, PANEL_THREADS, smem) != cudaSuccess) return 0;
     return per * sms;
 }
 
-template size_t panel_smem_bytes<double>(int, int, int);
-template size_t panel_smem_bytes<float>(int, int, int);
+template size_t panel_smem_bytes<double>(int, int, int, int);
+template size_t panel_smem_bytes<float>(int, int, int, int);
 template cudaError_t launch_panel<double>(const FactorWork<double> &, cudaStream_t);
 template cudaError_t launch_panel<float>(const FactorWork<float> &, cudaStream_t);
-template int panel_max_grid<double>(int, int, int);
-template int panel_max_grid<float>(int, int, int);
+template int panel_max_grid<double>(int, int, int, int);
+template int panel_max_grid<float>(int, int, int, int);
 
 }  // namespace rcpk

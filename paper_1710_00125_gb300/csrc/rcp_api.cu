@@ -42,7 +42,7 @@ struct rcp_handle {
     std::vector<cudaEvent_t> pool;      // free events
     int launches[PH_COUNT] = {0};
     Buf status, state, bar, scal;                 // small persistent buffers
-    Buf om, B, Wbuf, Lc, Lg, lpos, moved, s1v, s2v, s1i, s2i, pay, tmpA, tmpL, tmpP;
+    Buf om, B, Wbuf, Lc, Lg, lpos, moved, s1v, s2v, s3v, s1i, s2i, pay, tmpA, tmpL, tmpP;
     Buf Y, flags, R, Dc, part;
     Buf A64, F, Bh, Xh, Dd, Ds, perm;              // rcp_sysv buffers
     Buf trace;                                     // per-step panel timestamps (profiling level 2)
@@ -105,7 +105,7 @@ rcp_status ensure_small(rcp_handle *h) {
 }
 
 struct Resolved {
-    int b, d, grid, chunk_cap, bw, maxmoved;
+    int b, d, grid, chunk_cap, bw, maxmoved, spec;
     double alpha;
     rcp_prec prec;
     uint64_t seed;
@@ -141,11 +141,16 @@ rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
     if (n > 0) g = std::min(g, n);
     g = std::max(1, g);
     r.chunk_cap = (n + g - 1) / g;
-    size_t smem = f64 ? panel_smem_bytes<double>(r.d, r.bw, r.chunk_cap) : panel_smem_bytes<float>(r.d, r.bw, r.chunk_cap);
-    (void)smem;
     if (r.chunk_cap > 1024) return RCP_EUNSUPPORTED;
-    if (f64) maxg = panel_max_grid<double>(r.d, r.bw, r.chunk_cap);
-    else maxg = panel_max_grid<float>(r.d, r.bw, r.chunk_cap);
+    // the FP32 panel speculates on SBKP case (1) when the shadow sketch fits in shared memory
+    r.spec = 0;
+    if (f64) {
+        maxg = panel_max_grid<double>(r.d, r.bw, r.chunk_cap, 0);
+    } else {
+        maxg = panel_max_grid<float>(r.d, r.bw, r.chunk_cap, 1);
+        if (maxg >= g) r.spec = 1;
+        else maxg = panel_max_grid<float>(r.d, r.bw, r.chunk_cap, 0);
+    }
     if (maxg <= 0 || g > maxg) return RCP_EUNSUPPORTED;
     r.grid = g;
     return RCP_OK;
@@ -164,11 +169,12 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->moved, 2 * N * sizeof(int)));
     RCP_TRY(grow(h->s1v, 4 * (size_t)r.grid * sizeof(double)));
     RCP_TRY(grow(h->s2v, 4 * (size_t)r.grid * sizeof(double)));
-    RCP_TRY(grow(h->keys, 16 * sizeof(unsigned long long)));
+    RCP_TRY(grow(h->keys, 32 * sizeof(unsigned long long)));
     if (r.prec == RCP_TF32X3) RCP_TRY(grow(h->tcops, tc_ops_floats(n, r.b) * sizeof(float)));
     RCP_TRY(grow(h->s1i, 2 * (size_t)r.grid * sizeof(int)));
     RCP_TRY(grow(h->s2i, 2 * (size_t)r.grid * sizeof(int)));
-    RCP_TRY(grow(h->pay, 2 * (size_t)r.grid * r.d * sizeof(T)));
+    RCP_TRY(grow(h->pay, 4 * (size_t)r.grid * r.d * sizeof(T)));
+    RCP_TRY(grow(h->s3v, 8 * (size_t)r.grid * sizeof(double)));
     RCP_TRY(grow(h->tmpA, (size_t)r.maxmoved * N * sizeof(T)));
     RCP_TRY(grow(h->tmpL, (size_t)r.maxmoved * N * sizeof(T)));
     RCP_TRY(grow(h->tmpP, (size_t)r.maxmoved * sizeof(int)));
@@ -194,6 +200,8 @@ FactorWork<T> make_work(rcp_handle *h, int n, T *A, int lda, double *Dd, double 
     w.tmpA = (T *)h->tmpA.p; w.tmpL = (T *)h->tmpL.p; w.tmpP = (int *)h->tmpP.p;
     w.maxmoved = r.maxmoved;
     w.keys = (unsigned long long *)h->keys.p;
+    w.spec = r.spec;
+    w.s3v = (double *)h->s3v.p;
     w.tcops = r.prec == RCP_TF32X3 ? (float *)h->tcops.p : nullptr;
     w.trace = nullptr;
     if (h->profiling >= 2 && grow(h->trace, (size_t)n * 10 * sizeof(unsigned long long)) == RCP_OK) {
@@ -257,7 +265,7 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
     FactorWork<T> w = make_work<T>(h, n, A, lda, Dd, Ds, perm, r);
     CU_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
     CU_TRY(cudaMemsetAsync(h->bar.p, 0, sizeof(unsigned), s));
-    CU_TRY(cudaMemsetAsync(h->keys.p, 0, 16 * sizeof(unsigned long long), s));
+    CU_TRY(cudaMemsetAsync(h->keys.p, 0, 32 * sizeof(unsigned long long), s));
     CU_TRY(launch_factor_init<T>(w, s));
     const T *om = (const T *)r.omega;
     {
@@ -336,7 +344,7 @@ rcp_status rcp_create(rcp_handle **h) {
 void rcp_destroy(rcp_handle *h) {
     if (!h) return;
     Buf *all[] = {&h->tcops, &h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
-                  &h->s1v, &h->s2v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
+                  &h->s1v, &h->s2v, &h->s3v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
                   &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm};
     for (Buf *b : all)
         if (b->p) cudaFree(b->p);
