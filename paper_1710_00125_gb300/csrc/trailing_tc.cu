@@ -177,14 +177,36 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(FactorWork<float> w, float
 }
 
 // ------------------------------------------------------------------------------------------
-// tcgen05 MMA kernel.
+// tcgen05 MMA kernel, warp-specialized.  Warp 0 (one elected thread) streams operand chunks
+// through the stage ring and issues the MMAs of each tile into one of two 128-column TMEM
+// accumulators; warps 1..4 drain the other accumulator (tcgen05.ld, lane quarter w % 4) and
+// update A, so the epilogue of tile t overlaps the MMAs of tile t + 1.
+//   full[s]  : operands of the chunk in stage s arrived (bulk-copy transaction count)
+//   free[s]  : the MMAs reading stage s completed (tcgen05.commit)
+//   accf[a]  : accumulator a holds a finished tile (tcgen05.commit)
+//   acce[a]  : the epilogue has read accumulator a (one arrival per epilogue warp)
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(tc::THREADS, 1) tc_trailing_kernel(FactorWork<float> w, const float *ops, int nrb_cap,
-                                                                     int nkc_cap) {
+constexpr int TC_THREADS = 160;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tile_ij(long long tile, int *I, int *J) {
+    int a = (int)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+    while ((long long)a * (a + 1) / 2 > tile) --a;
+    while ((long long)(a + 1) * (a + 2) / 2 <= tile) ++a;
+    *I = a;
+    *J = (int)(tile - (long long)a * (a + 1) / 2);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<float> w, const float *ops, int nrb_cap,
+                                                                    int nkc_cap) {
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[tc::STAGES];
     __shared__ __align__(8) uint64_t free_bar[tc::STAGES];
-    __shared__ __align__(8) uint64_t acc_bar;
+    __shared__ __align__(8) uint64_t accf[2];
+    __shared__ __align__(8) uint64_t acce[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
 
@@ -197,21 +219,21 @@ __global__ void __launch_bounds__(tc::THREADS, 1) tc_trailing_kernel(FactorWork<
     if (nrb > nrb_cap || nkc > nkc_cap) return;   // prep has flagged it
     const long long total = (long long)nrb * (nrb + 1) / 2;
     if ((long long)blockIdx.x >= total) return;
+    const int ntiles = (int)((total - blockIdx.x + gridDim.x - 1) / gridDim.x);   // tiles of this CTA
 
-    // 1024-byte aligned stage ring
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
     float *stage0 = reinterpret_cast<float *>(base);
 
     if (tid == 0) {
         for (int s = 0; s < tc::STAGES; ++s) { tc::mbar_init(&full_bar[s], 1); tc::mbar_init(&free_bar[s], 1); }
-        tc::mbar_init(&acc_bar, 1);
+        for (int a = 0; a < 2; ++a) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], 4); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
     if (warp == 0) {
-        // 128 columns of tensor memory for the FP32 128 x 128 accumulator
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" :: "r"(tc::smem_u32(&s_tmem))
+        // 256 columns: two FP32 128 x 128 accumulators
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" :: "r"(tc::smem_u32(&s_tmem))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -223,46 +245,54 @@ __global__ void __launch_bounds__(tc::THREADS, 1) tc_trailing_kernel(FactorWork<
     const size_t per = (size_t)nrb_cap * nkc_cap * tc::TILE_FLOATS;
     const float *whi = ops, *wlo = ops + per, *lhi = ops + 2 * per, *llo = ops + 3 * per;
 
-    // producer/consumer state (thread 0 only)
-    uint32_t full_phase[tc::STAGES] = {0, 0, 0}, free_phase[tc::STAGES] = {0, 0, 0};
-    int issued_free[tc::STAGES] = {0, 0, 0};   // stage has an outstanding MMA commit
-    int pending_full[tc::STAGES] = {0, 0, 0};  // stage has copies not yet waited for
-    uint32_t acc_phase = 0;
-    float *__restrict__ A = w.A;
-
-    for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        int I = (int)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
-        while ((long long)I * (I + 1) / 2 > tile) --I;
-        while ((long long)(I + 1) * (I + 2) / 2 <= tile) ++I;
-        const int J = (int)(tile - (long long)I * (I + 1) / 2);
-
-        if (tid == 0 && !s_abort) {
-            // prologue: fill up to STAGES chunks, then MMA chunk by chunk, refilling
-            int next = 0;
-            auto issue = [&](int c) -> bool {
-                const int s = c % tc::STAGES;
-                if (issued_free[s]) {
-                    if (!tc::mbar_wait(&free_bar[s], free_phase[s])) return false;
-                    free_phase[s] ^= 1u;
-                    issued_free[s] = 0;
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer + MMA issuer ----------------
+            uint32_t full_ph[tc::STAGES] = {0, 0, 0}, free_ph[tc::STAGES] = {0, 0, 0};
+            int used[tc::STAGES] = {0, 0, 0};        // stage has a commit not yet waited for
+            int loaded[tc::STAGES] = {0, 0, 0};      // stage has copies not yet waited for
+            uint32_t acce_ph[2] = {0, 0};
+            const int nchunks = ntiles * nkc;          // every chunk of every tile, in order
+            bool ok = true;
+            auto chunk_src = [&](int g, size_t *ti, size_t *tj) {
+                const int lt = g / nkc, c = g % nkc;
+                int I, J;
+                tile_ij(blockIdx.x + (long long)lt * gridDim.x, &I, &J);
+                *ti = ((size_t)I * nkc + c) * tc::TILE_FLOATS;
+                *tj = ((size_t)J * nkc + c) * tc::TILE_FLOATS;
+            };
+            auto load = [&](int g) -> bool {
+                const int s = g % tc::STAGES;
+                if (used[s]) {
+                    if (!tc::mbar_wait(&free_bar[s], free_ph[s])) return false;
+                    free_ph[s] ^= 1u;
+                    used[s] = 0;
                 }
+                size_t ti, tj;
+                chunk_src(g, &ti, &tj);
                 float *dst = stage0 + (size_t)s * (tc::STAGE_BYTES / 4);
                 tc::mbar_expect_tx(&full_bar[s], tc::STAGE_BYTES);
-                const size_t ti = ((size_t)I * nkc + c) * tc::TILE_FLOATS, tj = ((size_t)J * nkc + c) * tc::TILE_FLOATS;
                 tc::bulk_g2s(dst, whi + ti, tc::TILE_FLOATS * 4, &full_bar[s]);
                 tc::bulk_g2s(dst + tc::TILE_FLOATS, wlo + ti, tc::TILE_FLOATS * 4, &full_bar[s]);
                 tc::bulk_g2s(dst + 2 * tc::TILE_FLOATS, lhi + tj, tc::TILE_FLOATS * 4, &full_bar[s]);
                 tc::bulk_g2s(dst + 3 * tc::TILE_FLOATS, llo + tj, tc::TILE_FLOATS * 4, &full_bar[s]);
-                pending_full[s] = 1;
+                loaded[s] = 1;
                 return true;
             };
-            bool ok = true;
-            for (; next < nkc && next < tc::STAGES && ok; ++next) ok = issue(next);
-            for (int c = 0; c < nkc && ok; ++c) {
-                const int s = c % tc::STAGES;
-                if (!tc::mbar_wait(&full_bar[s], full_phase[s])) { ok = false; break; }
-                full_phase[s] ^= 1u;
-                pending_full[s] = 0;
+            for (int g = 0; g < nchunks && g < tc::STAGES && ok; ++g) ok = load(g);
+            for (int g = 0; g < nchunks && ok; ++g) {
+                const int lt = g / nkc, c = g % nkc, a = lt & 1;
+                const uint32_t dacc = tmem + (uint32_t)(a * tc::TM);
+                if (c == 0 && lt >= 2) {
+                    // accumulator a is free once the epilogue has read tile lt - 2
+                    if (!tc::mbar_wait(&acce[a], acce_ph[a])) { ok = false; break; }
+                    acce_ph[a] ^= 1u;
+                    tc::tc_fence_after();
+                }
+                const int s = g % tc::STAGES;
+                if (!tc::mbar_wait(&full_bar[s], full_ph[s])) { ok = false; break; }
+                full_ph[s] ^= 1u;
+                loaded[s] = 0;
                 tc::tc_fence_after();
                 const float *st = stage0 + (size_t)s * (tc::STAGE_BYTES / 4);
                 const uint32_t a_hi = tc::smem_u32(st), a_lo = tc::smem_u32(st + tc::TILE_FLOATS);
@@ -270,68 +300,72 @@ __global__ void __launch_bounds__(tc::THREADS, 1) tc_trailing_kernel(FactorWork<
 #pragma unroll
                 for (int kk = 0; kk < tc::KC / 8; ++kk) {
                     const uint32_t off = kk * 32;   // 8 tf32 = 32 bytes along the swizzled row
-                    const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-                    tc::mma_tf32(tmem, tc::sdesc_k128(a_hi + off), tc::sdesc_k128(b_hi + off), acc);
-                    tc::mma_tf32(tmem, tc::sdesc_k128(a_hi + off), tc::sdesc_k128(b_lo + off), 1u);
-                    tc::mma_tf32(tmem, tc::sdesc_k128(a_lo + off), tc::sdesc_k128(b_hi + off), 1u);
+                    tc::mma_tf32(dacc, tc::sdesc_k128(a_hi + off), tc::sdesc_k128(b_hi + off), (c > 0 || kk > 0) ? 1u : 0u);
+                    tc::mma_tf32(dacc, tc::sdesc_k128(a_hi + off), tc::sdesc_k128(b_lo + off), 1u);
+                    tc::mma_tf32(dacc, tc::sdesc_k128(a_lo + off), tc::sdesc_k128(b_hi + off), 1u);
                 }
                 tc::mma_commit(&free_bar[s]);
-                issued_free[s] = 1;
-                if (next < nkc) { ok = issue(next); ++next; }
+                used[s] = 1;
+                if (c == nkc - 1) tc::mma_commit(&accf[a]);
+                // refill the stage of the previous chunk (its MMAs were queued before these)
+                if (g >= 1 && g - 1 + tc::STAGES < nchunks) ok = load(g - 1 + tc::STAGES);
             }
-            if (ok) tc::mma_commit(&acc_bar);
             if (!ok) {
                 s_abort = 1;
                 atomicOr(w.status, ST_TIMEOUT);
             }
-        }
-        __syncthreads();
-        if (s_abort) break;
-        // epilogue: wait for the accumulator, then C -= acc on the lower triangle
-        if (!tc::mbar_wait(&acc_bar, acc_phase)) {
-            atomicOr(w.status, ST_TIMEOUT);
-            s_abort = 1;
-        }
-        acc_phase ^= 1u;
-        __syncthreads();
-        if (s_abort) break;
-        tc::tc_fence_after();
-        const int p = kend + I * tc::TM + warp * 32 + lane;
-        const int q0 = kend + J * tc::TM;
-        for (int c0 = 0; c0 < tc::TM; c0 += 16) {
-            uint32_t r[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            tc::tmem_wait_ld();
-            if (p < n) {
-                float cv[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int q = q0 + c0 + j;
-                    cv[j] = (q < n && p >= q) ? A[(size_t)p + (size_t)q * lda] : 0.f;
-                }
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int q = q0 + c0 + j;
-                    if (q < n && p >= q) A[(size_t)p + (size_t)q * lda] = cv[j] - __uint_as_float(r[j]);
-                }
+            // drain the ring before the CTA can leave
+            for (int s = 0; s < tc::STAGES; ++s) {
+                if (loaded[s]) tc::mbar_wait(&full_bar[s], full_ph[s]);
+                if (used[s]) tc::mbar_wait(&free_bar[s], free_ph[s]);
             }
         }
-        tc::tc_fence_before();
-        __syncthreads();
-    }
-    // drain: every issued copy and MMA must finish before the CTA (and its shared memory and
-    // tensor memory) goes away
-    if (tid == 0) {
-        for (int s = 0; s < tc::STAGES; ++s) {
-            if (pending_full[s]) tc::mbar_wait(&full_bar[s], full_phase[s]);
-            if (issued_free[s]) tc::mbar_wait(&free_bar[s], free_phase[s]);
+    } else {
+        // ---------------- epilogue warps: lane quarter q of the accumulator ----------------
+        const int q = warp & 3;
+        uint32_t accf_ph[2] = {0, 0};
+        float *__restrict__ A = w.A;
+        for (int lt = 0; lt < ntiles; ++lt) {
+            const int a = lt & 1;
+            bool ok = tc::mbar_wait(&accf[a], accf_ph[a]);
+            accf_ph[a] ^= 1u;
+            if (!ok || *(volatile int *)&s_abort) {
+                if (!ok) atomicOr(w.status, ST_TIMEOUT);
+                break;
+            }
+            tc::tc_fence_after();
+            int I, J;
+            tile_ij(blockIdx.x + (long long)lt * gridDim.x, &I, &J);
+            const int p = kend + I * tc::TM + q * 32 + lane;
+            const int q0 = kend + J * tc::TM;
+            for (int c0 = 0; c0 < tc::TM; c0 += 16) {
+                uint32_t r[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * tc::TM + c0), r);
+                tc::tmem_wait_ld();
+                if (p < n) {
+                    float cv[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int qq = q0 + c0 + j;
+                        cv[j] = (qq < n && p >= qq) ? A[(size_t)p + (size_t)qq * lda] : 0.f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int qq = q0 + c0 + j;
+                        if (qq < n && p >= qq) A[(size_t)p + (size_t)qq * lda] = cv[j] - __uint_as_float(r[j]);
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[a]);
         }
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" :: "r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
 }
 
 size_t tc_ops_floats(int n, int bmax) {
@@ -362,7 +396,7 @@ cudaError_t launch_trailing_tc(const FactorWork<float> &w, float *ops, int kmin,
     count_launches(1);
     const long long tiles = nrb * (nrb + 1) / 2;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    tc_trailing_kernel<<<grid > 0 ? grid : 1, tc::THREADS, smem, s>>>(w, ops, nrb_cap, nkc_cap);
+    tc_trailing_kernel<<<grid > 0 ? grid : 1, TC_THREADS, smem, s>>>(w, ops, nrb_cap, nkc_cap);
     count_launches(1);
     return cudaGetLastError();
 }
