@@ -184,6 +184,60 @@ long long rcp_kernel_launches(void);
 rcp_status rcp_profile_read(rcp_handle *h, double *ms, int *launches, int nphase);
 
 /*
+ * Batched ragged systems: many independent symmetric systems A_i x_i = b_i of small order
+ * (n_i <= nmax, typically 32..512), each factored by Algorithm 1 (q = 1) exactly as rcp_factor
+ * does, and solved or refined exactly as rcp_solve / rcp_refine do.  One persistent kernel per
+ * phase covers the whole batch: one CTA works on one system at a time, taking systems from an
+ * atomic ticket in decreasing order of n_i; the sketch and the current panel of a system live
+ * in that CTA's shared memory, A_i in global memory.  No call allocates memory once the handle's
+ * batch workspace (order array, ticket, Omega: about 4 * batch + 8 * d * nmax bytes) is large
+ * enough, so after one warm-up call with the same batch and nmax the calls can be captured
+ * into a CUDA graph.
+ *
+ * Pointer arrays ("device array of device pointers") hold one pointer per system; every other
+ * per-system array is a device array of length batch.  nmax (host) bounds every n_i; systems
+ * with n_i outside [0, nmax] are not processed correctly and must not be passed.
+ *
+ * rcp_factor_batched -- P_i^T A_i P_i = L_i D_i L_i^T for every system.
+ *   A[i]    device, n_i x n_i, ld lda[i], lower triangle; overwritten by L_i (strictly lower,
+ *           unit diagonal implicit) with D_i(j, j) on the diagonal.  Element type: double for
+ *           RCP_FP64, float for every other opts->prec (the batched factor runs on CUDA cores;
+ *           RCP_TF32X3 and RCP_TF32 run as RCP_FP32 here).
+ *   A64     optional (NULL allowed) device array of pointers to FP64 originals (ld lda64[i]):
+ *           their lower triangles are first copied (rounded) into A[i] by the same kernel.
+ *   Dd, Ds, perm: per-system outputs with the meaning they have for rcp_factor.
+ *   opts    b (default 32), d (default b + 8, at most 128), seed, alpha, omega as for
+ *           rcp_factor; one Omega (d x nmax) serves every system, system i using its first
+ *           n_i columns (the same columns a d x n_i draw with that seed gives).  q_mode 1 only.
+ *   info    device [batch]: 0, or 1 + position of the first exactly-zero 1x1 pivot, or -4
+ *           (RCP_ENONFINITE) when the system met a NaN or Inf (its factor is then incomplete).
+ *   Returns RCP_EUNSUPPORTED when the shared-memory state of one system, (d + 2 (b + 1) + 2)
+ *   * nmax + 2 d elements (4 or 8 bytes), does not fit one CTA (nmax = 512 at the defaults
+ *   in FP32, 256 in FP64).  Asynchronous.
+ *
+ * rcp_refine_batched -- x_i = solve(b_i), then, when A64 != NULL, FP64 iterative refinement
+ *   (r = b - A x in FP64, berr as rcp_refine, x += solve(r)) until berr_i <= tol or max_iter
+ *   corrections.  Right-hand sides are processed 16 at a time; each group iterates on its own
+ *   and iters[i] is the largest count of a group.
+ *   LA/ldla: factors from rcp_factor_batched (prec RCP_FP64: double, else float).
+ *   Bv/ldb:  right-hand sides (n_i x nrhs, FP64); X/ldx: solutions (n_i x nrhs, FP64); X must
+ *            not overlap Bv.
+ *   berr, iters: device [batch] or NULL; berr is 0 when A64 is NULL.
+ *   The convergence test is per system; systems that miss the tolerance are not an error of
+ *   the call: compare berr with tol.  Asynchronous.
+ */
+rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, const double *const *A64,
+                              const int *lda64, void *const *A, const int *lda, double *const *Dd,
+                              double *const *Ds, int *const *perm, const rcp_opts *opts, int *info,
+                              rcp_stream_t stream);
+rcp_status rcp_refine_batched(rcp_handle *h, int batch, int nmax, int nrhs, const int *n,
+                              const double *const *A64, const int *lda64, const void *const *LA,
+                              const int *ldla, const double *const *Dd, const double *const *Ds,
+                              const int *const *perm, rcp_prec prec, const double *const *Bv, const int *ldb,
+                              double *const *X, const int *ldx, double tol, int max_iter, double *berr,
+                              int *iters, rcp_stream_t stream);
+
+/*
  * Building blocks exposed for testing.
  * rcp_omega:  Omega (d x n, ld d, FP64, device) from Philox4x64-10: entries (2t, 2t+1) of
  *             column j come from counter (j, t, 0, 0) and key (seed, 0) through Box-Muller

@@ -94,4 +94,27 @@ cudaError_t launch_axpy_update(int n, int nrhs, double *X, int ldx, const double
 cudaError_t launch_copy_lower_f64(int n, const double *src, int lds, void *dst, int ldd, int to_f32,
                                   cudaStream_t s);
 
+// Batched small systems (one CTA per system at a time).  info of a system that met a NaN or
+// Inf is BT_INFO_NONFINITE.
+constexpr int BT_INFO_NONFINITE = -4;
+size_t batched_max_smem();
+template <typename T>
+size_t batched_factor_smem(int d, int b, int nmax);
+template <typename TL>
+size_t batched_refine_smem(int nrhs, int nmax);
+cudaError_t launch_batched_order(int batch, int nmax, const int *n, int *order, cudaStream_t s);
+template <typename T>
+cudaError_t launch_batched_factor(int batch, int d, int b, int nmax, const int *n, const double *const *A64,
+                                  const int *lda64, T *const *A, const int *lda, double *const *Dd, double *const *Ds,
+                                  int *const *perm, const T *om, double alpha, int *info, const int *order,
+                                  int *ticket, cudaStream_t s);
+template <typename TL>
+cudaError_t launch_batched_refine(int batch, int nrhs, int nmax, int max_iter, double tol, const int *n,
+                                  const TL *const *LA, const int *ldla, const double *const *Dd,
+                                  const double *const *Ds, const int *const *perm, const double *const *A64,
+                                  const int *lda64, const double *const *Bv, const int *ldb, double *const *X,
+                                  const int *ldx, double *berr, int *iters, const int *order, int *ticket,
+                                  cudaStream_t s);
+
 }  // namespace rcpk
+

@@ -49,6 +49,11 @@ struct rcp_handle {
     Buf keys;                                      // packed argmax keys of the FP32 panel
     Buf tcops;                                     // tensor-core operand tiles
     int trace_n = 0;
+    Buf bord, bom, bticket;                        // batched path: order, Omega, ticket
+    const int *bord_n = nullptr;                   // (n, batch, nmax) the order was made for
+    int bord_batch = -1, bord_nmax = -1;
+    uint64_t bom_seed = 0;                         // (seed, d, nmax, fp64) of the drawn Omega
+    int bom_d = -1, bom_nmax = -1, bom_f64 = -1;
 };
 
 namespace {
@@ -343,7 +348,7 @@ rcp_status rcp_create(rcp_handle **h) {
 
 void rcp_destroy(rcp_handle *h) {
     if (!h) return;
-    Buf *all[] = {&h->tcops, &h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
+    Buf *all[] = {&h->bord, &h->bom, &h->bticket, &h->tcops, &h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
                   &h->s1v, &h->s2v, &h->s3v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
                   &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm};
     for (Buf *b : all)
@@ -529,6 +534,94 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
     if (e != RCP_OK) return e;
     if (st.info > 0) return (rcp_status)st.info;
     if (max_iter > 0 && !(host.berr <= tol)) return RCP_ENOCONV;
+    return RCP_OK;
+}
+
+// ---- batched ragged systems ----
+
+static rcp_status batched_order(rcp_handle *h, int batch, int nmax, const int *n, cudaStream_t s) {
+    RCP_TRY(grow(h->bord, (size_t)batch * sizeof(int)));
+    RCP_TRY(grow(h->bticket, 64));
+    if (h->bord_n == n && h->bord_batch == batch && h->bord_nmax == nmax) return RCP_OK;
+    // any permutation of the systems gives the same results; this one is for load balance
+    CU_TRY(launch_batched_order(batch, nmax, n, (int *)h->bord.p, s));
+    h->bord_n = n;
+    h->bord_batch = batch;
+    h->bord_nmax = nmax;
+    return RCP_OK;
+}
+
+rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, const double *const *A64,
+                              const int *lda64, void *const *A, const int *lda, double *const *Dd,
+                              double *const *Ds, int *const *perm, const rcp_opts *opts, int *info,
+                              rcp_stream_t stream) {
+    if (!h || batch < 0 || nmax < 0 || nmax > 65535) return RCP_EINVAL;
+    if (batch == 0 || nmax == 0) return RCP_OK;
+    if (!n || !A || !lda || !Dd || !Ds || !perm || !info || (A64 && !lda64)) return RCP_EINVAL;
+    const rcp_prec prec = opts ? opts->prec : RCP_FP64;
+    if (!valid_prec(prec)) return RCP_EINVAL;
+    const bool f64 = prec == RCP_FP64;
+    const int b = (opts && opts->b > 0) ? opts->b : 32;
+    const int d = (opts && opts->d > 0) ? opts->d : std::min(b + 8, 128);
+    if (opts && opts->q_mode != 0 && opts->q_mode != 1) return RCP_EUNSUPPORTED;
+    if (b > 512 || d > 128) return RCP_EUNSUPPORTED;
+    const double alpha = (opts && opts->alpha > 0.0) ? opts->alpha : std::sqrt(2.0) / 2.0;
+    if (!(alpha < 1.0)) return RCP_EINVAL;
+    const size_t smem = f64 ? batched_factor_smem<double>(d, b, nmax) : batched_factor_smem<float>(d, b, nmax);
+    if (smem > batched_max_smem()) return RCP_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    RCP_TRY(batched_order(h, batch, nmax, n, s));
+    const void *om = opts ? opts->omega : nullptr;
+    if (!om) {
+        const uint64_t seed = opts ? opts->seed : 0;
+        RCP_TRY(grow(h->bom, (size_t)d * nmax * (f64 ? sizeof(double) : sizeof(float))));
+        if (h->bom_seed != seed || h->bom_d != d || h->bom_nmax != nmax || h->bom_f64 != (int)f64) {
+            if (f64) CU_TRY(launch_omega<double>(d, nmax, seed, (double *)h->bom.p, s));
+            else CU_TRY(launch_omega<float>(d, nmax, seed, (float *)h->bom.p, s));
+            h->bom_seed = seed;
+            h->bom_d = d;
+            h->bom_nmax = nmax;
+            h->bom_f64 = (int)f64;
+        }
+        om = h->bom.p;
+    }
+    PhaseScope ps(h, s, PH_PANEL);
+    if (f64)
+        CU_TRY(launch_batched_factor<double>(batch, d, b, nmax, n, A64, lda64, (double *const *)A, lda, Dd, Ds, perm,
+                                             (const double *)om, alpha, info, (const int *)h->bord.p,
+                                             (int *)h->bticket.p, s));
+    else
+        CU_TRY(launch_batched_factor<float>(batch, d, b, nmax, n, A64, lda64, (float *const *)A, lda, Dd, Ds, perm,
+                                            (const float *)om, alpha, info, (const int *)h->bord.p,
+                                            (int *)h->bticket.p, s));
+    return RCP_OK;
+}
+
+rcp_status rcp_refine_batched(rcp_handle *h, int batch, int nmax, int nrhs, const int *n,
+                              const double *const *A64, const int *lda64, const void *const *LA,
+                              const int *ldla, const double *const *Dd, const double *const *Ds,
+                              const int *const *perm, rcp_prec prec, const double *const *Bv, const int *ldb,
+                              double *const *X, const int *ldx, double tol, int max_iter, double *berr,
+                              int *iters, rcp_stream_t stream) {
+    if (!h || batch < 0 || nmax < 0 || nmax > 65535 || nrhs < 0 || max_iter < 0 || !valid_prec(prec))
+        return RCP_EINVAL;
+    if (batch == 0 || nmax == 0 || nrhs == 0) return RCP_OK;
+    if (!n || !LA || !ldla || !Dd || !Ds || !perm || !Bv || !ldb || !X || !ldx || (A64 && !lda64))
+        return RCP_EINVAL;
+    const bool f64 = prec == RCP_FP64;
+    const size_t smem = f64 ? batched_refine_smem<double>(nrhs, nmax) : batched_refine_smem<float>(nrhs, nmax);
+    if (smem > batched_max_smem()) return RCP_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    RCP_TRY(batched_order(h, batch, nmax, n, s));
+    PhaseScope ps(h, s, A64 ? PH_RESIDUAL : PH_SOLVE);
+    if (f64)
+        CU_TRY(launch_batched_refine<double>(batch, nrhs, nmax, max_iter, tol, n, (const double *const *)LA, ldla, Dd,
+                                             Ds, perm, A64, lda64, Bv, ldb, X, ldx, berr, iters,
+                                             (const int *)h->bord.p, (int *)h->bticket.p, s));
+    else
+        CU_TRY(launch_batched_refine<float>(batch, nrhs, nmax, max_iter, tol, n, (const float *const *)LA, ldla, Dd,
+                                            Ds, perm, A64, lda64, Bv, ldb, X, ldx, berr, iters,
+                                            (const int *)h->bord.p, (int *)h->bticket.p, s));
     return RCP_OK;
 }
 

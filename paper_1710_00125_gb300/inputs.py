@@ -195,3 +195,45 @@ def batched_sizes(batch: int, lo: int = 32, hi: int = 512, seed: int = 0) -> np.
 def batched_gaussian(sizes, seed: int = 0):
     """A_i = (G_i + G_i^T)/2 for every order in ``sizes`` (system i uses seed + i)."""
     return [gaussian_sym(int(n), seed=seed * 1000003 + i) for i, n in enumerate(sizes)]
+
+
+def fill_batched_gaussian_device(sizes, offsets, pool, seed: int = 0) -> None:
+    """Type 6 for a whole ragged batch, drawn on the device (for workloads too large to draw
+    with numpy quickly): system i, of order sizes[i], gets A_i = (G_i + G_i^T)/2 written
+    column-major at ``pool[offsets[i]:offsets[i] + n_i^2]`` (FP64).  G comes from torch's
+    device generator seeded with ``seed``, drawn group by group of equal order (increasing
+    order), so the values are reproducible on one device type but differ from
+    ``batched_gaussian``'s numpy draws."""
+    import torch
+    g = torch.Generator(device=pool.device)
+    g.manual_seed(int(seed))
+    by_n = {}
+    for i, n in enumerate(sizes):
+        by_n.setdefault(int(n), []).append(i)
+    for n in sorted(by_n):
+        idx = by_n[n]
+        if n == 0:
+            continue
+        G = torch.randn((len(idx), n, n), generator=g, device=pool.device, dtype=torch.float64)
+        A = (G + G.transpose(1, 2)) * 0.5
+        for j, i in enumerate(idx):
+            pool[offsets[i]:offsets[i] + n * n].copy_(A[j].reshape(-1))
+
+
+def fill_batched_rhs_device(sizes, offsets_sq, a_pool, offsets_rhs, b_pool, nrhs: int, seed: int = 0,
+                            x_pool=None) -> None:
+    """Right-hand sides b_i = A_i x_i with x_i i.i.d. N(0, 1) (nrhs columns, column-major
+    ``n_i x nrhs`` at ``b_pool[offsets_rhs[i]:]``), drawn on the device; x_i is kept in
+    ``x_pool`` when given."""
+    import torch
+    g = torch.Generator(device=a_pool.device)
+    g.manual_seed(int(seed) + 1)
+    for i, n in enumerate(sizes):
+        n = int(n)
+        if n == 0:
+            continue
+        A = a_pool[offsets_sq[i]:offsets_sq[i] + n * n].view(n, n)     # symmetric
+        X = torch.randn((nrhs, n), generator=g, device=a_pool.device, dtype=torch.float64)
+        b_pool[offsets_rhs[i]:offsets_rhs[i] + n * nrhs].view(nrhs, n).copy_(X @ A)
+        if x_pool is not None:
+            x_pool[offsets_rhs[i]:offsets_rhs[i] + n * nrhs].view(nrhs, n).copy_(X)

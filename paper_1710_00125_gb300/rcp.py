@@ -87,6 +87,10 @@ def lib():
         L.rcp_panel_trace.restype = ctypes.c_int
         L.rcp_kernel_launches.argtypes = []
         L.rcp_kernel_launches.restype = ctypes.c_longlong
+        L.rcp_factor_batched.argtypes = [P, I, I, P, P, P, P, P, P, P, P, ctypes.POINTER(Opts), P, P]
+        L.rcp_refine_batched.argtypes = [P, I, I, I, P, P, P, P, P, P, P, P, I, P, P, P, P, D, I, P, P, P]
+        L.rcp_factor_batched.restype = ctypes.c_int
+        L.rcp_refine_batched.restype = ctypes.c_int
         for name in ("rcp_profile", "rcp_profile_read", "rcp_create", "rcp_sync", "rcp_reserve", "rcp_factor", "rcp_solve", "rcp_refine", "rcp_sysv",
                      "rcp_omega", "rcp_sketch"):
             getattr(L, name).restype = ctypes.c_int
@@ -285,3 +289,119 @@ def block_d(Dd: torch.Tensor, Ds: torch.Tensor) -> torch.Tensor:
 def rcp_kernel_launches() -> int:
     """Kernels launched by the library in this process so far."""
     return int(lib().rcp_kernel_launches())
+
+
+# ---------------------------------------------------------------------------------------------
+# batched ragged systems
+# ---------------------------------------------------------------------------------------------
+def rcp_factor_batched(h: Handle, batch: int, nmax: int, n, A64, lda64, A, lda, Dd, Ds, perm,
+                       opts: Opts | None, info, stream=None) -> None:
+    """One-to-one call of ``rcp_factor_batched``: every array argument is a device tensor
+    (int32 per-system values, int64 pointer tables) or None for A64/lda64."""
+    _check(lib().rcp_factor_batched(h.h, int(batch), int(nmax), _ptr(n), _ptr(A64), _ptr(lda64), _ptr(A),
+                                    _ptr(lda), _ptr(Dd), _ptr(Ds), _ptr(perm),
+                                    ctypes.byref(opts) if opts else None, _ptr(info), _stream(stream)),
+           "rcp_factor_batched")
+
+
+def rcp_refine_batched(h: Handle, batch: int, nmax: int, nrhs: int, n, A64, lda64, LA, ldla, Dd, Ds, perm,
+                       prec, Bv, ldb, X, ldx, tol=1e-12, max_iter=10, berr=None, iters=None,
+                       stream=None) -> None:
+    """One-to-one call of ``rcp_refine_batched`` (A64/lda64 None: solve only)."""
+    if isinstance(prec, str):
+        prec = PREC_NAMES[prec]
+    _check(lib().rcp_refine_batched(h.h, int(batch), int(nmax), int(nrhs), _ptr(n), _ptr(A64), _ptr(lda64),
+                                    _ptr(LA), _ptr(ldla), _ptr(Dd), _ptr(Ds), _ptr(perm), int(prec), _ptr(Bv),
+                                    _ptr(ldb), _ptr(X), _ptr(ldx), float(tol), int(max_iter), _ptr(berr),
+                                    _ptr(iters), _stream(stream)), "rcp_refine_batched")
+
+
+class Batch:
+    """Pooled device storage and pointer tables for a ragged batch (argument marshalling only).
+
+    System i owns an ``n_i x n_i`` FP64 original (``A64``), its factor (``F``: float64 for
+    ``prec='fp64'``, else float32), ``Dd``/``Ds``/``perm`` of length n_i, right-hand sides
+    ``B`` and solutions ``X`` (``nrhs x n_i`` row-major, i.e. column-major ``n_i x nrhs``).
+    Each pool is one allocation; ``a64(i)``, ``b(i)``, ``x(i)`` ... return views."""
+
+    def __init__(self, ns, nrhs: int, prec="fp32", device="cuda"):
+        if isinstance(prec, str):
+            prec = PREC_NAMES[prec]
+        self.prec = prec
+        self.ns = [int(v) for v in ns]
+        self.batch = len(self.ns)
+        self.nmax = max(self.ns) if self.ns else 0
+        self.nrhs = int(nrhs)
+        dev = torch.device(device)
+        sq, ln, rh = [0], [0], [0]
+        for v in self.ns:
+            sq.append(sq[-1] + v * v)
+            ln.append(ln[-1] + v)
+            rh.append(rh[-1] + v * self.nrhs)
+        self.off_sq, self.off_n, self.off_rhs = sq, ln, rh
+        fdt = torch.float64 if prec == RCP_FP64 else torch.float32
+        self.A64_pool = torch.zeros(max(sq[-1], 1), dtype=torch.float64, device=dev)
+        self.F_pool = torch.zeros(max(sq[-1], 1), dtype=fdt, device=dev)
+        self.Dd_pool = torch.zeros(max(ln[-1], 1), dtype=torch.float64, device=dev)
+        self.Ds_pool = torch.zeros(max(ln[-1], 1), dtype=torch.float64, device=dev)
+        self.perm_pool = torch.zeros(max(ln[-1], 1), dtype=torch.int32, device=dev)
+        self.B_pool = torch.zeros(max(rh[-1], 1), dtype=torch.float64, device=dev)
+        self.X_pool = torch.zeros(max(rh[-1], 1), dtype=torch.float64, device=dev)
+        self.n = torch.tensor(self.ns, dtype=torch.int32, device=dev)
+        self.ld = torch.tensor([max(v, 1) for v in self.ns], dtype=torch.int32, device=dev)
+        self.info = torch.zeros(self.batch, dtype=torch.int32, device=dev)
+        self.berr = torch.zeros(self.batch, dtype=torch.float64, device=dev)
+        self.iters = torch.zeros(self.batch, dtype=torch.int32, device=dev)
+
+        def table(pool, offs):
+            base, es = pool.data_ptr(), pool.element_size()
+            return torch.tensor([base + o * es for o in offs[:-1]], dtype=torch.int64, device=dev)
+
+        self.p_A64 = table(self.A64_pool, sq)
+        self.p_F = table(self.F_pool, sq)
+        self.p_Dd = table(self.Dd_pool, ln)
+        self.p_Ds = table(self.Ds_pool, ln)
+        self.p_perm = table(self.perm_pool, ln)
+        self.p_B = table(self.B_pool, rh)
+        self.p_X = table(self.X_pool, rh)
+
+    def _mat(self, pool, i):
+        v = self.ns[i]
+        return pool[self.off_sq[i]:self.off_sq[i] + v * v].view(v, v)
+
+    def a64(self, i):
+        return self._mat(self.A64_pool, i)
+
+    def f(self, i):
+        return self._mat(self.F_pool, i)
+
+    def dd(self, i):
+        return self.Dd_pool[self.off_n[i]:self.off_n[i + 1]]
+
+    def ds(self, i):
+        return self.Ds_pool[self.off_n[i]:self.off_n[i + 1]]
+
+    def perm(self, i):
+        return self.perm_pool[self.off_n[i]:self.off_n[i + 1]]
+
+    def b(self, i):
+        return self.B_pool[self.off_rhs[i]:self.off_rhs[i + 1]].view(self.nrhs, self.ns[i])
+
+    def x(self, i):
+        return self.X_pool[self.off_rhs[i]:self.off_rhs[i + 1]].view(self.nrhs, self.ns[i])
+
+    def factor(self, h: Handle, opts: Opts | None = None, from_a64=True, stream=None) -> None:
+        """rcp_factor_batched on every system (FP64 originals copied into the factors first)."""
+        if opts is None:
+            opts = Opts(b=32, d=40, q_mode=1, seed=0, prec=self.prec, alpha=math.sqrt(2.0) / 2.0, omega=None, grid=0)
+        rcp_factor_batched(h, self.batch, self.nmax, self.n, self.p_A64 if from_a64 else None,
+                           self.ld if from_a64 else None, self.p_F, self.ld, self.p_Dd, self.p_Ds, self.p_perm,
+                           opts, self.info, stream)
+
+    def refine(self, h: Handle, tol=1e-12, max_iter=10, refine=True, stream=None) -> None:
+        """rcp_refine_batched: X = solve(B), then FP64 refinement when ``refine``."""
+        rcp_refine_batched(h, self.batch, self.nmax, self.nrhs, self.n, self.p_A64 if refine else None,
+                           self.ld if refine else None, self.p_F, self.ld, self.p_Dd, self.p_Ds, self.p_perm,
+                           self.prec, self.p_B, self.ld, self.p_X, self.ld, tol, max_iter, self.berr, self.iters,
+                           stream)
+
