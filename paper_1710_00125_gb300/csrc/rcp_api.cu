@@ -49,7 +49,7 @@ struct rcp_handle {
     Buf keys;                                      // packed argmax keys of the FP32 panel
     Buf tcops;                                     // tensor-core operand tiles
     int trace_n = 0;
-    Buf bord, bom, bticket;                        // batched path: order, Omega, ticket
+    Buf bord, bom, bticket, bscr;                  // batched path: order, Omega, ticket, per-CTA scratch
     const int *bord_n = nullptr;                   // (n, batch, nmax) the order was made for
     int bord_batch = -1, bord_nmax = -1;
     uint64_t bom_seed = 0;                         // (seed, d, nmax, fp64) of the drawn Omega
@@ -348,7 +348,7 @@ rcp_status rcp_create(rcp_handle **h) {
 
 void rcp_destroy(rcp_handle *h) {
     if (!h) return;
-    Buf *all[] = {&h->bord, &h->bom, &h->bticket, &h->tcops, &h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
+    Buf *all[] = {&h->bord, &h->bom, &h->bticket, &h->bscr, &h->tcops, &h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
                   &h->s1v, &h->s2v, &h->s3v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
                   &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm};
     for (Buf *b : all)
@@ -585,15 +585,18 @@ rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, 
         }
         om = h->bom.p;
     }
+    const int grid = f64 ? batched_factor_grid<double>(d, b, nmax) : batched_factor_grid<float>(d, b, nmax);
+    if (grid <= 0) return RCP_ECUDA;
+    RCP_TRY(grow(h->bscr, batched_factor_scratch_ints(b, nmax) * sizeof(int) * (size_t)grid));
     PhaseScope ps(h, s, PH_PANEL);
     if (f64)
         CU_TRY(launch_batched_factor<double>(batch, d, b, nmax, n, A64, lda64, (double *const *)A, lda, Dd, Ds, perm,
                                              (const double *)om, alpha, info, (const int *)h->bord.p,
-                                             (int *)h->bticket.p, s));
+                                             (int *)h->bticket.p, (int *)h->bscr.p, grid, s));
     else
         CU_TRY(launch_batched_factor<float>(batch, d, b, nmax, n, A64, lda64, (float *const *)A, lda, Dd, Ds, perm,
                                             (const float *)om, alpha, info, (const int *)h->bord.p,
-                                            (int *)h->bticket.p, s));
+                                            (int *)h->bticket.p, (int *)h->bscr.p, grid, s));
     return RCP_OK;
 }
 
