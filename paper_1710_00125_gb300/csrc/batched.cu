@@ -161,8 +161,13 @@ size_t batched_factor_smem(int d, int b, int nmax) {
     return bt_factor_elems(d, b, nmax) * sizeof(T);
 }
 
-template <typename T>
+// DR > 0: thread j keeps the sketch column of position j in registers (n <= THREADS, dp <= DR,
+// FP32 only); DR == 0: the sketch stays in shared memory.
+template <typename T, int DR>
 __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared<T> &sh, int &cnt) {
+    static_assert(DR == 0 || (sizeof(T) == 4 && DR % 4 == 0), "register sketch: FP32, whole float4s");
+    constexpr int DR4 = DR > 0 ? DR / 4 : 1;
+    float4 b4[DR4];   // the register sketch column (DR > 0)
     const int n = a.n[sys], d = a.d, nmax = bt_stride(a.nmax), tid = threadIdx.x;
     const int lda = a.lda[sys];
     T *A = a.A[sys];
@@ -249,10 +254,24 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
 
     // ---- first pivot candidate: max column norm of B ----
     BtCand<T> cand{T(-1), INT_MAX};
-    for (int j = tid; j < n; j += bt::THREADS) {
-        T s = T(0);
-        for (int r = 0; r < d; ++r) { const T v = Bs[(size_t)j * dp + r]; s += v * v; }
-        if (bt_better(s, j, cand.v, cand.j)) cand = BtCand<T>{s, j};
+    if constexpr (DR > 0) {
+        if (tid < n) {
+            const float4 *c4 = reinterpret_cast<const float4 *>(Bs + (size_t)tid * dp);
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < DR4; ++q) {
+                b4[q] = 4 * q < dp ? c4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                s0 += b4[q].x * b4[q].x + b4[q].z * b4[q].z;
+                s1 += b4[q].y * b4[q].y + b4[q].w * b4[q].w;
+            }
+            cand = BtCand<T>{(T)(s0 + s1), tid};
+        }
+    } else {
+        for (int j = tid; j < n; j += bt::THREADS) {
+            T s = T(0);
+            for (int r = 0; r < d; ++r) { const T v = Bs[(size_t)j * dp + r]; s += v * v; }
+            if (bt_better(s, j, cand.v, cand.j)) cand = BtCand<T>{s, j};
+        }
     }
     cand = bt_argmax(cand, sh, cnt);
 
@@ -296,9 +315,23 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                 c1[x] = av;
                 if (x > k && bt_better(bt_abs(av), x, lc.v, lc.j)) lc = BtCand<T>{bt_abs(av), x};
             }
-            for (int e = tid; e < 2 * dp; e += bt::THREADS) {
-                const int r = e < dp ? e : e - dp;
-                stg[e < dp ? r : 2 * dp + r] = Bs[(size_t)(e < dp ? k : P) * dp + r];
+            if constexpr (DR > 0) {
+                // the owners of positions k and P stage their columns
+                if (tid == k || tid == P) {
+                    float4 *o0 = reinterpret_cast<float4 *>(stg), *o2 = reinterpret_cast<float4 *>(stg + 2 * dp);
+#pragma unroll
+                    for (int q = 0; q < DR4; ++q) {
+                        if (4 * q < dp) {
+                            if (tid == k) o0[q] = b4[q];
+                            if (tid == P) o2[q] = b4[q];
+                        }
+                    }
+                }
+            } else {
+                for (int e = tid; e < 2 * dp; e += bt::THREADS) {
+                    const int r = e < dp ? e : e - dp;
+                    stg[e < dp ? r : 2 * dp + r] = Bs[(size_t)(e < dp ? k : P) * dp + r];
+                }
             }
             lc = bt_argmax(lc, sh, cnt);
             // ---- SBKP decision (every thread, in the factor's type) ----
@@ -342,9 +375,22 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                         sh.kase = kk;
                     }
                 }
-                for (int e = tid; e < 2 * dp; e += bt::THREADS) {
-                    const int r = e < dp ? e : e - dp;
-                    stg[e < dp ? dp + r : 3 * dp + r] = Bs[(size_t)(e < dp ? k + 1 : sR) * dp + r];
+                if constexpr (DR > 0) {
+                    if (tid == k + 1 || tid == sR) {
+                        float4 *o1 = reinterpret_cast<float4 *>(stg + dp), *o3 = reinterpret_cast<float4 *>(stg + 3 * dp);
+#pragma unroll
+                        for (int q = 0; q < DR4; ++q) {
+                            if (4 * q < dp) {
+                                if (tid == k + 1) o1[q] = b4[q];
+                                if (tid == sR) o3[q] = b4[q];
+                            }
+                        }
+                    }
+                } else {
+                    for (int e = tid; e < 2 * dp; e += bt::THREADS) {
+                        const int r = e < dp ? e : e - dp;
+                        stg[e < dp ? dp + r : 3 * dp + r] = Bs[(size_t)(e < dp ? k + 1 : sR) * dp + r];
+                    }
                 }
                 __syncthreads();
                 kase = sh.kase;
@@ -384,66 +430,116 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                 }
             }
             BtCand<T> nc{T(-1), INT_MAX};
-            for (int j = k + s + tid; j < n; j += bt::THREADS) {
-                const int u = j == Rm ? tgt : j;                   // label after the first interchange
-                const int o = u == k ? P : (u == P ? k : u);         // label before the step
-                const T *src = o == j ? Bs + (size_t)j * dp
-                                      : stg + (o == k ? 0 : (o == k + 1 ? dp : (o == P ? 2 * dp : 3 * dp)));
-                T *dst = Bs + (size_t)j * dp;
-                T l1, l2 = T(0);
-                if (s == 1) {
-                    const T cj = cp[u];
-                    l1 = cj * finv;
-                    W[(size_t)i * nmax + j] = cj;
-                    Lp[(size_t)i * nmax + j] = l1;
-                } else {
-                    const T x1 = c1[u], x2 = c2[u];
-                    l1 = f11 * x1 + f21 * x2;
-                    l2 = f21 * x1 + f22 * x2;
-                    W[(size_t)i * nmax + j] = x1;
-                    W[(size_t)(i + 1) * nmax + j] = x2;
-                    Lp[(size_t)i * nmax + j] = l1;
-                    Lp[(size_t)(i + 1) * nmax + j] = l2;
-                }
-                T nrm0 = T(0), nrm1 = T(0);
-                if constexpr (sizeof(T) == 4) {
-                    // 16-byte rows: the column, the pivot columns and the update move as float4
-                    const float4 *s4 = reinterpret_cast<const float4 *>(src);
-                    const float4 *a4 = reinterpret_cast<const float4 *>(pbA);
-                    const float4 *b4 = reinterpret_cast<const float4 *>(pbB);
-                    float4 *d4 = reinterpret_cast<float4 *>(dst);
+            if constexpr (DR > 0) {
+                const int j = tid;
+                if (j >= k + s && j < n) {
+                    const int u = j == Rm ? tgt : j;                   // label after the first interchange
+                    const int o = u == k ? P : (u == P ? k : u);         // label before the step
+                    float l1, l2 = 0.f;
                     if (s == 1) {
-#pragma unroll 2
-                        for (int r4 = 0; r4 < dp / 4; ++r4) {
-                            float4 v = s4[r4];
-                            const float4 pa = a4[r4];
+                        const T cj = cp[u];
+                        l1 = cj * finv;
+                        W[(size_t)i * nmax + j] = cj;
+                        Lp[(size_t)i * nmax + j] = l1;
+                    } else {
+                        const T x1 = c1[u], x2 = c2[u];
+                        l1 = f11 * x1 + f21 * x2;
+                        l2 = f21 * x1 + f22 * x2;
+                        W[(size_t)i * nmax + j] = x1;
+                        W[(size_t)(i + 1) * nmax + j] = x2;
+                        Lp[(size_t)i * nmax + j] = l1;
+                        Lp[(size_t)(i + 1) * nmax + j] = l2;
+                    }
+                    if (o != j) {
+                        // this position receives a column moved by the interchanges (staged)
+                        const float4 *src4 = reinterpret_cast<const float4 *>(
+                            stg + (o == k ? 0 : (o == k + 1 ? dp : (o == P ? 2 * dp : 3 * dp))));
+#pragma unroll
+                        for (int q = 0; q < DR4; ++q)
+                            if (4 * q < dp) b4[q] = src4[q];
+                    }
+                    const float4 *a4 = reinterpret_cast<const float4 *>(pbA);
+                    const float4 *q4 = reinterpret_cast<const float4 *>(pbB);
+                    float n0 = 0.f, n1 = 0.f;
+#pragma unroll
+                    for (int q = 0; q < DR4; ++q) {
+                        if (4 * q < dp) {
+                            const float4 pa = a4[q];
+                            float4 v = b4[q];
                             v.x -= pa.x * l1; v.y -= pa.y * l1; v.z -= pa.z * l1; v.w -= pa.w * l1;
-                            d4[r4] = v;
-                            nrm0 += v.x * v.x + v.z * v.z;
-                            nrm1 += v.y * v.y + v.w * v.w;
+                            if (s == 2) {
+                                const float4 pq = q4[q];
+                                v.x -= pq.x * l2; v.y -= pq.y * l2; v.z -= pq.z * l2; v.w -= pq.w * l2;
+                            }
+                            b4[q] = v;
+                            n0 += v.x * v.x + v.z * v.z;
+                            n1 += v.y * v.y + v.w * v.w;
+                        }
+                    }
+                    nc = BtCand<T>{(T)(n0 + n1), j};
+                }
+            } else {
+                for (int j = k + s + tid; j < n; j += bt::THREADS) {
+                    const int u = j == Rm ? tgt : j;                   // label after the first interchange
+                    const int o = u == k ? P : (u == P ? k : u);         // label before the step
+                    const T *src = o == j ? Bs + (size_t)j * dp
+                                          : stg + (o == k ? 0 : (o == k + 1 ? dp : (o == P ? 2 * dp : 3 * dp)));
+                    T *dst = Bs + (size_t)j * dp;
+                    T l1, l2 = T(0);
+                    if (s == 1) {
+                        const T cj = cp[u];
+                        l1 = cj * finv;
+                        W[(size_t)i * nmax + j] = cj;
+                        Lp[(size_t)i * nmax + j] = l1;
+                    } else {
+                        const T x1 = c1[u], x2 = c2[u];
+                        l1 = f11 * x1 + f21 * x2;
+                        l2 = f21 * x1 + f22 * x2;
+                        W[(size_t)i * nmax + j] = x1;
+                        W[(size_t)(i + 1) * nmax + j] = x2;
+                        Lp[(size_t)i * nmax + j] = l1;
+                        Lp[(size_t)(i + 1) * nmax + j] = l2;
+                    }
+                    T nrm0 = T(0), nrm1 = T(0);
+                    if constexpr (sizeof(T) == 4) {
+                        // 16-byte rows: the column, the pivot columns and the update move as float4
+                        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+                        const float4 *a4 = reinterpret_cast<const float4 *>(pbA);
+                        const float4 *b4 = reinterpret_cast<const float4 *>(pbB);
+                        float4 *d4 = reinterpret_cast<float4 *>(dst);
+                        if (s == 1) {
+    #pragma unroll 2
+                            for (int r4 = 0; r4 < dp / 4; ++r4) {
+                                float4 v = s4[r4];
+                                const float4 pa = a4[r4];
+                                v.x -= pa.x * l1; v.y -= pa.y * l1; v.z -= pa.z * l1; v.w -= pa.w * l1;
+                                d4[r4] = v;
+                                nrm0 += v.x * v.x + v.z * v.z;
+                                nrm1 += v.y * v.y + v.w * v.w;
+                            }
+                        } else {
+    #pragma unroll 2
+                            for (int r4 = 0; r4 < dp / 4; ++r4) {
+                                float4 v = s4[r4];
+                                const float4 pa = a4[r4], pq = b4[r4];
+                                v.x -= pa.x * l1 + pq.x * l2; v.y -= pa.y * l1 + pq.y * l2;
+                                v.z -= pa.z * l1 + pq.z * l2; v.w -= pa.w * l1 + pq.w * l2;
+                                d4[r4] = v;
+                                nrm0 += v.x * v.x + v.z * v.z;
+                                nrm1 += v.y * v.y + v.w * v.w;
+                            }
                         }
                     } else {
-#pragma unroll 2
-                        for (int r4 = 0; r4 < dp / 4; ++r4) {
-                            float4 v = s4[r4];
-                            const float4 pa = a4[r4], pq = b4[r4];
-                            v.x -= pa.x * l1 + pq.x * l2; v.y -= pa.y * l1 + pq.y * l2;
-                            v.z -= pa.z * l1 + pq.z * l2; v.w -= pa.w * l1 + pq.w * l2;
-                            d4[r4] = v;
-                            nrm0 += v.x * v.x + v.z * v.z;
-                            nrm1 += v.y * v.y + v.w * v.w;
+                        for (int r = 0; r < d; ++r) {
+                            T w = src[r] - pbA[r] * l1;
+                            if (s == 2) w -= pbB[r] * l2;
+                            dst[r] = w;
+                            if (r & 1) nrm1 += w * w; else nrm0 += w * w;
                         }
                     }
-                } else {
-                    for (int r = 0; r < d; ++r) {
-                        T w = src[r] - pbA[r] * l1;
-                        if (s == 2) w -= pbB[r] * l2;
-                        dst[r] = w;
-                        if (r & 1) nrm1 += w * w; else nrm0 += w * w;
-                    }
+                    const T nrm = nrm0 + nrm1;
+                    if (bt_better(nrm, j, nc.v, nc.j)) nc = BtCand<T>{nrm, j};
                 }
-                const T nrm = nrm0 + nrm1;
-                if (bt_better(nrm, j, nc.v, nc.j)) nc = BtCand<T>{nrm, j};
             }
             // the interchanges of the panel rows: new row q of W and Lp is old row sigma(tau(q))
             for (int e = tid; e < 2 * i; e += bt::THREADS) {
@@ -578,7 +674,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
     __syncthreads();
 }
 
-template <typename T>
+template <typename T, int DR>
 __global__ void __launch_bounds__(bt::THREADS, 1) batched_factor_kernel(BtFactorArgs<T> a) {
     extern __shared__ __align__(16) unsigned char bt_raw[];
     __shared__ BtShared<T> sh;
@@ -590,7 +686,7 @@ __global__ void __launch_bounds__(bt::THREADS, 1) batched_factor_kernel(BtFactor
         const int idx = sh.s_idx;
         __syncthreads();
         if (idx >= a.batch) return;
-        bt_factor_one<T>(a, a.order[idx], reinterpret_cast<T *>(bt_raw), sh, cnt);
+        bt_factor_one<T, DR>(a, a.order[idx], reinterpret_cast<T *>(bt_raw), sh, cnt);
     }
 }
 
@@ -994,18 +1090,30 @@ size_t batched_max_smem() {
     return (size_t)v > 1024 ? (size_t)v - 1024 : 0;   // room for the kernels' static shared memory
 }
 
+// the factor kernel for a shape: the register sketch when it fits (FP32, d <= 48, nmax <= THREADS)
+constexpr int BT_DR = 48;
+template <typename T>
+static void (*bt_factor_fn(int d, int nmax))(BtFactorArgs<T>) {
+    if constexpr (sizeof(T) == 4) {
+        if (bt_stride(d) <= BT_DR && nmax <= bt::THREADS) return batched_factor_kernel<T, BT_DR>;
+    }
+    (void)d;
+    (void)nmax;
+    return batched_factor_kernel<T, 0>;
+}
+
 template <typename T>
 int batched_factor_grid(int d, int b, int nmax) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = batched_factor_smem<T>(d, b, nmax);
-    if (cudaFuncSetAttribute(batched_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
+    void (*fn)(BtFactorArgs<T>) = bt_factor_fn<T>(d, nmax);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_factor_kernel<T>, bt::THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, bt::THREADS, smem);
     return sms * (per > 0 ? per : 1);
 }
 
@@ -1016,11 +1124,12 @@ cudaError_t launch_batched_factor(int batch, int d, int b, int nmax, const int *
                                   int *ticket, int *pscr, int grid, cudaStream_t s) {
     BtFactorArgs<T> a{batch, d, b, nmax, n, A64, lda64, A, lda, Dd, Ds, perm, om, alpha, info, order, ticket, pscr};
     const size_t smem = batched_factor_smem<T>(d, b, nmax);
-    cudaError_t e = cudaFuncSetAttribute(batched_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    void (*fn)(BtFactorArgs<T>) = bt_factor_fn<T>(d, nmax);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(ticket, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    batched_factor_kernel<T><<<grid < batch ? grid : batch, bt::THREADS, smem, s>>>(a);
+    fn<<<grid < batch ? grid : batch, bt::THREADS, smem, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
