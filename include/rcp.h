@@ -60,7 +60,12 @@ typedef enum {
 typedef struct {
     int b;              /* panel width (block size of Algorithm 1); 0 = default 64           */
     int d;              /* sketch rows (the paper's p; 1..128); 0 = default min(b + 16, 128) */
-    int q_mode;         /* 1: one sketch pivot per step (q = 1).  Only 1 is supported.       */
+    int q_mode;         /* 1 (or 0): q = 1, one sketch argmax and one sketch update per      */
+                        /* pivot step.  2: q = b (Section 3.1): a b-step partial QRCP of the */
+                        /* sketch picks each block's candidates, the block's steps take them */
+                        /* in order (SBKP may still bring in other columns), and the sketch  */
+                        /* is updated once per block, B(:, k1:n) -= B_blk L11^{-T} L21^T.    */
+                        /* rcp_factor_batched supports q = 1 only.                            */
     uint64_t seed;      /* Philox key of the sketch matrix Omega                             */
     rcp_prec prec;      /* arithmetic of the factor                                          */
     double alpha;       /* SBKP threshold; 0 = default sqrt(2)/2                             */

@@ -48,10 +48,22 @@ struct FactorWork {
     float *tcops;                // tensor-core operand tiles (TF32x3 trailing update)
     int spec;                    // FP32 panel: speculative case-(1) path enabled (shadow sketch fits)
     double *s3v;                 // [2][grid][4] records of the speculative candidates
+    int qb;                      // Algorithm 1 with q = b: the pivot of step k is the column at
+                                 // position k (candidates chosen by the block QRCP); no per-step
+                                 // sketch update (the block update follows the panel)
 };
 
 template <typename T>
 size_t panel_smem_bytes(int d, int bw, int chunk_cap, int spec);
+
+// q = b: block QRCP of the sketch (interchanges in the panel's format) and block sketch update
+template <typename T>
+size_t qrcp_smem_bytes(int d, int chunk_cap);
+size_t qrcp_smem_limit();
+template <typename T>
+cudaError_t launch_qrcp(const FactorWork<T> &w, int steps, cudaStream_t s);
+template <typename T>
+cudaError_t launch_block_sketch_update(const FactorWork<T> &w, T *ytmp, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_panel(const FactorWork<T> &w, cudaStream_t s);

@@ -406,8 +406,11 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         // (skipped when the previous step's speculation already found this step's pivot)
         if (!have_next) {
         CandT<T> c{T(-1), INT_MAX, -1};
-        for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
-            if (alive[jl] && better(nrm[jl], lp[jl], c.v, c.lpos)) c = CandT<T>{nrm[jl], lp[jl], j_lo + jl};
+        for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
+            // q = b: the candidate is the column at position k (placed there by the block QRCP)
+            const T v = w.qb ? (lp[jl] == k ? T(1) : T(-1)) : nrm[jl];
+            if (alive[jl] && v >= T(0) && better(v, lp[jl], c.v, c.lpos)) c = CandT<T>{v, lp[jl], j_lo + jl};
+        }
         c = block_argmax(c, s_red);
         if (c.phys >= 0) {
             const int jc = c.phys - j_lo;
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             win[k - k0] = P;
             if (P >= j_lo && P < j_lo + cnt) lp[P - j_lo] = k;
             if (Q != P && Q >= j_lo && Q < j_lo + cnt) lp[Q - j_lo] = LP;
-            if (cta == 0) {
+            if (cta == 0 && !w.qb) {
                 if (k == 0) { beta2 = s_d[0]; w.st->beta2 = beta2; }
                 minnorm2 = fmin(minnorm2, s_d[0]);
             }
@@ -765,7 +768,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                     }
                     tmaxL = fmax(tmaxL, fmax(fabs(l1), fabs(l2)));
                     T *col = Bs + (size_t)jl * ds;
-                    if (s == 2) {
+                    if (w.qb) {
+                        // q = b: the sketch is updated once per block, after the panel
+                    } else if (s == 2) {
                         for (int r = sub; r < d; r += 4) {
                             T v = col[r] - b1[r] * l1 - bR[r] * l2;
                             col[r] = v;
@@ -829,7 +834,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     }
     for (int e = tid; e < cnt * d; e += PANEL_THREADS) {
         int jl = e / d, r = e - jl * d;
-        if (alive[jl]) w.B[(size_t)r + (size_t)lp[jl] * d] = Bs[(size_t)jl * ds + r];
+        if (alive[jl] || w.qb) w.B[(size_t)r + (size_t)lp[jl] * d] = Bs[(size_t)jl * ds + r];
     }
     for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
         int j = j_lo + jl;

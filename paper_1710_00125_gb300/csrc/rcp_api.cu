@@ -110,7 +110,7 @@ rcp_status ensure_small(rcp_handle *h) {
 }
 
 struct Resolved {
-    int b, d, grid, chunk_cap, bw, maxmoved, spec;
+    int b, d, grid, chunk_cap, bw, maxmoved, spec, qb;
     double alpha;
     rcp_prec prec;
     uint64_t seed;
@@ -129,7 +129,8 @@ rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
     if (r.prec < RCP_FP64 || r.prec > RCP_TF32X3) return RCP_EINVAL;
     r.b = (o && o->b > 0) ? o->b : 64;
     r.d = (o && o->d > 0) ? o->d : std::min(r.b + 16, 128);
-    if (o && o->q_mode != 0 && o->q_mode != 1) return RCP_EUNSUPPORTED;
+    if (o && (o->q_mode < 0 || o->q_mode > 2)) return RCP_EUNSUPPORTED;
+    r.qb = (o && o->q_mode == 2) ? 1 : 0;
     if (r.b < 1 || r.b > 512 || r.d < 1 || r.d > 128) return RCP_EUNSUPPORTED;
     r.alpha = (o && o->alpha > 0.0) ? o->alpha : std::sqrt(2.0) / 2.0;
     if (!(r.alpha < 1.0)) return RCP_EINVAL;
@@ -149,7 +150,16 @@ rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
     if (r.chunk_cap > 1024) return RCP_EUNSUPPORTED;
     // the FP32 panel speculates on SBKP case (1) when the shadow sketch fits in shared memory
     r.spec = 0;
-    if (f64) {
+    if (r.qb) {
+        // q = b: the block QRCP keeps its chunk of the sketch in shared memory, and the block
+        // sketch update keeps Y^T (bw x d) there; no speculation (no per-step sketch argmax)
+        const size_t el = f64 ? sizeof(double) : sizeof(float);
+        if ((f64 ? qrcp_smem_bytes<double>(r.d, r.chunk_cap) : qrcp_smem_bytes<float>(r.d, r.chunk_cap)) >
+                qrcp_smem_limit() ||
+            (size_t)r.bw * r.d * el > qrcp_smem_limit())
+            return RCP_EUNSUPPORTED;
+        maxg = f64 ? panel_max_grid<double>(r.d, r.bw, r.chunk_cap, 0) : panel_max_grid<float>(r.d, r.bw, r.chunk_cap, 0);
+    } else if (f64) {
         maxg = panel_max_grid<double>(r.d, r.bw, r.chunk_cap, 0);
     } else {
         maxg = panel_max_grid<float>(r.d, r.bw, r.chunk_cap, 1);
@@ -180,8 +190,10 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->s2i, 2 * (size_t)r.grid * sizeof(int)));
     RCP_TRY(grow(h->pay, 4 * (size_t)r.grid * r.d * sizeof(T)));
     RCP_TRY(grow(h->s3v, 8 * (size_t)r.grid * sizeof(double)));
-    RCP_TRY(grow(h->tmpA, (size_t)r.maxmoved * N * sizeof(T)));
-    RCP_TRY(grow(h->tmpL, (size_t)r.maxmoved * N * sizeof(T)));
+    // interchange scratch; with q = b it also holds the moved sketch columns and Y (d x bw)
+    const size_t NT = std::max(N, (size_t)r.d);
+    RCP_TRY(grow(h->tmpA, (size_t)r.maxmoved * NT * sizeof(T)));
+    RCP_TRY(grow(h->tmpL, (size_t)r.maxmoved * NT * sizeof(T)));
     RCP_TRY(grow(h->tmpP, (size_t)r.maxmoved * sizeof(int)));
     return RCP_OK;
 }
@@ -206,6 +218,7 @@ FactorWork<T> make_work(rcp_handle *h, int n, T *A, int lda, double *Dd, double 
     w.maxmoved = r.maxmoved;
     w.keys = (unsigned long long *)h->keys.p;
     w.spec = r.spec;
+    w.qb = r.qb;
     w.s3v = (double *)h->s3v.p;
     w.tcops = r.prec == RCP_TF32X3 ? (float *)h->tcops.p : nullptr;
     w.trace = nullptr;
@@ -283,6 +296,13 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
     }
     const int nblk = (n + r.b - 1) / r.b;
     for (int blk = 0; blk < nblk; ++blk) {
+        if (r.qb) {
+            // q = b: the block's candidates from a partial QRCP of the sketch, interchanged to
+            // the first positions of the block before the panel
+            PhaseScope ps(h, s, PH_SKETCH);
+            CU_TRY(launch_qrcp<T>(w, r.b, s));
+            CU_TRY(launch_interchange<T>(w, s));
+        }
         {
             PhaseScope ps(h, s, PH_PANEL);
             CU_TRY(launch_panel<T>(w, s));
@@ -294,6 +314,10 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
         {
             PhaseScope ps(h, s, PH_TRAILING);
             CU_TRY(launch_trailing<T>(w, std::min(n, (blk + 1) * r.b), (int)r.prec, s));
+        }
+        if (r.qb) {
+            PhaseScope ps(h, s, PH_SKETCH);
+            CU_TRY(launch_block_sketch_update<T>(w, w.tmpL, s));
         }
     }
     CU_TRY(launch_factor_finish<T>(w, s));

@@ -273,3 +273,74 @@ def test_tf32x3_refine_reaches_fp64_backward_error(rcp, handle, kexp):
     assert code == 0, rst.as_dict()
     assert oracle.berr(a, X.cpu().numpy().T, rhs.T) <= 1e-12
     assert rst.refine_iters <= 6
+
+
+# ------------------------------------------------------------------------------------------
+# q = b: block QRCP candidates, block sketch update (Section 3.1)
+# ------------------------------------------------------------------------------------------
+
+QB_CASES = [
+    (37, 8, 12, 3), (100, 16, 20, 4),   # many blocks, ragged tails
+    (256, 32, 40, 0),                  # the n = 256 workload with q = b
+    (300, 32, 12, 5),                  # b > d: the QRCP ranks only d candidates per block
+]
+
+
+@pytest.mark.parametrize("n,b,d,seed", QB_CASES)
+def test_fp64_qb_factor_matches_oracle(rcp, handle, n, b, d, seed):
+    a = inputs.gaussian_sym(n, seed=seed)
+    ref = oracle.rcp(a, oracle.omega(seed, d, n), q_mode=2, block=b, record=False)
+    A = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    Dd = torch.zeros(n, dtype=torch.float64, device=DEV)
+    Ds = torch.zeros(n, dtype=torch.float64, device=DEV)
+    perm = torch.zeros(n, dtype=torch.int32, device=DEV)
+    code, st = rcp.rcp_factor(handle, A, Dd, Ds, perm, rcp.make_opts(b=b, d=d, seed=seed, prec="fp64", q_mode=2))
+    assert code == ref["info"]
+    assert np.array_equal(perm.cpu().numpy(), ref["perm"])
+    ds = Ds.cpu().numpy()
+    assert np.array_equal(ds != 0, ref["Ds"] != 0)
+    scale = np.abs(a).max()
+    assert np.allclose(Dd.cpu().numpy(), ref["Dd"], rtol=0, atol=1e-11 * scale * max(1, n / 64))
+    assert np.allclose(ds, ref["Ds"], rtol=0, atol=1e-11 * scale * max(1, n / 64))
+    assert np.allclose(_unit_lower(A), ref["L"], rtol=0, atol=1e-10 * max(1, n / 64))
+    assert st.n_2x2 == ref["n_2x2"]
+
+
+def test_qb_differs_from_q1(rcp, handle):
+    # the two modes pick different pivot sequences on the same input (the mode is really used)
+    n, b, d, seed = 200, 16, 24, 7
+    a = inputs.gaussian_sym(n, seed=seed)
+    om = oracle.omega(seed, d, n)
+    r1 = oracle.rcp(a, om, q_mode=1, record=False)
+    r2 = oracle.rcp(a, om, q_mode=2, block=b, record=False)
+    assert not np.array_equal(r1["perm"], r2["perm"])
+    A = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    Dd = torch.zeros(n, dtype=torch.float64, device=DEV)
+    Ds = torch.zeros_like(Dd)
+    perm = torch.zeros(n, dtype=torch.int32, device=DEV)
+    rcp.rcp_factor(handle, A, Dd, Ds, perm, rcp.make_opts(b=b, d=d, seed=seed, prec="fp64", q_mode=2))
+    assert np.array_equal(perm.cpu().numpy(), r2["perm"])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_qb_mixed_refine_reaches_fp64_backward_error(rcp, handle, prec):
+    n = 1000
+    a = inputs.spectrum(n, seed=5, kexp=4.0, nrefl=16)
+    x = inputs.x_true(n, 1, seed=5)
+    rhs = inputs.rhs_for(a, x)
+    A = torch.from_numpy(np.ascontiguousarray(a)).to(DEV).float()
+    Dd = torch.zeros(n, dtype=torch.float64, device=DEV)
+    Ds = torch.zeros_like(Dd)
+    perm = torch.zeros(n, dtype=torch.int32, device=DEV)
+    code, st = rcp.rcp_factor(handle, A, Dd, Ds, perm, rcp.make_opts(b=64, d=80, seed=1, prec=prec, q_mode=2))
+    assert code == 0
+    L = _unit_lower(A)
+    D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
+    p = perm.cpu().numpy()
+    assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() / np.abs(a).max() < 2e-5 * max(1.0, st.growth_D)
+    A64 = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    Bv = torch.from_numpy(rhs.copy()).to(DEV)
+    X = torch.zeros_like(Bv)
+    code, rst = rcp.rcp_refine(handle, A64, A, Dd, Ds, perm, prec, Bv, X, tol=1e-12, max_iter=30)
+    assert code == 0, rst.as_dict()
+    assert oracle.berr(a, X.cpu().numpy().T, rhs.T) <= 1e-12
