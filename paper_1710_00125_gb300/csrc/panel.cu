@@ -170,29 +170,35 @@ __device__ __forceinline__ unsigned long long ld_key(const unsigned long long *p
 
 constexpr int KEY_RING = 16;
 
-// Block-wide maximum of two packed keys per thread (the result to every thread).
-__device__ __forceinline__ void block_max2_u64(unsigned long long &a, unsigned long long &b, unsigned long long *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        a = max(a, __shfl_xor_sync(FULL, a, off));
-        b = max(b, __shfl_xor_sync(FULL, b, off));
+// Block-wide maximum of two packed keys per thread (the result to every thread): per warp two
+// 32-bit redux.sync per key (high word, then the low word among the lanes holding the maximal
+// high word), per block one shared 64-bit atomicMax per key and warp.  Three slot pairs are
+// used in rotation (call counter `cnt`, uniform over the block): the pair of the next call,
+// last read two barriers ago, is cleared here, so one barrier per call suffices.
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+    const unsigned m = __reduce_max_sync(FULL, hi);
+    const unsigned l = __reduce_max_sync(FULL, hi == m ? lo : 0u);
+    return ((unsigned long long)m << 32) | l;
+}
+
+__device__ __forceinline__ void block_max2_u64(unsigned long long &a, unsigned long long &b, unsigned long long *red,
+                                               int &cnt) {
+    const unsigned long long wa = warp_max_u64(a), wb = warp_max_u64(b);
+    const int slot = cnt % 3;
+    if (threadIdx.x == 0) {
+        const int nx = (cnt + 1) % 3;
+        red[2 * nx] = 0ull;
+        red[2 * nx + 1] = 0ull;
     }
-    if (lane == 0) { red[warp] = a; red[PANEL_WARPS + warp] = b; }
-    __syncthreads();
-    if (warp == 0) {
-        unsigned long long x = lane < PANEL_WARPS ? red[lane] : 0ull, y = lane < PANEL_WARPS ? red[PANEL_WARPS + lane] : 0ull;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            x = max(x, __shfl_xor_sync(FULL, x, off));
-            y = max(y, __shfl_xor_sync(FULL, y, off));
-        }
-        if (lane == 0) { red[2 * PANEL_WARPS] = x; red[2 * PANEL_WARPS + 1] = y; }
+    if ((threadIdx.x & 31) == 0) {
+        if (wa) atomicMax(red + 2 * slot, wa);
+        if (wb) atomicMax(red + 2 * slot + 1, wb);
     }
     __syncthreads();
-    a = red[2 * PANEL_WARPS];
-    b = red[2 * PANEL_WARPS + 1];
-    __syncthreads();
+    a = red[2 * slot];
+    b = red[2 * slot + 1];
+    ++cnt;
 }
 
 // The multiplier L(j, t) of a row from its W = L D row and the panel's per-column D scalars,
@@ -222,7 +228,7 @@ __device__ __forceinline__ T l_entry(const T *wr, int t, const int *kind, const 
 template <typename T, typename Hook>
 __device__ void schur_column(const T *__restrict__ A, int lda, int j_lo, int cnt, int X, int i, int bw,
                              const T *Ws, const T *payg, T *bX, const T *lXg, T *lX, int d,
-                             const int *alive, T *c, const double *xsrc, double *xs, int nx, Hook hook,
+                             const int *alive, T *c, const T *xsrc, T *xs, int nx, Hook hook,
                              bool preloaded = false, T pa0 = T(0), T pa1 = T(0)) {
     T a0 = pa0, a1 = pa1;
     const int r0 = threadIdx.x, r1 = threadIdx.x + PANEL_THREADS;
@@ -257,6 +263,10 @@ __device__ void schur_column(const T *__restrict__ A, int lda, int j_lo, int cnt
 struct NoHook {
     __device__ void operator()() const {}
 };
+
+// correctly rounded reciprocal in the factor's type
+__device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip_rn(double x) { return 1.0 / x; }
 
 constexpr int CASE_PENDING = 4;   // lambda > 0 and |a_kk| < alpha lambda: case 2 or 3, a_rr needed
 
@@ -297,6 +307,8 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     __shared__ int s_i[16];
     __shared__ double s_d[16];
     __shared__ T s_t[8];
+    __shared__ T s_x[16];   // per-step scalars in the factor's type: [0] pivot norm, [2] lambda,
+                            // [6] next pivot norm (speculation), [8] a_kk, [10..11] a_rk, a_rr
     __shared__ unsigned long long s_red2[2 * PANEL_WARPS + 2];
 
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -362,6 +374,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         alive[jl] = 1;
     }
     for (int x = tid; x < wsz; x += PANEL_THREADS) win[x] = k0 + x;
+    if (tid < 6) s_red2[tid] = 0ull;   // the first slot pairs of block_max2_u64
     double beta2 = 0.0;   // thread 0 of CTA 0: ||B^(1)||_{1,2}^2
     if (tid == 0) {
         s_i[0] = (int)barrier_base(w.bar, (unsigned)G);
@@ -383,6 +396,8 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     unsigned nbar = 0;
     int k = k0, i = 0, n2 = 0;
     double maxD = 0.0, minnorm2 = INFINITY;
+    T maxDf = T(0), beta2f = T(0), minnorm2f = (T)INFINITY;   // FP32 path: the same, in the factor's type
+    int red2_cnt = 0;   // calls of block_max2_u64 (slot rotation)
     T tmaxL = T(0);
     int info = 0, fail = 0;
     const double alpha = w.alpha;
@@ -418,13 +433,13 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         }
         const unsigned g1 = gbase + nbar + 1;
         if (tid == 0) {
-            const double dgc = c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0;
             if (KEYS) {
                 if (c.phys >= 0) {
-                    stcg(rec1 + 4 * (size_t)cta, dgc);
+                    stcg(reinterpret_cast<T *>(rec1 + 4 * (size_t)cta), dg[c.phys - j_lo]);
                     red_max_u64(keys + (g1 % KEY_RING), make_key((float)c.v, c.lpos, c.phys));
                 }
             } else {
+                const double dgc = c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0;
                 slot_write(rec1, cta, (double)c.v, dgc, 0.0, c.lpos, c.phys);
             }
         }
@@ -442,7 +457,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                     s_i[1] = (int)(key & 0xFFFFull);
                     s_i[2] = 0xFFFF - (int)((key >> 16) & 0xFFFFull);
                     s_i[3] = (s_i[1] - k0) / chunk;
-                    s_d[0] = (double)__uint_as_float((unsigned)(key >> 32));
+                    s_x[0] = (T)__uint_as_float((unsigned)(key >> 32));
                 } else {
                     s_i[1] = -1;
                 }
@@ -452,6 +467,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             if (lane == 0) {
                 s_i[1] = b.phys; s_i[2] = b.lpos; s_i[3] = b.cta;
                 s_d[0] = b.v; s_d[1] = b.a1;
+                s_x[0] = (T)b.v;
             }
         }
         if (tid == 0 && s_i[1] >= 0) {
@@ -463,27 +479,35 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             if (P >= j_lo && P < j_lo + cnt) lp[P - j_lo] = k;
             if (Q != P && Q >= j_lo && Q < j_lo + cnt) lp[Q - j_lo] = LP;
             if (cta == 0 && !w.qb) {
-                if (k == 0) { beta2 = s_d[0]; w.st->beta2 = beta2; }
-                minnorm2 = fmin(minnorm2, s_d[0]);
+                if (KEYS) {
+                    if (k == 0) beta2f = s_x[0];
+                    minnorm2f = fminf((float)minnorm2f, (float)s_x[0]);
+                } else {
+                    if (k == 0) { beta2 = s_d[0]; w.st->beta2 = beta2; }
+                    minnorm2 = fmin(minnorm2, s_d[0]);
+                }
             }
         }
         }   // !have_next (a committed speculation did this step's interchange bookkeeping)
         __syncthreads();
         const int P = s_i[1], gP = s_i[3];
-        if (P < 0 || !isfinite(s_d[0])) { fail = ST_NONFINITE; break; }
+        if (P < 0 || !isfinite(s_x[0])) { fail = ST_NONFINITE; break; }
         // where P's sketch column and a_kk were published: by step (1), or by the speculation
         const T *payP = have_next ? spec_pay + (size_t)(spec_par * G + gP) * ps : pay1 + (size_t)gP * ps;
-        const double *recP = have_next ? spec_rec + (size_t)(spec_par * G + gP) * 4 : rec1 + 4 * (size_t)gP;
+        const T *recP = reinterpret_cast<const T *>(have_next ? spec_rec + (size_t)(spec_par * G + gP) * 4
+                                                              : rec1 + 4 * (size_t)gP);
 
         // ---------------- (2) column P of the Schur complement, lambda and r ----------------
         PANEL_MARK(3);
         schur_column<T>(A, lda, j_lo, cnt, P, i, ws, Ws, payP, bP, w.Lg + (size_t)P * bw, lP, d,
-                        alive, c1, recP, s_d + 8, KEYS ? 1 : 0, [&]() {
+                        alive, c1, recP, s_x + 8, KEYS ? 1 : 0, [&]() {
                             // reciprocal of a_kk, used by case (1) and by the speculation
-                            if (KEYS) s_t[7] = s_d[8] != 0.0 ? (T)(1.0 / s_d[8]) : T(0);
+                            if (KEYS) s_t[7] = s_x[8] != T(0) ? recip_rn(s_x[8]) : T(0);
                         }, have_next, preA0, preA1);
-        const double akk = KEYS ? s_d[8] : s_d[1];
-        if (!isfinite(akk)) { fail = ST_NONFINITE; break; }
+        // a_kk: FP32 path in the factor's type (its tests and reciprocal stay off the FP64 pipe)
+        const T akkT = KEYS ? s_x[8] : (T)s_d[1];
+        const double akk = KEYS ? 0.0 : s_d[1];
+        if (!isfinite(akkT)) { fail = ST_NONFINITE; break; }
         PANEL_MARK(4);
         const unsigned g2 = gbase + nbar + 1;
         // speculation (FP32): assume case (1) (multipliers c / a_kk), update the sketch into the
@@ -503,10 +527,23 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                         const T l1 = c1[jl] * f;
                         const T *col = Bs + (size_t)jl * ds;
                         T *col2 = Bs2 + (size_t)jl * ds;
-                        for (int r = sub; r < d; r += 4) {
-                            T v = col[r] - bP[r] * l1;
-                            col2[r] = v;
-                            sacc = fma(v, v, sacc);
+                        // rows sub, sub+4, ...: five at a time, all loads of a chunk before its
+                        // stores (the sketch copies and the pivot column share one base)
+                        for (int r0 = sub; r0 < d; r0 += 20) {
+                            T v[5], pb[5];
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) {
+                                const int r = r0 + 4 * q;
+                                v[q] = r < d ? col[r] : T(0);
+                                pb[q] = r < d ? bP[r] : T(0);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) {
+                                const int r = r0 + 4 * q;
+                                const T x = v[q] - pb[q] * l1;
+                                if (r < d) col2[r] = x;
+                                sacc = fma(x, x, sacc);
+                            }
                         }
                     }
                     sacc += __shfl_xor_sync(FULL, sacc, 1);
@@ -521,12 +558,14 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
                     if (alive[jl] && j_lo + jl != P) kl = max(kl, make_key((float)fabs(c1[jl]), lp[jl], j_lo + jl));
             }
-            block_max2_u64(kl, ks, s_red2);
+            block_max2_u64(kl, ks, s_red2, red2_cnt);
             if (kl != 0ull) {
                 const int jc = (int)(kl & 0xFFFFull) - j_lo;
                 for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay2 + (size_t)cta * ps + r, Bs[(size_t)jc * ds + r]);
                 if (tid == 0) {
-                    stcg(reinterpret_cast<double2 *>(rec2 + 4 * (size_t)cta), make_double2((double)c1[jc], (double)dg[jc]));
+                    T *rp = reinterpret_cast<T *>(rec2 + 4 * (size_t)cta);
+                    stcg(rp, c1[jc]);
+                    stcg(rp + 1, dg[jc]);
                     red_max_u64(keys + (g2 % KEY_RING), kl);
                 }
             }
@@ -537,8 +576,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 if (tid == 0) {
                     const T cv = c1[jc], l1 = cv * s_t[7];
                     const T dnew = fma(-cv, l1, dg[jc]);
-                    stcg(reinterpret_cast<double2 *>(spec_rec + (size_t)(par * G + cta) * 4),
-                         make_double2((double)dnew, (double)l1));
+                    T *rp = reinterpret_cast<T *>(spec_rec + (size_t)(par * G + cta) * 4);
+                    stcg(rp, dnew);
+                    stcg(rp + 1, l1);
                     red_max_u64(spec_keys + (g2 % KEY_RING), ks);
                 }
             }
@@ -570,21 +610,31 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 const unsigned long long key3 = spec ? ld_key(spec_keys + (g2 % KEY_RING)) : 0ull;
                 if (cta == 0) keys[(g2 + KEY_RING / 2) % KEY_RING] = 0ull;
                 int R = -1, LR = -1;
-                double lam = 0.0;
+                T lam = T(0);
                 if (key != 0ull) {
                     R = (int)(key & 0xFFFFull);
                     LR = 0xFFFF - (int)((key >> 16) & 0xFFFFull);
-                    lam = (double)__uint_as_float((unsigned)(key >> 32));
+                    lam = (T)__uint_as_float((unsigned)(key >> 32));
                 }
                 s_i[4] = R; s_i[5] = LR; s_i[6] = R >= 0 ? (R - k0) / chunk : 0;
-                s_d[2] = lam;
+                s_x[2] = lam;
+                // SBKP test on the FP32 values, in FP32
                 int kase;
                 if (!isfinite(lam)) kase = -1;
-                else if (lam == 0.0) kase = 0;
-                else if (fabs(akk) >= alpha * lam) kase = 1;
+                else if (lam == T(0)) kase = 0;
+                else if (fabs(akkT) >= (T)alpha * lam) kase = 1;
                 else kase = CASE_PENDING;
-                if (kase == CASE_PENDING) s_i[7] = CASE_PENDING;
-                else sbkp_scalars<T>(kase, akk, lam, 0.0, 0.0, alpha, s_i, s_d, s_t, s_t[7]);
+                if (kase == CASE_PENDING) {
+                    s_i[7] = CASE_PENDING;
+                } else {
+                    // cases (0)/(1): the 1x1 pivot a_kk and its reciprocal, no FP64 arithmetic
+                    s_i[7] = kase;
+                    s_t[0] = s_t[1] = s_t[2] = T(0);
+                    s_t[3] = T(1); s_t[4] = T(1);
+                    s_t[5] = akkT;
+                    s_t[6] = kase == 1 ? s_t[7] : T(0);
+                    s_i[8] = akkT != T(0);
+                }
                 s_i[9] = 0;
                 if (spec_keys && cta == 0) spec_keys[(g2 + KEY_RING / 2) % KEY_RING] = 0ull;
                 if (spec) {
@@ -593,7 +643,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                         s_i[10] = (int)(key3 & 0xFFFFull);
                         s_i[11] = 0xFFFF - (int)((key3 >> 16) & 0xFFFFull);
                         s_i[12] = (s_i[10] - k0) / chunk;
-                        s_d[6] = (double)__uint_as_float((unsigned)(key3 >> 32));
+                        s_x[6] = (T)__uint_as_float((unsigned)(key3 >> 32));
                     }
                 }
             }
@@ -631,8 +681,12 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             }
             const T pb = tid < d ? ldcg(spec_pay + (size_t)(par * G + gc2) * ps + tid) : T(0);
             const T pl = tid < i ? ldcg(w.Lg + (size_t)P2 * bw + tid) : T(0);
-            double2 prec = make_double2(0.0, 0.0);
-            if (tid == 0) prec = __ldcg(reinterpret_cast<const double2 *>(spec_rec + (size_t)(par * G + gc2) * 4));
+            T prec_d = T(0), prec_l = T(0);   // the next pivot's a_kk and L(P2, k), from its record
+            if (tid == 0) {
+                const T *rp = reinterpret_cast<const T *>(spec_rec + (size_t)(par * G + gc2) * 4);
+                prec_d = ldcg(rp);
+                prec_l = ldcg(rp + 1);
+            }
             for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
                 if (!alive[jl]) continue;
                 const int j = j_lo + jl;
@@ -658,10 +712,10 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 ckind[i] = (kase == 0 || !s_i[8]) ? 0 : 1;
                 cs0[i] = s_t[6];
                 if (cta == 0) {
-                    w.Dd[k] = akk; w.Ds[k] = 0.0;
-                    maxD = fmax(maxD, fabs(akk));
+                    w.Dd[k] = (double)akkT; w.Ds[k] = 0.0;
+                    maxDf = fmax(maxDf, fabs(akkT));
                     if (!s_i[8] && info == 0) info = k + 1;
-                    minnorm2 = fmin(minnorm2, s_d[6]);
+                    minnorm2f = fminf((float)minnorm2f, (float)s_x[6]);
                 }
                 // the next step: pivot P2 to position k + 1
                 const int kn = k + 1;
@@ -671,9 +725,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 if (P2 >= j_lo && P2 < j_lo + cnt) lp[P2 - j_lo] = kn;
                 if (Q != P2 && Q >= j_lo && Q < j_lo + cnt) lp[Q - j_lo] = LP2;
                 s_i[1] = P2; s_i[2] = LP2; s_i[3] = gc2;
-                s_d[0] = s_d[6];
-                s_d[8] = prec.x;            // a_kk of P2 after this step
-                lP[i] = (T)prec.y;          // L(P2, k)
+                s_x[0] = s_x[6];
+                s_x[8] = prec_d;            // a_kk of P2 after this step
+                lP[i] = prec_l;             // L(P2, k)
             }
             if (tid < d) bP[tid] = pb;
             if (tid < i) lP[tid] = pl;
@@ -690,12 +744,13 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         if (kase >= 2) {
             // column r of the Schur complement; in FP32 its record (a_rk, a_rr) arrives with the
             // column loads and thread 0 settles case 2 versus 3 right after them
-            const double lam = s_d[2];
             auto hook = [&]() {
-                if (KEYS) sbkp_scalars<T>(CASE_PENDING, akk, lam, s_d[10], s_d[11], alpha, s_i, s_d, s_t, s_t[7]);
+                if (KEYS)
+                    sbkp_scalars<T>(CASE_PENDING, (double)akkT, (double)s_x[2], (double)s_x[10], (double)s_x[11], alpha,
+                                    s_i, s_d, s_t, s_t[7]);
             };
             schur_column<T>(A, lda, j_lo, cnt, R, i, ws, Ws, pay2 + (size_t)gR * ps, bR, w.Lg + (size_t)R * bw, lR, d,
-                            alive, c2, rec2 + 4 * (size_t)gR, s_d + 10, KEYS ? 2 : 0, hook);
+                            alive, c2, reinterpret_cast<const T *>(rec2 + 4 * (size_t)gR), s_x + 10, KEYS ? 2 : 0, hook);
             kase = s_i[7];
             if (kase < 0) { fail = ST_NONFINITE; break; }
             if (tid == 0) {
@@ -770,17 +825,24 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                     T *col = Bs + (size_t)jl * ds;
                     if (w.qb) {
                         // q = b: the sketch is updated once per block, after the panel
-                    } else if (s == 2) {
-                        for (int r = sub; r < d; r += 4) {
-                            T v = col[r] - b1[r] * l1 - bR[r] * l2;
-                            col[r] = v;
-                            sacc = fma(v, v, sacc);
-                        }
                     } else {
-                        for (int r = sub; r < d; r += 4) {
-                            T v = col[r] - b1[r] * l1;
-                            col[r] = v;
-                            sacc = fma(v, v, sacc);
+                        // rows sub, sub+4, ...: five at a time, loads of a chunk before its stores
+                        for (int r0 = sub; r0 < d; r0 += 20) {
+                            T v[5], p1[5], p2[5];
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) {
+                                const int r = r0 + 4 * q;
+                                v[q] = r < d ? col[r] : T(0);
+                                p1[q] = r < d ? b1[r] : T(0);
+                                p2[q] = (r < d && s == 2) ? bR[r] : T(0);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) {
+                                const int r = r0 + 4 * q;
+                                const T x = v[q] - p1[q] * l1 - p2[q] * l2;
+                                if (r < d) col[r] = x;
+                                sacc = fma(x, x, sacc);
+                            }
                         }
                     }
                 }
@@ -808,13 +870,15 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             }
         }
         if (cta == 0 && tid == 0) {
+            const double akk_d = KEYS ? (double)akkT : akk;
             if (kase == 3) {
-                w.Dd[k] = akk; w.Ds[k] = ark; w.Dd[k + 1] = arr; w.Ds[k + 1] = 0.0;
-                maxD = fmax(maxD, fmax(fabs(akk), fmax(fabs(ark), fabs(arr))));
+                w.Dd[k] = akk_d; w.Ds[k] = ark; w.Dd[k + 1] = arr; w.Ds[k + 1] = 0.0;
+                maxD = fmax(maxD, fmax(fabs(akk_d), fmax(fabs(ark), fabs(arr))));
                 ++n2;
             } else {
-                w.Dd[k] = dpiv; w.Ds[k] = 0.0;
-                maxD = fmax(maxD, fabs(dpiv));
+                const double dp = KEYS ? (double)s_t[5] : dpiv;
+                w.Dd[k] = dp; w.Ds[k] = 0.0;
+                maxD = fmax(maxD, fabs(dp));
                 if (!nonzero_piv && info == 0) info = k + 1;
             }
         }
@@ -852,6 +916,14 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         if (lane == 0 && v > 0.0) atomic_max_nonneg(&w.st->maxL_bits, v);
     }
     if (tid == 0 && cta == 0) {
+        if (KEYS) {
+            if (beta2f > T(0)) {
+                beta2 = (double)beta2f;
+                w.st->beta2 = beta2;
+            }
+            minnorm2 = fmin(minnorm2, (double)minnorm2f);
+            maxD = fmax(maxD, (double)maxDf);
+        }
         if (fail) {
             atomicOr(w.status, fail);
             w.st->next = n;
