@@ -5,11 +5,14 @@
 // moved (at most twice the panel width).  For each moved index j with new position
 // p = lpos[j]:
 //   perm[p]              <- perm[j]
-//   L(p, 0:k0)           <- L(j, 0:k0)                (rows of the earlier L columns)
 //   A_sym(p, q), q >= kend <- A_sym(j, phi(q))         (only when p itself is >= kend)
 // done as a gather into scratch followed by a scatter (two launches, so no read sees a
 // half-written line).  Then the panel's multipliers go to A(:, k0:kend) in position order,
 // and the trailing update A22 -= W L21^T runs on the lower triangle of A(kend:n, kend:n).
+// The rows of the earlier L columns (L(p, 0:k0) <- L(j, 0:k0)) are not moved here: nothing
+// reads them before the factorization ends, so the permutation after every panel is recorded
+// and each panel's L columns are permuted once at the end (the deferred row interchanges of
+// blocked LAPACK factorizations), with column-contiguous accesses instead of strided rows.
 #include "kernels.h"
 
 namespace rcpk {
@@ -49,7 +52,7 @@ __global__ void gather_kernel(FactorWork<T> w, const int *phi) {
     if (ldcg(w.status) != 0) return;
     const int M = min(ldcg(&w.st->n_moved), w.maxmoved);
     const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
-    const int nl = (k0 + SEG - 1) / SEG, nt = (n - kend + SEG - 1) / SEG;
+    const int nl = 0, nt = (n - kend + SEG - 1) / SEG;   // L rows: deferred to the end
     const T *__restrict__ A = w.A;
     int m, part, seg;
     for (long long item = blockIdx.x; moved_item(item, M, nl, nt, &m, &part, &seg); item += gridDim.x) {
@@ -74,7 +77,7 @@ __global__ void scatter_kernel(FactorWork<T> w) {
     if (ldcg(w.status) != 0) return;
     const int M = min(ldcg(&w.st->n_moved), w.maxmoved);
     const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
-    const int nl = (k0 + SEG - 1) / SEG, nt = (n - kend + SEG - 1) / SEG;
+    const int nl = 0, nt = (n - kend + SEG - 1) / SEG;   // L rows: deferred to the end
     T *__restrict__ A = w.A;
     int m, part, seg;
     for (long long item = blockIdx.x; moved_item(item, M, nl, nt, &m, &part, &seg); item += gridDim.x) {
@@ -282,6 +285,76 @@ __global__ void factor_finish_kernel(FactorWork<T> w) {
         w.A[(size_t)i + (size_t)i * w.lda] = (T)w.Dd[i];
 }
 
+// perm and the panel bounds after panel blk (after its interchange kernels)
+template <typename T>
+__global__ void panel_record_kernel(FactorWork<T> w, int blk) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        w.pbounds[2 * blk] = w.st->k0;
+        w.pbounds[2 * blk + 1] = w.st->kend;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < w.n; i += gridDim.x * blockDim.x)
+        w.psnap[(size_t)blk * w.n + i] = w.perm[i];
+}
+
+template <typename T>
+__global__ void perm_inverse_kernel(FactorWork<T> w, int npanels) {
+    const long long total = (long long)npanels * w.n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int J = (int)(e / w.n), p = (int)(e % w.n);
+        const int v = w.psnap[e];
+        if ((unsigned)v < (unsigned)w.n) w.pinv[(size_t)J * w.n + v] = p;
+    }
+}
+
+// Column c of panel J = [k0, kend): the row at final position q >= kend is the row that sat at
+// position pinv_J[perm[q]] when panel J ended.  One CTA per column at a time; the column is
+// staged in this CTA's slice of the scratch (global, n entries) and gathered back.
+template <typename T>
+__global__ void lrows_permute_kernel(FactorWork<T> w, int npanels) {
+    if (ldcg(w.status) != 0) return;
+    const int n = w.n, lda = w.lda;
+    T *scr = w.tmpA + (size_t)blockIdx.x * n;
+    int J = 0;
+    for (int c = blockIdx.x; c < n; c += gridDim.x) {
+        while (J < npanels && w.pbounds[2 * J + 1] <= c) ++J;
+        if (J >= npanels) break;
+        const int k0 = w.pbounds[2 * J], kend = w.pbounds[2 * J + 1];
+        if (c < k0 || kend >= n) continue;
+        const int *inv = w.pinv + (size_t)J * n;
+        for (int q = kend + threadIdx.x; q < n; q += blockDim.x) scr[q] = w.A[(size_t)q + (size_t)c * lda];
+        __syncthreads();
+        for (int q = kend + threadIdx.x; q < n; q += blockDim.x) {
+            int src = inv[w.perm[q]];
+            if (src < kend || src >= n) src = q;   // cannot happen for a valid record
+            w.A[(size_t)q + (size_t)c * lda] = scr[src];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t launch_panel_record(const FactorWork<T> &w, int blk, cudaStream_t s) {
+    int blocks = (w.n + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 1024) blocks = 1024;
+    panel_record_kernel<T><<<blocks, 256, 0, s>>>(w, blk);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lrows_permute(const FactorWork<T> &w, int npanels, cudaStream_t s) {
+    if (w.n == 0 || npanels <= 0) return cudaSuccess;
+    perm_inverse_kernel<T><<<1024, 256, 0, s>>>(w, npanels);
+    count_launches(1);
+    // grid-stride over columns in increasing order, so each CTA's panel index only advances;
+    // the scratch holds maxmoved slices of n entries
+    int grid = w.n < w.maxmoved ? w.n : w.maxmoved;
+    lrows_permute_kernel<T><<<grid, 256, 0, s>>>(w, npanels);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_factor_init(const FactorWork<T> &w, cudaStream_t s) {
     int blocks = (w.n + 255) / 256;
@@ -305,6 +378,10 @@ cudaError_t launch_factor_finish(const FactorWork<T> &w, cudaStream_t s) {
 
 template cudaError_t launch_interchange<double>(const FactorWork<double> &, cudaStream_t);
 template cudaError_t launch_interchange<float>(const FactorWork<float> &, cudaStream_t);
+template cudaError_t launch_panel_record<double>(const FactorWork<double> &, int, cudaStream_t);
+template cudaError_t launch_panel_record<float>(const FactorWork<float> &, int, cudaStream_t);
+template cudaError_t launch_lrows_permute<double>(const FactorWork<double> &, int, cudaStream_t);
+template cudaError_t launch_lrows_permute<float>(const FactorWork<float> &, int, cudaStream_t);
 template cudaError_t launch_factor_init<double>(const FactorWork<double> &, cudaStream_t);
 template cudaError_t launch_factor_init<float>(const FactorWork<float> &, cudaStream_t);
 template cudaError_t launch_factor_finish<double>(const FactorWork<double> &, cudaStream_t);

@@ -48,6 +48,9 @@ struct FactorWork {
     float *tcops;                // tensor-core operand tiles (TF32x3 trailing update)
     int spec;                    // FP32 panel: speculative case-(1) path enabled (shadow sketch fits)
     double *s3v;                 // [2][grid][4] records of the speculative candidates
+    int *psnap;                  // [panels][n]: perm after each panel (deferred L-row interchanges)
+    int *pinv;                   // [panels][n]: their inverses
+    int *pbounds;                // [panels][2]: (k0, kend) of each panel
     int qb;                      // Algorithm 1 with q = b: the pivot of step k is the column at
                                  // position k (candidates chosen by the block QRCP); no per-step
                                  // sketch update (the block update follows the panel)
@@ -79,6 +82,13 @@ cudaError_t launch_trailing_tc(const FactorWork<float> &w, float *ops, int kmin,
 
 template <typename T>
 cudaError_t launch_factor_init(const FactorWork<T> &w, cudaStream_t s);
+
+// Deferred row interchanges of the L columns: record the permutation and bounds after panel
+// `blk`; at the end permute the rows of every panel's L columns once.
+template <typename T>
+cudaError_t launch_panel_record(const FactorWork<T> &w, int blk, cudaStream_t s);
+template <typename T>
+cudaError_t launch_lrows_permute(const FactorWork<T> &w, int npanels, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_factor_finish(const FactorWork<T> &w, cudaStream_t s);

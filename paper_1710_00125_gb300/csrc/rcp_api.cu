@@ -46,6 +46,7 @@ struct rcp_handle {
     Buf Y, flags, R, Dc, part;
     Buf A64, F, Bh, Xh, Dd, Ds, perm;              // rcp_sysv buffers
     Buf trace;                                     // per-step panel timestamps (profiling level 2)
+    Buf psnap, pinv, pbounds;                      // deferred L-row interchanges
     Buf keys;                                      // packed argmax keys of the FP32 panel
     Buf tcops;                                     // tensor-core operand tiles
     int trace_n = 0;
@@ -195,6 +196,10 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->tmpA, (size_t)r.maxmoved * NT * sizeof(T)));
     RCP_TRY(grow(h->tmpL, (size_t)r.maxmoved * NT * sizeof(T)));
     RCP_TRY(grow(h->tmpP, (size_t)r.maxmoved * sizeof(int)));
+    const size_t npan = (N + r.b - 1) / r.b;
+    RCP_TRY(grow(h->psnap, npan * N * sizeof(int)));
+    RCP_TRY(grow(h->pinv, npan * N * sizeof(int)));
+    RCP_TRY(grow(h->pbounds, 2 * npan * sizeof(int)));
     return RCP_OK;
 }
 
@@ -219,6 +224,9 @@ FactorWork<T> make_work(rcp_handle *h, int n, T *A, int lda, double *Dd, double 
     w.keys = (unsigned long long *)h->keys.p;
     w.spec = r.spec;
     w.qb = r.qb;
+    w.psnap = (int *)h->psnap.p;
+    w.pinv = (int *)h->pinv.p;
+    w.pbounds = (int *)h->pbounds.p;
     w.s3v = (double *)h->s3v.p;
     w.tcops = r.prec == RCP_TF32X3 ? (float *)h->tcops.p : nullptr;
     w.trace = nullptr;
@@ -310,6 +318,7 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
         {
             PhaseScope ps(h, s, PH_INTERCHANGE);
             CU_TRY(launch_interchange<T>(w, s));
+            CU_TRY(launch_panel_record<T>(w, blk, s));
         }
         {
             PhaseScope ps(h, s, PH_TRAILING);
@@ -319,6 +328,10 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
             PhaseScope ps(h, s, PH_SKETCH);
             CU_TRY(launch_block_sketch_update<T>(w, w.tmpL, s));
         }
+    }
+    {
+        PhaseScope ps(h, s, PH_INTERCHANGE);
+        CU_TRY(launch_lrows_permute<T>(w, nblk, s));
     }
     CU_TRY(launch_factor_finish<T>(w, s));
     if (!stats) return RCP_OK;
@@ -372,7 +385,7 @@ rcp_status rcp_create(rcp_handle **h) {
 
 void rcp_destroy(rcp_handle *h) {
     if (!h) return;
-    Buf *all[] = {&h->bord, &h->bom, &h->bticket, &h->bscr, &h->tcops, &h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
+    Buf *all[] = {&h->psnap, &h->pinv, &h->pbounds, &h->bord, &h->bom, &h->bticket, &h->bscr, &h->tcops, &h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
                   &h->s1v, &h->s2v, &h->s3v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
                   &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm};
     for (Buf *b : all)
