@@ -31,7 +31,6 @@ constexpr int TM = 128;              // tile rows (M) and columns (N)
 constexpr int KC = 32;               // K chunk: 32 tf32 = one 128-byte swizzle row
 constexpr int TILE_FLOATS = TM * KC; // 4096 floats = 16 KB
 constexpr int STAGES = 3;
-constexpr int THREADS = 128;
 constexpr uint32_t STAGE_BYTES = 4u * TILE_FLOATS * 4u;   // W_hi, W_lo, L_hi, L_lo
 
 // Offset (in floats) of element (m, k) of a 128 x 32 K-major tile in the 128-byte swizzle
@@ -179,21 +178,27 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(FactorWork<float> w, float
 // ------------------------------------------------------------------------------------------
 // tcgen05 MMA kernel, warp-specialized.  Warp 0 (one elected thread) streams operand chunks
 // through the stage ring and issues the MMAs of each tile into one of two 128-column TMEM
-// accumulators; warps 1..4 drain the other accumulator (tcgen05.ld, lane quarter w % 4) and
-// update A, so the epilogue of tile t overlaps the MMAs of tile t + 1.
+// accumulators; warps 1..8 drain the other accumulator (tcgen05.ld: lane quarter w % 4, a
+// 64-column half each) and update A, so the epilogue of tile t overlaps the MMAs of tile t + 1.
+// Each epilogue warp reads its 32 x 64 block of A in four 16-column chunks, two chunks ahead:
+// the first two are loaded before it waits for the accumulator, so the HBM latency of the
+// read-modify-write stays behind the tile's MMAs.
 //   full[s]  : operands of the chunk in stage s arrived (bulk-copy transaction count)
 //   free[s]  : the MMAs reading stage s completed (tcgen05.commit)
 //   accf[a]  : accumulator a holds a finished tile (tcgen05.commit)
 //   acce[a]  : the epilogue has read accumulator a (one arrival per epilogue warp)
 // ------------------------------------------------------------------------------------------
-constexpr int TC_THREADS = 160;
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_EPI_COLS = tc::TM * 4 / TC_EPI_WARPS;   // columns per epilogue warp
+constexpr int TC_THREADS = 32 * (1 + TC_EPI_WARPS);
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void tile_ij(long long tile, int *I, int *J) {
-    int a = (int)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+    // FP32 estimate, corrected in integers (no FP64 on this part's slow FP64 pipe)
+    int a = (int)((sqrtf(8.f * (float)tile + 1.f) - 1.f) * 0.5f);
     while ((long long)a * (a + 1) / 2 > tile) --a;
     while ((long long)(a + 1) * (a + 2) / 2 <= tile) ++a;
     *I = a;
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
 
     if (tid == 0) {
         for (int s = 0; s < tc::STAGES; ++s) { tc::mbar_init(&full_bar[s], 1); tc::mbar_init(&free_bar[s], 1); }
-        for (int a = 0; a < 2; ++a) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], 4); }
+        for (int a = 0; a < 2; ++a) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], TC_EPI_WARPS); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
@@ -321,12 +326,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
             }
         }
     } else {
-        // ---------------- epilogue warps: lane quarter q of the accumulator ----------------
-        const int q = warp & 3;
+        // ---------------- epilogue warps: lane quarter q, columns h*EC .. h*EC+EC-1 ----------------
+        constexpr int EC = TC_EPI_COLS;
+        const int q = warp & 3, h = (warp - 1) >> 2;
         uint32_t accf_ph[2] = {0, 0};
         float *__restrict__ A = w.A;
         for (int lt = 0; lt < ntiles; ++lt) {
             const int a = lt & 1;
+            int I, J;
+            tile_ij(blockIdx.x + (long long)lt * gridDim.x, &I, &J);
+            const int p = kend + I * tc::TM + q * 32 + lane;
+            const int q0 = kend + J * tc::TM + h * EC;
+            // chunks 0 and 1 of the block of A this warp updates, loaded while the MMAs run
+            const bool rowok = p < n;
+            float *blk = A + (size_t)(rowok ? p : 0) + (size_t)q0 * lda;
+            float c0v[16], c1v[16];
+            auto load16 = [&](float (&dst)[16], int cb) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int qq = q0 + cb + j;
+                    dst[j] = (rowok && qq < n && p >= qq) ? blk[(unsigned)((cb + j) * lda)] : 0.f;
+                }
+            };
+            auto finish16 = [&](float (&src)[16], int cb, uint32_t taddr) {
+                uint32_t r[16];
+                tc::tmem_ld16(taddr + cb, r);
+                tc::tmem_wait_ld();
+                if (rowok) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int qq = q0 + cb + j;
+                        if (qq < n && p >= qq) blk[(unsigned)((cb + j) * lda)] = src[j] - __uint_as_float(r[j]);
+                    }
+                }
+            };
+            load16(c0v, 0);
+            load16(c1v, 16);
             bool ok = tc::mbar_wait(&accf[a], accf_ph[a]);
             accf_ph[a] ^= 1u;
             if (!ok || *(volatile int *)&s_abort) {
@@ -334,31 +369,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
                 break;
             }
             tc::tc_fence_after();
-            int I, J;
-            tile_ij(blockIdx.x + (long long)lt * gridDim.x, &I, &J);
-            const int p = kend + I * tc::TM + q * 32 + lane;
-            const int q0 = kend + J * tc::TM;
-            for (int c0 = 0; c0 < tc::TM; c0 += 16) {
-                uint32_t r[16];
-                tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * tc::TM + c0), r);
-                tc::tmem_wait_ld();
-                if (p < n) {
-                    float cv[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int qq = q0 + c0 + j;
-                        cv[j] = (qq < n && p >= qq) ? A[(size_t)p + (size_t)qq * lda] : 0.f;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int qq = q0 + c0 + j;
-                        if (qq < n && p >= qq) A[(size_t)p + (size_t)qq * lda] = cv[j] - __uint_as_float(r[j]);
-                    }
-                }
-            }
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * tc::TM + h * EC);
+            static_assert(EC == 64, "four 16-column chunks per epilogue warp");
+            finish16(c0v, 0, taddr);
+            load16(c0v, 32);
+            finish16(c1v, 16, taddr);
+            load16(c1v, 48);
+            finish16(c0v, 32, taddr);
+            finish16(c1v, 48, taddr);
             tc::tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[a]);
+            if (lane == 0) mbar_arrive(&acce[a]);   // the accumulator may be reused
         }
     }
     tc::tc_fence_before();
