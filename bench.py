@@ -67,7 +67,7 @@ def workload_name(a):
 
 def batched_workload_name(a):
     return (f"C5: {a.batch} systems, n_i ~ U{{32..512}} (seeded), A_i = (G_i + G_i^T)/2 with G_i N(0,1), "
-            f"16 RHS b_i = A_i x_i; FP32 factor (b=32, d=40) + FP64 refinement to berr<={a.tol:g}, "
+            f"16 RHS b_i = A_i x_i; FP32 factor (d=40, panel width autotuned) + FP64 refinement to berr<={a.tol:g}, "
             f"one persistent launch per phase, replayed from a CUDA graph")
 
 
@@ -343,7 +343,9 @@ def run_batched(a, dev, stream, rank, world, dist):
     inputs.fill_batched_gaussian_device(sizes, bt.off_sq, bt.A64_pool, seed=rank)
     inputs.fill_batched_rhs_device(sizes, bt.off_sq, bt.A64_pool, bt.off_rhs, bt.B_pool, nrhs, seed=rank)
     h = rcp.rcp_create()
-    opts = rcp.make_opts(b=32, d=40, seed=rank, prec="fp32")
+    # the autotuner picks the panel width on this batch; b = 0 then selects it
+    tuned_b, tuned_ms = bt.tune(h, rcp.make_opts(b=0, d=40, seed=rank, prec="fp32"))
+    opts = rcp.make_opts(b=0, d=40, seed=rank, prec="fp32")
     s = torch.cuda.Stream(device=dev)
     s.wait_stream(stream)
     with torch.cuda.stream(s):
@@ -399,7 +401,7 @@ def run_batched(a, dev, stream, rank, world, dist):
             "factor_ms": f0.elapsed_time(f1), "refine_ms": ref_ms,
             "berr_max": float(berr.max()), "all_berr_le_tol": bool((berr <= a.tol).all()),
             "info_nonzero": int((info != 0).sum()), "refine_iters_hist": np.bincount(iters).tolist(),
-            "gpu_launches_per_replay": 2, "steps": a.batch_steps, "roofline": roof}
+            "gpu_launches_per_replay": 2, "steps": a.batch_steps, "tuned_b": tuned_b, "roofline": roof}
 
 
 def roofline_for(name, ms, launches, a, hbm_peak, peaks, peak_src):

@@ -55,6 +55,8 @@ struct rcp_handle {
     int bord_batch = -1, bord_nmax = -1;
     uint64_t bom_seed = 0;                         // (seed, d, nmax, fp64) of the drawn Omega
     int bom_d = -1, bom_nmax = -1, bom_f64 = -1;
+    struct Tuned { int nmax, d, f64, b; };
+    std::vector<Tuned> tuned;                      // batched panel widths chosen by rcp_tune_batched
 };
 
 namespace {
@@ -598,8 +600,11 @@ rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, 
     const rcp_prec prec = opts ? opts->prec : RCP_FP64;
     if (!valid_prec(prec)) return RCP_EINVAL;
     const bool f64 = prec == RCP_FP64;
-    const int b = (opts && opts->b > 0) ? opts->b : 32;
+    int b = (opts && opts->b > 0) ? opts->b : 32;
     const int d = (opts && opts->d > 0) ? opts->d : std::min(b + 8, 128);
+    if (!(opts && opts->b > 0))
+        for (const auto &t : h->tuned)
+            if (t.nmax == nmax && t.d == d && t.f64 == (int)f64) b = t.b;   // the autotuned width
     if (opts && opts->q_mode != 0 && opts->q_mode != 1) return RCP_EUNSUPPORTED;
     if (b > 512 || d > 128) return RCP_EUNSUPPORTED;
     const double alpha = (opts && opts->alpha > 0.0) ? opts->alpha : std::sqrt(2.0) / 2.0;
@@ -634,6 +639,54 @@ rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, 
         CU_TRY(launch_batched_factor<float>(batch, d, b, nmax, n, A64, lda64, (float *const *)A, lda, Dd, Ds, perm,
                                             (const float *)om, alpha, info, (const int *)h->bord.p,
                                             (int *)h->bticket.p, (int *)h->bscr.p, grid, s));
+    return RCP_OK;
+}
+
+rcp_status rcp_tune_batched(rcp_handle *h, int batch, int nmax, const int *n, const double *const *A64,
+                            const int *lda64, void *const *A, const int *lda, double *const *Dd, double *const *Ds,
+                            int *const *perm, const rcp_opts *opts, int *info, rcp_stream_t stream, int *best_b,
+                            float *best_ms) {
+    if (!h || !A64 || batch <= 0 || nmax <= 0) return RCP_EINVAL;
+    const rcp_prec prec = opts ? opts->prec : RCP_FP64;
+    if (!valid_prec(prec)) return RCP_EINVAL;
+    const bool f64 = prec == RCP_FP64;
+    const int d = (opts && opts->d > 0) ? opts->d : 40;
+    cudaStream_t s = (cudaStream_t)stream;
+    rcp_opts o = opts ? *opts : rcp_opts{};
+    o.d = d;
+    o.prec = prec;
+    static const int cand[] = {8, 12, 16, 24, 32, 48, 64};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU_TRY(cudaEventCreate(&e0));
+    CU_TRY(cudaEventCreate(&e1));
+    int bb = 0;
+    float bms = 0.f;
+    rcp_status err = RCP_OK;
+    for (int b : cand) {
+        const size_t smem = f64 ? batched_factor_smem<double>(d, b, nmax) : batched_factor_smem<float>(d, b, nmax);
+        if (smem > batched_max_smem()) continue;
+        o.b = b;
+        err = rcp_factor_batched(h, batch, nmax, n, A64, lda64, A, lda, Dd, Ds, perm, &o, info, stream);   // warm-up
+        if (err != RCP_OK) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { err = RCP_ECUDA; break; }
+        err = rcp_factor_batched(h, batch, nmax, n, A64, lda64, A, lda, Dd, Ds, perm, &o, info, stream);
+        if (err != RCP_OK) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { err = RCP_ECUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (bb == 0 || ms < bms) { bb = b; bms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    if (err != RCP_OK) return err;
+    if (bb == 0) return RCP_EUNSUPPORTED;
+    bool found = false;
+    for (auto &t : h->tuned)
+        if (t.nmax == nmax && t.d == d && t.f64 == (int)f64) { t.b = bb; found = true; }
+    if (!found) h->tuned.push_back({nmax, d, (int)f64, bb});
+    if (best_b) *best_b = bb;
+    if (best_ms) *best_ms = bms;
     return RCP_OK;
 }
 

@@ -90,6 +90,9 @@ def lib():
         L.rcp_factor_batched.argtypes = [P, I, I, P, P, P, P, P, P, P, P, ctypes.POINTER(Opts), P, P]
         L.rcp_refine_batched.argtypes = [P, I, I, I, P, P, P, P, P, P, P, P, I, P, P, P, P, D, I, P, P, P]
         L.rcp_factor_batched.restype = ctypes.c_int
+        L.rcp_tune_batched.argtypes = [P, I, I, P, P, P, P, P, P, P, P, ctypes.POINTER(Opts), P, P,
+                                       ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]
+        L.rcp_tune_batched.restype = ctypes.c_int
         L.rcp_refine_batched.restype = ctypes.c_int
         for name in ("rcp_profile", "rcp_profile_read", "rcp_create", "rcp_sync", "rcp_reserve", "rcp_factor", "rcp_solve", "rcp_refine", "rcp_sysv",
                      "rcp_omega", "rcp_sketch"):
@@ -397,6 +400,18 @@ class Batch:
         rcp_factor_batched(h, self.batch, self.nmax, self.n, self.p_A64 if from_a64 else None,
                            self.ld if from_a64 else None, self.p_F, self.ld, self.p_Dd, self.p_Ds, self.p_perm,
                            opts, self.info, stream)
+
+    def tune(self, h: Handle, opts: Opts | None = None, stream=None):
+        """rcp_tune_batched on this batch: returns (chosen b, its factor time in ms); later
+        factor() calls with opts.b == 0 use the choice."""
+        if opts is None:
+            opts = Opts(b=0, d=40, q_mode=1, seed=0, prec=self.prec, alpha=math.sqrt(2.0) / 2.0, omega=None, grid=0)
+        bb, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+        _check(lib().rcp_tune_batched(h.h, self.batch, self.nmax, _ptr(self.n), _ptr(self.p_A64), _ptr(self.ld),
+                                      _ptr(self.p_F), _ptr(self.ld), _ptr(self.p_Dd), _ptr(self.p_Ds),
+                                      _ptr(self.p_perm), ctypes.byref(opts), _ptr(self.info), _stream(stream),
+                                      ctypes.byref(bb), ctypes.byref(ms)), "rcp_tune_batched")
+        return bb.value, ms.value
 
     def refine(self, h: Handle, tol=1e-12, max_iter=10, refine=True, stream=None) -> None:
         """rcp_refine_batched: X = solve(B), then FP64 refinement when ``refine``."""

@@ -246,3 +246,22 @@ def test_batched_invalid_arguments(rcp, handle):
         rcp.rcp_factor_batched(handle, 2, 20, bt.n, None, None, bt.p_F, bt.ld, bt.p_Dd, bt.p_Ds, bt.p_perm,
                                _opts(rcp, "fp64", b=32, d=129), bt.info)
     assert e.value.code == -7
+
+
+def test_batched_autotuner(rcp, handle):
+    sizes = inputs.batched_sizes(20, 32, 300, seed=5).tolist()
+    mats = inputs.batched_gaussian(sizes, seed=5)
+    bt = rcp.Batch(sizes, 1, prec="fp32", device=DEV)
+    _load(bt, mats)
+    b, ms = bt.tune(handle, rcp.make_opts(b=0, d=40, seed=2, prec="fp32"))
+    assert b in (8, 12, 16, 24, 32, 48, 64) and ms > 0
+    bt.factor(handle, rcp.make_opts(b=0, d=40, seed=2, prec="fp32"))   # uses the tuned width
+    torch.cuda.synchronize()
+    assert (bt.info == 0).all()
+    for i, a in enumerate(mats):
+        n = a.shape[0]
+        L = _unit_lower(bt.f(i))
+        D = oracle.block_d(bt.dd(i).cpu().numpy(), bt.ds(i).cpu().numpy())
+        p = bt.perm(i).cpu().numpy()
+        growth = oracle.growth_d(bt.dd(i).cpu().numpy(), bt.ds(i).cpu().numpy(), a)
+        assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() / np.abs(a).max() < 2e-5 * max(1.0, growth)
