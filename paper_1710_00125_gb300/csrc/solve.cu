@@ -35,6 +35,38 @@ __device__ __forceinline__ bool wait_flag(const int *flag, int epoch, int *statu
     return s_ok != 0;
 }
 
+// Blocks finish in dependency order (block J is done only after every block it depends on), so
+// once the flag of block J is set, warp 0 reads the next 32 flags in one round and returns the
+// last block of the finished run: J + m, m = number of consecutive set flags after J, stepping by
+// `dir` (+1 forward, -1 backward) and not past `last`.  -1 on a timeout.
+__device__ __forceinline__ int wait_run(const int *flags, int J, int last, int dir, int epoch, int *status) {
+    __shared__ int s_known;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int ok = 1;
+        if (lane == 0 && ld_acquire_s32(flags + J) != epoch) {
+            unsigned long long t0 = global_ns();
+            unsigned spins = 0;
+            while (ld_acquire_s32(flags + J) != epoch) {
+                if ((++spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+                    ok = 0;
+                    atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        const int j = J + dir * (lane + 1);
+        const bool in = dir > 0 ? j <= last : j >= last;
+        const bool set = ok && in && ld_acquire_s32(flags + j) == epoch;
+        const unsigned bal = __ballot_sync(0xffffffffu, set);
+        const int m = bal == 0xffffffffu ? 32 : __ffs(~bal) - 1;
+        if (lane == 0) s_known = ok ? J + dir * m : -1;
+    }
+    __syncthreads();
+    return s_known;
+}
+
 // acc[r][c] -= sum_jj M(r, jj) y[jj][c] with M given by (Ms, transposed?) in shared memory.
 template <typename T, bool TRANS>
 __device__ __forceinline__ void block_gemv_sub(T (*acc)[SV_RC], const T (*Ms)[SV_NB + 1], const T (*ys)[SV_RC],
@@ -111,6 +143,29 @@ __device__ __forceinline__ void tile_store(const T (&reg)[TILE_PER_THREAD], T (*
     }
 }
 
+// y of one finished block (SV_NB x SV_RC, rows past nj and columns past rc zero) through
+// registers, so that it can be loaded a tile ahead.
+constexpr int YS_PER_THREAD = SV_NB * SV_RC / SV_THREADS;
+
+template <typename T>
+__device__ __forceinline__ void ys_load(T (&reg)[YS_PER_THREAD], const T *Y, int n, int j0, int nj, int c0, int rc) {
+#pragma unroll
+    for (int u = 0; u < YS_PER_THREAD; ++u) {
+        const int e = threadIdx.x + u * SV_THREADS;
+        const int jj = e % SV_NB, c = e / SV_NB;
+        reg[u] = (jj < nj && c < rc) ? ldcg(Y + (size_t)(j0 + jj) + (size_t)(c0 + c) * n) : T(0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void ys_store(const T (&reg)[YS_PER_THREAD], T (*ys)[SV_RC]) {
+#pragma unroll
+    for (int u = 0; u < YS_PER_THREAD; ++u) {
+        const int e = threadIdx.x + u * SV_THREADS;
+        ys[e % SV_NB][e / SV_NB] = reg[u];
+    }
+}
+
 // Forward: L y = Pi^T x (L unit lower).  Y (work, type T, n x nrhs, ld n) receives y.  The next
 // tile of L is loaded into registers before the flag of the block it multiplies is awaited, and
 // the diagonal block is applied through its precomputed inverse (a GEMV, not a sequential sweep).
@@ -139,17 +194,25 @@ fwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const T *__restric
                 int r = e % SV_NB, c = e / SV_NB;
                 acc[r][c] = (r < nr && c < rc) ? (T)X[(size_t)perm[r0 + r] + (size_t)(c0 + c) * ldx] : T(0);
             }
+            // the inverse of the diagonal block, needed last, is loaded first
+            T lreg[TILE_PER_THREAD];
+            tile_load(lreg, Linv + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
             T cur[TILE_PER_THREAD], nxt[TILE_PER_THREAD];
+            T ysr[YS_PER_THREAD];   // y of the next finished block, prefetched
+            bool have = false;
+            int known = -1;         // every block <= known is finished
             if (I > 0) tile_load(cur, L, lda, r0, 0, nr, SV_NB);
             for (int J = 0; J < I; ++J) {
                 if (J + 1 < I) tile_load(nxt, L, lda, r0, (J + 1) * SV_NB, nr, SV_NB);
                 tile_store(cur, Ms);
-                if (!wait_flag<T>(flags + J, epoch, status)) return;
-                const int j0 = J * SV_NB;
-                for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
-                    int jj = e % SV_NB, c = e / SV_NB;
-                    ys[jj][c] = c < rc ? ldcg(Y + (size_t)(j0 + jj) + (size_t)(c0 + c) * n) : T(0);
+                if (J > known) {
+                    known = wait_run(flags, J, I - 1, 1, epoch, status);
+                    if (known < 0) return;
                 }
+                if (!have) ys_load<T>(ysr, Y, n, J * SV_NB, SV_NB, c0, rc);
+                ys_store<T>(ysr, ys);
+                have = J + 1 < I && J + 1 <= known;
+                if (have) ys_load<T>(ysr, Y, n, (J + 1) * SV_NB, SV_NB, c0, rc);
                 __syncthreads();
                 block_gemv_sub<T, false>(acc, Ms, ys, nr, SV_NB, rc);
                 __syncthreads();
@@ -157,11 +220,7 @@ fwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const T *__restric
                 for (int u = 0; u < TILE_PER_THREAD; ++u) cur[u] = nxt[u];
             }
             // y_I = L_II^{-1} acc
-            {
-                T reg[TILE_PER_THREAD];
-                tile_load(reg, Linv + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
-                tile_store(reg, Ms);
-            }
+            tile_store(lreg, Ms);
             for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
                 int r = e % SV_NB, c = e / SV_NB;
                 ys[r][c] = acc[r][c];
@@ -234,17 +293,25 @@ bwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const T *__restric
                 acc[r][c] = (r < nr && c < rc) ? ldcg(Y + (size_t)(r0 + r) + (size_t)(c0 + c) * n) : T(0);
             }
             // tiles L(J, I) for J = nb-1 down to I+1, Ms[jj][r] = L(j0 + jj, r0 + r)
+            T lreg[TILE_PER_THREAD];
+            tile_load(lreg, Linv + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
             T cur[TILE_PER_THREAD], nxt[TILE_PER_THREAD];
+            T ysr[YS_PER_THREAD];
+            bool have = false;
+            int known = nb;         // every block >= known is finished
             if (I + 1 < nb) tile_load(cur, L, lda, (nb - 1) * SV_NB, r0, min(SV_NB, n - (nb - 1) * SV_NB), nr);
             for (int J = nb - 1; J > I; --J) {
                 if (J - 1 > I) tile_load(nxt, L, lda, (J - 1) * SV_NB, r0, min(SV_NB, n - (J - 1) * SV_NB), nr);
                 tile_store(cur, Ms);
-                if (!wait_flag<T>(flags + J, epoch, status)) return;
-                const int j0 = J * SV_NB, nj = min(SV_NB, n - j0);
-                for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
-                    int jj = e % SV_NB, c = e / SV_NB;
-                    ys[jj][c] = (jj < nj && c < rc) ? ldcg(Y + (size_t)(j0 + jj) + (size_t)(c0 + c) * n) : T(0);
+                if (J < known) {
+                    known = wait_run(flags, J, I + 1, -1, epoch, status);
+                    if (known < 0) return;
                 }
+                const int j0 = J * SV_NB, nj = min(SV_NB, n - j0);
+                if (!have) ys_load<T>(ysr, Y, n, j0, nj, c0, rc);
+                ys_store<T>(ysr, ys);
+                have = J - 1 > I && J - 1 >= known;
+                if (have) ys_load<T>(ysr, Y, n, (J - 1) * SV_NB, min(SV_NB, n - (J - 1) * SV_NB), c0, rc);
                 __syncthreads();
                 block_gemv_sub<T, true>(acc, Ms, ys, nr, nj, rc);
                 __syncthreads();
@@ -252,11 +319,7 @@ bwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const T *__restric
                 for (int u = 0; u < TILE_PER_THREAD; ++u) cur[u] = nxt[u];
             }
             // v_I = (L_II^{-1})^T acc: Ms[jj][r] = Linv(jj, r) used transposed
-            {
-                T reg[TILE_PER_THREAD];
-                tile_load(reg, Linv + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
-                tile_store(reg, Ms);
-            }
+            tile_store(lreg, Ms);
             for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
                 int r = e % SV_NB, c = e / SV_NB;
                 ys[r][c] = acc[r][c];
