@@ -344,3 +344,76 @@ def test_qb_mixed_refine_reaches_fp64_backward_error(rcp, handle, prec):
     code, rst = rcp.rcp_refine(handle, A64, A, Dd, Ds, perm, prec, Bv, X, tol=1e-12, max_iter=30)
     assert code == 0, rst.as_dict()
     assert oracle.berr(a, X.cpu().numpy().T, rhs.T) <= 1e-12
+
+
+# ------------------------------------------------------------------------------------------
+# full sizes, in the bench's launch configuration: sampled entries of P^T A P - L D L^T (each
+# computed in FP64 from one row of L), and the FP64 backward error of the refined solution
+# ------------------------------------------------------------------------------------------
+
+def _sampled_reconstruction(A64, LA, Dd, Ds, perm, samples=512, seed=0):
+    """max over sampled (i, j), i >= j, of |A(perm[i], perm[j]) - (L D L^T)(i, j)| / max|A|."""
+    n = A64.shape[0]
+    g = np.random.default_rng(seed)
+    ii = g.integers(0, n, samples)
+    jj = g.integers(0, n, samples)
+    i_t = torch.from_numpy(np.maximum(ii, jj)).to(DEV)
+    j_t = torch.from_numpy(np.minimum(ii, jj)).to(DEV)
+    # rows of L (unit lower, stored in the library's lower triangle = the tensor's upper one)
+    Lr = lambda idx: torch.where(torch.arange(n, device=DEV)[None, :] < idx[:, None], LA.t()[idx].double(),
+                                 (torch.arange(n, device=DEV)[None, :] == idx[:, None]).double())
+    li, lj = Lr(i_t), Lr(j_t)
+    # (L D)(i, :) with D block diagonal: D(k, k) = Dd[k], D(k+1, k) = D(k, k+1) = Ds[k]
+    ds_up = torch.cat([torch.zeros(1, dtype=torch.float64, device=DEV), Ds[:-1]])
+    ld = li * Dd[None, :] + torch.roll(li, -1, 1) * Ds[None, :] + torch.roll(li, 1, 1) * ds_up[None, :]
+    rec = (ld * lj).sum(1)
+    p = perm.long()
+    a = A64[p[i_t], p[j_t]]
+    return float((a - rec).abs().max() / A64.abs().max())
+
+
+@pytest.mark.parametrize("prec", ["tf32x3"])
+def test_full_size_mixed_n16384(rcp, handle, prec):
+    n = 16384
+    A64 = inputs.spectrum(n, seed=0, kexp=4.0, nrefl=64, device=DEV)
+    xt = torch.from_numpy(inputs.x_true(n, 1, seed=0)).to(DEV)
+    Bv = (A64 @ xt.T).T.contiguous()
+    X = torch.zeros_like(Bv)
+    opts = rcp.make_opts(b=256, d=80, seed=0, prec=prec)
+    code, st = rcp.rcp_sysv(handle, A64, Bv, X, opts, tol=1e-12, max_iter=10)
+    assert code == 0 and st.berr <= 1e-12
+    r = Bv - (A64 @ X.T).T
+    berr = float((r.abs().amax() / (A64.abs().sum(1).amax() * X.abs().amax())))
+    assert berr <= 4e-12
+    # the FP32 factor itself
+    A = A64.float().contiguous()
+    Dd = torch.zeros(n, dtype=torch.float64, device=DEV)
+    Ds = torch.zeros_like(Dd)
+    perm = torch.zeros(n, dtype=torch.int32, device=DEV)
+    code, fst = rcp.rcp_factor(handle, A, Dd, Ds, perm, opts)
+    assert code == 0
+    assert torch.equal(torch.sort(perm.long())[0], torch.arange(n, device=DEV))
+    assert _sampled_reconstruction(A64, A, Dd, Ds, perm) < 1e-4 * max(1.0, fst.growth_D)
+
+
+def test_full_size_fp64_n8192(rcp, handle):
+    n = 8192
+    A64 = torch.from_numpy(inputs.gaussian_sym(n, seed=0)).to(DEV)
+    A = A64.clone()
+    Dd = torch.zeros(n, dtype=torch.float64, device=DEV)
+    Ds = torch.zeros_like(Dd)
+    perm = torch.zeros(n, dtype=torch.int32, device=DEV)
+    code, st = rcp.rcp_factor(handle, A, Dd, Ds, perm, rcp.make_opts(b=64, d=80, seed=0, prec="fp64"))
+    assert code == 0
+    assert torch.equal(torch.sort(perm.long())[0], torch.arange(n, device=DEV))
+    assert _sampled_reconstruction(A64, A, Dd, Ds, perm) < 1e-12 * max(1.0, st.growth_D) * n / 64
+    # complete-pivoting-like bounds of Section 4 hold comfortably: modest growth and |L|
+    assert st.growth_D < 100.0 and st.max_abs_L < 50.0
+    xt = torch.from_numpy(inputs.x_true(n, 32, seed=1)).to(DEV)
+    Bv = (A64 @ xt.T).T.contiguous()
+    X = Bv.clone()
+    rcp.rcp_solve(handle, A, Dd, Ds, perm, "fp64", X)
+    torch.cuda.synchronize()
+    r = Bv - (A64 @ X.T).T
+    berr = float((r.abs().amax(1) / (A64.abs().sum(1).amax() * X.abs().amax(1))).amax())
+    assert berr <= 1e-13
