@@ -177,11 +177,12 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
  */
 rcp_status rcp_profile(rcp_handle *h, int enable);
 
-/* With rcp_profile(h, 2), the next factorizations also record, for every pivot position k, ten
- * SM clock stamps (clock64 of one thread of the first CTA) at fixed points of the panel step
- * (top, before/after barrier 1, Schur column P, before/after barrier 2, decision, column r,
- * multipliers, sketch update).  rcp_panel_trace copies up to cap stamps (10 per position, zero
- * where a step started at another position) of the last such factorization. */
+/* With rcp_profile(h, 2), the next factorizations also record, for every pivot position k,
+ * sixteen SM clock stamps (clock64 of one thread of the first CTA) at fixed points of the panel
+ * step (top, before/after barrier 1, Schur column P, before/after barrier 2, decision, column r,
+ * multipliers, sketch update, and inside the argmax and the committed speculation).
+ * rcp_panel_trace copies up to cap stamps (16 per position, zero where a step started at
+ * another position or a point was not reached) of the last such factorization. */
 rcp_status rcp_panel_trace(rcp_handle *h, unsigned long long *out, int cap);
 
 /* Number of kernels this library has launched in the process so far (all handles). */

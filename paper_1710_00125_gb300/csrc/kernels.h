@@ -7,6 +7,9 @@
 
 namespace rcpk {
 
+// clock64 stamps per pivot position in the panel trace (profiling level 2)
+constexpr int PANEL_TRACE_SLOTS = 16;
+
 template <typename T>
 cudaError_t launch_omega(int d, int n, uint64_t seed, T *om, cudaStream_t s);
 

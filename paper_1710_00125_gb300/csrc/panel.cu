@@ -172,9 +172,9 @@ constexpr int KEY_RING = 16;
 
 // Block-wide maximum of two packed keys per thread (the result to every thread): per warp two
 // 32-bit redux.sync per key (high word, then the low word among the lanes holding the maximal
-// high word), per block one shared 64-bit atomicMax per key and warp.  Three slot pairs are
-// used in rotation (call counter `cnt`, uniform over the block): the pair of the next call,
-// last read two barriers ago, is cleared here, so one barrier per call suffices.
+// high word), one shared slot per key and warp, and the same warp reduction over the slots.
+// Two slot sets are used in alternation (call counter `cnt`, uniform over the block): the set
+// of call c is rewritten at call c + 2, after the CTA barrier of call c + 1.
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
     const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
     const unsigned m = __reduce_max_sync(FULL, hi);
@@ -182,22 +182,22 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return ((unsigned long long)m << 32) | l;
 }
 
+constexpr int RED2_SLOTS = 4 * (PANEL_THREADS / 32);   // [2 sets][2 keys][warps]
+
 __device__ __forceinline__ void block_max2_u64(unsigned long long &a, unsigned long long &b, unsigned long long *red,
                                                int &cnt) {
+    constexpr int W = PANEL_THREADS / 32;
+    static_assert(W <= 32, "one warp reduces the per-warp slots");
     const unsigned long long wa = warp_max_u64(a), wb = warp_max_u64(b);
-    const int slot = cnt % 3;
-    if (threadIdx.x == 0) {
-        const int nx = (cnt + 1) % 3;
-        red[2 * nx] = 0ull;
-        red[2 * nx + 1] = 0ull;
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (wa) atomicMax(red + 2 * slot, wa);
-        if (wb) atomicMax(red + 2 * slot + 1, wb);
+    unsigned long long *set = red + (cnt & 1) * 2 * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        set[warp] = wa;
+        set[W + warp] = wb;
     }
     __syncthreads();
-    a = red[2 * slot];
-    b = red[2 * slot + 1];
+    a = warp_max_u64(lane < W ? set[lane] : 0ull);
+    b = warp_max_u64(lane < W ? set[W + lane] : 0ull);
     ++cnt;
 }
 
@@ -260,6 +260,15 @@ __device__ void schur_column(const T *__restrict__ A, int lda, int j_lo, int cnt
     __syncthreads();
 }
 
+// A(j, X) for the owned row that the fused FP32 step assigns to this thread's register m:
+// row q + 128 (s + 4 m) for quad q and quad lane s (0 for dead rows and for index `skip`).
+template <typename T>
+__device__ __forceinline__ T a_quad(const T *__restrict__ A, int lda, int j_lo, int cnt, const int *alive, int X,
+                                    int m, int skip) {
+    const int jl = (threadIdx.x >> 2) + (PANEL_THREADS / 4) * ((threadIdx.x & 3) + 4 * m);
+    return (jl < cnt && alive[jl] && j_lo + jl != skip) ? a_sym(A, lda, j_lo + jl, X) : T(0);
+}
+
 struct NoHook {
     __device__ void operator()() const {}
 };
@@ -309,7 +318,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     __shared__ T s_t[8];
     __shared__ T s_x[16];   // per-step scalars in the factor's type: [0] pivot norm, [2] lambda,
                             // [6] next pivot norm (speculation), [8] a_kk, [10..11] a_rk, a_rr
-    __shared__ unsigned long long s_red2[2 * PANEL_WARPS + 2];
+    __shared__ unsigned long long s_red2[RED2_SLOTS];
 
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ldcg(w.status) != 0) return;
@@ -360,7 +369,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     // optional per-step timestamps of CTA 0 (profiling only)
     unsigned long long *const trace = (cta == 0 && tid == 0) ? w.trace : nullptr;
 #define PANEL_MARK(slot) \
-    do { if (trace) trace[(size_t)k * 10 + (slot)] = clock64(); } while (0)
+    do { if (trace) trace[(size_t)k * PANEL_TRACE_SLOTS + (slot)] = clock64(); } while (0)
     // ---- load the owned state ----
     for (int e = tid; e < cnt * d; e += PANEL_THREADS) {
         int jl = e / d, r = e - jl * d;
@@ -374,7 +383,6 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         alive[jl] = 1;
     }
     for (int x = tid; x < wsz; x += PANEL_THREADS) win[x] = k0 + x;
-    if (tid < 6) s_red2[tid] = 0ull;   // the first slot pairs of block_max2_u64
     double beta2 = 0.0;   // thread 0 of CTA 0: ||B^(1)||_{1,2}^2
     if (tid == 0) {
         s_i[0] = (int)barrier_base(w.bar, (unsigned)G);
@@ -488,8 +496,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 }
             }
         }
-        }   // !have_next (a committed speculation did this step's interchange bookkeeping)
         __syncthreads();
+        }   // !have_next (a committed speculation did this step's interchange bookkeeping and
+            // ended with a CTA barrier)
         const int P = s_i[1], gP = s_i[3];
         if (P < 0 || !isfinite(s_x[0])) { fail = ST_NONFINITE; break; }
         // where P's sketch column and a_kk were published: by step (1), or by the speculation
@@ -499,70 +508,103 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
 
         // ---------------- (2) column P of the Schur complement, lambda and r ----------------
         PANEL_MARK(3);
-        schur_column<T>(A, lda, j_lo, cnt, P, i, ws, Ws, payP, bP, w.Lg + (size_t)P * bw, lP, d,
-                        alive, c1, recP, s_x + 8, KEYS ? 1 : 0, [&]() {
-                            // reciprocal of a_kk, used by case (1) and by the speculation
-                            if (KEYS) s_t[7] = s_x[8] != T(0) ? recip_rn(s_x[8]) : T(0);
-                        }, have_next, preA0, preA1);
-        // a_kk: FP32 path in the factor's type (its tests and reciprocal stay off the FP64 pipe)
-        const T akkT = KEYS ? s_x[8] : (T)s_d[1];
-        const double akk = KEYS ? 0.0 : s_d[1];
-        if (!isfinite(akkT)) { fail = ST_NONFINITE; break; }
-        PANEL_MARK(4);
         const unsigned g2 = gbase + nbar + 1;
         // speculation (FP32): assume case (1) (multipliers c / a_kk), update the sketch into the
         // shadow buffer and find the next step's pivot candidate before the barrier
         const bool spec = KEYS && spec_keys && run1 >= 2 && i + 1 < w.bmax && k + 1 < n;
         const int par = (int)(g2 & 1u);
+        unsigned long long kl = 0ull, ks = 0ull;   // FP32: best lambda key, best speculative sketch key
+        T akkT = T(0);                              // a_kk in the factor's type
+        T fk = T(0);                                // FP32: its reciprocal (0 for a zero pivot)
+        double akk = 0.0;                           // FP64 path: a_kk
         if (KEYS) {
-            unsigned long long kl = 0ull, ks = 0ull;   // best lambda key, best speculative sketch key
-            if (spec) {
-                const T f = s_t[7];
-                const int sub = tid & 3;
-                for (int jl0 = 0; jl0 < cnt; jl0 += PANEL_THREADS / 4) {
-                    const int jl = jl0 + (tid >> 2);
-                    const bool live = jl < cnt && alive[jl] && j_lo + jl != P;
-                    T sacc = T(0);
-                    if (live) {
-                        const T l1 = c1[jl] * f;
-                        const T *col = Bs + (size_t)jl * ds;
-                        T *col2 = Bs2 + (size_t)jl * ds;
-                        // rows sub, sub+4, ...: five at a time, all loads of a chunk before its
-                        // stores (the sketch copies and the pivot column share one base)
-                        for (int r0 = sub; r0 < d; r0 += 20) {
-                            T v[5], pb[5];
+            // One pass per quad of threads and owned row: the row's entry of column P of the
+            // Schur complement, its lambda key and, when speculating, its case-(1) sketch update
+            // and norm.  A(j, P) of row q + 128 m sits in quad lane m % 4, register m / 4.
+            if (!have_next) {
+                preA0 = a_quad<T>(A, lda, j_lo, cnt, alive, P, 0, -1);
+                preA1 = a_quad<T>(A, lda, j_lo, cnt, alive, P, 1, -1);
+                for (int r = tid; r < d; r += PANEL_THREADS) bP[r] = ldcg(payP + r);
+                for (int t = tid; t < i; t += PANEL_THREADS) lP[t] = ldcg(w.Lg + (size_t)P * bw + t);
+                if (tid == 0) s_x[8] = ldcg(recP);
+                __syncthreads();
+            }
+            akkT = s_x[8];
+            if (!isfinite(akkT)) { fail = ST_NONFINITE; break; }
+            // reciprocal of a_kk (case (1) and the speculation), in every thread
+            const T f = akkT != T(0) ? recip_rn(akkT) : T(0);
+            fk = f;
+            if (tid == 0) s_t[7] = f;
+            PANEL_MARK(10);
+            const int sub = tid & 3;
+            for (int m = 0; m * (PANEL_THREADS / 4) < cnt; ++m) {
+                const int jl = m * (PANEL_THREADS / 4) + (tid >> 2);
+                const bool in = jl < cnt && alive[jl];
+                T sdot = T(0);
+                if (in && i > 0) {
+                    const T *wr = Ws + (size_t)jl * ws;
+                    for (int t = sub; t < i; t += 4) sdot = fma(wr[t], lP[t], sdot);
+                }
+                sdot += __shfl_xor_sync(FULL, sdot, 1);
+                sdot += __shfl_xor_sync(FULL, sdot, 2);
+                const T aj = __shfl_sync(FULL, (m >> 2) == 0 ? preA0 : preA1, (lane & ~3) | (m & 3));
+                const T cv = in ? (T)(aj - sdot) : T(0);
+                if (sub == 0 && jl < cnt) c1[jl] = cv;
+                const bool live = in && j_lo + jl != P;
+                T sacc = T(0);
+                if (spec && live) {
+                    const T l1 = cv * f;
+                    const T *col = Bs + (size_t)jl * ds;
+                    T *col2 = Bs2 + (size_t)jl * ds;
+                    // rows sub, sub+4, ...: five at a time, all loads of a chunk before its
+                    // stores (the sketch copies and the pivot column share one base)
+                    for (int r0 = sub; r0 < d; r0 += 20) {
+                        T v[5], pb[5];
 #pragma unroll
-                            for (int q = 0; q < 5; ++q) {
-                                const int r = r0 + 4 * q;
-                                v[q] = r < d ? col[r] : T(0);
-                                pb[q] = r < d ? bP[r] : T(0);
-                            }
+                        for (int q = 0; q < 5; ++q) {
+                            const int r = r0 + 4 * q;
+                            v[q] = r < d ? col[r] : T(0);
+                            pb[q] = r < d ? bP[r] : T(0);
+                        }
 #pragma unroll
-                            for (int q = 0; q < 5; ++q) {
-                                const int r = r0 + 4 * q;
-                                const T x = v[q] - pb[q] * l1;
-                                if (r < d) col2[r] = x;
-                                sacc = fma(x, x, sacc);
-                            }
+                        for (int q = 0; q < 5; ++q) {
+                            const int r = r0 + 4 * q;
+                            const T x = v[q] - pb[q] * l1;
+                            if (r < d) col2[r] = x;
+                            sacc = fma(x, x, sacc);
                         }
                     }
+                }
+                if (spec) {
                     sacc += __shfl_xor_sync(FULL, sacc, 1);
                     sacc += __shfl_xor_sync(FULL, sacc, 2);
-                    if (live && sub == 0) {
+                }
+                if (live && sub == 0) {
+                    kl = max(kl, make_key((float)fabs(cv), lp[jl], j_lo + jl));
+                    if (spec) {
                         nrm2[jl] = sacc;
-                        kl = max(kl, make_key((float)fabs(c1[jl]), lp[jl], j_lo + jl));
                         ks = max(ks, make_key((float)sacc, lp[jl], j_lo + jl));
                     }
                 }
-            } else {
-                for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
-                    if (alive[jl] && j_lo + jl != P) kl = max(kl, make_key((float)fabs(c1[jl]), lp[jl], j_lo + jl));
             }
+        } else {
+            schur_column<T>(A, lda, j_lo, cnt, P, i, ws, Ws, payP, bP, w.Lg + (size_t)P * bw, lP, d,
+                            alive, c1, recP, s_x + 8, 0, NoHook{}, false, T(0), T(0));
+            akkT = (T)s_d[1];
+            akk = s_d[1];
+            if (!isfinite(akkT)) { fail = ST_NONFINITE; break; }
+        }
+        PANEL_MARK(4);
+        if (KEYS) {
             block_max2_u64(kl, ks, s_red2, red2_cnt);
+            PANEL_MARK(11);
+            // the two candidates' payloads and records from disjoint warps (threads 0..127 and
+            // 128: lambda candidate; 256..383 and 384: sketch candidate), so that no thread
+            // chains more than one of them before the barrier (d <= 128)
             if (kl != 0ull) {
                 const int jc = (int)(kl & 0xFFFFull) - j_lo;
-                for (int r = tid; r < d; r += PANEL_THREADS) stcg(pay2 + (size_t)cta * ps + r, Bs[(size_t)jc * ds + r]);
-                if (tid == 0) {
+                if (tid < d) stcg(pay2 + (size_t)cta * ps + tid, Bs[(size_t)jc * ds + tid]);
+                if (tid == 128) {
                     T *rp = reinterpret_cast<T *>(rec2 + 4 * (size_t)cta);
                     stcg(rp, c1[jc]);
                     stcg(rp + 1, dg[jc]);
@@ -572,9 +614,10 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             if (ks != 0ull) {
                 const int jc = (int)(ks & 0xFFFFull) - j_lo;
                 T *dst = spec_pay + (size_t)(par * G + cta) * ps;
-                for (int r = tid; r < d; r += PANEL_THREADS) stcg(dst + r, Bs2[(size_t)jc * ds + r]);
-                if (tid == 0) {
-                    const T cv = c1[jc], l1 = cv * s_t[7];
+                const int r = tid - 256;
+                if (r >= 0 && r < d) stcg(dst + r, Bs2[(size_t)jc * ds + r]);
+                if (tid == 384) {
+                    const T cv = c1[jc], l1 = cv * fk;
                     const T dnew = fma(-cv, l1, dg[jc]);
                     T *rp = reinterpret_cast<T *>(spec_rec + (size_t)(par * G + cta) * 4);
                     stcg(rp, dnew);
@@ -674,11 +717,8 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             // elimination (W, L, diagonal) with the same multipliers while they are in flight.
             const T f = s_t[7];
             const int P2 = s_i[10], LP2 = s_i[11], gc2 = s_i[12];
-            {
-                const int r0 = tid, r1 = tid + PANEL_THREADS;
-                preA0 = (r0 < cnt && alive[r0] && j_lo + r0 != P) ? a_sym(A, lda, j_lo + r0, P2) : T(0);
-                preA1 = (r1 < cnt && alive[r1] && j_lo + r1 != P) ? a_sym(A, lda, j_lo + r1, P2) : T(0);
-            }
+            preA0 = a_quad<T>(A, lda, j_lo, cnt, alive, P2, 0, P);
+            preA1 = a_quad<T>(A, lda, j_lo, cnt, alive, P2, 1, P);
             const T pb = tid < d ? ldcg(spec_pay + (size_t)(par * G + gc2) * ps + tid) : T(0);
             const T pl = tid < i ? ldcg(w.Lg + (size_t)P2 * bw + tid) : T(0);
             T prec_d = T(0), prec_l = T(0);   // the next pivot's a_kk and L(P2, k), from its record
@@ -704,7 +744,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 stcg(lrow + i, l1);
                 tmaxL = fmax(tmaxL, fabs(l1));
             }
+            PANEL_MARK(12);
             __syncthreads();
+            PANEL_MARK(13);
             for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
                 if (j_lo + jl == P) alive[jl] = 0;
             { T *t = Bs; Bs = Bs2; Bs2 = t; t = nrm; nrm = nrm2; nrm2 = t; }
@@ -733,6 +775,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             if (tid < i) lP[tid] = pl;
             have_next = true;
             ++run1;
+            PANEL_MARK(14);
             k += 1;
             i += 1;
             __syncthreads();

@@ -151,7 +151,7 @@ rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
     g = std::max(1, g);
     r.chunk_cap = (n + g - 1) / g;
     if (r.chunk_cap > 1024) return RCP_EUNSUPPORTED;
-    // the FP32 panel speculates on SBKP case (1) when the shadow sketch fits in shared memory
+    // the FP32 panel speculates on SBKP case (1) when its shadow norms fit in shared memory
     r.spec = 0;
     if (r.qb) {
         // q = b: the block QRCP keeps its chunk of the sketch in shared memory, and the block
@@ -232,9 +232,9 @@ FactorWork<T> make_work(rcp_handle *h, int n, T *A, int lda, double *Dd, double 
     w.s3v = (double *)h->s3v.p;
     w.tcops = r.prec == RCP_TF32X3 ? (float *)h->tcops.p : nullptr;
     w.trace = nullptr;
-    if (h->profiling >= 2 && grow(h->trace, (size_t)n * 10 * sizeof(unsigned long long)) == RCP_OK) {
+    if (h->profiling >= 2 && grow(h->trace, (size_t)n * PANEL_TRACE_SLOTS * sizeof(unsigned long long)) == RCP_OK) {
         w.trace = (unsigned long long *)h->trace.p;
-        cudaMemset(h->trace.p, 0, (size_t)n * 10 * sizeof(unsigned long long));
+        cudaMemset(h->trace.p, 0, (size_t)n * PANEL_TRACE_SLOTS * sizeof(unsigned long long));
         h->trace_n = n;
     }
     return w;
@@ -749,7 +749,7 @@ rcp_status rcp_profile_read(rcp_handle *h, double *ms, int *launches, int nphase
 rcp_status rcp_panel_trace(rcp_handle *h, unsigned long long *out, int cap) {
     if (!h || !out || cap < 0) return RCP_EINVAL;
     if (!h->trace.p) return RCP_EINVAL;
-    size_t m = std::min((size_t)cap, (size_t)h->trace_n * 10);
+    size_t m = std::min((size_t)cap, (size_t)h->trace_n * PANEL_TRACE_SLOTS);
     CU_TRY(cudaDeviceSynchronize());
     CU_TRY(cudaMemcpy(out, h->trace.p, m * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     return RCP_OK;

@@ -236,11 +236,11 @@ def rcp_profile(h: Handle, enable=True) -> None:
 
 
 def rcp_panel_trace(h: Handle, n: int):
-    """(n, 10) uint64 SM clock stamps of the panel steps of the last traced factorization."""
+    """(n, 16) uint64 SM clock stamps of the panel steps of the last traced factorization."""
     import numpy as np
-    out = np.zeros(n * 10, dtype=np.uint64)
+    out = np.zeros(n * 16, dtype=np.uint64)
     _check(lib().rcp_panel_trace(h.h, ctypes.c_void_p(out.ctypes.data), out.size), "rcp_panel_trace")
-    return out.reshape(n, 10)
+    return out.reshape(n, 16)
 
 
 def rcp_profile_read(h: Handle) -> dict:
