@@ -13,6 +13,8 @@
 // reads them before the factorization ends, so the permutation after every panel is recorded
 // and each panel's L columns are permuted once at the end (the deferred row interchanges of
 // blocked LAPACK factorizations), with column-contiguous accesses instead of strided rows.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace rcpk {
@@ -99,19 +101,27 @@ __global__ void scatter_kernel(FactorWork<T> w) {
 }
 
 // Panel multipliers (already in position order, column-major) into A(:, k0:kend); clears the
-// position marks.
+// position marks.  Grid: (row chunks of PS_ROWS, panel columns).
+constexpr int PS_THREADS = 256, PS_ROWS = 4 * PS_THREADS;
 template <typename T>
 __global__ void panel_store_kernel(FactorWork<T> w, int *phi) {
     if (ldcg(w.status) != 0) return;
     const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
     const int width = kend - k0;
     T *__restrict__ A = w.A;
-    const long long total = (long long)width * (n - k0);
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const int t = (int)(e / (n - k0)), p = k0 + (int)(e % (n - k0));
-        if (p > k0 + t) A[(size_t)p + (size_t)(k0 + t) * lda] = w.Lc[(size_t)p + (size_t)t * n];
+    // block (x, t): column k0 + t, rows k0 + t + 1 + [x, x + 1) * PS_ROWS
+    const int t = blockIdx.y;
+    if (t < width) {
+        const int p0 = k0 + t + 1 + blockIdx.x * PS_ROWS;
+        const T *__restrict__ src = w.Lc + (size_t)t * n;
+        T *__restrict__ dst = A + (size_t)(k0 + t) * lda;
+#pragma unroll
+        for (int u = 0; u < PS_ROWS / PS_THREADS; ++u) {
+            const int p = p0 + u * PS_THREADS + threadIdx.x;
+            if (p < n) dst[p] = src[p];
+        }
     }
-    if (blockIdx.x == 0) {
+    if (blockIdx.x == 0 && blockIdx.y == 0) {
         const int M = min(w.st->n_moved, w.maxmoved);
         for (int m = threadIdx.x; m < M; m += blockDim.x) {
             const int j = w.moved[m];
@@ -204,8 +214,9 @@ cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s) {
     count_launches(1);
     scatter_kernel<T><<<g, 256, 0, s>>>(w);
     count_launches(1);
-    int blocks = (w.n + 255) / 256;
-    panel_store_kernel<T><<<blocks, 256, 0, s>>>(w, phi);
+    // the panel width (device-side) is at most bw columns, each with fewer than n rows to store
+    const dim3 grid((unsigned)std::max(1, (w.n + PS_ROWS - 1) / PS_ROWS), (unsigned)w.bw);
+    panel_store_kernel<T><<<grid, PS_THREADS, 0, s>>>(w, phi);
     count_launches(1);
     return cudaGetLastError();
 }
