@@ -13,9 +13,12 @@ constexpr int PANEL_TRACE_SLOTS = 16;
 template <typename T>
 cudaError_t launch_omega(int d, int n, uint64_t seed, T *om, cudaStream_t s);
 
+// B = Omega A (d x n).  In FP32, `part` (nullable, part_elems elements) holds the partial sums
+// of a split over K; sketch_scratch_floats(n, d) elements allow the full split.
 template <typename TA, typename TC>
-cudaError_t launch_sketch(int n, int d, const TA *A, int lda, const TC *om, TC *B, float *A32, int lda32,
+cudaError_t launch_sketch(int n, int d, const TA *A, int lda, const TC *om, TC *B, TC *part, size_t part_elems,
                           cudaStream_t s);
+size_t sketch_scratch_floats(int n, int d);
 
 // Per-factorization workspace pointers used by the panel / interchange / trailing kernels.
 template <typename T>

@@ -48,6 +48,7 @@ struct rcp_handle {
     Buf trace;                                     // per-step panel timestamps (profiling level 2)
     Buf psnap, pinv, pbounds;                      // deferred L-row interchanges
     Buf keys;                                      // packed argmax keys of the FP32 panel
+    Buf skp;                                       // partial sums of the FP32 sketch
     Buf tcops;                                     // tensor-core operand tiles
     int trace_n = 0;
     Buf bord, bom, bticket, bscr;                  // batched path: order, Omega, ticket, per-CTA scratch
@@ -188,6 +189,7 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->s1v, 4 * (size_t)r.grid * sizeof(double)));
     RCP_TRY(grow(h->s2v, 4 * (size_t)r.grid * sizeof(double)));
     RCP_TRY(grow(h->keys, 32 * sizeof(unsigned long long)));
+    if (sizeof(T) == sizeof(float)) RCP_TRY(grow(h->skp, sketch_scratch_floats(n, r.d) * sizeof(float)));
     if (r.prec == RCP_TF32X3) RCP_TRY(grow(h->tcops, tc_ops_floats(n, r.b) * sizeof(float)));
     RCP_TRY(grow(h->s1i, 2 * (size_t)r.grid * sizeof(int)));
     RCP_TRY(grow(h->s2i, 2 * (size_t)r.grid * sizeof(int)));
@@ -302,7 +304,7 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
             CU_TRY(launch_omega<T>(r.d, n, r.seed, (T *)h->om.p, s));
             om = (const T *)h->om.p;
         }
-        CU_TRY((launch_sketch<T, T>(n, r.d, A, lda, om, w.B, nullptr, 0, s)));
+        CU_TRY((launch_sketch<T, T>(n, r.d, A, lda, om, w.B, (T *)h->skp.p, h->skp.bytes / sizeof(T), s)));
     }
     const int nblk = (n + r.b - 1) / r.b;
     for (int blk = 0; blk < nblk; ++blk) {
@@ -387,7 +389,7 @@ rcp_status rcp_create(rcp_handle **h) {
 
 void rcp_destroy(rcp_handle *h) {
     if (!h) return;
-    Buf *all[] = {&h->psnap, &h->pinv, &h->pbounds, &h->bord, &h->bom, &h->bticket, &h->bscr, &h->tcops, &h->keys, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
+    Buf *all[] = {&h->psnap, &h->pinv, &h->pbounds, &h->bord, &h->bom, &h->bticket, &h->bscr, &h->tcops, &h->keys, &h->skp, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
                   &h->s1v, &h->s2v, &h->s3v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
                   &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm};
     for (Buf *b : all)
@@ -787,7 +789,14 @@ rcp_status rcp_sketch(int n, int d, const void *A, int lda, rcp_prec prec, uint6
             CU_TRY(launch_omega<float>(d, n, seed, tmp, s));
             om = tmp;
         }
-        cudaError_t e = launch_sketch<float, float>(n, d, (const float *)A, lda, om, (float *)B, nullptr, 0, s);
+        float *part = nullptr;
+        const size_t pf = sketch_scratch_floats(n, d);
+        if (pf > 0 && cudaMallocAsync((void **)&part, pf * sizeof(float), s) != cudaSuccess) {
+            cudaGetLastError();   // no scratch: the sketch runs without the K split
+            part = nullptr;
+        }
+        cudaError_t e = launch_sketch<float, float>(n, d, (const float *)A, lda, om, (float *)B, part, part ? pf : 0, s);
+        if (part) cudaFreeAsync(part, s);
         if (tmp) cudaFreeAsync(tmp, s);
         CU_TRY(e);
     }

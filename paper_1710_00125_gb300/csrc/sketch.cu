@@ -4,6 +4,9 @@
 //
 // Omega is drawn once into workspace (d*n values; FP64 transcendental throughput on this
 // part is too low to redraw it inside every GEMM tile) and stays L2-resident for the GEMM.
+#include <algorithm>
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -129,6 +132,186 @@ sketch_kernel(int n, int d, const TA *__restrict__ A, int lda, const TC *__restr
     }
 }
 
+// FP32 sketch, B(:, J) = sum over K slices of Omega(:, I) A(I, J): work units of 128 columns
+// x one K slice, spread evenly over a persistent grid; with S > 1 slices each unit writes its
+// partial sum to scratch and sketch_reduce_kernel adds the S partials in slice order (the
+// result does not depend on the schedule).  Per K step of 32 rows the next tiles are loaded
+// into registers while the current ones are used; the A tile sits in shared memory with its
+// 16-byte slots XOR-swizzled by row (slot c of row k at c ^ (k & 7)), so that both the
+// transposing stores of tiles below the diagonal (8 rows x 4 columns per warp) and the
+// straight stores of tiles above it (32 columns of one row) hit 32 distinct banks.  Each
+// thread accumulates RPT rows of Omega (ty + 16 u) x 8 consecutive columns (tx * 8 + c).
+constexpr int SKF_BJ = 128, SKF_BK = 32, SKF_THREADS = 256;
+
+template <int RPT>
+__global__ void __launch_bounds__(SKF_THREADS, RPT <= 5 ? 2 : 1)
+sketch_f32_kernel(int n, int d, const float *__restrict__ A, int lda, const float *__restrict__ om,
+                  float *__restrict__ out, int S, int Jb, int ksteps) {
+    constexpr int DP = 16 * RPT;                          // Omega rows, padded
+    constexpr int AV = SKF_BK * SKF_BJ / SKF_THREADS;     // A values staged per thread (16)
+    constexpr int OV = SKF_BK * DP / SKF_THREADS;         // Omega values staged per thread
+    static_assert(AV == 16 && (SKF_BK * DP) % SKF_THREADS == 0, "tile shape");
+    __shared__ __align__(16) float As[SKF_BK][SKF_BJ];
+    __shared__ float Os[SKF_BK][DP];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31, wid = tid >> 5;
+    const int units = Jb * S;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const int jb = u % Jb, sl = u / Jb;
+        const int j0 = jb * SKF_BJ;
+        const int kb = (int)((long long)ksteps * sl / S), ke = (int)((long long)ksteps * (sl + 1) / S);
+        float acc[RPT][8];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+        float ra[AV], ro[OV];
+        int kind = 0;   // of the staged tile: 0 below the diagonal or mixed, 1 above
+        auto fetch = [&](int ks) {
+            const int i0 = ks * SKF_BK;
+            kind = (i0 + SKF_BK <= j0) ? 1 : 0;
+            if (kind == 1) {
+                // A(i, j) = A[j + i lda]: 32 consecutive columns of one row per warp
+#pragma unroll
+                for (int v = 0; v < AV; ++v) {
+                    const int j = j0 + lane + 32 * (v & 3), i = i0 + wid + 8 * (v >> 2);
+                    ra[v] = (i < n && j < n) ? A[(size_t)j + (size_t)i * lda] : 0.f;
+                }
+            } else {
+                // 8 consecutive rows x 4 columns per warp (32-byte segments of the stored columns)
+                const bool below = i0 >= j0 + SKF_BJ;
+#pragma unroll
+                for (int v = 0; v < AV; ++v) {
+                    const int i = i0 + (lane & 7) + 8 * (v & 3);
+                    const int j = j0 + (lane >> 3) + 4 * wid + 32 * (v >> 2);
+                    float x = 0.f;
+                    if (i < n && j < n) x = (below || i >= j) ? A[(size_t)i + (size_t)j * lda] : A[(size_t)j + (size_t)i * lda];
+                    ra[v] = x;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < OV; ++v) {
+                const int e = tid + SKF_THREADS * v, k = e / DP, r = e - k * DP;
+                ro[v] = (r < d && i0 + k < n) ? om[(size_t)r + (size_t)(i0 + k) * d] : 0.f;
+            }
+        };
+        auto stage = [&]() {
+#pragma unroll
+            for (int v = 0; v < AV; ++v) {
+                int k, j;
+                if (kind == 1) { j = lane + 32 * (v & 3); k = wid + 8 * (v >> 2); }
+                else { k = (lane & 7) + 8 * (v & 3); j = (lane >> 3) + 4 * wid + 32 * (v >> 2); }
+                As[k][4 * ((j >> 2) ^ (k & 7)) + (j & 3)] = ra[v];
+            }
+#pragma unroll
+            for (int v = 0; v < OV; ++v) {
+                const int e = tid + SKF_THREADS * v, k = e / DP, r = e - k * DP;
+                Os[k][r] = ro[v];
+            }
+        };
+        if (kb < ke) fetch(kb);
+        for (int ks = kb; ks < ke; ++ks) {
+            __syncthreads();   // the previous step's reads of As / Os are done
+            stage();
+            __syncthreads();
+            if (ks + 1 < ke) fetch(ks + 1);
+#pragma unroll 4
+            for (int k = 0; k < SKF_BK; ++k) {
+                const float4 *row = reinterpret_cast<const float4 *>(&As[k][0]);
+                const float4 a0 = row[(2 * tx) ^ (k & 7)], a1 = row[(2 * tx + 1) ^ (k & 7)];
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const float o = Os[k][ty + 16 * r];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(o, a[c], acc[r][c]);
+                }
+            }
+        }
+        float *dst = out + (size_t)sl * d * n;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int row = ty + 16 * r;
+            if (row >= d) continue;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = j0 + tx * 8 + c;
+                if (j < n) dst[(size_t)row + (size_t)j * d] = acc[r][c];
+            }
+        }
+    }
+}
+
+// B = sum_{s < S} part[s] (slice order), d x n
+__global__ void sketch_reduce_kernel(size_t count, int S, const float *__restrict__ part, float *__restrict__ B) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        float v = part[e];
+        for (int s = 1; s < S; ++s) v += part[(size_t)s * count + e];
+        B[e] = v;
+    }
+}
+
+template <int RPT>
+static int sketch_f32_grid() {
+    static int g = 0;
+    if (g == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sketch_f32_kernel<RPT>, SKF_THREADS, 0);
+        g = sms * (per > 0 ? per : 1);
+    }
+    return g;
+}
+
+// K slices for the FP32 sketch: about three work units per resident CTA, as far as the
+// scratch (part_floats) holds the partial sums
+static int sketch_slices(int n, int d, int grid, size_t part_floats) {
+    const int Jb = (n + SKF_BJ - 1) / SKF_BJ, ksteps = (n + SKF_BK - 1) / SKF_BK;
+    int S = (3 * grid + Jb / 2) / Jb;
+    S = std::max(1, std::min(S, ksteps));
+    const size_t per = (size_t)d * n;
+    if (S > 1 && part_floats < per * S) S = per > 0 ? (int)std::max<size_t>(1, part_floats / per) : 1;
+    return S;
+}
+
+size_t sketch_scratch_floats(int n, int d) {
+    // an upper bound for the slice count of any resident grid on this device
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int S = sketch_slices(n, d, 2 * std::max(sms, 1), ~(size_t)0);
+    return S > 1 ? (size_t)S * d * n : 0;
+}
+
+static cudaError_t launch_sketch_f32(int n, int d, const float *A, int lda, const float *om, float *B, float *part,
+                                     size_t part_floats, cudaStream_t s) {
+    const int rpt = (d + 15) / 16;
+    int grid = 0;
+    switch (rpt) {
+#define SKF_G(R) case R: grid = sketch_f32_grid<R>(); break;
+        SKF_G(1) SKF_G(2) SKF_G(3) SKF_G(4) SKF_G(5) SKF_G(6) SKF_G(7) SKF_G(8)
+#undef SKF_G
+        default: return cudaErrorInvalidValue;
+    }
+    const int Jb = (n + SKF_BJ - 1) / SKF_BJ, ksteps = (n + SKF_BK - 1) / SKF_BK;
+    const int S = part ? sketch_slices(n, d, grid, part_floats) : 1;
+    float *out = S > 1 ? part : B;
+    grid = std::min(grid, Jb * S);
+    switch (rpt) {
+#define SKF_CASE(R) case R: sketch_f32_kernel<R><<<grid, SKF_THREADS, 0, s>>>(n, d, A, lda, om, out, S, Jb, ksteps); break;
+        SKF_CASE(1) SKF_CASE(2) SKF_CASE(3) SKF_CASE(4) SKF_CASE(5) SKF_CASE(6) SKF_CASE(7) SKF_CASE(8)
+#undef SKF_CASE
+    }
+    count_launches(1);
+    if (S > 1) {
+        const size_t count = (size_t)d * n;
+        const int blocks = (int)std::min<size_t>((count + 255) / 256, 4096);
+        sketch_reduce_kernel<<<blocks, 256, 0, s>>>(count, S, part, B);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_omega(int d, int n, uint64_t seed, T *om, cudaStream_t s) {
     long long total = (long long)((d + 1) / 2) * n;
@@ -155,20 +338,20 @@ static cudaError_t launch_sketch_rpt(int n, int d, const TA *A, int lda, const T
 }
 
 template <typename TA, typename TC>
-cudaError_t launch_sketch(int n, int d, const TA *A, int lda, const TC *om, TC *B, float *A32,
-                          int lda32, cudaStream_t s) {
+cudaError_t launch_sketch(int n, int d, const TA *A, int lda, const TC *om, TC *B, TC *part, size_t part_elems,
+                          cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     if (d < 1 || d > 16 * SK_MAXRPT) return cudaErrorInvalidValue;
-    return launch_sketch_rpt<TA, TC>(n, d, A, lda, om, B, A32, lda32, s);
+    if constexpr (std::is_same<TA, float>::value && std::is_same<TC, float>::value)
+        return launch_sketch_f32(n, d, A, lda, om, B, part, part_elems, s);
+    return launch_sketch_rpt<TA, TC>(n, d, A, lda, om, B, nullptr, 0, s);
 }
 
 template cudaError_t launch_omega<double>(int, int, uint64_t, double *, cudaStream_t);
 template cudaError_t launch_omega<float>(int, int, uint64_t, float *, cudaStream_t);
 template cudaError_t launch_sketch<double, double>(int, int, const double *, int, const double *, double *,
-                                                   float *, int, cudaStream_t);
-template cudaError_t launch_sketch<double, float>(int, int, const double *, int, const float *, float *,
-                                                  float *, int, cudaStream_t);
-template cudaError_t launch_sketch<float, float>(int, int, const float *, int, const float *, float *,
-                                                 float *, int, cudaStream_t);
+                                                   double *, size_t, cudaStream_t);
+template cudaError_t launch_sketch<float, float>(int, int, const float *, int, const float *, float *, float *,
+                                                 size_t, cudaStream_t);
 
 }  // namespace rcpk
