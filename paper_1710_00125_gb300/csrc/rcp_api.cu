@@ -51,6 +51,7 @@ struct rcp_handle {
     Buf skp;                                       // partial sums of the FP32 sketch
     Buf tcops;                                     // tensor-core operand tiles
     int trace_n = 0;
+    int y_words = -1;                              // solve work last used by: 1 FP32 (epoch words), 0 FP64
     Buf bord, bom, bticket, bscr;                  // batched path: order, Omega, ticket, per-CTA scratch
     const int *bord_n = nullptr;                   // (n, batch, nmax) the order was made for
     int bord_batch = -1, bord_nmax = -1;
@@ -61,6 +62,10 @@ struct rcp_handle {
 };
 
 namespace {
+
+// grow(), and zero the buffer (on stream s, or synchronously when s is null) when it was
+// reallocated
+rcp_status grow_zeroed(Buf &b, size_t bytes, cudaStream_t s, bool sync);
 
 rcp_status grow(Buf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -73,6 +78,21 @@ rcp_status grow(Buf &b, size_t bytes) {
         return RCP_ENOMEM;
     }
     b.bytes = bytes;
+    return RCP_OK;
+}
+
+rcp_status grow_zeroed(Buf &b, size_t bytes, cudaStream_t s, bool sync) {
+    void *old = b.p;
+    const size_t had = b.bytes;
+    const rcp_status g = grow(b, bytes);
+    if (g != RCP_OK) return g;
+    if (b.p != old || b.bytes != had) {
+        if (sync) {
+            if (cudaMemset(b.p, 0, b.bytes) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return RCP_ECUDA;
+        } else if (cudaMemsetAsync(b.p, 0, b.bytes, s) != cudaSuccess) {
+            return RCP_ECUDA;
+        }
+    }
     return RCP_OK;
 }
 
@@ -362,7 +382,14 @@ template <typename T>
 rcp_status solve_impl(rcp_handle *h, int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
                       const int *perm, double *X, int ldx, const int *skip, cudaStream_t s) {
     RCP_TRY(ensure_small(h));
-    RCP_TRY(grow(h->Y, solve_work_bytes<T>(n, nrhs)));
+    RCP_TRY(grow_zeroed(h->Y, solve_work_bytes<T>(n, nrhs), s, false));
+    // the FP32 solves take a 64-bit word of the work area as published once its high half is the
+    // current epoch: FP64 solves leave other bit patterns there, so the area is cleared on a switch
+    const int words = sizeof(T) == sizeof(float) ? 1 : 0;
+    if (h->y_words != words) {
+        if (h->y_words >= 0) CU_TRY(cudaMemsetAsync(h->Y.p, 0, h->Y.bytes, s));
+        h->y_words = words;
+    }
     const int nb = solve_nb(n);
     bool fresh = h->flags.bytes < (size_t)(2 * nb + 2) * sizeof(int);
     RCP_TRY(grow(h->flags, (size_t)(2 * nb + 2) * sizeof(int)));
@@ -428,8 +455,10 @@ rcp_status rcp_reserve(rcp_handle *h, int n, int nrhs, const rcp_opts *opts) {
     RCP_TRY(resolve(n, opts, r));
     if (r.prec == RCP_FP64) RCP_TRY(ensure_factor_ws<double>(h, n, r));
     else RCP_TRY(ensure_factor_ws<float>(h, n, r));
-    RCP_TRY(grow(h->Y, r.prec == RCP_FP64 ? solve_work_bytes<double>(n, std::max(nrhs, 1))
-                                          : solve_work_bytes<float>(n, std::max(nrhs, 1))));
+    RCP_TRY(grow_zeroed(h->Y,
+                        r.prec == RCP_FP64 ? solve_work_bytes<double>(n, std::max(nrhs, 1))
+                                           : solve_work_bytes<float>(n, std::max(nrhs, 1)),
+                        nullptr, true));
     RCP_TRY(grow(h->R, (size_t)n * std::max(nrhs, 1) * sizeof(double)));
     RCP_TRY(grow(h->Dc, (size_t)n * std::max(nrhs, 1) * sizeof(double)));
     RCP_TRY(grow(h->part, symv_part_doubles(n, std::max(nrhs, 1)) * sizeof(double)));

@@ -7,6 +7,8 @@
 // handed out in dependency order through an atomic ticket; a block waits (bounded) on the
 // "done" flags of the blocks it depends on, subtracts their contributions tile by tile,
 // solves its diagonal block one warp per right-hand side, and publishes its flag.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace rcpk {
@@ -344,13 +346,234 @@ bwd_kernel(int n, int nrhs, const T *__restrict__ L, int lda, const T *__restric
     }
 }
 
-// Work layout (solve_work_bytes): T Y[n * nrhs] (rounded up to 256 bytes), then T Linv[nb * NB * NB].
-// flags: int[2 * nb] (forward, backward), then the two tickets.
+// ------------------------------------------------------------------------------------------
+// FP32 triangular solves with self-validating results.  Every entry of a finished block is
+// published as one 64-bit word (epoch << 32 | float bits) with a single relaxed store, and a
+// reader polls the words it needs until their epoch is the current one: the poll returns the
+// data itself, so a block's result reaches the blocks below it in one L2 round trip, without a
+// separate flag, fence or second load.  The words of the next finished block are requested a
+// tile ahead; a block re-polls only the words that were not yet current.  Epochs start at 1 and
+// the buffers are zeroed when allocated, so a word never matches before it is written.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void st_word(unsigned long long *p, float v, int epoch) {
+    const unsigned long long w = ((unsigned long long)(unsigned)epoch << 32) | __float_as_uint(v);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(w) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long *p) {
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
+}
+
+// request the words of rows j0 .. j0+nj-1 (columns c0 .. c0+rc-1); entries outside are 0 and
+// marked current
+__device__ __forceinline__ void words_issue(unsigned long long (&w)[YS_PER_THREAD], const unsigned long long *Yp, int n,
+                                            int j0, int nj, int c0, int rc, int epoch) {
+#pragma unroll
+    for (int u = 0; u < YS_PER_THREAD; ++u) {
+        const int e = threadIdx.x + u * SV_THREADS;
+        const int jj = e % SV_NB, c = e / SV_NB;
+        w[u] = (jj < nj && c < rc) ? ld_word(Yp + (size_t)(j0 + jj) + (size_t)(c0 + c) * n)
+                                   : (unsigned long long)(unsigned)epoch << 32;
+    }
+}
+
+// wait until every requested word is current (bounded), then stage the values; false to every
+// thread of the CTA when any thread's wait ran out
+__device__ __forceinline__ bool words_stage(unsigned long long (&w)[YS_PER_THREAD], const unsigned long long *Yp, int n,
+                                            int j0, int c0, int epoch, float (*ys)[SV_RC], int *status) {
+    int ok = 1;
+#pragma unroll
+    for (int u = 0; u < YS_PER_THREAD; ++u) {
+        if ((int)(w[u] >> 32) != epoch) {
+            const int e = threadIdx.x + u * SV_THREADS;
+            const unsigned long long *p = Yp + (size_t)(j0 + e % SV_NB) + (size_t)(c0 + e / SV_NB) * n;
+            const unsigned long long t0 = global_ns();
+            unsigned spins = 0;
+            while ((int)((w[u] = ld_word(p)) >> 32) != epoch) {
+                if ((++spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+                    ok = 0;
+                    atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        const int e = threadIdx.x + u * SV_THREADS;
+        ys[e % SV_NB][e / SV_NB] = __uint_as_float((unsigned)w[u]);
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// Forward: L y = Pi^T x, y published as words in Yp (n x nrhs, ld n).
+__global__ void __launch_bounds__(SV_THREADS)
+fwd_words_kernel(int n, int nrhs, const float *__restrict__ L, int lda, const float *__restrict__ Linv,
+                 const int *__restrict__ perm, const double *__restrict__ X, int ldx, unsigned long long *Yp, int epoch,
+                 int *ticket, int *status, const int *skip) {
+    __shared__ float Ms[SV_NB][SV_NB + 1];
+    __shared__ float acc[SV_NB][SV_RC];
+    __shared__ float ys[SV_NB][SV_RC];
+    __shared__ int s_I;
+    if (skip && ldcg(skip)) return;
+    if (ldcg(status) != 0) return;
+    const int nb = (n + SV_NB - 1) / SV_NB;
+    for (;;) {
+        if (threadIdx.x == 0) s_I = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int I = s_I;
+        __syncthreads();
+        if (I >= nb) return;
+        const int r0 = I * SV_NB, nr = min(SV_NB, n - r0);
+        for (int c0 = 0; c0 < nrhs; c0 += SV_RC) {
+            const int rc = min(SV_RC, nrhs - c0);
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                acc[r][c] = (r < nr && c < rc) ? (float)X[(size_t)perm[r0 + r] + (size_t)(c0 + c) * ldx] : 0.f;
+            }
+            float lreg[TILE_PER_THREAD];
+            tile_load(lreg, Linv + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
+            float cur[TILE_PER_THREAD], nxt[TILE_PER_THREAD];
+            unsigned long long wr[YS_PER_THREAD];
+            if (I > 0) {
+                tile_load(cur, L, lda, r0, 0, nr, SV_NB);
+                words_issue(wr, Yp, n, 0, SV_NB, c0, rc, epoch);
+            }
+            for (int J = 0; J < I; ++J) {
+                if (J + 1 < I) tile_load(nxt, L, lda, r0, (J + 1) * SV_NB, nr, SV_NB);
+                tile_store(cur, Ms);
+                if (!words_stage(wr, Yp, n, J * SV_NB, c0, epoch, ys, status)) return;
+                if (J + 1 < I) words_issue(wr, Yp, n, (J + 1) * SV_NB, SV_NB, c0, rc, epoch);
+                block_gemv_sub<float, false>(acc, Ms, ys, nr, SV_NB, rc);
+                __syncthreads();
+#pragma unroll
+                for (int u = 0; u < TILE_PER_THREAD; ++u) cur[u] = nxt[u];
+            }
+            // y_I = L_II^{-1} acc
+            tile_store(lreg, Ms);
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                ys[r][c] = acc[r][c];
+                acc[r][c] = 0.f;
+            }
+            __syncthreads();
+            block_gemv_sub<float, false>(acc, Ms, ys, nr, nr, rc);   // acc = -Linv * y
+            __syncthreads();
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                if (r < nr && c < rc) st_word(Yp + (size_t)(r0 + r) + (size_t)(c0 + c) * n, -acc[r][c], epoch);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Block-diagonal solve D w = y (FP64 arithmetic for the 2x2 blocks), from the words of the
+// forward solve into the plain array W.
+__global__ void dsolve_words_kernel(int n, int nrhs, const double *__restrict__ Dd, const double *__restrict__ Ds,
+                                    const unsigned long long *__restrict__ Yp, float *W, int *status, const int *skip) {
+    if (skip && ldcg(skip)) return;
+    if (ldcg(status) != 0) return;
+    auto yv = [&](int i, int k) { return (double)__uint_as_float((unsigned)ldcg(Yp + (size_t)i + (size_t)k * n)); };
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i > 0 && Ds[i - 1] != 0.0) continue;       // second row of a 2x2 block
+        if (i + 1 < n && Ds[i] != 0.0) {
+            const double b = Ds[i], a = Dd[i] / b, c = Dd[i + 1] / b, den = a * c - 1.0;
+            for (int k = 0; k < nrhs; ++k) {
+                const double y1 = yv(i, k) / b, y2 = yv(i + 1, k) / b;
+                W[(size_t)i + (size_t)k * n] = (float)((c * y1 - y2) / den);
+                W[(size_t)i + 1 + (size_t)k * n] = (float)((a * y2 - y1) / den);
+            }
+        } else {
+            const double dv = Dd[i];
+            for (int k = 0; k < nrhs; ++k) W[(size_t)i + (size_t)k * n] = (float)(yv(i, k) / dv);
+        }
+    }
+}
+
+// Backward: L^T v = w (w from W), v published as words in Vp, X(perm[i], :) = v(i, :).
+__global__ void __launch_bounds__(SV_THREADS)
+bwd_words_kernel(int n, int nrhs, const float *__restrict__ L, int lda, const float *__restrict__ Linv,
+                 const int *__restrict__ perm, double *X, int ldx, const float *__restrict__ W, unsigned long long *Vp,
+                 int epoch, int *ticket, int *status, const int *skip) {
+    __shared__ float Ms[SV_NB][SV_NB + 1];
+    __shared__ float acc[SV_NB][SV_RC];
+    __shared__ float ys[SV_NB][SV_RC];
+    __shared__ int s_I;
+    if (skip && ldcg(skip)) return;
+    if (ldcg(status) != 0) return;
+    const int nb = (n + SV_NB - 1) / SV_NB;
+    for (;;) {
+        if (threadIdx.x == 0) s_I = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int It = s_I;
+        __syncthreads();
+        if (It >= nb) return;
+        const int I = nb - 1 - It;
+        const int r0 = I * SV_NB, nr = min(SV_NB, n - r0);
+        for (int c0 = 0; c0 < nrhs; c0 += SV_RC) {
+            const int rc = min(SV_RC, nrhs - c0);
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                acc[r][c] = (r < nr && c < rc) ? W[(size_t)(r0 + r) + (size_t)(c0 + c) * n] : 0.f;
+            }
+            // tiles L(J, I) for J = nb-1 down to I+1, Ms[jj][r] = L(j0 + jj, r0 + r)
+            float lreg[TILE_PER_THREAD];
+            tile_load(lreg, Linv + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
+            float cur[TILE_PER_THREAD], nxt[TILE_PER_THREAD];
+            unsigned long long wr[YS_PER_THREAD];
+            if (I + 1 < nb) {
+                const int jl = (nb - 1) * SV_NB;
+                tile_load(cur, L, lda, jl, r0, min(SV_NB, n - jl), nr);
+                words_issue(wr, Vp, n, jl, min(SV_NB, n - jl), c0, rc, epoch);
+            }
+            for (int J = nb - 1; J > I; --J) {
+                if (J - 1 > I) tile_load(nxt, L, lda, (J - 1) * SV_NB, r0, min(SV_NB, n - (J - 1) * SV_NB), nr);
+                tile_store(cur, Ms);
+                const int j0 = J * SV_NB, nj = min(SV_NB, n - j0);
+                if (!words_stage(wr, Vp, n, j0, c0, epoch, ys, status)) return;
+                if (J - 1 > I) words_issue(wr, Vp, n, (J - 1) * SV_NB, min(SV_NB, n - (J - 1) * SV_NB), c0, rc, epoch);
+                block_gemv_sub<float, true>(acc, Ms, ys, nr, nj, rc);
+                __syncthreads();
+#pragma unroll
+                for (int u = 0; u < TILE_PER_THREAD; ++u) cur[u] = nxt[u];
+            }
+            // v_I = (L_II^{-1})^T acc
+            tile_store(lreg, Ms);
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                ys[r][c] = acc[r][c];
+                acc[r][c] = 0.f;
+            }
+            __syncthreads();
+            block_gemv_sub<float, true>(acc, Ms, ys, nr, nr, rc);   // acc = -Linv^T * w
+            __syncthreads();
+            for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
+                int r = e % SV_NB, c = e / SV_NB;
+                if (r < nr && c < rc) {
+                    const float v = -acc[r][c];
+                    st_word(Vp + (size_t)(r0 + r) + (size_t)(c0 + c) * n, v, epoch);
+                    X[(size_t)perm[r0 + r] + (size_t)(c0 + c) * ldx] = (double)v;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Work layout (solve_work_bytes).  FP64: T Y[n * nrhs] (rounded up to 256 bytes), then
+// T Linv[nb * NB * NB]; flags: int[2 * nb] (forward, backward), then the two tickets.  FP32:
+// u64 Yp[n * nrhs], u64 Vp[n * nrhs], float W[n * nrhs] (rounded up to 256 bytes), then
+// float Linv[nb * NB * NB]; of the flags only the two tickets are used.  The caller zeroes the
+// work area when it is allocated.
+template <typename T>
+static size_t solve_vec_bytes(int n, int nrhs) {
+    const size_t v = ((size_t)n * nrhs * sizeof(T) + 255) / 256 * 256;
+    return std::is_same<T, float>::value ? 2 * (size_t)n * nrhs * sizeof(unsigned long long) + v : v;
+}
+
 template <typename T>
 size_t solve_work_bytes(int n, int nrhs) {
     const size_t nb = ((size_t)n + SV_NB - 1) / SV_NB;
-    const size_t y = ((size_t)n * nrhs * sizeof(T) + 255) / 256 * 256;
-    return y + nb * SV_NB * SV_NB * sizeof(T);
+    return solve_vec_bytes<T>(n, nrhs) + nb * SV_NB * SV_NB * sizeof(T);
 }
 
 template <typename T>
@@ -362,9 +585,7 @@ cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd,
     epoch = epoch % 1000000000 + 1;
     const int nb = (n + SV_NB - 1) / SV_NB;
     int *tickets = flags + 2 * nb;
-    T *Y = work;
-    T *Linv = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(work) +
-                                    ((size_t)n * nrhs * sizeof(T) + 255) / 256 * 256);
+    T *Linv = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(work) + solve_vec_bytes<T>(n, nrhs));
     cudaError_t e = cudaMemsetAsync(tickets, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
@@ -373,14 +594,29 @@ cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd,
     const int grid = nb < sms ? nb : sms;
     inv_diag_kernel<T><<<nb, SV_NB, 0, s>>>(n, L, lda, Linv, status, skip);
     count_launches(1);
-    fwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, Y, flags, epoch, tickets, status,
-                                              skip);
-    count_launches(1);
-    dsolve_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(n, nrhs, Dd, Ds, Y, status, skip);
-    count_launches(1);
-    bwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, Y, flags + nb, epoch, tickets + 1,
-                                              status, skip);
-    count_launches(1);
+    if constexpr (std::is_same<T, float>::value) {
+        unsigned long long *Yp = reinterpret_cast<unsigned long long *>(work);
+        unsigned long long *Vp = Yp + (size_t)n * nrhs;
+        float *W = reinterpret_cast<float *>(Vp + (size_t)n * nrhs);
+        fwd_words_kernel<<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, Yp, epoch, tickets, status,
+                                                     skip);
+        count_launches(1);
+        dsolve_words_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, nrhs, Dd, Ds, Yp, W, status, skip);
+        count_launches(1);
+        bwd_words_kernel<<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, W, Vp, epoch, tickets + 1,
+                                                     status, skip);
+        count_launches(1);
+    } else {
+        T *Y = work;
+        fwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, Y, flags, epoch, tickets, status,
+                                                  skip);
+        count_launches(1);
+        dsolve_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(n, nrhs, Dd, Ds, Y, status, skip);
+        count_launches(1);
+        bwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, Y, flags + nb, epoch,
+                                                  tickets + 1, status, skip);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 
