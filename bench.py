@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--kexp", type=float, default=4.0, help="log10 of the condition number")
-    ap.add_argument("--prec", default="tf32x3")
+    ap.add_argument("--prec", default="f16x3")
     ap.add_argument("--b", type=int, default=256)
     ap.add_argument("--d", type=int, default=80)
     ap.add_argument("--tol", type=float, default=1e-12)

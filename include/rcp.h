@@ -53,8 +53,12 @@ typedef enum {
     RCP_FP64 = 0,           /* everything in FP64 (CUDA cores)                             */
     RCP_FP32 = 1,           /* FP32 factor; FP32 trailing update on CUDA cores                  */
     RCP_TF32 = 2,           /* reserved: currently runs as RCP_FP32                              */
-    RCP_TF32X3 = 3          /* FP32 factor; trailing update on tcgen05 tensor cores with split  */
+    RCP_TF32X3 = 3,         /* FP32 factor; trailing update on tcgen05 tensor cores with split  */
                             /* TF32 operands (hi*hi + hi*lo + lo*hi, FP32 accumulation)        */
+    RCP_F16X3 = 4           /* as RCP_TF32X3 with the split in FP16 (the same 11 significant    */
+                            /* bits per part): W and L21 are scaled by powers of two so that    */
+                            /* their panel maxima sit below 2^15, the three products run at the */
+                            /* FP16 tensor rate and move half the operand bytes of TF32         */
 } rcp_prec;
 
 typedef struct {
@@ -208,7 +212,7 @@ rcp_status rcp_profile_read(rcp_handle *h, double *ms, int *launches, int nphase
  *   A[i]    device, n_i x n_i, ld lda[i], lower triangle; overwritten by L_i (strictly lower,
  *           unit diagonal implicit) with D_i(j, j) on the diagonal.  Element type: double for
  *           RCP_FP64, float for every other opts->prec (the batched factor runs on CUDA cores;
- *           RCP_TF32X3 and RCP_TF32 run as RCP_FP32 here).
+ *           RCP_TF32X3, RCP_F16X3 and RCP_TF32 run as RCP_FP32 here).
  *   A64     optional (NULL allowed) device array of pointers to FP64 originals (ld lda64[i]):
  *           their lower triangles are first copied (rounded) into A[i] by the same kernel.
  *   Dd, Ds, perm: per-system outputs with the meaning they have for rcp_factor.

@@ -33,6 +33,8 @@ struct FactorState {
     unsigned long long maxD_bits;   // max |D_ij| as ordered bits of a non-negative double
     unsigned long long maxL_bits;   // max |L_ij|
     unsigned long long maxA_bits;   // max |A_ij| of the input
+    unsigned long long tcW_bits;    // FP16 split update: max |W| of the current panel's trailing rows
+    unsigned long long tcL_bits;    //   and max |L21| (ordered bits of non-negative doubles)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {

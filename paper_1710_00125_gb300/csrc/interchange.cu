@@ -246,7 +246,7 @@ cudaError_t launch_trailing<double>(const FactorWork<double> &w, int kmin, int m
 
 template <>
 cudaError_t launch_trailing<float>(const FactorWork<float> &w, int kmin, int mode, cudaStream_t s) {
-    if (mode == 3 && w.tcops) return launch_trailing_tc(w, w.tcops, kmin, s);   // RCP_TF32X3
+    if ((mode == 3 || mode == 4) && w.tcops) return launch_trailing_tc(w, w.tcops, kmin, mode == 4, s);   // RCP_TF32X3, RCP_F16X3
     constexpr int TM = 128, TK = 16, RM = 8;
     static int grid = 0;
     if (!grid) grid = trailing_grid<float>((const void *)trailing_simt_kernel<float, TM, TK, RM>, 256);

@@ -84,7 +84,8 @@ template <typename T>
 cudaError_t launch_trailing(const FactorWork<T> &w, int kmin, int mode, cudaStream_t s);
 
 size_t tc_ops_floats(int n, int bmax);
-cudaError_t launch_trailing_tc(const FactorWork<float> &w, float *ops, int kmin, cudaStream_t s);
+// tcgen05 trailing update with split operands: TF32 (f16 = false) or scaled FP16 parts
+cudaError_t launch_trailing_tc(const FactorWork<float> &w, float *ops, int kmin, bool f16, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_factor_init(const FactorWork<T> &w, cudaStream_t s);

@@ -66,7 +66,7 @@ size_t scratch_needed(int n, int nrhs, bool f64) {
 extern "C" rcp_status rcp_solve_noalloc(int n, int nrhs, const void *LA, int lda, const double *Dd,
                                         const double *Ds, const int *perm, rcp_prec prec, double *X,
                                         int ldx, rcp_stream_t stream) {
-    if (n < 0 || nrhs < 0 || prec < RCP_FP64 || prec > RCP_TF32X3) return RCP_EINVAL;
+    if (n < 0 || nrhs < 0 || prec < RCP_FP64 || prec > RCP_F16X3) return RCP_EINVAL;
     if (n == 0 || nrhs == 0) return RCP_OK;
     if (!LA || !Dd || !Ds || !perm || !X || lda < n || ldx < n) return RCP_EINVAL;
     const bool f64 = prec == RCP_FP64;

@@ -150,7 +150,7 @@ int sm_count() {
 
 rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
     r.prec = o ? o->prec : RCP_FP64;
-    if (r.prec < RCP_FP64 || r.prec > RCP_TF32X3) return RCP_EINVAL;
+    if (r.prec < RCP_FP64 || r.prec > RCP_F16X3) return RCP_EINVAL;
     r.b = (o && o->b > 0) ? o->b : 64;
     r.d = (o && o->d > 0) ? o->d : std::min(r.b + 16, 128);
     if (o && (o->q_mode < 0 || o->q_mode > 2)) return RCP_EUNSUPPORTED;
@@ -210,7 +210,7 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->s2v, 4 * (size_t)r.grid * sizeof(double)));
     RCP_TRY(grow(h->keys, 32 * sizeof(unsigned long long)));
     if (sizeof(T) == sizeof(float)) RCP_TRY(grow(h->skp, sketch_scratch_floats(n, r.d) * sizeof(float)));
-    if (r.prec == RCP_TF32X3) RCP_TRY(grow(h->tcops, tc_ops_floats(n, r.b) * sizeof(float)));
+    if (r.prec == RCP_TF32X3 || r.prec == RCP_F16X3) RCP_TRY(grow(h->tcops, tc_ops_floats(n, r.b) * sizeof(float)));
     RCP_TRY(grow(h->s1i, 2 * (size_t)r.grid * sizeof(int)));
     RCP_TRY(grow(h->s2i, 2 * (size_t)r.grid * sizeof(int)));
     RCP_TRY(grow(h->pay, 4 * (size_t)r.grid * r.d * sizeof(T)));
@@ -252,7 +252,7 @@ FactorWork<T> make_work(rcp_handle *h, int n, T *A, int lda, double *Dd, double 
     w.pinv = (int *)h->pinv.p;
     w.pbounds = (int *)h->pbounds.p;
     w.s3v = (double *)h->s3v.p;
-    w.tcops = r.prec == RCP_TF32X3 ? (float *)h->tcops.p : nullptr;
+    w.tcops = (r.prec == RCP_TF32X3 || r.prec == RCP_F16X3) ? (float *)h->tcops.p : nullptr;
     w.trace = nullptr;
     if (h->profiling >= 2 && grow(h->trace, (size_t)n * PANEL_TRACE_SLOTS * sizeof(unsigned long long)) == RCP_OK) {
         w.trace = (unsigned long long *)h->trace.p;
@@ -400,7 +400,7 @@ rcp_status solve_impl(rcp_handle *h, int n, int nrhs, const T *L, int lda, const
     return RCP_OK;
 }
 
-bool valid_prec(rcp_prec p) { return p >= RCP_FP64 && p <= RCP_TF32X3; }
+bool valid_prec(rcp_prec p) { return p >= RCP_FP64 && p <= RCP_F16X3; }
 
 }  // namespace
 

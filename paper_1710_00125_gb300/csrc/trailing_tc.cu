@@ -5,6 +5,14 @@
 // is ~1e-3 relative, too large for FP64 refinement to converge at condition numbers of 1e4.
 // Each operand is split as x = hi + lo with hi = tf32(x), lo = tf32(x - hi), and three products
 // hi*hi + hi*lo + lo*hi are accumulated in FP32 (the dropped lo*lo term is ~2^-22 relative).
+// The FP16 variant splits the same way in FP16, whose 11 significant bits equal TF32's: before
+// the split W is multiplied by 2^sw and L21 by 2^sl, the powers of two that put the panel's
+// max |W| and max |L21| (one reduction launch) in [2^14, 2^15), below the FP16 maximum; the
+// epilogue multiplies the accumulator by 2^-sw 2^-sl (exact).  An entry keeps the full 22 bits
+// of its two parts while its low part is an FP16 normal, i.e. down to 2^-18 of the panel maximum;
+// the parts of smaller entries lose bits only far below the update's normwise FP32 error.  The
+// FP16 products run at twice the TF32 rate, and a 16 KB operand tile carries K = 64 instead of 32,
+// which halves the operand traffic per product.
 //
 // Data path per panel:
 //   prep kernel: rows kend..n of W (Wbuf) and of L21 (the panel columns of A) are rounded to
@@ -13,12 +21,16 @@
 //   MMA kernel: persistent CTAs walk the 128 x 128 tiles (I >= J) of the trailing lower
 //     triangle.  Per K chunk one thread issues four 16 KB bulk copies (W_hi, W_lo of row block
 //     I; L_hi, L_lo of row block J) into a 3-stage ring guarded by mbarriers, then 4 K-steps x 3
-//     tcgen05.mma (M = N = 128, K = 8) into a 128-column TMEM accumulator, and commits the stage
+//     tcgen05.mma (M = N = 128, K = 8 in TF32, 16 in FP16) into a 128-column TMEM accumulator,
+//     and commits the stage
 //     back to its "free" barrier.  After the last chunk the accumulator is drained by four warps
 //     (tcgen05.ld 32x32b, one TMEM lane quarter each) and subtracted from A in place.
 // Every wait is bounded (kWaitLimitNs); on expiry the status word is set, the CTA stops
 // issuing work, waits for its issued copies and MMAs (bounded), frees its tensor memory and
 // returns.
+#include <cuda_fp16.h>
+
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.h"
@@ -28,16 +40,32 @@ namespace rcpk {
 namespace tc {
 
 constexpr int TM = 128;              // tile rows (M) and columns (N)
-constexpr int KC = 32;               // K chunk: 32 tf32 = one 128-byte swizzle row
-constexpr int TILE_FLOATS = TM * KC; // 4096 floats = 16 KB
+constexpr int TILE_FLOATS = 4096;    // one 128 x 128-byte tile = 16 KB
 constexpr int STAGES = 3;
 constexpr uint32_t STAGE_BYTES = 4u * TILE_FLOATS * 4u;   // W_hi, W_lo, L_hi, L_lo
+// K chunk: one 128-byte swizzle row, 32 TF32 or 64 FP16 values
+template <bool F16> constexpr int KC = F16 ? 64 : 32;
 
-// Offset (in floats) of element (m, k) of a 128 x 32 K-major tile in the 128-byte swizzle
-// image: 8-row groups of 1024 bytes, rows of 128 bytes, 16-byte chunks xor-ed with row % 8.
+// Offset (in elements) of element (m, k) of a 128-row K-major tile in the 128-byte swizzle
+// image: 8-row groups of 1024 bytes, rows of 128 bytes, 16-byte chunks xor-ed with row % 8
+// (4 FP32/TF32 or 8 FP16 values per chunk).
 __host__ __device__ __forceinline__ int swz(int m, int k) {
     const int r = m & 7;
     return (m >> 3) * 256 + r * 32 + (((k >> 2) ^ r) << 2) + (k & 3);
+}
+__host__ __device__ __forceinline__ int swz16(int m, int k) {
+    const int r = m & 7;
+    return (m >> 3) * 512 + r * 64 + (((k >> 3) ^ r) << 3) + (k & 7);
+}
+
+// Scale exponent for the FP16 split: the largest e with bound * 2^e < 2^15 (0 for a zero or
+// non-finite bound), from the bits of a non-negative double; clamped to the FP32 range.
+__device__ __forceinline__ int f16_scale_exp(unsigned long long bits) {
+    const int ef = (int)((bits >> 52) & 0x7FFu);   // biased exponent: bound < 2^(ef - 1022)
+    if (bits == 0ull || ef == 0x7FF) return 0;
+    const int e = ef == 0 ? -1022 : ef - 1022;
+    const int s = 15 - e;
+    return s < -126 ? -126 : (s > 126 ? 126 : s);
 }
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -79,10 +107,35 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
     }
 }
 
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+// L2 eviction policies: the operand tiles are read by many tiles of the panel and should stay
+// in L2 while the trailing block A22 (up to a few GB per panel) streams through it once.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float ld_stream(const float *a, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_stream(float *a, float v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" :: "l"(a), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep_v4(float4 *a, float4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+                 :: "l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
 
@@ -99,16 +152,27 @@ __device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, N = 128, M = 128.
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// Instruction descriptors: D = F32, A = B = TF32 (kind::tf32) or F16 (kind::f16), both
+// K-major, N = 128, M = 128.
+constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t IDESC_F16 = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-        :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
-        : "memory");
+template <bool F16>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    if (F16)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(IDESC_F16), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+            :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(IDESC_TF32), "r"(accumulate)
+            : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -132,43 +196,84 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 }  // namespace tc
 
 // ------------------------------------------------------------------------------------------
+// FP16 split: max |W| and max |L21| over the trailing rows of the panel (into the device
+// state, zeroed by the launcher).  Block (x, k): column k, rows strided by the grid.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) tc_absmax_kernel(FactorWork<float> w) {
+    if (ldcg(w.status) != 0) return;
+    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
+    const int K = kend - k0;
+    const int k = blockIdx.y;
+    float mw = 0.f, ml = 0.f;
+    if (k < K)
+        for (int p = kend + blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+            mw = fmaxf(mw, fabsf(w.Wbuf[(size_t)p + (size_t)k * n]));
+            ml = fmaxf(ml, fabsf(w.A[(size_t)p + (size_t)(k0 + k) * lda]));
+        }
+    for (int off = 16; off > 0; off >>= 1) {
+        mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, off));
+        ml = fmaxf(ml, __shfl_xor_sync(0xffffffffu, ml, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (mw > 0.f) atomic_max_nonneg(&w.st->tcW_bits, (double)mw);
+        if (ml > 0.f) atomic_max_nonneg(&w.st->tcL_bits, (double)ml);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // prep: hi/lo split of W(kend:n, 0:K) and L21 = A(kend:n, k0:kend) into swizzled tiles.
 // Tile (R, c) of an operand starts at (R * nkc + c) * TILE_FLOATS; rows past n and columns past
 // K are zero.  Layout of the operand buffer: [W_hi | W_lo | L_hi | L_lo], each nrb * nkc tiles.
 // ------------------------------------------------------------------------------------------
 // One CTA per (row block R, K chunk c): coalesced column reads of W and L21, the hi/lo split,
 // the swizzle in shared memory, then contiguous 16-byte stores of the four 16 KB tiles.
+template <bool F16>
 __global__ void __launch_bounds__(256) tc_prep_kernel(FactorWork<float> w, float *ops, int nrb_cap, int nkc_cap) {
-    __shared__ __align__(16) float t2[2][tc::TILE_FLOATS];   // hi, lo of one operand (32 KB)
+    constexpr int KC = tc::KC<F16>;
+    __shared__ __align__(16) float t2[2][tc::TILE_FLOATS];   // hi, lo images of one operand tile (32 KB)
     if (ldcg(w.status) != 0) return;
     const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
     const int K = kend - k0, N = n - kend;
     if (K <= 0 || N <= 0) return;
-    const int nrb = (N + tc::TM - 1) / tc::TM, nkc = (K + tc::KC - 1) / tc::KC;
+    const int nrb = (N + tc::TM - 1) / tc::TM, nkc = (K + KC - 1) / KC;
     if (nrb > nrb_cap || nkc > nkc_cap) {
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(w.status, ST_INTERNAL);
         return;
     }
+    float scale[2] = {1.f, 1.f};   // FP16: 2^sw for W, 2^sl for L21
+    if (F16) {
+        scale[0] = ldexpf(1.f, tc::f16_scale_exp(ldcg(&w.st->tcW_bits)));
+        scale[1] = ldexpf(1.f, tc::f16_scale_exp(ldcg(&w.st->tcL_bits)));
+    }
     const size_t per = (size_t)nrb_cap * nkc_cap * tc::TILE_FLOATS;
+    const uint64_t keep = tc::policy_evict_last();
     for (int tile = blockIdx.x; tile < nrb * nkc; tile += gridDim.x) {
         const int R = tile / nkc, c = tile % nkc;
         const size_t toff = ((size_t)R * nkc + c) * tc::TILE_FLOATS;
         for (int op = 0; op < 2; ++op) {   // 0: W rows, 1: L21 rows
-            for (int idx = threadIdx.x; idx < tc::TILE_FLOATS; idx += blockDim.x) {
+            for (int idx = threadIdx.x; idx < tc::TM * KC; idx += blockDim.x) {
                 const int m = idx % tc::TM, kk = idx / tc::TM;
-                const int p = kend + R * tc::TM + m, k = c * tc::KC + kk;
+                const int p = kend + R * tc::TM + m, k = c * KC + kk;
                 float v = 0.f;
                 if (p < n && k < K) v = op == 0 ? w.Wbuf[(size_t)p + (size_t)k * n] : w.A[(size_t)p + (size_t)(k0 + k) * lda];
-                const float h = tc::tf32_rna(v);
-                const int o = tc::swz(m, kk);
-                t2[0][o] = h;
-                t2[1][o] = tc::tf32_rna(v - h);
+                if (F16) {
+                    const float xs = v * scale[op];
+                    const __half h = __float2half_rn(xs);
+                    const int o = tc::swz16(m, kk);
+                    reinterpret_cast<__half *>(t2[0])[o] = h;
+                    reinterpret_cast<__half *>(t2[1])[o] = __float2half_rn(xs - __half2float(h));
+                } else {
+                    const float h = tc::tf32_rna(v);
+                    const int o = tc::swz(m, kk);
+                    t2[0][o] = h;
+                    t2[1][o] = tc::tf32_rna(v - h);
+                }
             }
             __syncthreads();
             for (int q = 0; q < 2; ++q) {
                 float4 *dst = reinterpret_cast<float4 *>(ops + (size_t)(2 * op + q) * per + toff);
                 const float4 *src = reinterpret_cast<const float4 *>(t2[q]);
-                for (int v = threadIdx.x; v < tc::TILE_FLOATS / 4; v += blockDim.x) dst[v] = src[v];
+                for (int v = threadIdx.x; v < tc::TILE_FLOATS / 4; v += blockDim.x) tc::st_keep_v4(dst + v, src[v], keep);
             }
             __syncthreads();
         }
@@ -205,8 +310,10 @@ __device__ __forceinline__ void tile_ij(long long tile, int *I, int *J) {
     *J = (int)(tile - (long long)a * (a + 1) / 2);
 }
 
+template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<float> w, const float *ops, int nrb_cap,
                                                                     int nkc_cap) {
+    constexpr int KC = tc::KC<F16>;
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[tc::STAGES];
     __shared__ __align__(8) uint64_t free_bar[tc::STAGES];
@@ -220,7 +327,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
     const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
     const int K = kend - k0, N = n - kend;
     if (K <= 0 || N <= 0) return;
-    const int nrb = (N + tc::TM - 1) / tc::TM, nkc = (K + tc::KC - 1) / tc::KC;
+    const int nrb = (N + tc::TM - 1) / tc::TM, nkc = (K + KC - 1) / KC;
     if (nrb > nrb_cap || nkc > nkc_cap) return;   // prep has flagged it
     const long long total = (long long)nrb * (nrb + 1) / 2;
     if ((long long)blockIdx.x >= total) return;
@@ -259,6 +366,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
             uint32_t acce_ph[2] = {0, 0};
             const int nchunks = ntiles * nkc;          // every chunk of every tile, in order
             bool ok = true;
+            const uint64_t keep = tc::policy_evict_last();
             auto chunk_src = [&](int g, size_t *ti, size_t *tj) {
                 const int lt = g / nkc, c = g % nkc;
                 int I, J;
@@ -277,10 +385,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
                 chunk_src(g, &ti, &tj);
                 float *dst = stage0 + (size_t)s * (tc::STAGE_BYTES / 4);
                 tc::mbar_expect_tx(&full_bar[s], tc::STAGE_BYTES);
-                tc::bulk_g2s(dst, whi + ti, tc::TILE_FLOATS * 4, &full_bar[s]);
-                tc::bulk_g2s(dst + tc::TILE_FLOATS, wlo + ti, tc::TILE_FLOATS * 4, &full_bar[s]);
-                tc::bulk_g2s(dst + 2 * tc::TILE_FLOATS, lhi + tj, tc::TILE_FLOATS * 4, &full_bar[s]);
-                tc::bulk_g2s(dst + 3 * tc::TILE_FLOATS, llo + tj, tc::TILE_FLOATS * 4, &full_bar[s]);
+                tc::bulk_g2s(dst, whi + ti, tc::TILE_FLOATS * 4, &full_bar[s], keep);
+                tc::bulk_g2s(dst + tc::TILE_FLOATS, wlo + ti, tc::TILE_FLOATS * 4, &full_bar[s], keep);
+                tc::bulk_g2s(dst + 2 * tc::TILE_FLOATS, lhi + tj, tc::TILE_FLOATS * 4, &full_bar[s], keep);
+                tc::bulk_g2s(dst + 3 * tc::TILE_FLOATS, llo + tj, tc::TILE_FLOATS * 4, &full_bar[s], keep);
                 loaded[s] = 1;
                 return true;
             };
@@ -303,11 +411,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
                 const uint32_t a_hi = tc::smem_u32(st), a_lo = tc::smem_u32(st + tc::TILE_FLOATS);
                 const uint32_t b_hi = tc::smem_u32(st + 2 * tc::TILE_FLOATS), b_lo = tc::smem_u32(st + 3 * tc::TILE_FLOATS);
 #pragma unroll
-                for (int kk = 0; kk < tc::KC / 8; ++kk) {
-                    const uint32_t off = kk * 32;   // 8 tf32 = 32 bytes along the swizzled row
-                    tc::mma_tf32(dacc, tc::sdesc_k128(a_hi + off), tc::sdesc_k128(b_hi + off), (c > 0 || kk > 0) ? 1u : 0u);
-                    tc::mma_tf32(dacc, tc::sdesc_k128(a_hi + off), tc::sdesc_k128(b_lo + off), 1u);
-                    tc::mma_tf32(dacc, tc::sdesc_k128(a_lo + off), tc::sdesc_k128(b_hi + off), 1u);
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t off = kk * 32;   // one K-step (8 tf32 or 16 f16) = 32 bytes along the swizzled row
+                    tc::mma<F16>(dacc, tc::sdesc_k128(a_hi + off), tc::sdesc_k128(b_hi + off), (c > 0 || kk > 0) ? 1u : 0u);
+                    tc::mma<F16>(dacc, tc::sdesc_k128(a_hi + off), tc::sdesc_k128(b_lo + off), 1u);
+                    tc::mma<F16>(dacc, tc::sdesc_k128(a_lo + off), tc::sdesc_k128(b_hi + off), 1u);
                 }
                 tc::mma_commit(&free_bar[s]);
                 used[s] = 1;
@@ -329,8 +437,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
         // ---------------- epilogue warps: lane quarter q, columns h*EC .. h*EC+EC-1 ----------------
         constexpr int EC = TC_EPI_COLS;
         const int q = warp & 3, h = (warp - 1) >> 2;
+        // FP16: the accumulator holds 2^(sw + sl) W L21^T
+        float inv_w = 1.f, inv_l = 1.f;
+        if (F16) {
+            inv_w = ldexpf(1.f, -tc::f16_scale_exp(ldcg(&w.st->tcW_bits)));
+            inv_l = ldexpf(1.f, -tc::f16_scale_exp(ldcg(&w.st->tcL_bits)));
+        }
         uint32_t accf_ph[2] = {0, 0};
         float *__restrict__ A = w.A;
+        const uint64_t stream = tc::policy_evict_first();   // A22 passes through L2 once per panel
         for (int lt = 0; lt < ntiles; ++lt) {
             const int a = lt & 1;
             int I, J;
@@ -345,7 +460,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int qq = q0 + cb + j;
-                    dst[j] = (rowok && qq < n && p >= qq) ? blk[(unsigned)((cb + j) * lda)] : 0.f;
+                    dst[j] = (rowok && qq < n && p >= qq) ? tc::ld_stream(blk + (unsigned)((cb + j) * lda), stream) : 0.f;
                 }
             };
             auto finish16 = [&](float (&src)[16], int cb, uint32_t taddr) {
@@ -356,7 +471,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int qq = q0 + cb + j;
-                        if (qq < n && p >= qq) blk[(unsigned)((cb + j) * lda)] = src[j] - __uint_as_float(r[j]);
+                        if (qq < n && p >= qq) {
+                            const float u = F16 ? (__uint_as_float(r[j]) * inv_w) * inv_l : __uint_as_float(r[j]);
+                            tc::st_stream(blk + (unsigned)((cb + j) * lda), src[j] - u, stream);
+                        }
                     }
                 }
             };
@@ -390,14 +508,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
 }
 
 size_t tc_ops_floats(int n, int bmax) {
+    // sized for the TF32 chunks (K = 32), which need at least as many tiles as the FP16 ones
     const size_t nrb = ((size_t)n + tc::TM - 1) / tc::TM;
-    const size_t nkc = ((size_t)bmax + 1 + tc::KC - 1) / tc::KC;
+    const size_t nkc = ((size_t)bmax + 1 + tc::KC<false> - 1) / tc::KC<false>;
     return 4 * nrb * nkc * tc::TILE_FLOATS;
 }
 
-cudaError_t launch_trailing_tc(const FactorWork<float> &w, float *ops, int kmin, cudaStream_t s) {
+template <bool F16>
+static cudaError_t launch_trailing_tc_fmt(const FactorWork<float> &w, float *ops, int kmin, cudaStream_t s) {
+    constexpr int KC = tc::KC<F16>;
     const int nrb_cap = (w.n + tc::TM - 1) / tc::TM;
-    const int nkc_cap = (w.bmax + 1 + tc::KC - 1) / tc::KC;
+    const int nkc_cap = (w.bmax + 1 + KC - 1) / KC;
     static int sms = 0;
     static bool attr = false;
     const size_t smem = (size_t)tc::STAGES * tc::STAGE_BYTES + 1024;
@@ -407,19 +528,31 @@ cudaError_t launch_trailing_tc(const FactorWork<float> &w, float *ops, int kmin,
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_trailing_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(tc_trailing_kernel<F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const long long rows = (long long)w.n - kmin;
     const long long nrb = rows > 0 ? (rows + tc::TM - 1) / tc::TM : 1;
-    tc_prep_kernel<<<8 * sms, 256, 0, s>>>(w, ops, nrb_cap, nkc_cap);
+    if (F16) {
+        // panel maxima of |W| and |L21| for the scales (the state lives in device memory)
+        cudaError_t e = cudaMemsetAsync(&w.st->tcW_bits, 0, 2 * sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+        const dim3 g((unsigned)std::max(1, std::min(16, (int)((rows + 255) / 256))), (unsigned)w.bw);
+        tc_absmax_kernel<<<g, 256, 0, s>>>(w);
+        count_launches(1);
+    }
+    tc_prep_kernel<F16><<<8 * sms, 256, 0, s>>>(w, ops, nrb_cap, nkc_cap);
     count_launches(1);
     const long long tiles = nrb * (nrb + 1) / 2;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    tc_trailing_kernel<<<grid > 0 ? grid : 1, TC_THREADS, smem, s>>>(w, ops, nrb_cap, nkc_cap);
+    tc_trailing_kernel<F16><<<grid > 0 ? grid : 1, TC_THREADS, smem, s>>>(w, ops, nrb_cap, nkc_cap);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_trailing_tc(const FactorWork<float> &w, float *ops, int kmin, bool f16, cudaStream_t s) {
+    return f16 ? launch_trailing_tc_fmt<true>(w, ops, kmin, s) : launch_trailing_tc_fmt<false>(w, ops, kmin, s);
 }
 
 }  // namespace rcpk

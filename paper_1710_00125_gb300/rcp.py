@@ -25,8 +25,8 @@ _LIB_PATH = os.path.join(_HERE, "_rcp_gb300.so")
 _lock = threading.Lock()
 _lib = None
 
-RCP_FP64, RCP_FP32, RCP_TF32, RCP_TF32X3 = 0, 1, 2, 3
-PREC_NAMES = {"fp64": RCP_FP64, "fp32": RCP_FP32, "tf32": RCP_TF32, "tf32x3": RCP_TF32X3}
+RCP_FP64, RCP_FP32, RCP_TF32, RCP_TF32X3, RCP_F16X3 = 0, 1, 2, 3, 4
+PREC_NAMES = {"fp64": RCP_FP64, "fp32": RCP_FP32, "tf32": RCP_TF32, "tf32x3": RCP_TF32X3, "f16x3": RCP_F16X3}
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT", -6: "ENOCONV",
           -7: "EUNSUPPORTED"}
 

@@ -236,10 +236,10 @@ def test_sysv_device_and_host_buffers(rcp, handle):
 
 
 # ------------------------------------------------------------------------------------------
-# FP32 factors: SIMT and tensor-core (tcgen05, split TF32) trailing updates
+# FP32 factors: SIMT and tensor-core (tcgen05, split TF32 or scaled split FP16) trailing updates
 # ------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "f16x3"])
 @pytest.mark.parametrize("n,b,d", [(300, 32, 40), (777, 64, 80), (1500, 128, 80)])
 def test_fp32_factor_backward_error(rcp, handle, prec, n, b, d):
     # ||P A P^T - L D L^T||_max / ||A||_max computed in FP64 from the FP32 factor: a wrong
@@ -258,21 +258,41 @@ def test_fp32_factor_backward_error(rcp, handle, prec, n, b, d):
     assert abs(st.n_2x2 - ref["n_2x2"]) <= max(3, 0.05 * ref["n_2x2"])
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "f16x3"])
 @pytest.mark.parametrize("kexp", [2.0, 4.0, 6.0])
-def test_tf32x3_refine_reaches_fp64_backward_error(rcp, handle, kexp):
+def test_tf32x3_refine_reaches_fp64_backward_error(rcp, handle, kexp, prec):
     n = 1024
     a = inputs.spectrum(n, seed=9, kexp=kexp, nrefl=16)
     x = inputs.x_true(n, 1, seed=9)
     rhs = inputs.rhs_for(a, x)
-    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, 128, 80, 2, prec="tf32x3")
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, 128, 80, 2, prec=prec)
     assert code == 0
     A64 = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
     Bv = torch.from_numpy(rhs.copy()).to(DEV)
     X = torch.zeros_like(Bv)
-    code, rst = rcp.rcp_refine(handle, A64, A, Dd, Ds, perm, "tf32x3", Bv, X, tol=1e-12, max_iter=30)
+    code, rst = rcp.rcp_refine(handle, A64, A, Dd, Ds, perm, prec, Bv, X, tol=1e-12, max_iter=30)
     assert code == 0, rst.as_dict()
     assert oracle.berr(a, X.cpu().numpy().T, rhs.T) <= 1e-12
     assert rst.refine_iters <= 6
+
+
+@pytest.mark.parametrize("scale", [1e-15, 1e15])
+def test_f16x3_scaled_matrix(rcp, handle, scale):
+    # the FP16 parts are formed after a power-of-two scaling by the panel maxima: matrices near
+    # either end of the FP32 range (short of overflowing the FP32 sketch norms) factor to the same
+    # relative accuracy as the TF32 split
+    n, b, d = 777, 64, 80
+    a = inputs.gaussian_sym(n, seed=11) * scale
+    errs = {}
+    for prec in ("tf32x3", "f16x3"):
+        code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, b, d, 3, prec=prec)
+        assert code == 0
+        L = _unit_lower(A)
+        D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
+        p = perm.cpu().numpy()
+        errs[prec] = np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() / np.abs(a).max()
+        assert errs[prec] < 2e-5 * max(1.0, st.growth_D), (prec, errs[prec])
+    assert errs["f16x3"] < 8 * errs["tf32x3"] + 1e-7, errs
 
 
 # ------------------------------------------------------------------------------------------
@@ -322,7 +342,7 @@ def test_qb_differs_from_q1(rcp, handle):
     assert np.array_equal(perm.cpu().numpy(), r2["perm"])
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "f16x3"])
 def test_qb_mixed_refine_reaches_fp64_backward_error(rcp, handle, prec):
     n = 1000
     a = inputs.spectrum(n, seed=5, kexp=4.0, nrefl=16)
@@ -372,7 +392,7 @@ def _sampled_reconstruction(A64, LA, Dd, Ds, perm, samples=512, seed=0):
     return float((a - rec).abs().max() / A64.abs().max())
 
 
-@pytest.mark.parametrize("prec", ["tf32x3"])
+@pytest.mark.parametrize("prec", ["tf32x3", "f16x3"])
 def test_full_size_mixed_n16384(rcp, handle, prec):
     n = 16384
     A64 = inputs.spectrum(n, seed=0, kexp=4.0, nrefl=64, device=DEV)
