@@ -33,8 +33,8 @@ struct FactorState {
     unsigned long long maxD_bits;   // max |D_ij| as ordered bits of a non-negative double
     unsigned long long maxL_bits;   // max |L_ij|
     unsigned long long maxA_bits;   // max |A_ij| of the input
-    unsigned long long tcW_bits;    // FP16 split update: max |W| of the current panel's trailing rows
-    unsigned long long tcL_bits;    //   and max |L21| (ordered bits of non-negative doubles)
+    unsigned long long tcW_bits;    // max |W| over the current panel's trailing rows (FP16 split
+    unsigned long long tcL_bits;    //   update) and max |L21|; ordered bits of non-negative doubles
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -77,6 +77,35 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int
     if (threadIdx.x == 0) {
         // the CTA's writes are ordered before this release by the __syncthreads above
         red_release_add_u32(bar, 1u);
+        int ok = 1;
+        if (ld_acquire_u32(bar) < target) {
+            unsigned long long t0 = global_ns();
+            unsigned spins = 0;
+            while (ld_acquire_u32(bar) < target) {
+                if ((++spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+                    ok = 0;
+                    atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The same barrier in two halves, so that a CTA can work between its arrival and its wait:
+// grid_arrive orders the CTA's earlier writes before the arrival (every thread must call it);
+// grid_wait returns the bounded wait's outcome to every thread.
+__device__ __forceinline__ void grid_arrive(unsigned *bar) {
+    __syncthreads();
+    if (threadIdx.x == 0) red_release_add_u32(bar, 1u);
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned *bar, unsigned target, int *status) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
         int ok = 1;
         if (ld_acquire_u32(bar) < target) {
             unsigned long long t0 = global_ns();

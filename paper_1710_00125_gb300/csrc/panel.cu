@@ -351,7 +351,8 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     T *dg = Ws + (size_t)cap * ws;
     T *c1 = dg + cap;
     T *c2 = c1 + cap;
-    T *bP = c2 + 3 * (size_t)cap;      // (two spare rows kept for alignment of the layout)
+    T *dg2 = c2 + cap;                 // shadow diagonal of the speculative case-(1) elimination
+    T *bP = c2 + 3 * (size_t)cap;      // (one spare row kept for alignment of the layout)
     T *bR = bP + d;
     T *lP = bR + d;
     T *lR = lP + bw;
@@ -389,6 +390,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         if (cta == 0) {
             w.st->n_moved = 0;
             beta2 = ldcg(&w.st->beta2);
+            // panel maxima, raised by every CTA's epilogue (after at least one grid barrier)
+            w.st->tcW_bits = 0ull;
+            w.st->tcL_bits = 0ull;
         }
     }
     __syncthreads();
@@ -645,7 +649,36 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             }
         }
         PANEL_MARK(5);
-        if (!grid_barrier(w.bar, base + (++nbar) * (unsigned)G, w.status)) return;
+        T tmaxLs = T(0);   // max |L(:, i)| of the speculative elimination
+        if (KEYS) {
+            grid_arrive(w.bar);
+            if (spec) {
+                // the case-(1) elimination of this step, speculatively, while thread 0 waits at the
+                // barrier: W(:, i), the shadow diagonal dg2 and L(:, i).  A failed speculation
+                // keeps dg, and the case (2)/(3) elimination rewrites W(:, i) and L(:, i) of every
+                // live row (nothing reads them before that).
+                for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
+                    if (!alive[jl]) continue;
+                    const int j = j_lo + jl;
+                    T *wrow = Ws + (size_t)jl * ws;
+                    T *lrow = w.Lg + (size_t)j * bw;
+                    if (j == P) {
+                        wrow[i] = T(0);
+                        stcg(lrow + i, T(0));
+                        continue;
+                    }
+                    const T cv = c1[jl];
+                    const T l1 = cv * fk;
+                    wrow[i] = cv;
+                    dg2[jl] = fma(-cv, l1, dg[jl]);
+                    stcg(lrow + i, l1);
+                    tmaxLs = fmax(tmaxLs, fabs(l1));
+                }
+            }
+            if (!grid_wait(w.bar, base + (++nbar) * (unsigned)G, w.status)) return;
+        } else {
+            if (!grid_barrier(w.bar, base + (++nbar) * (unsigned)G, w.status)) return;
+        }
         PANEL_MARK(6);
         if (KEYS) {
             if (tid == 0) {
@@ -711,11 +744,10 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         if (kase < 0) { fail = ST_NONFINITE; break; }
         if (s_i[9]) {
             PANEL_MARK(7);
-            // case (0)/(1) confirmed: the speculative sketch update stands.  Issue the loads of
-            // the next step first (its pivot's column of A, sketch column, multipliers and a_kk,
-            // the last multiplier coming with the speculation record), then finish this step's
-            // elimination (W, L, diagonal) with the same multipliers while they are in flight.
-            const T f = s_t[7];
+            // case (0)/(1) confirmed: the speculative sketch update and elimination stand.  Issue
+            // the loads of the next step (its pivot's column of A, sketch column, multipliers and
+            // a_kk, the last multiplier coming with the speculation record), then adopt the
+            // shadow sketch, norms and diagonal while they are in flight.
             const int P2 = s_i[10], LP2 = s_i[11], gc2 = s_i[12];
             preA0 = a_quad<T>(A, lda, j_lo, cnt, alive, P2, 0, P);
             preA1 = a_quad<T>(A, lda, j_lo, cnt, alive, P2, 1, P);
@@ -727,29 +759,13 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 prec_d = ldcg(rp);
                 prec_l = ldcg(rp + 1);
             }
-            for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
-                if (!alive[jl]) continue;
-                const int j = j_lo + jl;
-                T *wrow = Ws + (size_t)jl * ws;
-                T *lrow = w.Lg + (size_t)j * bw;
-                if (j == P) {
-                    wrow[i] = T(0);
-                    stcg(lrow + i, T(0));
-                    continue;
-                }
-                const T cv = c1[jl];
-                const T l1 = cv * f;
-                wrow[i] = cv;
-                dg[jl] = fma(-cv, l1, dg[jl]);
-                stcg(lrow + i, l1);
-                tmaxL = fmax(tmaxL, fabs(l1));
-            }
+            tmaxL = fmax(tmaxL, tmaxLs);
             PANEL_MARK(12);
             __syncthreads();
             PANEL_MARK(13);
             for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
                 if (j_lo + jl == P) alive[jl] = 0;
-            { T *t = Bs; Bs = Bs2; Bs2 = t; t = nrm; nrm = nrm2; nrm2 = t; }
+            { T *t = Bs; Bs = Bs2; Bs2 = t; t = nrm; nrm = nrm2; nrm2 = t; t = dg; dg = dg2; dg2 = t; }
             if (tid == 0) {
                 ckind[i] = (kase == 0 || !s_i[8]) ? 0 : 1;
                 cs0[i] = s_t[6];
@@ -933,11 +949,17 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
 
     // ---------------- epilogue: publish the panel in logical order ----------------
     __syncthreads();
+    T amw = T(0), aml = T(0);   // max |W| and |L| over the rows left for the trailing update
     for (int e = tid; e < cnt * i; e += PANEL_THREADS) {
         int t = e / cnt, jl = e - t * cnt;
         const T *wrow = Ws + (size_t)jl * ws;
-        if (alive[jl]) w.Wbuf[(size_t)lp[jl] + (size_t)t * n] = wrow[t];
-        w.Lc[(size_t)lp[jl] + (size_t)t * n] = l_entry<T>(wrow, t, ckind, cs0, cs1, cs2, cs3);
+        const T lv = l_entry<T>(wrow, t, ckind, cs0, cs1, cs2, cs3);
+        if (alive[jl]) {
+            w.Wbuf[(size_t)lp[jl] + (size_t)t * n] = wrow[t];
+            amw = fmax(amw, fabs(wrow[t]));
+            aml = fmax(aml, fabs(lv));
+        }
+        w.Lc[(size_t)lp[jl] + (size_t)t * n] = lv;
     }
     for (int e = tid; e < cnt * d; e += PANEL_THREADS) {
         int jl = e / d, r = e - jl * d;
@@ -957,6 +979,22 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         double v = (double)tmaxL;
         for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, off));
         if (lane == 0 && v > 0.0) atomic_max_nonneg(&w.st->maxL_bits, v);
+    }
+    // panel maxima of |W| and |L21| over the trailing rows (scales of the FP16 split update):
+    // per block, then one atomic pair per CTA
+    {
+        __shared__ T s_am[2][PANEL_WARPS];
+        for (int off = 16; off > 0; off >>= 1) {
+            amw = fmax(amw, __shfl_xor_sync(FULL, amw, off));
+            aml = fmax(aml, __shfl_xor_sync(FULL, aml, off));
+        }
+        if (lane == 0) { s_am[0][warp] = amw; s_am[1][warp] = aml; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int q = 1; q < PANEL_WARPS; ++q) { amw = fmax(amw, s_am[0][q]); aml = fmax(aml, s_am[1][q]); }
+            if (amw > T(0)) atomic_max_nonneg(&w.st->tcW_bits, (double)amw);
+            if (aml > T(0)) atomic_max_nonneg(&w.st->tcL_bits, (double)aml);
+        }
     }
     if (tid == 0 && cta == 0) {
         if (KEYS) {

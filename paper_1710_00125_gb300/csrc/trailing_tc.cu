@@ -7,7 +7,8 @@
 // hi*hi + hi*lo + lo*hi are accumulated in FP32 (the dropped lo*lo term is ~2^-22 relative).
 // The FP16 variant splits the same way in FP16, whose 11 significant bits equal TF32's: before
 // the split W is multiplied by 2^sw and L21 by 2^sl, the powers of two that put the panel's
-// max |W| and max |L21| (one reduction launch) in [2^14, 2^15), below the FP16 maximum; the
+// max |W| and max |L21| (reduced by the panel kernel as it publishes them) in [2^14, 2^15),
+// below the FP16 maximum; the
 // epilogue multiplies the accumulator by 2^-sw 2^-sl (exact).  An entry keeps the full 22 bits
 // of its two parts while its low part is an FP16 normal, i.e. down to 2^-18 of the panel maximum;
 // the parts of smaller entries lose bits only far below the update's normwise FP32 error.  The
@@ -194,31 +195,6 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 }  // namespace tc
-
-// ------------------------------------------------------------------------------------------
-// FP16 split: max |W| and max |L21| over the trailing rows of the panel (into the device
-// state, zeroed by the launcher).  Block (x, k): column k, rows strided by the grid.
-// ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) tc_absmax_kernel(FactorWork<float> w) {
-    if (ldcg(w.status) != 0) return;
-    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
-    const int K = kend - k0;
-    const int k = blockIdx.y;
-    float mw = 0.f, ml = 0.f;
-    if (k < K)
-        for (int p = kend + blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-            mw = fmaxf(mw, fabsf(w.Wbuf[(size_t)p + (size_t)k * n]));
-            ml = fmaxf(ml, fabsf(w.A[(size_t)p + (size_t)(k0 + k) * lda]));
-        }
-    for (int off = 16; off > 0; off >>= 1) {
-        mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, off));
-        ml = fmaxf(ml, __shfl_xor_sync(0xffffffffu, ml, off));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (mw > 0.f) atomic_max_nonneg(&w.st->tcW_bits, (double)mw);
-        if (ml > 0.f) atomic_max_nonneg(&w.st->tcL_bits, (double)ml);
-    }
-}
 
 // ------------------------------------------------------------------------------------------
 // prep: hi/lo split of W(kend:n, 0:K) and L21 = A(kend:n, k0:kend) into swizzled tiles.
@@ -534,14 +510,6 @@ static cudaError_t launch_trailing_tc_fmt(const FactorWork<float> &w, float *ops
     }
     const long long rows = (long long)w.n - kmin;
     const long long nrb = rows > 0 ? (rows + tc::TM - 1) / tc::TM : 1;
-    if (F16) {
-        // panel maxima of |W| and |L21| for the scales (the state lives in device memory)
-        cudaError_t e = cudaMemsetAsync(&w.st->tcW_bits, 0, 2 * sizeof(unsigned long long), s);
-        if (e != cudaSuccess) return e;
-        const dim3 g((unsigned)std::max(1, std::min(16, (int)((rows + 255) / 256))), (unsigned)w.bw);
-        tc_absmax_kernel<<<g, 256, 0, s>>>(w);
-        count_launches(1);
-    }
     tc_prep_kernel<F16><<<8 * sms, 256, 0, s>>>(w, ops, nrb_cap, nkc_cap);
     count_launches(1);
     const long long tiles = nrb * (nrb + 1) / 2;
