@@ -552,6 +552,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 sdot += __shfl_xor_sync(FULL, sdot, 1);
                 sdot += __shfl_xor_sync(FULL, sdot, 2);
                 const T aj = __shfl_sync(FULL, (m >> 2) == 0 ? preA0 : preA1, (lane & ~3) | (m & 3));
+                if (m == 0) PANEL_MARK(15);
                 const T cv = in ? (T)(aj - sdot) : T(0);
                 if (sub == 0 && jl < cnt) c1[jl] = cv;
                 const bool live = in && j_lo + jl != P;
