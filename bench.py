@@ -424,9 +424,16 @@ def roofline_for(name, ms, launches, a, hbm_peak, peaks, peak_src):
         m_avg = n / 2.0
         byts = (2 * d * m_avg + b * m_avg * 1.5 + 2 * b * m_avg) * 4
         ach = byts / (per_launch_ms * 1e-3) / 1e9
+        # DRAM bytes of one launch from ncu (profiles/panel_kernel_f32_n16384.md: the third panel at
+        # n = 16384, b = 256, d = 80 moved 257 MB over 15872 remaining columns), scaled to the
+        # average launch (n / 2 remaining columns); only for that configuration
+        traffic = None
+        if (n, b, d) == (16384, 256, 80) and a.prec in ("f16x3", "tf32x3"):
+            traffic = 257.0e6 * (n / 2.0) / 15872.0
         return {"kernel": "panel_kernel<float>", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
-                "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None, "peak_note": peak_src,
-                "note": "latency-bound: two grid barriers and two dependent L2/HBM round trips per pivot step"}
+                "unit": "GB/s", "frac": ach / hbm_peak, "traffic": traffic, "peak_note": peak_src,
+                "note": "latency-bound: per pivot step one grid barrier (two on the non-speculative path) "
+                        "and dependent L2/HBM round trips for the keys and the next pivot's column"}
     byts = 0
     return {"kernel": name, "bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s", "frac": None,
             "traffic": None}
