@@ -163,7 +163,9 @@ rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda
  * rcp_sysv -- solve A X = B end to end: copy the lower triangle of A64 (rounding it to
  * FP32 for the mixed precisions) into handle workspace, rcp_factor, rcp_refine.
  *   A64, lda, Bv, ldb, X, ldx   device pointers, or host pointers when host_buffers != 0 (then
- *                the copies in and out are part of the call; pinned host memory is fastest)
+ *                the copies in and out are part of the call; pinned host memory is fastest; of
+ *                A64 only the lower triangle is transferred, as rectangles of 256 columns from
+ *                each block's diagonal down: sum over blocks of (n - j0) x 256 doubles)
  *   tol, max_iter               refinement control (max_iter = 0: plain solve, no refinement)
  *   stats                       host, required (the call synchronizes)
  */

@@ -343,6 +343,50 @@ __global__ void lrows_permute_kernel(FactorWork<T> w, int npanels) {
     }
 }
 
+// The same permutation with the row map of a panel built once per work unit: a unit is (panel J,
+// LP_COLS of its columns); the map q -> pinv_J[perm[q]] of the rows kend..n-1 and one column
+// segment at a time sit in shared memory (dynamic: (n - kend) ints + (n - kend) values), so the
+// column is read and written in coalesced runs.
+constexpr int LP_COLS = 16, LP_THREADS = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(LP_THREADS) lrows_permute_smem_kernel(FactorWork<T> w, int npanels) {
+    extern __shared__ __align__(16) unsigned char lp_smem[];
+    if (ldcg(w.status) != 0) return;
+    const int n = w.n, lda = w.lda;
+    int nunits = 0;
+    for (int J = 0; J < npanels; ++J) nunits += (w.pbounds[2 * J + 1] - w.pbounds[2 * J] + LP_COLS - 1) / LP_COLS;
+    int J = 0, ubase = 0;   // units of panels before J
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+        int k0 = w.pbounds[2 * J], kend = w.pbounds[2 * J + 1];
+        while (u >= ubase + (kend - k0 + LP_COLS - 1) / LP_COLS) {
+            ubase += (kend - k0 + LP_COLS - 1) / LP_COLS;
+            ++J;
+            k0 = w.pbounds[2 * J];
+            kend = w.pbounds[2 * J + 1];
+        }
+        const int m = n - kend;
+        if (m <= 0) continue;
+        int *map = reinterpret_cast<int *>(lp_smem);
+        T *seg = reinterpret_cast<T *>(lp_smem + (((size_t)m * sizeof(int) + 15) & ~(size_t)15));
+        const int *inv = w.pinv + (size_t)J * n;
+        __syncthreads();   // the previous unit's reads of map and seg are done
+        for (int q = threadIdx.x; q < m; q += LP_THREADS) {
+            int src = inv[w.perm[kend + q]];
+            if (src < kend || src >= n) src = kend + q;   // cannot happen for a valid record
+            map[q] = src - kend;
+        }
+        const int c_lo = k0 + (u - ubase) * LP_COLS, c_hi = min(kend, c_lo + LP_COLS);
+        for (int c = c_lo; c < c_hi; ++c) {
+            T *col = w.A + (size_t)kend + (size_t)c * lda;
+            for (int q = threadIdx.x; q < m; q += LP_THREADS) seg[q] = col[q];
+            __syncthreads();
+            for (int q = threadIdx.x; q < m; q += LP_THREADS) col[q] = seg[map[q]];
+            __syncthreads();
+        }
+    }
+}
+
 template <typename T>
 cudaError_t launch_panel_record(const FactorWork<T> &w, int blk, cudaStream_t s) {
     int blocks = (w.n + 255) / 256;
@@ -358,10 +402,35 @@ cudaError_t launch_lrows_permute(const FactorWork<T> &w, int npanels, cudaStream
     if (w.n == 0 || npanels <= 0) return cudaSuccess;
     perm_inverse_kernel<T><<<1024, 256, 0, s>>>(w, npanels);
     count_launches(1);
-    // grid-stride over columns in increasing order, so each CTA's panel index only advances;
-    // the scratch holds maxmoved slices of n entries
-    int grid = w.n < w.maxmoved ? w.n : w.maxmoved;
-    lrows_permute_kernel<T><<<grid, 256, 0, s>>>(w, npanels);
+    // rows after the first panel: at most n - 1; map and one column segment in shared memory
+    const size_t smem = (((size_t)w.n * sizeof(int) + 15) & ~(size_t)15) + (size_t)w.n * sizeof(T);
+    static size_t optin = 0;
+    static bool attr[2] = {false, false};
+    if (!optin) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        optin = (size_t)v;
+    }
+    const int ti = sizeof(T) == sizeof(float) ? 0 : 1;
+    if (smem <= optin) {
+        if (!attr[ti]) {
+            // once per type, to the largest size any later call may need
+            cudaError_t e = cudaFuncSetAttribute(lrows_permute_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)optin);
+            if (e != cudaSuccess) return e;
+            attr[ti] = true;
+        }
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        lrows_permute_smem_kernel<T><<<sms, LP_THREADS, smem, s>>>(w, npanels);
+    } else {
+        // grid-stride over columns in increasing order, so each CTA's panel index only advances;
+        // the scratch holds maxmoved slices of n entries
+        int grid = w.n < w.maxmoved ? w.n : w.maxmoved;
+        lrows_permute_kernel<T><<<grid, 256, 0, s>>>(w, npanels);
+    }
     count_launches(1);
     return cudaGetLastError();
 }

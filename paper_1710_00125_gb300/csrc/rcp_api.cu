@@ -302,6 +302,9 @@ struct PhaseScope {
     }
 };
 
+// column block of the host-to-device copy of A in rcp_sysv (host_buffers)
+constexpr int kHostCopyCols = 256;
+
 double bits_to_double(unsigned long long b) {
     double v;
     std::memcpy(&v, &b, sizeof v);
@@ -555,8 +558,14 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
         RCP_TRY(grow(h->A64, (size_t)n * n * sizeof(double)));
         RCP_TRY(grow(h->Bh, (size_t)n * nrhs * sizeof(double)));
         RCP_TRY(grow(h->Xh, (size_t)n * nrhs * sizeof(double)));
-        CU_TRY(cudaMemcpy2DAsync(h->A64.p, (size_t)n * sizeof(double), A64, (size_t)lda * sizeof(double),
-                                 (size_t)n * sizeof(double), n, cudaMemcpyHostToDevice, s));
+        // only the lower triangle is read: copy it as rectangles of kHostCopyCols columns from
+        // each block's diagonal down (half the bytes of the full matrix)
+        for (int j0 = 0; j0 < n; j0 += kHostCopyCols) {
+            const int wcols = std::min(kHostCopyCols, n - j0);
+            CU_TRY(cudaMemcpy2DAsync((double *)h->A64.p + (size_t)j0 + (size_t)j0 * n, (size_t)n * sizeof(double),
+                                     A64 + (size_t)j0 + (size_t)j0 * lda, (size_t)lda * sizeof(double),
+                                     (size_t)(n - j0) * sizeof(double), wcols, cudaMemcpyHostToDevice, s));
+        }
         CU_TRY(cudaMemcpy2DAsync(h->Bh.p, (size_t)n * sizeof(double), Bv, (size_t)ldb * sizeof(double),
                                  (size_t)n * sizeof(double), nrhs, cudaMemcpyHostToDevice, s));
         dA = (const double *)h->A64.p; dB = (const double *)h->Bh.p; dX = (double *)h->Xh.p;
