@@ -120,8 +120,12 @@ cudaError_t launch_refine_check(int nrhs, const unsigned long long *mx, const do
                                 double *berr, int *iters, int count_iter, cudaStream_t s);
 cudaError_t launch_axpy_update(int n, int nrhs, double *X, int ldx, const double *D, int ldd,
                                const int *skip, cudaStream_t s);
-cudaError_t launch_copy_lower_f64(int n, const double *src, int lds, void *dst, int ldd, int to_f32,
-                                  cudaStream_t s);
+// lower triangle of columns c0 .. c1-1 (c1 < 0: all) of an FP64 matrix, FP64 or rounded to FP32
+cudaError_t launch_copy_lower_f64(int n, const double *src, int lds, void *dst, int ldd, int to_f32, cudaStream_t s,
+                                  int c0 = 0, int c1 = -1);
+// columns c0 .. c1-1 of B = Omega A (FP32); A must hold its final values in columns < c1
+cudaError_t launch_sketch_cols_f32(int n, int d, const float *A, int lda, const float *om, float *B, float *part,
+                                   size_t part_floats, int c0, int c1, cudaStream_t s);
 
 // Batched small systems (one CTA per system at a time).  info of a system that met a NaN or
 // Inf is BT_INFO_NONFINITE.

@@ -59,6 +59,8 @@ struct rcp_handle {
     int bom_d = -1, bom_nmax = -1, bom_f64 = -1;
     struct Tuned { int nmax, d, f64, b; };
     std::vector<Tuned> tuned;                      // batched panel widths chosen by rcp_tune_batched
+    cudaStream_t copy_stream = nullptr;            // rcp_sysv with host buffers: block copies of A
+    std::vector<cudaEvent_t> copy_events;          //   one per block, and one for the start
 };
 
 namespace {
@@ -313,7 +315,7 @@ double bits_to_double(unsigned long long b) {
 
 template <typename T>
 rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *Ds, int *perm, const Resolved &r,
-                       cudaStream_t s, rcp_stats *stats) {
+                       cudaStream_t s, rcp_stats *stats, bool presketched = false) {
     RCP_TRY(ensure_factor_ws<T>(h, n, r));
     FactorWork<T> w = make_work<T>(h, n, A, lda, Dd, Ds, perm, r);
     CU_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
@@ -321,7 +323,7 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
     CU_TRY(cudaMemsetAsync(h->keys.p, 0, 32 * sizeof(unsigned long long), s));
     CU_TRY(launch_factor_init<T>(w, s));
     const T *om = (const T *)r.omega;
-    {
+    if (!presketched) {   // (else Omega and B = Omega A were formed while A arrived)
         PhaseScope ps(h, s, PH_SKETCH);
         if (!om) {
             CU_TRY(launch_omega<T>(r.d, n, r.seed, (T *)h->om.p, s));
@@ -426,6 +428,8 @@ void rcp_destroy(rcp_handle *h) {
         if (b->p) cudaFree(b->p);
     for (auto &e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
+    for (auto e : h->copy_events) cudaEventDestroy(e);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     delete h;
 }
 
@@ -554,33 +558,72 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
     const double *dA = A64, *dB = Bv;
     double *dX = X;
     int dlda = lda, dldb = ldb, dldx = ldx;
-    if (host_buffers) {
-        RCP_TRY(grow(h->A64, (size_t)n * n * sizeof(double)));
-        RCP_TRY(grow(h->Bh, (size_t)n * nrhs * sizeof(double)));
-        RCP_TRY(grow(h->Xh, (size_t)n * nrhs * sizeof(double)));
-        // only the lower triangle is read: copy it as rectangles of kHostCopyCols columns from
-        // each block's diagonal down (half the bytes of the full matrix)
-        for (int j0 = 0; j0 < n; j0 += kHostCopyCols) {
-            const int wcols = std::min(kHostCopyCols, n - j0);
-            CU_TRY(cudaMemcpy2DAsync((double *)h->A64.p + (size_t)j0 + (size_t)j0 * n, (size_t)n * sizeof(double),
-                                     A64 + (size_t)j0 + (size_t)j0 * lda, (size_t)lda * sizeof(double),
-                                     (size_t)(n - j0) * sizeof(double), wcols, cudaMemcpyHostToDevice, s));
-        }
-        CU_TRY(cudaMemcpy2DAsync(h->Bh.p, (size_t)n * sizeof(double), Bv, (size_t)ldb * sizeof(double),
-                                 (size_t)n * sizeof(double), nrhs, cudaMemcpyHostToDevice, s));
-        dA = (const double *)h->A64.p; dB = (const double *)h->Bh.p; dX = (double *)h->Xh.p;
-        dlda = dldb = dldx = n;
-    }
     const bool f64 = r.prec == RCP_FP64;
     RCP_TRY(grow(h->F, (size_t)n * n * (f64 ? sizeof(double) : sizeof(float))));
     RCP_TRY(grow(h->Dd, (size_t)n * sizeof(double)));
     RCP_TRY(grow(h->Ds, (size_t)n * sizeof(double)));
     RCP_TRY(grow(h->perm, (size_t)n * sizeof(int)));
-    CU_TRY(launch_copy_lower_f64(n, dA, dlda, h->F.p, n, f64 ? 0 : 1, s));
+    bool presketched = false;
+    if (host_buffers) {
+        RCP_TRY(grow(h->A64, (size_t)n * n * sizeof(double)));
+        RCP_TRY(grow(h->Bh, (size_t)n * nrhs * sizeof(double)));
+        RCP_TRY(grow(h->Xh, (size_t)n * nrhs * sizeof(double)));
+        dA = (const double *)h->A64.p; dB = (const double *)h->Bh.p; dX = (double *)h->Xh.p;
+        dlda = dldb = dldx = n;
+        const int nblk = (n + kHostCopyCols - 1) / kHostCopyCols;
+        // FP32 factors: the blocks of A are copied on a second stream, and as each lands its
+        // columns are rounded to FP32 and its columns of B = Omega A formed (they read only this
+        // block and the rows of earlier ones), so the copy hides that work
+        const bool overlap = !f64;
+        if (overlap) {
+            if (!h->copy_stream) CU_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+            while ((int)h->copy_events.size() < nblk + 1) {
+                cudaEvent_t e;
+                CU_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                h->copy_events.push_back(e);
+            }
+            RCP_TRY(ensure_factor_ws<float>(h, n, r));
+            // the copies may start once the call's earlier work on s is done with the buffers
+            CU_TRY(cudaEventRecord(h->copy_events[nblk], s));
+            CU_TRY(cudaStreamWaitEvent(h->copy_stream, h->copy_events[nblk], 0));
+        }
+        cudaStream_t cs = overlap ? h->copy_stream : s;
+        // only the lower triangle is read: copy it as rectangles of kHostCopyCols columns from
+        // each block's diagonal down (half the bytes of the full matrix)
+        for (int b = 0; b < nblk; ++b) {
+            const int j0 = b * kHostCopyCols, wcols = std::min(kHostCopyCols, n - j0);
+            CU_TRY(cudaMemcpy2DAsync((double *)h->A64.p + (size_t)j0 + (size_t)j0 * n, (size_t)n * sizeof(double),
+                                     A64 + (size_t)j0 + (size_t)j0 * lda, (size_t)lda * sizeof(double),
+                                     (size_t)(n - j0) * sizeof(double), wcols, cudaMemcpyHostToDevice, cs));
+            if (overlap) CU_TRY(cudaEventRecord(h->copy_events[b], cs));
+        }
+        CU_TRY(cudaMemcpy2DAsync(h->Bh.p, (size_t)n * sizeof(double), Bv, (size_t)ldb * sizeof(double),
+                                 (size_t)n * sizeof(double), nrhs, cudaMemcpyHostToDevice, cs));
+        if (overlap) {
+            const float *om = (const float *)r.omega;
+            if (!om) {
+                CU_TRY(launch_omega<float>(r.d, n, r.seed, (float *)h->om.p, s));
+                om = (const float *)h->om.p;
+            }
+            for (int b = 0; b < nblk; ++b) {
+                const int j0 = b * kHostCopyCols, j1 = std::min(n, j0 + kHostCopyCols);
+                CU_TRY(cudaStreamWaitEvent(s, h->copy_events[b], 0));
+                CU_TRY(launch_copy_lower_f64(n, dA, dlda, h->F.p, n, 1, s, j0, j1));
+                CU_TRY(launch_sketch_cols_f32(n, r.d, (const float *)h->F.p, n, om, (float *)h->B.p, (float *)h->skp.p,
+                                              h->skp.bytes / sizeof(float), j0, j1, s));
+            }
+            // the right-hand sides (last on the copy stream) before the refinement
+            CU_TRY(cudaEventRecord(h->copy_events[nblk], cs));
+            CU_TRY(cudaStreamWaitEvent(s, h->copy_events[nblk], 0));
+            presketched = true;
+        }
+    }
+    if (!presketched) CU_TRY(launch_copy_lower_f64(n, dA, dlda, h->F.p, n, f64 ? 0 : 1, s));
     rcp_stats fst;
     rcp_status fs;
     if (f64) fs = factor_impl<double>(h, n, (double *)h->F.p, n, (double *)h->Dd.p, (double *)h->Ds.p, (int *)h->perm.p, r, s, nullptr);
-    else fs = factor_impl<float>(h, n, (float *)h->F.p, n, (double *)h->Dd.p, (double *)h->Ds.p, (int *)h->perm.p, r, s, nullptr);
+    else fs = factor_impl<float>(h, n, (float *)h->F.p, n, (double *)h->Dd.p, (double *)h->Ds.p, (int *)h->perm.p, r, s, nullptr,
+                                 presketched);
     if (fs != RCP_OK) return fs;
     (void)fst;
     rcp_stats rst;
@@ -830,8 +873,9 @@ rcp_status rcp_sketch(int n, int d, const void *A, int lda, rcp_prec prec, uint6
         float *part = nullptr;
         const size_t pf = sketch_scratch_floats(n, d);
         if (pf > 0 && cudaMallocAsync((void **)&part, pf * sizeof(float), s) != cudaSuccess) {
-            cudaGetLastError();   // no scratch: the sketch runs without the K split
-            part = nullptr;
+            cudaGetLastError();
+            if (tmp) cudaFreeAsync(tmp, s);
+            return RCP_ENOMEM;
         }
         cudaError_t e = launch_sketch<float, float>(n, d, (const float *)A, lda, om, (float *)B, part, part ? pf : 0, s);
         if (part) cudaFreeAsync(part, s);

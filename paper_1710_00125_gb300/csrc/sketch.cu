@@ -146,7 +146,7 @@ constexpr int SKF_BJ = 128, SKF_BK = 32, SKF_THREADS = 256;
 template <int RPT>
 __global__ void __launch_bounds__(SKF_THREADS, RPT <= 5 ? 2 : 1)
 sketch_f32_kernel(int n, int d, const float *__restrict__ A, int lda, const float *__restrict__ om,
-                  float *__restrict__ out, int S, int Jb, int ksteps) {
+                  float *__restrict__ out, int S, int Jb, int ksteps, int c0, int c1) {
     constexpr int DP = 16 * RPT;                          // Omega rows, padded
     constexpr int AV = SKF_BK * SKF_BJ / SKF_THREADS;     // A values staged per thread (16)
     constexpr int OV = SKF_BK * DP / SKF_THREADS;         // Omega values staged per thread
@@ -157,7 +157,7 @@ sketch_f32_kernel(int n, int d, const float *__restrict__ A, int lda, const floa
     const int units = Jb * S;
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
         const int jb = u % Jb, sl = u / Jb;
-        const int j0 = jb * SKF_BJ;
+        const int j0 = c0 + jb * SKF_BJ;   // columns c0 .. c1-1 of B (A is read in columns < c1 only)
         const int kb = (int)((long long)ksteps * sl / S), ke = (int)((long long)ksteps * (sl + 1) / S);
         float acc[RPT][8];
 #pragma unroll
@@ -174,7 +174,7 @@ sketch_f32_kernel(int n, int d, const float *__restrict__ A, int lda, const floa
 #pragma unroll
                 for (int v = 0; v < AV; ++v) {
                     const int j = j0 + lane + 32 * (v & 3), i = i0 + wid + 8 * (v >> 2);
-                    ra[v] = (i < n && j < n) ? A[(size_t)j + (size_t)i * lda] : 0.f;
+                    ra[v] = (i < n && j < c1) ? A[(size_t)j + (size_t)i * lda] : 0.f;
                 }
             } else {
                 // 8 consecutive rows x 4 columns per warp (32-byte segments of the stored columns)
@@ -184,7 +184,7 @@ sketch_f32_kernel(int n, int d, const float *__restrict__ A, int lda, const floa
                     const int i = i0 + (lane & 7) + 8 * (v & 3);
                     const int j = j0 + (lane >> 3) + 4 * wid + 32 * (v >> 2);
                     float x = 0.f;
-                    if (i < n && j < n) x = (below || i >= j) ? A[(size_t)i + (size_t)j * lda] : A[(size_t)j + (size_t)i * lda];
+                    if (i < n && j < c1) x = (below || i >= j) ? A[(size_t)i + (size_t)j * lda] : A[(size_t)j + (size_t)i * lda];
                     ra[v] = x;
                 }
             }
@@ -227,7 +227,8 @@ sketch_f32_kernel(int n, int d, const float *__restrict__ A, int lda, const floa
                 }
             }
         }
-        float *dst = out + (size_t)sl * d * n;
+        // out holds the columns c0 .. c1-1 (slice sl of S)
+        float *dst = out + (size_t)sl * d * (c1 - c0);
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             const int row = ty + 16 * r;
@@ -235,7 +236,7 @@ sketch_f32_kernel(int n, int d, const float *__restrict__ A, int lda, const floa
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int j = j0 + tx * 8 + c;
-                if (j < n) dst[(size_t)row + (size_t)j * d] = acc[r][c];
+                if (j < c1) dst[(size_t)row + (size_t)(j - c0) * d] = acc[r][c];
             }
         }
     }
@@ -263,28 +264,21 @@ static int sketch_f32_grid() {
     return g;
 }
 
-// K slices for the FP32 sketch: about three work units per resident CTA, as far as the
-// scratch (part_floats) holds the partial sums
-static int sketch_slices(int n, int d, int grid, size_t part_floats) {
-    const int Jb = (n + SKF_BJ - 1) / SKF_BJ, ksteps = (n + SKF_BK - 1) / SKF_BK;
-    int S = (3 * grid + Jb / 2) / Jb;
-    S = std::max(1, std::min(S, ksteps));
-    const size_t per = (size_t)d * n;
-    if (S > 1 && part_floats < per * S) S = per > 0 ? (int)std::max<size_t>(1, part_floats / per) : 1;
-    return S;
+// K slices of the FP32 sketch: a function of n alone (8 K steps of 32 rows or more per slice, at
+// most 64 slices), so that every column is summed in the same slices and order whichever columns
+// a launch covers (the whole sketch, or one block of columns as it arrives from the host)
+static int sketch_slices(int n) {
+    const int ksteps = (n + SKF_BK - 1) / SKF_BK;
+    return std::max(1, std::min(64, ksteps / 8));
 }
 
 size_t sketch_scratch_floats(int n, int d) {
-    // an upper bound for the slice count of any resident grid on this device
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int S = sketch_slices(n, d, 2 * std::max(sms, 1), ~(size_t)0);
+    const int S = sketch_slices(n);
     return S > 1 ? (size_t)S * d * n : 0;
 }
 
 static cudaError_t launch_sketch_f32(int n, int d, const float *A, int lda, const float *om, float *B, float *part,
-                                     size_t part_floats, cudaStream_t s) {
+                                     size_t part_floats, int c0, int c1, cudaStream_t s) {
     const int rpt = (d + 15) / 16;
     int grid = 0;
     switch (rpt) {
@@ -293,23 +287,32 @@ static cudaError_t launch_sketch_f32(int n, int d, const float *A, int lda, cons
 #undef SKF_G
         default: return cudaErrorInvalidValue;
     }
-    const int Jb = (n + SKF_BJ - 1) / SKF_BJ, ksteps = (n + SKF_BK - 1) / SKF_BK;
-    const int S = part ? sketch_slices(n, d, grid, part_floats) : 1;
-    float *out = S > 1 ? part : B;
+    const int nc = c1 - c0;
+    const int Jb = (nc + SKF_BJ - 1) / SKF_BJ, ksteps = (n + SKF_BK - 1) / SKF_BK;
+    const int S = sketch_slices(n);
+    if (S > 1 && (!part || part_floats < (size_t)S * d * nc)) return cudaErrorInvalidValue;   // scratch too small
+    float *out = S > 1 ? part : B + (size_t)c0 * d;
     grid = std::min(grid, Jb * S);
     switch (rpt) {
-#define SKF_CASE(R) case R: sketch_f32_kernel<R><<<grid, SKF_THREADS, 0, s>>>(n, d, A, lda, om, out, S, Jb, ksteps); break;
+#define SKF_CASE(R) case R: sketch_f32_kernel<R><<<grid, SKF_THREADS, 0, s>>>(n, d, A, lda, om, out, S, Jb, ksteps, c0, c1); break;
         SKF_CASE(1) SKF_CASE(2) SKF_CASE(3) SKF_CASE(4) SKF_CASE(5) SKF_CASE(6) SKF_CASE(7) SKF_CASE(8)
 #undef SKF_CASE
     }
     count_launches(1);
     if (S > 1) {
-        const size_t count = (size_t)d * n;
+        const size_t count = (size_t)d * nc;
         const int blocks = (int)std::min<size_t>((count + 255) / 256, 4096);
-        sketch_reduce_kernel<<<blocks, 256, 0, s>>>(count, S, part, B);
+        sketch_reduce_kernel<<<blocks, 256, 0, s>>>(count, S, part, B + (size_t)c0 * d);
         count_launches(1);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_cols_f32(int n, int d, const float *A, int lda, const float *om, float *B, float *part,
+                                   size_t part_floats, int c0, int c1, cudaStream_t s) {
+    if (n == 0 || c1 <= c0) return cudaSuccess;
+    if (d < 1 || d > 16 * SK_MAXRPT || c0 < 0 || c1 > n) return cudaErrorInvalidValue;
+    return launch_sketch_f32(n, d, A, lda, om, B, part, part_floats, c0, c1, s);
 }
 
 template <typename T>
@@ -343,7 +346,7 @@ cudaError_t launch_sketch(int n, int d, const TA *A, int lda, const TC *om, TC *
     if (n == 0) return cudaSuccess;
     if (d < 1 || d > 16 * SK_MAXRPT) return cudaErrorInvalidValue;
     if constexpr (std::is_same<TA, float>::value && std::is_same<TC, float>::value)
-        return launch_sketch_f32(n, d, A, lda, om, B, part, part_elems, s);
+        return launch_sketch_f32(n, d, A, lda, om, B, part, part_elems, 0, n, s);
     return launch_sketch_rpt<TA, TC>(n, d, A, lda, om, B, nullptr, 0, s);
 }
 

@@ -806,9 +806,10 @@ cudaError_t launch_axpy_update(int n, int nrhs, double *X, int ldx, const double
     return cudaGetLastError();
 }
 
-// Copy of the lower triangle of an FP64 matrix, optionally rounded to FP32.
-__global__ void copy_lower_kernel(int n, const double *__restrict__ src, int lds, void *dst, int ldd, int to_f32) {
-    for (int j = blockIdx.x; j < n; j += gridDim.x)
+// Copy of the lower triangle of an FP64 matrix (columns c0 .. c1-1), optionally rounded to FP32.
+__global__ void copy_lower_kernel(int n, const double *__restrict__ src, int lds, void *dst, int ldd, int to_f32, int c0,
+                                  int c1) {
+    for (int j = c0 + blockIdx.x; j < c1; j += gridDim.x)
         for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
             double v = src[(size_t)i + (size_t)j * lds];
             if (to_f32) static_cast<float *>(dst)[(size_t)i + (size_t)j * ldd] = (float)v;
@@ -816,9 +817,12 @@ __global__ void copy_lower_kernel(int n, const double *__restrict__ src, int lds
         }
 }
 
-cudaError_t launch_copy_lower_f64(int n, const double *src, int lds, void *dst, int ldd, int to_f32, cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    copy_lower_kernel<<<n < 4096 ? n : 4096, 256, 0, s>>>(n, src, lds, dst, ldd, to_f32);
+cudaError_t launch_copy_lower_f64(int n, const double *src, int lds, void *dst, int ldd, int to_f32, cudaStream_t s,
+                                  int c0, int c1) {
+    if (c1 < 0) c1 = n;
+    if (n == 0 || c1 <= c0) return cudaSuccess;
+    const int cols = c1 - c0;
+    copy_lower_kernel<<<cols < 4096 ? cols : 4096, 256, 0, s>>>(n, src, lds, dst, ldd, to_f32, c0, c1);
     count_launches(1);
     return cudaGetLastError();
 }
