@@ -98,9 +98,15 @@ __device__ __forceinline__ void block_gemv_sub(T (*acc)[SV_RC], const T (*Ms)[SV
 // Inverses of the unit lower triangular diagonal blocks L(I, I) (SV_NB x SV_NB, column-major
 // at Linv + I * SV_NB * SV_NB; the last block is padded with the identity).  One CTA per block,
 // one thread per column: x = L_II^{-1} e_c by forward substitution.
+//
+// With Mneg / Nneg (the FP32 solves), also the couplings to the neighbouring blocks, negated:
+// Mneg_I = -L_II^{-1} L_{I,I-1} (I >= 1) and Nneg_I = -L_{I+1,I} L_II^{-1} (I < nb-1), both
+// column-major SV_NB x SV_NB, so that a block's last dependency costs one product:
+// y_I = u_I + Mneg_I y_{I-1}, v_I = u_I + Nneg_I^T v_{I+1}.
 template <typename T>
 __global__ void __launch_bounds__(SV_NB)
-inv_diag_kernel(int n, const T *__restrict__ L, int lda, T *Linv, int *status, const int *skip) {
+inv_diag_kernel(int n, const T *__restrict__ L, int lda, T *Linv, int *status, const int *skip, T *Mneg = nullptr,
+                T *Nneg = nullptr) {
     __shared__ T Ls[SV_NB][SV_NB + 1];
     __shared__ T Xs[SV_NB][SV_NB + 1];
     if (skip && ldcg(skip)) return;
@@ -119,6 +125,32 @@ inv_diag_kernel(int n, const T *__restrict__ L, int lda, T *Linv, int *status, c
     __syncthreads();
     T *out = Linv + (size_t)I * SV_NB * SV_NB;
     for (int r = 0; r < SV_NB; ++r) out[(size_t)r + (size_t)c * SV_NB] = Xs[r][c];
+    const int nb = (n + SV_NB - 1) / SV_NB;
+    if (Mneg && I > 0) {
+        __syncthreads();   // Ls is read by every column's substitution above
+        for (int r = 0; r < SV_NB; ++r)
+            Ls[r][c] = r < nr ? L[(size_t)(r0 + r) + (size_t)(r0 - SV_NB + c) * lda] : T(0);   // L_{I,I-1}
+        __syncthreads();
+        T *m = Mneg + (size_t)I * SV_NB * SV_NB;
+        for (int r = 0; r < SV_NB; ++r) {
+            T sum = T(0);
+            for (int k = 0; k < SV_NB; ++k) sum = fma(Xs[r][k], Ls[k][c], sum);
+            m[(size_t)r + (size_t)c * SV_NB] = -sum;
+        }
+    }
+    if (Nneg && I + 1 < nb) {
+        const int nr2 = min(SV_NB, n - r0 - SV_NB);
+        __syncthreads();
+        for (int r = 0; r < SV_NB; ++r)
+            Ls[r][c] = (r < nr2 && c < nr) ? L[(size_t)(r0 + SV_NB + r) + (size_t)(r0 + c) * lda] : T(0);   // L_{I+1,I}
+        __syncthreads();
+        T *m = Nneg + (size_t)I * SV_NB * SV_NB;
+        for (int jj = 0; jj < SV_NB; ++jj) {
+            T sum = T(0);
+            for (int k = 0; k < SV_NB; ++k) sum = fma(Ls[jj][k], Xs[k][c], sum);
+            m[(size_t)jj + (size_t)c * SV_NB] = -sum;
+        }
+    }
 }
 
 // A SV_NB x SV_NB tile of L, column-major with leading dimension lda, staged through registers:
@@ -404,11 +436,13 @@ __device__ __forceinline__ bool words_stage(unsigned long long (&w)[YS_PER_THREA
     return __syncthreads_and(ok) != 0;
 }
 
-// Forward: L y = Pi^T x, y published as words in Yp (n x nrhs, ld n).
+// Forward: L y = Pi^T x, y published as words in Yp (n x nrhs, ld n).  Every finished block but
+// the last enters through its tile of L; then u = L_II^{-1} acc, and the last block through
+// y_I = u + Mneg_I y_{I-1} (its words were requested a tile ahead).
 __global__ void __launch_bounds__(SV_THREADS)
 fwd_words_kernel(int n, int nrhs, const float *__restrict__ L, int lda, const float *__restrict__ Linv,
-                 const int *__restrict__ perm, const double *__restrict__ X, int ldx, unsigned long long *Yp, int epoch,
-                 int *ticket, int *status, const int *skip) {
+                 const float *__restrict__ Mneg, const int *__restrict__ perm, const double *__restrict__ X, int ldx,
+                 unsigned long long *Yp, int epoch, int *ticket, int *status, const int *skip) {
     __shared__ float Ms[SV_NB][SV_NB + 1];
     __shared__ float acc[SV_NB][SV_RC];
     __shared__ float ys[SV_NB][SV_RC];
@@ -429,25 +463,26 @@ fwd_words_kernel(int n, int nrhs, const float *__restrict__ L, int lda, const fl
                 int r = e % SV_NB, c = e / SV_NB;
                 acc[r][c] = (r < nr && c < rc) ? (float)X[(size_t)perm[r0 + r] + (size_t)(c0 + c) * ldx] : 0.f;
             }
-            float lreg[TILE_PER_THREAD];
+            float lreg[TILE_PER_THREAD], mreg[TILE_PER_THREAD];
             tile_load(lreg, Linv + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
+            if (I > 0) tile_load(mreg, Mneg + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
             float cur[TILE_PER_THREAD], nxt[TILE_PER_THREAD];
             unsigned long long wr[YS_PER_THREAD];
             if (I > 0) {
-                tile_load(cur, L, lda, r0, 0, nr, SV_NB);
+                if (I >= 2) tile_load(cur, L, lda, r0, 0, nr, SV_NB);
                 words_issue(wr, Yp, n, 0, SV_NB, c0, rc, epoch);
             }
-            for (int J = 0; J < I; ++J) {
-                if (J + 1 < I) tile_load(nxt, L, lda, r0, (J + 1) * SV_NB, nr, SV_NB);
+            for (int J = 0; J + 1 < I; ++J) {
+                if (J + 2 < I) tile_load(nxt, L, lda, r0, (J + 1) * SV_NB, nr, SV_NB);
                 tile_store(cur, Ms);
                 if (!words_stage(wr, Yp, n, J * SV_NB, c0, epoch, ys, status)) return;
-                if (J + 1 < I) words_issue(wr, Yp, n, (J + 1) * SV_NB, SV_NB, c0, rc, epoch);
+                words_issue(wr, Yp, n, (J + 1) * SV_NB, SV_NB, c0, rc, epoch);
                 block_gemv_sub<float, false>(acc, Ms, ys, nr, SV_NB, rc);
                 __syncthreads();
 #pragma unroll
                 for (int u = 0; u < TILE_PER_THREAD; ++u) cur[u] = nxt[u];
             }
-            // y_I = L_II^{-1} acc
+            // u = L_II^{-1} acc, before the last finished block is awaited
             tile_store(lreg, Ms);
             for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
                 int r = e % SV_NB, c = e / SV_NB;
@@ -455,8 +490,14 @@ fwd_words_kernel(int n, int nrhs, const float *__restrict__ L, int lda, const fl
                 acc[r][c] = 0.f;
             }
             __syncthreads();
-            block_gemv_sub<float, false>(acc, Ms, ys, nr, nr, rc);   // acc = -Linv * y
+            block_gemv_sub<float, false>(acc, Ms, ys, nr, nr, rc);   // acc = -u
             __syncthreads();
+            if (I > 0) {
+                tile_store(mreg, Ms);
+                if (!words_stage(wr, Yp, n, (I - 1) * SV_NB, c0, epoch, ys, status)) return;
+                block_gemv_sub<float, false>(acc, Ms, ys, nr, SV_NB, rc);   // acc = -u - Mneg y_{I-1} = -y_I
+                __syncthreads();
+            }
             for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
                 int r = e % SV_NB, c = e / SV_NB;
                 if (r < nr && c < rc) st_word(Yp + (size_t)(r0 + r) + (size_t)(c0 + c) * n, -acc[r][c], epoch);
@@ -489,11 +530,14 @@ __global__ void dsolve_words_kernel(int n, int nrhs, const double *__restrict__ 
     }
 }
 
-// Backward: L^T v = w (w from W), v published as words in Vp, X(perm[i], :) = v(i, :).
+// Backward: L^T v = w (w from W), v published as words in Vp, X(perm[i], :) = v(i, :).  Every
+// finished block but the last (I + 1) enters through its tile of L; then u = L_II^{-T} acc, and
+// v_I = u + Nneg_I^T v_{I+1}.
 __global__ void __launch_bounds__(SV_THREADS)
 bwd_words_kernel(int n, int nrhs, const float *__restrict__ L, int lda, const float *__restrict__ Linv,
-                 const int *__restrict__ perm, double *X, int ldx, const float *__restrict__ W, unsigned long long *Vp,
-                 int epoch, int *ticket, int *status, const int *skip) {
+                 const float *__restrict__ Nneg, const int *__restrict__ perm, double *X, int ldx,
+                 const float *__restrict__ W, unsigned long long *Vp, int epoch, int *ticket, int *status,
+                 const int *skip) {
     __shared__ float Ms[SV_NB][SV_NB + 1];
     __shared__ float acc[SV_NB][SV_RC];
     __shared__ float ys[SV_NB][SV_RC];
@@ -515,28 +559,29 @@ bwd_words_kernel(int n, int nrhs, const float *__restrict__ L, int lda, const fl
                 int r = e % SV_NB, c = e / SV_NB;
                 acc[r][c] = (r < nr && c < rc) ? W[(size_t)(r0 + r) + (size_t)(c0 + c) * n] : 0.f;
             }
-            // tiles L(J, I) for J = nb-1 down to I+1, Ms[jj][r] = L(j0 + jj, r0 + r)
-            float lreg[TILE_PER_THREAD];
+            // tiles L(J, I) for J = nb-1 down to I+2, Ms[jj][r] = L(j0 + jj, r0 + r)
+            float lreg[TILE_PER_THREAD], nreg[TILE_PER_THREAD];
             tile_load(lreg, Linv + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
+            if (I + 1 < nb) tile_load(nreg, Nneg + (size_t)I * SV_NB * SV_NB, SV_NB, 0, 0, SV_NB, SV_NB);
             float cur[TILE_PER_THREAD], nxt[TILE_PER_THREAD];
             unsigned long long wr[YS_PER_THREAD];
             if (I + 1 < nb) {
                 const int jl = (nb - 1) * SV_NB;
-                tile_load(cur, L, lda, jl, r0, min(SV_NB, n - jl), nr);
+                if (I + 2 < nb) tile_load(cur, L, lda, jl, r0, min(SV_NB, n - jl), nr);
                 words_issue(wr, Vp, n, jl, min(SV_NB, n - jl), c0, rc, epoch);
             }
-            for (int J = nb - 1; J > I; --J) {
-                if (J - 1 > I) tile_load(nxt, L, lda, (J - 1) * SV_NB, r0, min(SV_NB, n - (J - 1) * SV_NB), nr);
+            for (int J = nb - 1; J > I + 1; --J) {
+                if (J - 1 > I + 1) tile_load(nxt, L, lda, (J - 1) * SV_NB, r0, min(SV_NB, n - (J - 1) * SV_NB), nr);
                 tile_store(cur, Ms);
                 const int j0 = J * SV_NB, nj = min(SV_NB, n - j0);
                 if (!words_stage(wr, Vp, n, j0, c0, epoch, ys, status)) return;
-                if (J - 1 > I) words_issue(wr, Vp, n, (J - 1) * SV_NB, min(SV_NB, n - (J - 1) * SV_NB), c0, rc, epoch);
+                words_issue(wr, Vp, n, (J - 1) * SV_NB, min(SV_NB, n - (J - 1) * SV_NB), c0, rc, epoch);
                 block_gemv_sub<float, true>(acc, Ms, ys, nr, nj, rc);
                 __syncthreads();
 #pragma unroll
                 for (int u = 0; u < TILE_PER_THREAD; ++u) cur[u] = nxt[u];
             }
-            // v_I = (L_II^{-1})^T acc
+            // u = L_II^{-T} acc, before the last finished block is awaited
             tile_store(lreg, Ms);
             for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
                 int r = e % SV_NB, c = e / SV_NB;
@@ -544,8 +589,15 @@ bwd_words_kernel(int n, int nrhs, const float *__restrict__ L, int lda, const fl
                 acc[r][c] = 0.f;
             }
             __syncthreads();
-            block_gemv_sub<float, true>(acc, Ms, ys, nr, nr, rc);   // acc = -Linv^T * w
+            block_gemv_sub<float, true>(acc, Ms, ys, nr, nr, rc);   // acc = -u
             __syncthreads();
+            if (I + 1 < nb) {
+                tile_store(nreg, Ms);
+                const int j0 = (I + 1) * SV_NB, nj = min(SV_NB, n - j0);
+                if (!words_stage(wr, Vp, n, j0, c0, epoch, ys, status)) return;
+                block_gemv_sub<float, true>(acc, Ms, ys, nr, nj, rc);   // acc = -u - Nneg^T v_{I+1} = -v_I
+                __syncthreads();
+            }
             for (int e = threadIdx.x; e < SV_NB * SV_RC; e += SV_THREADS) {
                 int r = e % SV_NB, c = e / SV_NB;
                 if (r < nr && c < rc) {
@@ -573,7 +625,9 @@ static size_t solve_vec_bytes(int n, int nrhs) {
 template <typename T>
 size_t solve_work_bytes(int n, int nrhs) {
     const size_t nb = ((size_t)n + SV_NB - 1) / SV_NB;
-    return solve_vec_bytes<T>(n, nrhs) + nb * SV_NB * SV_NB * sizeof(T);
+    // the inverted diagonal blocks; FP32 also the negated couplings Mneg, Nneg
+    const size_t mats = std::is_same<T, float>::value ? 3 : 1;
+    return solve_vec_bytes<T>(n, nrhs) + mats * nb * SV_NB * SV_NB * sizeof(T);
 }
 
 template <typename T>
@@ -592,21 +646,24 @@ cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = nb < sms ? nb : sms;
-    inv_diag_kernel<T><<<nb, SV_NB, 0, s>>>(n, L, lda, Linv, status, skip);
-    count_launches(1);
     if constexpr (std::is_same<T, float>::value) {
+        float *Mneg = Linv + (size_t)nb * SV_NB * SV_NB, *Nneg = Mneg + (size_t)nb * SV_NB * SV_NB;
+        inv_diag_kernel<T><<<nb, SV_NB, 0, s>>>(n, L, lda, Linv, status, skip, Mneg, Nneg);
+        count_launches(1);
         unsigned long long *Yp = reinterpret_cast<unsigned long long *>(work);
         unsigned long long *Vp = Yp + (size_t)n * nrhs;
         float *W = reinterpret_cast<float *>(Vp + (size_t)n * nrhs);
-        fwd_words_kernel<<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, Yp, epoch, tickets, status,
-                                                     skip);
+        fwd_words_kernel<<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, Mneg, perm, X, ldx, Yp, epoch, tickets,
+                                                     status, skip);
         count_launches(1);
         dsolve_words_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, nrhs, Dd, Ds, Yp, W, status, skip);
         count_launches(1);
-        bwd_words_kernel<<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, W, Vp, epoch, tickets + 1,
-                                                     status, skip);
+        bwd_words_kernel<<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, Nneg, perm, X, ldx, W, Vp, epoch,
+                                                     tickets + 1, status, skip);
         count_launches(1);
     } else {
+        inv_diag_kernel<T><<<nb, SV_NB, 0, s>>>(n, L, lda, Linv, status, skip);
+        count_launches(1);
         T *Y = work;
         fwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, Y, flags, epoch, tickets, status,
                                                   skip);
