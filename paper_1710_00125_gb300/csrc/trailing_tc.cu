@@ -227,22 +227,33 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(FactorWork<float> w, float
         const int R = tile / nkc, c = tile % nkc;
         const size_t toff = ((size_t)R * nkc + c) * tc::TILE_FLOATS;
         for (int op = 0; op < 2; ++op) {   // 0: W rows, 1: L21 rows
-            for (int idx = threadIdx.x; idx < tc::TM * KC; idx += blockDim.x) {
-                const int m = idx % tc::TM, kk = idx / tc::TM;
-                const int p = kend + R * tc::TM + m, k = c * KC + kk;
-                float v = 0.f;
-                if (p < n && k < K) v = op == 0 ? w.Wbuf[(size_t)p + (size_t)k * n] : w.A[(size_t)p + (size_t)(k0 + k) * lda];
+            // all of this thread's loads first (the reads miss L2: many in flight), then the split
+            // element u of this thread: row m = tid % 128, K index kk = tid / 128 + 2 u
+            constexpr int PER = tc::TM * KC / 256;
+            static_assert(tc::TM * KC % 256 == 0 && 256 % tc::TM == 0, "elements per thread");
+            const int m = threadIdx.x % tc::TM, kk0 = threadIdx.x / tc::TM;
+            const int p = kend + R * tc::TM + m;
+            const int kleft = p < n ? K - (c * KC + kk0) : 0;   // elements u < (kleft + 1) / 2 exist
+            const size_t ld = op == 0 ? (size_t)n : (size_t)lda;
+            const float *src = (op == 0 ? w.Wbuf + (size_t)(c * KC + kk0) * n : w.A + (size_t)(k0 + c * KC + kk0) * lda) +
+                               (p < n ? p : 0);
+            float v[PER];
+#pragma unroll
+            for (int u = 0; u < PER; ++u) v[u] = 2 * u < kleft ? src[(size_t)(2 * u) * ld] : 0.f;
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int kk = kk0 + 2 * u;
                 if (F16) {
-                    const float xs = v * scale[op];
+                    const float xs = v[u] * scale[op];
                     const __half h = __float2half_rn(xs);
                     const int o = tc::swz16(m, kk);
                     reinterpret_cast<__half *>(t2[0])[o] = h;
                     reinterpret_cast<__half *>(t2[1])[o] = __float2half_rn(xs - __half2float(h));
                 } else {
-                    const float h = tc::tf32_rna(v);
+                    const float h = tc::tf32_rna(v[u]);
                     const int o = tc::swz(m, kk);
                     t2[0][o] = h;
-                    t2[1][o] = tc::tf32_rna(v - h);
+                    t2[1][o] = tc::tf32_rna(v[u] - h);
                 }
             }
             __syncthreads();
