@@ -37,7 +37,7 @@ __global__ void mark_kernel(FactorWork<T> w, int *phi) {
 
 // Work items of the gather and scatter: for every moved index m, segments of SEG entries of its
 // L row (t < k0) and, when its new position is in the trailing block, of its trailing line.
-constexpr int SEG = 1024;
+constexpr int SEG = 1024, IC_THREADS = 256;   // entries per work item, threads of the gather/scatter
 
 __device__ __forceinline__ bool moved_item(long long item, int M, int nl, int nt, int *m, int *part, int *seg) {
     const int per = nl + nt;
@@ -64,11 +64,27 @@ __global__ void gather_kernel(FactorWork<T> w, const int *phi) {
             const int hi = min(k0, (seg + 1) * SEG);
             for (int t = seg * SEG + threadIdx.x; t < hi; t += blockDim.x) tl[t] = A[(size_t)j + (size_t)t * lda];
         } else if (p >= kend) {
+            // SEG / IC_THREADS entries per thread: their marks, then their entries of A, then the
+            // stores (the loads of a thread in flight together)
             T *ta = w.tmpA + (size_t)m * n;
             const int hi = min(n, kend + (seg + 1) * SEG);
-            for (int q = kend + seg * SEG + threadIdx.x; q < hi; q += blockDim.x) {
-                const int src = phi[q];
-                ta[q] = a_sym_ld(A, lda, j, src >= 0 ? src : q);
+            const int q0 = kend + seg * SEG + threadIdx.x;
+            int srcq[SEG / IC_THREADS];
+            T v[SEG / IC_THREADS];
+#pragma unroll
+            for (int u = 0; u < SEG / IC_THREADS; ++u) {
+                const int q = q0 + u * IC_THREADS;
+                srcq[u] = q < hi ? phi[q] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < SEG / IC_THREADS; ++u) {
+                const int q = q0 + u * IC_THREADS;
+                if (q < hi) v[u] = a_sym_ld(A, lda, j, srcq[u] >= 0 ? srcq[u] : q);
+            }
+#pragma unroll
+            for (int u = 0; u < SEG / IC_THREADS; ++u) {
+                const int q = q0 + u * IC_THREADS;
+                if (q < hi) ta[q] = v[u];
             }
         }
     }
@@ -91,10 +107,20 @@ __global__ void scatter_kernel(FactorWork<T> w) {
         } else if (p >= kend) {
             const T *ta = w.tmpA + (size_t)m * n;
             const int hi = min(n, kend + (seg + 1) * SEG);
-            for (int q = kend + seg * SEG + threadIdx.x; q < hi; q += blockDim.x) {
-                const T v = ta[q];
-                if (p >= q) A[(size_t)p + (size_t)q * lda] = v;
-                else A[(size_t)q + (size_t)p * lda] = v;
+            const int q0 = kend + seg * SEG + threadIdx.x;
+            T v[SEG / IC_THREADS];
+#pragma unroll
+            for (int u = 0; u < SEG / IC_THREADS; ++u) {
+                const int q = q0 + u * IC_THREADS;
+                if (q < hi) v[u] = ta[q];
+            }
+#pragma unroll
+            for (int u = 0; u < SEG / IC_THREADS; ++u) {
+                const int q = q0 + u * IC_THREADS;
+                if (q < hi) {
+                    if (p >= q) A[(size_t)p + (size_t)q * lda] = v[u];
+                    else A[(size_t)q + (size_t)p * lda] = v[u];
+                }
             }
         }
     }
@@ -210,9 +236,9 @@ cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int g = 4 * sms;
-    gather_kernel<T><<<g, 256, 0, s>>>(w, phi);
+    gather_kernel<T><<<g, IC_THREADS, 0, s>>>(w, phi);
     count_launches(1);
-    scatter_kernel<T><<<g, 256, 0, s>>>(w);
+    scatter_kernel<T><<<g, IC_THREADS, 0, s>>>(w);
     count_launches(1);
     // the panel width (device-side) is at most bw columns, each with fewer than n rows to store
     const dim3 grid((unsigned)std::max(1, (w.n + PS_ROWS - 1) / PS_ROWS), (unsigned)w.bw);
