@@ -35,17 +35,14 @@ __global__ void mark_kernel(FactorWork<T> w, int *phi) {
     }
 }
 
-// Work items of the gather and scatter: for every moved index m, segments of SEG entries of its
-// L row (t < k0) and, when its new position is in the trailing block, of its trailing line.
+// Work items of the gather and scatter: for every moved index m whose new position is in the
+// trailing block, segments of SEG entries of its trailing line (its L row is permuted at the end).
 constexpr int SEG = 1024, IC_THREADS = 256;   // entries per work item, threads of the gather/scatter
 
-__device__ __forceinline__ bool moved_item(long long item, int M, int nl, int nt, int *m, int *part, int *seg) {
-    const int per = nl + nt;
-    if (item >= (long long)M * per) return false;
-    *m = (int)(item / per);
-    const int r = (int)(item % per);
-    *part = r < nl ? 0 : 1;
-    *seg = r < nl ? r : r - nl;
+__device__ __forceinline__ bool moved_item(long long item, int M, int nt, int *m, int *seg) {
+    if (item >= (long long)M * nt) return false;
+    *m = (int)(item / nt);
+    *seg = (int)(item % nt);
     return true;
 }
 
@@ -53,17 +50,13 @@ template <typename T>
 __global__ void gather_kernel(FactorWork<T> w, const int *phi) {
     if (ldcg(w.status) != 0) return;
     const int M = min(ldcg(&w.st->n_moved), w.maxmoved);
-    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
-    const int nl = 0, nt = (n - kend + SEG - 1) / SEG;   // L rows: deferred to the end
+    const int n = w.n, lda = w.lda, kend = w.st->kend;
+    const int nt = (n - kend + SEG - 1) / SEG;
     const T *__restrict__ A = w.A;
-    int m, part, seg;
-    for (long long item = blockIdx.x; moved_item(item, M, nl, nt, &m, &part, &seg); item += gridDim.x) {
+    int m, seg;
+    for (long long item = blockIdx.x; moved_item(item, M, nt, &m, &seg); item += gridDim.x) {
         const int j = w.moved[m], p = w.lpos[j];
-        if (part == 0) {
-            T *tl = w.tmpL + (size_t)m * n;
-            const int hi = min(k0, (seg + 1) * SEG);
-            for (int t = seg * SEG + threadIdx.x; t < hi; t += blockDim.x) tl[t] = A[(size_t)j + (size_t)t * lda];
-        } else if (p >= kend) {
+        if (p >= kend) {
             // SEG / IC_THREADS entries per thread: their marks, then their entries of A, then the
             // stores (the loads of a thread in flight together)
             T *ta = w.tmpA + (size_t)m * n;
@@ -94,17 +87,13 @@ template <typename T>
 __global__ void scatter_kernel(FactorWork<T> w) {
     if (ldcg(w.status) != 0) return;
     const int M = min(ldcg(&w.st->n_moved), w.maxmoved);
-    const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
-    const int nl = 0, nt = (n - kend + SEG - 1) / SEG;   // L rows: deferred to the end
+    const int n = w.n, lda = w.lda, kend = w.st->kend;
+    const int nt = (n - kend + SEG - 1) / SEG;
     T *__restrict__ A = w.A;
-    int m, part, seg;
-    for (long long item = blockIdx.x; moved_item(item, M, nl, nt, &m, &part, &seg); item += gridDim.x) {
-        const int j = w.moved[m], p = w.lpos[j];
-        if (part == 0) {
-            const T *tl = w.tmpL + (size_t)m * n;
-            const int hi = min(k0, (seg + 1) * SEG);
-            for (int t = seg * SEG + threadIdx.x; t < hi; t += blockDim.x) A[(size_t)p + (size_t)t * lda] = tl[t];
-        } else if (p >= kend) {
+    int m, seg;
+    for (long long item = blockIdx.x; moved_item(item, M, nt, &m, &seg); item += gridDim.x) {
+        const int p = w.lpos[w.moved[m]];
+        if (p >= kend) {
             const T *ta = w.tmpA + (size_t)m * n;
             const int hi = min(n, kend + (seg + 1) * SEG);
             const int q0 = kend + seg * SEG + threadIdx.x;

@@ -424,7 +424,6 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     bool have_next = false;
     int run1 = 2;   // consecutive case-(0)/(1) steps; speculate when >= 2
     T preA0 = T(0), preA1 = T(0);   // next pivot's column of A, loaded during a commit
-    int spec_par = 0;
     __syncthreads();
 
     while (i < w.bmax && k < n) {
@@ -505,10 +504,10 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             // ended with a CTA barrier)
         const int P = s_i[1], gP = s_i[3];
         if (P < 0 || !isfinite(s_x[0])) { fail = ST_NONFINITE; break; }
-        // where P's sketch column and a_kk were published: by step (1), or by the speculation
-        const T *payP = have_next ? spec_pay + (size_t)(spec_par * G + gP) * ps : pay1 + (size_t)gP * ps;
-        const T *recP = reinterpret_cast<const T *>(have_next ? spec_rec + (size_t)(spec_par * G + gP) * 4
-                                                              : rec1 + 4 * (size_t)gP);
+        // where step (1) published P's sketch column and a_kk (read only without a committed
+        // speculation, whose commit already loaded them)
+        const T *payP = pay1 + (size_t)gP * ps;
+        const T *recP = reinterpret_cast<const T *>(rec1 + 4 * (size_t)gP);
 
         // ---------------- (2) column P of the Schur complement, lambda and r ----------------
         PANEL_MARK(3);

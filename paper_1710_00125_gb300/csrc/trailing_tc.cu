@@ -23,9 +23,9 @@
 //     triangle.  Per K chunk one thread issues four 16 KB bulk copies (W_hi, W_lo of row block
 //     I; L_hi, L_lo of row block J) into a 3-stage ring guarded by mbarriers, then 4 K-steps x 3
 //     tcgen05.mma (M = N = 128, K = 8 in TF32, 16 in FP16) into a 128-column TMEM accumulator,
-//     and commits the stage
-//     back to its "free" barrier.  After the last chunk the accumulator is drained by four warps
-//     (tcgen05.ld 32x32b, one TMEM lane quarter each) and subtracted from A in place.
+//     and commits the stage back to its "free" barrier.  After the last chunk the accumulator
+//     is drained by eight warps (tcgen05.ld 32x32b: TMEM lane quarter w % 4, 64 of the 128
+//     columns each) and subtracted from A in place.
 // Every wait is bounded (kWaitLimitNs); on expiry the status word is set, the CTA stops
 // issuing work, waits for its issued copies and MMAs (bounded), frees its tensor memory and
 // returns.
