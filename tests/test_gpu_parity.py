@@ -53,7 +53,8 @@ def test_omega_matches_oracle(rcp, d, n, seed):
     assert np.allclose(got, ref, rtol=4e-15, atol=4e-15)
 
 
-@pytest.mark.parametrize("n,d", [(1, 3), (63, 5), (130, 40), (257, 80)])
+@pytest.mark.parametrize("n,d", [(1, 3), (63, 5), (130, 40), (257, 80),
+                                 (2600, 80), (2048, 128)])   # the last two: the FP32 sketch in K slices
 def test_sketch_matches_oracle(rcp, n, d):
     a = inputs.gaussian_sym(n, seed=n)
     A = torch.from_numpy(a).to(DEV)
@@ -214,22 +215,25 @@ def test_mixed_refine_reaches_fp64_backward_error(rcp, handle, prec, kexp):
     assert np.abs(xs - x).max() / np.abs(x).max() <= 50 * cond * 1e-12
 
 
-def test_sysv_device_and_host_buffers(rcp, handle):
-    n = 200
+@pytest.mark.parametrize("n,d,precs", [(200, 40, ("fp64", "fp32")),
+                                        # several host copy blocks and K slices of the sketch: the
+                                        # overlapped block-by-block path must give the same bits
+                                        (700, 40, ("fp32", "f16x3"))])
+def test_sysv_device_and_host_buffers(rcp, handle, n, d, precs):
     a = inputs.gaussian_sym(n, seed=11)
     x = inputs.x_true(n, 4, seed=11)
     rhs = inputs.rhs_for(a, x)
-    for prec in ("fp64", "fp32"):
+    for prec in precs:
         A64 = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
         Bv = torch.from_numpy(rhs.copy()).to(DEV)
         X = torch.zeros_like(Bv)
-        code, st = rcp.rcp_sysv(handle, A64, Bv, X, rcp.make_opts(b=32, d=40, prec=prec), tol=1e-12, max_iter=10)
+        code, st = rcp.rcp_sysv(handle, A64, Bv, X, rcp.make_opts(b=32, d=d, prec=prec), tol=1e-12, max_iter=10)
         assert code == 0
         assert oracle.berr(a, X.cpu().numpy().T, rhs.T) <= 1e-12
         Ah = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         Bh = torch.from_numpy(rhs.copy()).pin_memory()
         Xh = torch.zeros_like(Bh).pin_memory()
-        code, st2 = rcp.rcp_sysv(handle, Ah, Bh, Xh, rcp.make_opts(b=32, d=40, prec=prec), tol=1e-12, max_iter=10,
+        code, st2 = rcp.rcp_sysv(handle, Ah, Bh, Xh, rcp.make_opts(b=32, d=d, prec=prec), tol=1e-12, max_iter=10,
                                  host_buffers=True)
         assert code == 0
         assert np.array_equal(Xh.numpy(), X.cpu().numpy())
