@@ -262,6 +262,26 @@ def test_fp32_factor_backward_error(rcp, handle, prec, n, b, d):
     assert abs(st.n_2x2 - ref["n_2x2"]) <= max(3, 0.05 * ref["n_2x2"])
 
 
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+@pytest.mark.parametrize("n,grid", [(2000, 8), (1040, 4), (1200, 4)])
+def test_fp32_panel_many_rows_per_cta(rcp, handle, prec, n, grid):
+    # 250, 260 and 300 rows per CTA: the fused panel step makes 2, 3 and 3 passes of 128 rows (the
+    # last with too little shared memory for the speculation's shadow sketch: the plain step)
+    a = inputs.gaussian_sym(n, seed=n + grid)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, 64, 40, 5, prec=prec, grid=grid)
+    assert code == 0
+    L = _unit_lower(A)
+    D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
+    p = perm.cpu().numpy()
+    assert sorted(p.tolist()) == list(range(n))
+    err = np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() / np.abs(a).max()
+    assert err < 2e-5 * max(1.0, st.growth_D), err
+    # the same factorization on the default grid: the pivot choices agree up to FP32 near-ties
+    code2, st2, A2, _, _, perm2 = _factor(rcp, handle, a, 64, 40, 5, prec=prec)
+    assert code2 == 0
+    assert abs(st.n_2x2 - st2.n_2x2) <= max(3, 0.05 * st2.n_2x2)
+
+
 @pytest.mark.parametrize("prec", ["tf32x3", "f16x3"])
 @pytest.mark.parametrize("kexp", [2.0, 4.0, 6.0])
 def test_tf32x3_refine_reaches_fp64_backward_error(rcp, handle, kexp, prec):
@@ -418,6 +438,24 @@ def test_full_size_mixed_n16384(rcp, handle, prec):
     assert code == 0
     assert torch.equal(torch.sort(perm.long())[0], torch.arange(n, device=DEV))
     assert _sampled_reconstruction(A64, A, Dd, Ds, perm) < 1e-4 * max(1.0, fst.growth_D)
+
+
+def test_full_size_mixed_n32768(rcp, handle):
+    # 216 rows per panel CTA: two passes of the fused step per pivot; b = 128 (the panel block of W
+    # rows for b = 256 does not fit in shared memory at this n)
+    n = 32768
+    A64 = inputs.spectrum(n, seed=1, kexp=4.0, nrefl=64, device=DEV)
+    xt = torch.from_numpy(inputs.x_true(n, 1, seed=1)).to(DEV)
+    Bv = (A64 @ xt.T).T.contiguous()
+    X = torch.zeros_like(Bv)
+    code, st = rcp.rcp_sysv(handle, A64, Bv, X, rcp.make_opts(b=128, d=80, seed=1, prec="f16x3"), tol=1e-12,
+                            max_iter=10)
+    assert code == 0 and st.berr <= 1e-12
+    r = Bv - (A64 @ X.T).T
+    berr = float((r.abs().amax() / (A64.abs().sum(1).amax() * X.abs().amax())))
+    assert berr <= 4e-12
+    del A64, Bv, X, r
+    torch.cuda.empty_cache()
 
 
 def test_full_size_fp64_n8192(rcp, handle):
