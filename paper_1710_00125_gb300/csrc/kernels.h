@@ -9,6 +9,11 @@ namespace rcpk {
 
 // clock64 stamps per pivot position in the panel trace (profiling level 2)
 constexpr int PANEL_TRACE_SLOTS = 16;
+// 64-bit words of the FP32 panel's argmax key rings (pivot keys, then speculative keys).  A ring
+// slot is indexed by the grid-barrier generation and cleared half a ring ahead of its use, which
+// assumes consecutive generations: a cooperative kernel that advances the generation without the
+// panel's clearing (the block QRCP) zeroes all of them.
+constexpr int PANEL_KEY_WORDS = 32;
 
 template <typename T>
 cudaError_t launch_omega(int d, int n, uint64_t seed, T *om, cudaStream_t s);

@@ -169,6 +169,7 @@ __device__ __forceinline__ unsigned long long ld_key(const unsigned long long *p
 }
 
 constexpr int KEY_RING = 16;
+static_assert(2 * KEY_RING <= PANEL_KEY_WORDS, "the pivot and speculative key rings");
 
 // Block-wide maximum of two packed keys per thread (the result to every thread): per warp two
 // 32-bit redux.sync per key (high word, then the low word among the lanes holding the maximal

@@ -40,6 +40,10 @@ __global__ void __launch_bounds__(QR_THREADS, 1) qrcp_kernel(FactorWork<T> w, in
     __shared__ int s_i[4];
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (ldcg(w.status) != 0) return;
+    // this kernel's grid barriers advance the generation that indexes the panel's key rings
+    // without clearing them: clear them here (no kernel reads them while this one runs)
+    if (cta == 0)
+        for (int e = tid; e < PANEL_KEY_WORDS; e += QR_THREADS) w.keys[e] = 0ull;
     const int n = w.n, d = w.d;
     const int k0 = ldcg(&w.st->next);
     if (k0 >= n) {

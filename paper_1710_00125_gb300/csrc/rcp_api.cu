@@ -210,7 +210,7 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->moved, 2 * N * sizeof(int)));
     RCP_TRY(grow(h->s1v, 4 * (size_t)r.grid * sizeof(double)));
     RCP_TRY(grow(h->s2v, 4 * (size_t)r.grid * sizeof(double)));
-    RCP_TRY(grow(h->keys, 32 * sizeof(unsigned long long)));
+    RCP_TRY(grow(h->keys, PANEL_KEY_WORDS * sizeof(unsigned long long)));
     if (sizeof(T) == sizeof(float)) RCP_TRY(grow(h->skp, sketch_scratch_floats(n, r.d) * sizeof(float)));
     if (r.prec == RCP_TF32X3 || r.prec == RCP_F16X3) RCP_TRY(grow(h->tcops, tc_ops_floats(n, r.b) * sizeof(float)));
     RCP_TRY(grow(h->s1i, 2 * (size_t)r.grid * sizeof(int)));
@@ -320,7 +320,7 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
     FactorWork<T> w = make_work<T>(h, n, A, lda, Dd, Ds, perm, r);
     CU_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
     CU_TRY(cudaMemsetAsync(h->bar.p, 0, sizeof(unsigned), s));
-    CU_TRY(cudaMemsetAsync(h->keys.p, 0, 32 * sizeof(unsigned long long), s));
+    CU_TRY(cudaMemsetAsync(h->keys.p, 0, PANEL_KEY_WORDS * sizeof(unsigned long long), s));
     CU_TRY(launch_factor_init<T>(w, s));
     const T *om = (const T *)r.omega;
     if (!presketched) {   // (else Omega and B = Omega A were formed while A arrived)

@@ -25,14 +25,15 @@ def handle(rcp):
     return rcp.rcp_create()
 
 
-def _factor(rcp, handle, a, b, d, seed, prec="fp64", grid=0):
+def _factor(rcp, handle, a, b, d, seed, prec="fp64", grid=0, q_mode=1):
     n = a.shape[0]
     dt = torch.float64 if prec == "fp64" else torch.float32
     A = torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(dt)
     Dd = torch.zeros(n, dtype=torch.float64, device=DEV)
     Ds = torch.zeros(n, dtype=torch.float64, device=DEV)
     perm = torch.zeros(n, dtype=torch.int32, device=DEV)
-    code, st = rcp.rcp_factor(handle, A, Dd, Ds, perm, rcp.make_opts(b=b, d=d, seed=seed, prec=prec, grid=grid))
+    code, st = rcp.rcp_factor(handle, A, Dd, Ds, perm, rcp.make_opts(b=b, d=d, seed=seed, prec=prec, grid=grid,
+                                                                      q_mode=q_mode))
     return code, st, A, Dd, Ds, perm
 
 
@@ -388,6 +389,25 @@ def test_qb_mixed_refine_reaches_fp64_backward_error(rcp, handle, prec):
     code, rst = rcp.rcp_refine(handle, A64, A, Dd, Ds, perm, prec, Bv, X, tol=1e-12, max_iter=30)
     assert code == 0, rst.as_dict()
     assert oracle.berr(a, X.cpu().numpy().T, rhs.T) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "f16x3"])
+@pytest.mark.parametrize("n", [300, 1000])
+def test_qb_mixed_gaussian_ragged_blocks(rcp, handle, prec, n):
+    # (G + G^T)/2: many 2x2 pivots, blocks of b and b + 1 columns and a ragged last block, with a
+    # block QRCP (its own grid barriers) between consecutive panels
+    a = inputs.gaussian_sym(n, seed=0)
+    ref = oracle.rcp(a, oracle.omega(1, 80, n), q_mode=2, block=64, record=False)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, 64, 80, 1, prec=prec, q_mode=2)
+    assert code == 0
+    assert torch.equal(torch.sort(perm.long())[0], torch.arange(n, device=DEV))
+    L = _unit_lower(A)
+    D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
+    p = perm.cpu().numpy()
+    assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() / np.abs(a).max() < 2e-5 * max(1.0, st.growth_D)
+    # FP32 decisions may part from the FP64 pivot sequence at near ties, not the growth's scale
+    assert st.growth_D <= 3.0 * oracle.growth_d(ref["Dd"], ref["Ds"], a)
+    assert abs(st.n_2x2 - ref["n_2x2"]) <= 0.1 * ref["n_2x2"] + 3
 
 
 # ------------------------------------------------------------------------------------------
