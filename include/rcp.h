@@ -88,6 +88,8 @@ typedef struct {
     int device_flags;         /* raw device status bits                                     */
     double berr;              /* final normwise backward error (rcp_refine)                 */
     double anorm;             /* ||A||_inf of the original matrix (rcp_refine)              */
+    int gmres_iters;          /* GMRES iterations (applications of M^{-1} A) of              */
+                              /* rcp_refine_gmres, or of rcp_sysv's fallback to it          */
 } rcp_stats;
 
 typedef struct rcp_handle rcp_handle;
@@ -145,8 +147,10 @@ rcp_status rcp_solve(rcp_handle *h, int n, int nrhs, const void *LA, int lda, co
  * rcp_refine -- FP64 iterative refinement on top of a (possibly FP32) factor:
  * x_0 = solve(b); repeat r = b - A x (FP64, original A), berr = ||r||_inf /
  * (||A||_inf ||x||_inf) (the experiments section's backward error), stop when berr <= tol,
- * else x += solve(r).  At most max_iter corrections.  The loop control stays on the device
- * (no host round trip per iteration).
+ * else x += solve(r).  At most max_iter corrections; the loop also stops when a correction
+ * fails to halve berr (the factor's error times the condition number is not small: the
+ * iteration stagnates or diverges; rcp_refine_gmres is the remedy).  The loop control stays
+ * on the device (no host round trip per iteration).
  *   A64, lda     device double: the ORIGINAL matrix (lower triangle)
  *   LA, ldla     device factor; Dd, Ds, perm from rcp_factor; prec its precision
  *   Bv, ldb      device double n x nrhs right-hand sides
@@ -160,8 +164,39 @@ rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda
                       rcp_stream_t stream, rcp_stats *stats);
 
 /*
+ * rcp_refine_gmres -- GMRES-based iterative refinement (Carson and Higham, "Accelerating the
+ * solution of linear systems by iterative refinement in three precisions", 2018): per outer
+ * step r = b - A x (FP64, original A), stop when berr <= tol (as rcp_refine), else solve the
+ * correction equation A d = r by one cycle of at most `restart` steps of GMRES (Saad and
+ * Schultz, 1986) on the left-preconditioned system M^{-1} A d = M^{-1} r, M = L D L^T the
+ * computed factor (applied by rcp_solve's kernels), FP64 Krylov basis with classical
+ * Gram-Schmidt applied twice, until the preconditioned residual falls by 1e-10; x += d.
+ * Converges where the factor is too inaccurate for rcp_refine: with FP32 factors it reaches
+ * berr <= 1e-12 on matrices with condition numbers up to about 1e10 (beyond that, factor in
+ * FP64).  Right-hand sides are refined one after another.
+ *   arguments as rcp_refine; restart: Krylov dimension per cycle (0 = 64, at most 128);
+ *   max_outer: corrections (GMRES cycles) per right-hand side; use_x != 0: X holds the starting
+ *   iterates, else X = solve(B) first.
+ *   stats (host, optional): berr (max over columns), refine_iters (cycles), gmres_iters
+ * The host takes the scalars of each GMRES step (one device-to-host read per step), so the
+ * call synchronizes the stream and cannot be captured in a graph.  Returns RCP_ENOCONV when
+ * berr > tol after max_outer cycles.
+ */
+rcp_status rcp_refine_gmres(rcp_handle *h, int n, int nrhs, const double *A64, int lda, const void *LA,
+                            int ldla, const double *Dd, const double *Ds, const int *perm, rcp_prec prec,
+                            const double *Bv, int ldb, double *X, int ldx, double tol, int max_outer,
+                            int restart, int use_x, rcp_stream_t stream, rcp_stats *stats);
+
+/* Host helper of rcp_refine_gmres (no device work): y = argmin || beta e_1 - H y ||_2 for the
+ * (k+1) x k upper Hessenberg H (column-major, ldh >= k+1; entries below the subdiagonal are
+ * ignored), by Givens rotations; *resid = the minimal residual norm.  A zero diagonal after
+ * the rotations (singular H) gives y_j = 0. */
+rcp_status rcp_gmres_lsq(int k, const double *H, int ldh, double beta, double *y, double *resid);
+
+/*
  * rcp_sysv -- solve A X = B end to end: copy the lower triangle of A64 (rounding it to
- * FP32 for the mixed precisions) into handle workspace, rcp_factor, rcp_refine.
+ * FP32 for the mixed precisions) into handle workspace, rcp_factor, rcp_refine; when that
+ * stops short of tol (stagnation), rcp_refine_gmres from its iterate (stats->gmres_iters > 0).
  *   A64, lda, Bv, ldb, X, ldx   device pointers, or host pointers when host_buffers != 0 (then
  *                the copies in and out are part of the call; pinned host memory is fastest; of
  *                A64 only the lower triangle is transferred, as rectangles of 256 columns from

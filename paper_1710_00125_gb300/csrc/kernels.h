@@ -121,8 +121,10 @@ cudaError_t launch_symv_residual(int n, int nrhs, const double *A, int lda, cons
                                  const double *Bv, int ldb, double *R, int ldr, double *part,
                                  unsigned long long *mx, const int *skip, cudaStream_t s);
 cudaError_t launch_anorm(int n, const double *A, int lda, double *part, double *anorm, cudaStream_t s);
+// berr from the residual maxima; conv = 1 when berr <= tol, 2 when a correction did not halve
+// berr (stagnation or divergence; prev holds the previous berr, 0 before the first)
 cudaError_t launch_refine_check(int nrhs, const unsigned long long *mx, const double *anorm, double tol, int *conv,
-                                double *berr, int *iters, int count_iter, cudaStream_t s);
+                                double *berr, double *prev, int *iters, int count_iter, cudaStream_t s);
 cudaError_t launch_axpy_update(int n, int nrhs, double *X, int ldx, const double *D, int ldd,
                                const int *skip, cudaStream_t s);
 // lower triangle of columns c0 .. c1-1 (c1 < 0: all) of an FP64 matrix, FP64 or rounded to FP32
@@ -131,6 +133,16 @@ cudaError_t launch_copy_lower_f64(int n, const double *src, int lds, void *dst, 
 // columns c0 .. c1-1 of B = Omega A (FP32); A must hold its final values in columns < c1
 cudaError_t launch_sketch_cols_f32(int n, int d, const float *A, int lda, const float *om, float *B, float *part,
                                    size_t part_floats, int c0, int c1, cudaStream_t s);
+
+// Krylov basis operations of GMRES-based refinement (FP64, basis column-major with ld ldv).
+// out[c] = V(:, c)^T w for c < ncol (part: gm_part_doubles(n, ncol) doubles, deterministic);
+// w += sign * V(:, 0:ncol) h (h on the device); w *= f.
+size_t gm_part_doubles(int n, int ncol_max);
+cudaError_t launch_gm_dots(int n, int ncol, const double *V, int ldv, const double *w, double *part, double *out,
+                           cudaStream_t s);
+cudaError_t launch_gm_update(int n, int ncol, const double *V, int ldv, const double *h, double sign, double *w,
+                             cudaStream_t s);
+cudaError_t launch_gm_scale(int n, double f, double *w, cudaStream_t s);
 
 // Batched small systems (one CTA per system at a time).  info of a system that met a NaN or
 // Inf is BT_INFO_NONFINITE.

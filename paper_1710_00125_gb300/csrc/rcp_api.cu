@@ -61,6 +61,7 @@ struct rcp_handle {
     std::vector<Tuned> tuned;                      // batched panel widths chosen by rcp_tune_batched
     cudaStream_t copy_stream = nullptr;            // rcp_sysv with host buffers: block copies of A
     std::vector<cudaEvent_t> copy_events;          //   one per block, and one for the start
+    Buf gmV, gmZ, gmP, gmH;                        // GMRES refinement: basis, zero vector, partial sums, scalars
 };
 
 namespace {
@@ -113,9 +114,9 @@ rcp_status grow_zeroed(Buf &b, size_t bytes, cudaStream_t s, bool sync) {
 
 // Scalars of the refinement loop, laid out in h->scal.
 struct RefineScalars {
-    int conv;
+    int conv;               // 0 running, 1 converged, 2 stopped: a correction did not halve berr
     int iters;
-    int pad[2];
+    double prev;            // berr of the previous iterate (0 before the first)
     double berr;
     double anorm;
     unsigned long long mx[2 * 1024];   // per right-hand side: max |r|, max |x|
@@ -423,7 +424,8 @@ void rcp_destroy(rcp_handle *h) {
     if (!h) return;
     Buf *all[] = {&h->psnap, &h->pinv, &h->pbounds, &h->bord, &h->bom, &h->bticket, &h->bscr, &h->tcops, &h->keys, &h->skp, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
                   &h->s1v, &h->s2v, &h->s3v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
-                  &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm};
+                  &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm,
+                  &h->gmV, &h->gmZ, &h->gmP, &h->gmH};
     for (Buf *b : all)
         if (b->p) cudaFree(b->p);
     for (auto &e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -508,7 +510,7 @@ rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda
     RCP_TRY(grow(h->part, symv_part_doubles(n, nrhs) * sizeof(double)));
     RefineScalars *sc = (RefineScalars *)h->scal.p;
     double *R = (double *)h->R.p, *Dc = (double *)h->Dc.p, *part = (double *)h->part.p;
-    CU_TRY(cudaMemsetAsync(sc, 0, 2 * sizeof(int), s));
+    CU_TRY(cudaMemsetAsync(sc, 0, offsetof(RefineScalars, berr), s));
     CU_TRY(launch_anorm(n, A64, lda, part, &sc->anorm, s));
     CU_TRY(cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double), Bv, (size_t)ldb * sizeof(double), (size_t)n * sizeof(double),
                              nrhs, cudaMemcpyDeviceToDevice, s));
@@ -522,7 +524,8 @@ rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda
             PhaseScope ps(h, s, PH_RESIDUAL);
             CU_TRY(launch_symv_residual(n, nrhs, A64, lda, X, ldx, Bv, ldb, R, n, part, sc->mx, &sc->conv, s));
         }
-        CU_TRY(launch_refine_check(nrhs, sc->mx, &sc->anorm, tol, &sc->conv, &sc->berr, &sc->iters, it < max_iter, s));
+        CU_TRY(launch_refine_check(nrhs, sc->mx, &sc->anorm, tol, &sc->conv, &sc->berr, &sc->prev, &sc->iters,
+                                   it < max_iter, s));
         if (it == max_iter) break;
         CU_TRY(cudaMemcpyAsync(Dc, R, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
         RCP_TRY(do_solve(Dc, &sc->conv));
@@ -541,6 +544,165 @@ rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda
     rcp_status e = status_from_bits(bits);
     if (e != RCP_OK) return e;
     if (!(host.berr <= tol)) return RCP_ENOCONV;
+    return RCP_OK;
+}
+
+// Least-squares problem of GMRES: min_y || beta e_1 - H y ||_2 with H the (k+1) x k upper
+// Hessenberg matrix of the Arnoldi process, by Givens rotations (Saad and Schultz, 1986).
+rcp_status rcp_gmres_lsq(int k, const double *H, int ldh, double beta, double *y, double *resid) {
+    if (k < 0 || !resid || (k > 0 && (!H || !y || ldh < k + 1))) return RCP_EINVAL;
+    std::vector<double> R((size_t)(k + 1) * (k > 0 ? k : 1)), g((size_t)k + 1, 0.0);
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i <= k; ++i) R[(size_t)i + (size_t)j * (k + 1)] = i <= j + 1 ? H[(size_t)i + (size_t)j * ldh] : 0.0;
+    g[0] = beta;
+    auto at = [&](int i, int j) -> double & { return R[(size_t)i + (size_t)j * (k + 1)]; };
+    for (int j = 0; j < k; ++j) {
+        // the rotation that zeroes H(j+1, j) against H(j, j), applied to rows j, j+1
+        const double a = at(j, j), b = at(j + 1, j), r = std::hypot(a, b);
+        const double c = r > 0.0 ? a / r : 1.0, sn = r > 0.0 ? b / r : 0.0;
+        for (int l = j; l < k; ++l) {
+            const double t1 = at(j, l), t2 = at(j + 1, l);
+            at(j, l) = c * t1 + sn * t2;
+            at(j + 1, l) = -sn * t1 + c * t2;
+        }
+        const double t1 = g[j], t2 = g[j + 1];
+        g[j] = c * t1 + sn * t2;
+        g[j + 1] = -sn * t1 + c * t2;
+    }
+    *resid = std::fabs(g[k]);
+    for (int j = k - 1; j >= 0; --j) {
+        double t = g[j];
+        for (int l = j + 1; l < k; ++l) t -= at(j, l) * y[l];
+        y[j] = at(j, j) != 0.0 ? t / at(j, j) : 0.0;   // a zero pivot: exact breakdown of a singular H
+    }
+    return RCP_OK;
+}
+
+namespace {
+constexpr int kGmresMaxRestart = 128;
+constexpr double kGmresInnerTol = 1e-10;   // relative reduction of the preconditioned residual per cycle
+}
+
+rcp_status rcp_refine_gmres(rcp_handle *h, int n, int nrhs, const double *A64, int lda, const void *LA, int ldla,
+                            const double *Dd, const double *Ds, const int *perm, rcp_prec prec, const double *Bv,
+                            int ldb, double *X, int ldx, double tol, int max_outer, int restart, int use_x,
+                            rcp_stream_t stream, rcp_stats *stats) {
+    if (!h || n < 0 || nrhs < 0 || nrhs > kMaxRhs || !valid_prec(prec) || max_outer < 0) return RCP_EINVAL;
+    if (restart <= 0) restart = 64;
+    if (restart > kGmresMaxRestart) return RCP_EINVAL;
+    if (stats) std::memset(stats, 0, sizeof *stats);
+    if (n == 0 || nrhs == 0) return RCP_OK;
+    if (!A64 || !LA || !Dd || !Ds || !perm || !Bv || !X || lda < n || ldla < n || ldb < n || ldx < n) return RCP_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int m = restart;
+    RCP_TRY(ensure_small(h));
+    RCP_TRY(grow(h->R, (size_t)n * sizeof(double)));
+    RCP_TRY(grow(h->part, symv_part_doubles(n, 1) * sizeof(double)));
+    RCP_TRY(grow(h->gmV, (size_t)n * (m + 1) * sizeof(double)));
+    RCP_TRY(grow(h->gmZ, (size_t)n * sizeof(double)));
+    RCP_TRY(grow(h->gmP, gm_part_doubles(n, m + 1) * sizeof(double)));
+    RCP_TRY(grow(h->gmH, (size_t)(2 * (m + 1) + 2) * sizeof(double)));
+    RefineScalars *sc = (RefineScalars *)h->scal.p;
+    double *R = (double *)h->R.p, *part = (double *)h->part.p, *V = (double *)h->gmV.p, *Z = (double *)h->gmZ.p;
+    double *gp = (double *)h->gmP.p, *hd = (double *)h->gmH.p;
+    double *h1 = hd, *h2 = hd + (m + 1), *nrm2 = hd + 2 * (m + 1);
+    CU_TRY(cudaMemsetAsync(Z, 0, (size_t)n * sizeof(double), s));
+    CU_TRY(launch_anorm(n, A64, lda, part, &sc->anorm, s));
+    auto solve1 = [&](double *v, int ld, int cols) -> rcp_status {
+        if (prec == RCP_FP64) return solve_impl<double>(h, n, cols, (const double *)LA, ldla, Dd, Ds, perm, v, ld, nullptr, s);
+        return solve_impl<float>(h, n, cols, (const float *)LA, ldla, Dd, Ds, perm, v, ld, nullptr, s);
+    };
+    if (!use_x) {
+        CU_TRY(cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double), Bv, (size_t)ldb * sizeof(double),
+                                 (size_t)n * sizeof(double), nrhs, cudaMemcpyDeviceToDevice, s));
+        RCP_TRY(solve1(X, ldx, nrhs));
+    }
+    double anorm = 0.0;
+    CU_TRY(cudaMemcpyAsync(&anorm, &sc->anorm, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    std::vector<double> H((size_t)(m + 1) * m), y((size_t)m), hh((size_t)2 * (m + 1) + 1);
+    int outer_total = 0, inner_total = 0;
+    double worst = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+        double *x = X + (size_t)c * ldx;
+        const double *b = Bv + (size_t)c * ldb;
+        double berr = INFINITY;
+        for (int outer = 0;; ++outer) {
+            // r = b - A x (FP64) and its backward error
+            {
+                PhaseScope ps(h, s, PH_RESIDUAL);
+                CU_TRY(launch_symv_residual(n, 1, A64, lda, x, ldx, b, ldb, R, n, part, sc->mx, nullptr, s));
+            }
+            unsigned long long mxh[2];
+            CU_TRY(cudaMemcpyAsync(mxh, sc->mx, sizeof mxh, cudaMemcpyDeviceToHost, s));
+            CU_TRY(cudaStreamSynchronize(s));
+            double rm, xm;
+            std::memcpy(&rm, &mxh[0], sizeof rm);
+            std::memcpy(&xm, &mxh[1], sizeof xm);
+            berr = (anorm > 0.0 && xm > 0.0) ? rm / (anorm * xm) : (rm > 0.0 ? INFINITY : 0.0);
+            if (!std::isfinite(berr) && outer > 0) return RCP_ENONFINITE;
+            if (berr <= tol || outer == max_outer) break;
+            // one GMRES cycle on M^{-1} A d = M^{-1} r: v_0 = M^{-1} r / beta
+            CU_TRY(cudaMemcpyAsync(V, R, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            RCP_TRY(solve1(V, n, 1));
+            CU_TRY(launch_gm_dots(n, 1, V, n, V, gp, nrm2, s));
+            double b2 = 0.0;
+            CU_TRY(cudaMemcpyAsync(&b2, nrm2, sizeof b2, cudaMemcpyDeviceToHost, s));
+            CU_TRY(cudaStreamSynchronize(s));
+            if (!std::isfinite(b2)) return RCP_ENONFINITE;
+            if (!(b2 > 0.0)) break;   // M^{-1} r = 0: nothing left to correct
+            const double beta = std::sqrt(b2);
+            CU_TRY(launch_gm_scale(n, 1.0 / beta, V, s));
+            int k = 0;
+            double res = beta;
+            for (int j = 0; j < m; ++j) {
+                double *vj = V + (size_t)j * n, *u = V + (size_t)(j + 1) * n;
+                // u = -M^{-1} A v_j (the residual kernel with a zero right-hand side gives -A v_j)
+                {
+                    PhaseScope ps(h, s, PH_RESIDUAL);
+                    CU_TRY(launch_symv_residual(n, 1, A64, lda, vj, n, Z, n, u, n, part, sc->mx, nullptr, s));
+                }
+                RCP_TRY(solve1(u, n, 1));
+                // classical Gram-Schmidt, twice, against v_0 .. v_j; then ||u||^2
+                CU_TRY(launch_gm_dots(n, j + 1, V, n, u, gp, h1, s));
+                CU_TRY(launch_gm_update(n, j + 1, V, n, h1, -1.0, u, s));
+                CU_TRY(launch_gm_dots(n, j + 1, V, n, u, gp, h2, s));
+                CU_TRY(launch_gm_update(n, j + 1, V, n, h2, -1.0, u, s));
+                CU_TRY(launch_gm_dots(n, 1, u, n, u, gp, nrm2, s));
+                CU_TRY(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
+                CU_TRY(cudaStreamSynchronize(s));
+                // u held -M^{-1} A v_j: H(i, j) = -(h1 + h2)_i, and v_{j+1} = -u / ||u||
+                for (int i = 0; i <= j; ++i) H[(size_t)i + (size_t)j * (m + 1)] = -(hh[i] + hh[(size_t)(m + 1) + i]);
+                const double un2 = hh[(size_t)2 * (m + 1)];
+                if (!std::isfinite(un2)) return RCP_ENONFINITE;
+                const double hn = std::sqrt(un2);
+                H[(size_t)(j + 1) + (size_t)j * (m + 1)] = hn;
+                k = j + 1;
+                ++inner_total;
+                RCP_TRY(rcp_gmres_lsq(k, H.data(), m + 1, beta, y.data(), &res));
+                if (!(hn > 0.0) || res <= kGmresInnerTol * beta) break;   // breakdown (exact) or converged
+                CU_TRY(launch_gm_scale(n, -1.0 / hn, u, s));
+            }
+            // x += V_k y
+            CU_TRY(cudaMemcpyAsync(h1, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+            CU_TRY(launch_gm_update(n, k, V, n, h1, 1.0, x, s));
+            ++outer_total;
+        }
+        if (!(berr <= worst)) worst = berr;
+    }
+    CU_TRY(cudaStreamSynchronize(s));
+    int bits = 0;
+    CU_TRY(cudaMemcpy(&bits, h->status.p, sizeof bits, cudaMemcpyDeviceToHost));
+    if (stats) {
+        stats->berr = worst;
+        stats->anorm = anorm;
+        stats->refine_iters = outer_total;
+        stats->gmres_iters = inner_total;
+        stats->device_flags = bits;
+    }
+    rcp_status e = status_from_bits(bits);
+    if (e != RCP_OK) return e;
+    if (!(worst <= tol)) return RCP_ENOCONV;
     return RCP_OK;
 }
 
@@ -630,13 +792,33 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
     rcp_status rs = rcp_refine(h, n, nrhs, dA, dlda, h->F.p, n, (double *)h->Dd.p, (double *)h->Ds.p, (int *)h->perm.p, r.prec,
                                dB, dldb, dX, dldx, tol, max_iter, stream, nullptr);
     if (rs != RCP_OK) return rs;
+    // classic refinement stopped short of the tolerance (the factor is too inaccurate for this
+    // system): GMRES-based refinement from the current iterate
+    RefineScalars host;
+    CU_TRY(cudaStreamSynchronize(s));
+    CU_TRY(cudaMemcpy(&host, h->scal.p, offsetof(RefineScalars, mx), cudaMemcpyDeviceToHost));
+    rcp_stats gst;
+    std::memset(&gst, 0, sizeof gst);
+    bool used_gmres = false;
+    {
+        FactorState fs0;
+        int bits0 = 0;
+        CU_TRY(cudaMemcpy(&fs0, h->state.p, sizeof fs0, cudaMemcpyDeviceToHost));
+        CU_TRY(cudaMemcpy(&bits0, h->status.p, sizeof bits0, cudaMemcpyDeviceToHost));
+        if (max_iter > 0 && !(host.berr <= tol) && bits0 == 0 && fs0.info == 0) {
+            rcp_status gs = rcp_refine_gmres(h, n, nrhs, dA, dlda, h->F.p, n, (double *)h->Dd.p, (double *)h->Ds.p,
+                                             (int *)h->perm.p, r.prec, dB, dldb, dX, dldx, tol, max_iter, 0, 1, stream,
+                                             &gst);
+            if (gs != RCP_OK && gs != RCP_ENOCONV) return gs;
+            used_gmres = true;
+        }
+    }
     if (host_buffers)
         CU_TRY(cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double), dX, (size_t)n * sizeof(double), (size_t)n * sizeof(double),
                                  nrhs, cudaMemcpyDeviceToHost, s));
     CU_TRY(cudaStreamSynchronize(s));
     // statistics of both phases
     FactorState st;
-    RefineScalars host;
     int bits = 0;
     CU_TRY(cudaMemcpy(&st, h->state.p, sizeof st, cudaMemcpyDeviceToHost));
     CU_TRY(cudaMemcpy(&host, h->scal.p, offsetof(RefineScalars, mx), cudaMemcpyDeviceToHost));
@@ -648,14 +830,16 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
     stats->n_2x2 = st.n2x2;
     stats->info = st.info;
     stats->device_flags = bits;
-    stats->berr = host.berr;
+    stats->berr = used_gmres ? gst.berr : host.berr;
     stats->anorm = host.anorm;
-    stats->refine_iters = host.iters;
+    stats->refine_iters = host.iters + gst.refine_iters;
+    stats->gmres_iters = gst.gmres_iters;
     (void)rst;
+    const double berr_final = stats->berr;
     rcp_status e = status_from_bits(bits);
     if (e != RCP_OK) return e;
     if (st.info > 0) return (rcp_status)st.info;
-    if (max_iter > 0 && !(host.berr <= tol)) return RCP_ENOCONV;
+    if (max_iter > 0 && !(berr_final <= tol)) return RCP_ENOCONV;
     return RCP_OK;
 }
 

@@ -783,7 +783,7 @@ __global__ void anorm_finish_kernel(int n, int nch, const double *part, const do
 
 // berr = max_c ||r_c||_inf / (||A||_inf ||x_c||_inf); sets conv when berr <= tol.
 __global__ void refine_check_kernel(int nrhs, const unsigned long long *mx, const double *anorm, double tol,
-                                    int *conv, double *berr, int *iters, int count_iter) {
+                                    int *conv, double *berr, double *prev, int *iters, int count_iter) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (*conv) return;
     double worst = 0.0;
@@ -794,7 +794,9 @@ __global__ void refine_check_kernel(int nrhs, const unsigned long long *mx, cons
     }
     *berr = worst;
     if (worst <= tol) *conv = 1;
+    else if (*prev > 0.0 && !(worst <= 0.5 * *prev)) *conv = 2;   // the last correction did not halve berr
     else if (count_iter) *iters += 1;
+    *prev = worst;
 }
 
 __global__ void axpy_kernel(int n, int nrhs, double *X, int ldx, const double *D, int ldd, const int *skip) {
@@ -846,8 +848,8 @@ cudaError_t launch_anorm(int n, const double *A, int lda, double *part, double *
 }
 
 cudaError_t launch_refine_check(int nrhs, const unsigned long long *mx, const double *anorm, double tol, int *conv,
-                                double *berr, int *iters, int count_iter, cudaStream_t s) {
-    refine_check_kernel<<<1, 32, 0, s>>>(nrhs, mx, anorm, tol, conv, berr, iters, count_iter);
+                                double *berr, double *prev, int *iters, int count_iter, cudaStream_t s) {
+    refine_check_kernel<<<1, 32, 0, s>>>(nrhs, mx, anorm, tol, conv, berr, prev, iters, count_iter);
     count_launches(1);
     return cudaGetLastError();
 }

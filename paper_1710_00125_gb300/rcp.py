@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("growth_D", ctypes.c_double), ("max_abs_L", ctypes.c_double),
                 ("min_sketch_ratio", ctypes.c_double), ("n_2x2", ctypes.c_int), ("info", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("device_flags", ctypes.c_int), ("berr", ctypes.c_double),
-                ("anorm", ctypes.c_double)]
+                ("anorm", ctypes.c_double), ("gmres_iters", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -76,6 +76,8 @@ def lib():
         L.rcp_factor.argtypes = [P, I, P, I, P, P, P, ctypes.POINTER(Opts), P, ctypes.POINTER(Stats)]
         L.rcp_solve.argtypes = [P, I, I, P, I, P, P, P, I, P, I, P]
         L.rcp_refine.argtypes = [P, I, I, P, I, P, I, P, P, P, I, P, I, P, I, D, I, P, ctypes.POINTER(Stats)]
+        L.rcp_refine_gmres.argtypes = [P, I, I, P, I, P, I, P, P, P, I, P, I, P, I, D, I, I, I, P,
+                                       ctypes.POINTER(Stats)]
         L.rcp_sysv.argtypes = [P, I, I, P, I, P, I, P, I, ctypes.POINTER(Opts), D, I, I, P, ctypes.POINTER(Stats)]
         L.rcp_omega.argtypes = [I, I, ctypes.c_uint64, P, P]
         L.rcp_sketch.argtypes = [I, I, P, I, I, ctypes.c_uint64, P, P, P]
@@ -210,6 +212,23 @@ def rcp_refine(h: Handle, A64, LA, Dd, Ds, perm, prec, Bv, X, tol=1e-12, max_ite
         return code, st
     _check(code, "rcp_refine")
     return code, (st if stats else None)
+
+
+def rcp_refine_gmres(h: Handle, A64, LA, Dd, Ds, perm, prec, Bv, X, tol=1e-12, max_outer=10, restart=0,
+                     use_x=False, stream=None, raise_noconv: bool = False):
+    """GMRES-based refinement (M^{-1} A preconditioned by the factor); returns (status, Stats)."""
+    n = A64.shape[0]
+    nrhs, ldb = _rhs_view(Bv, n)
+    if isinstance(prec, str):
+        prec = PREC_NAMES[prec]
+    st = Stats()
+    code = lib().rcp_refine_gmres(h.h, n, nrhs, _ptr(A64), n, _ptr(LA), n, _ptr(Dd), _ptr(Ds), _ptr(perm), prec,
+                                  _ptr(Bv), ldb, _ptr(X), ldb, float(tol), int(max_outer), int(restart),
+                                  int(bool(use_x)), _stream(stream), ctypes.byref(st))
+    if code == -6 and not raise_noconv:
+        return code, st
+    _check(code, "rcp_refine_gmres")
+    return code, st
 
 
 def rcp_sysv(h: Handle, A64, Bv, X, opts: Opts | None = None, tol=1e-12, max_iter=10, host_buffers=False,

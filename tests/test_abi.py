@@ -1,0 +1,101 @@
+"""The C ABI without a GPU: the library loads, exports every function ``include/rcp.h``
+declares, and its host-only helpers compute what they document (no device work)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rcp.h")
+
+
+@pytest.fixture(scope="module")
+def clib():
+    from paper_1710_00125_gb300 import build
+    return ctypes.CDLL(build.build())   # compiles only when a source is newer than the library
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^[A-Za-z_][\w \*]*?\b(rcp_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("rcp_create", "rcp_destroy", "rcp_factor", "rcp_solve", "rcp_refine", "rcp_refine_gmres",
+                 "rcp_sysv", "rcp_factor_batched", "rcp_refine_batched", "rcp_omega", "rcp_sketch"):
+        assert must in names
+
+
+def test_library_exports_every_declared_function(clib):
+    missing = [nm for nm in _declared() if not hasattr(clib, nm)]
+    assert missing == []
+
+
+def test_status_strings(clib):
+    clib.rcp_status_string.restype = ctypes.c_char_p
+    clib.rcp_status_string.argtypes = [ctypes.c_int]
+    assert clib.rcp_status_string(0) == b"ok"
+    assert clib.rcp_status_string(-6) == b"refinement did not reach the tolerance"
+    assert clib.rcp_status_string(-7) == b"unsupported size or option"
+
+
+def _lsq(clib, H, beta):
+    k = H.shape[1]
+    Hf = np.asfortranarray(H, dtype=np.float64)
+    y = np.zeros(max(k, 1))
+    res = ctypes.c_double(-1.0)
+    clib.rcp_gmres_lsq.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_double)]
+    code = clib.rcp_gmres_lsq(k, Hf.ctypes.data, H.shape[0], beta, y.ctypes.data, ctypes.byref(res))
+    return code, y[:k], res.value
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 17, 30, 64])
+def test_gmres_lsq_matches_numpy_lstsq(clib, k):
+    rng = np.random.default_rng(k)
+    H = np.triu(rng.standard_normal((k + 1, k)), -1)
+    beta = 2.5
+    code, y, res = _lsq(clib, H, beta)
+    assert code == 0
+    rhs = np.zeros(k + 1)
+    rhs[0] = beta
+    yref = np.linalg.lstsq(H, rhs, rcond=None)[0]
+    # forward error bounded by the conditioning of H; the residual is optimal and reported
+    assert np.abs(y - yref).max() <= 1e-14 * np.linalg.cond(H) * np.abs(yref).max()
+    assert np.linalg.norm(rhs - H @ y) == pytest.approx(np.linalg.norm(rhs - H @ yref), rel=1e-9, abs=1e-13)
+    assert res == pytest.approx(np.linalg.norm(rhs - H @ yref), rel=1e-9, abs=1e-13)
+
+
+def test_gmres_lsq_ignores_entries_below_the_subdiagonal(clib):
+    rng = np.random.default_rng(3)
+    H = np.triu(rng.standard_normal((7, 6)), -1)
+    noisy = H + np.tril(rng.standard_normal((7, 6)), -2)
+    assert np.array_equal(_lsq(clib, H, 1.0)[1], _lsq(clib, noisy, 1.0)[1])
+
+
+def test_gmres_lsq_exact_breakdown(clib):
+    # H(k, k-1) = 0 (an invariant Krylov space): the square part is solved exactly
+    rng = np.random.default_rng(4)
+    k = 6
+    H = np.triu(rng.standard_normal((k + 1, k)), -1)
+    H[k, k - 1] = 0.0
+    code, y, res = _lsq(clib, H, 1.0)
+    assert code == 0 and res < 1e-14
+    e1 = np.zeros(k)
+    e1[0] = 1.0
+    assert np.allclose(H[:k] @ y, e1, atol=1e-12)
+
+
+def test_gmres_lsq_rejects_bad_arguments(clib):
+    res = ctypes.c_double()
+    clib.rcp_gmres_lsq.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_double)]
+    H = np.zeros((3, 2), order="F")
+    y = np.zeros(2)
+    assert clib.rcp_gmres_lsq(2, H.ctypes.data, 2, 1.0, y.ctypes.data, ctypes.byref(res)) == -1   # ldh < k + 1
+    assert clib.rcp_gmres_lsq(-1, H.ctypes.data, 3, 1.0, y.ctypes.data, ctypes.byref(res)) == -1
+    # k = 0: the residual is beta
+    assert clib.rcp_gmres_lsq(0, None, 1, 3.0, None, ctypes.byref(res)) == 0 and res.value == 3.0

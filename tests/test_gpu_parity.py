@@ -410,6 +410,63 @@ def test_qb_mixed_gaussian_ragged_blocks(rcp, handle, prec, n):
     assert abs(st.n_2x2 - ref["n_2x2"]) <= 0.1 * ref["n_2x2"] + 3
 
 
+def _mixed_system(rcp, handle, n, kexp, prec, seed=7, nrhs=1):
+    a = inputs.spectrum(n, seed=seed, kexp=kexp, nrefl=16)
+    x = inputs.x_true(n, nrhs, seed=seed)
+    rhs = inputs.rhs_for(a, x)
+    A = torch.from_numpy(np.ascontiguousarray(a)).to(DEV).float()
+    Dd = torch.zeros(n, dtype=torch.float64, device=DEV)
+    Ds = torch.zeros_like(Dd)
+    perm = torch.zeros(n, dtype=torch.int32, device=DEV)
+    code, _ = rcp.rcp_factor(handle, A, Dd, Ds, perm, rcp.make_opts(b=64, d=80, seed=1, prec=prec))
+    assert code == 0
+    A64 = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    Bv = torch.from_numpy(rhs.copy()).to(DEV)
+    return a, rhs, A64, A, Dd, Ds, perm, Bv
+
+
+@pytest.mark.parametrize("n,prec", [(1000, "f16x3"), (4000, "f16x3"), (4000, "fp32")])
+def test_gmres_refinement_where_classic_refinement_stalls(rcp, handle, n, prec):
+    # condition number 1e10: the FP32 factor's error times kappa is far above one
+    a, rhs, A64, A, Dd, Ds, perm, Bv = _mixed_system(rcp, handle, n, 10.0, prec)
+    X = torch.zeros_like(Bv)
+    code, st = rcp.rcp_refine(handle, A64, A, Dd, Ds, perm, prec, Bv, X, tol=1e-12, max_iter=10)
+    assert code == -6 and st.berr > 1e-12   # stops early: a correction did not halve berr
+    assert st.refine_iters <= 3
+    X2 = torch.zeros_like(Bv)
+    code, st = rcp.rcp_refine_gmres(handle, A64, A, Dd, Ds, perm, prec, Bv, X2, tol=1e-12, max_outer=10)
+    assert code == 0 and st.berr <= 1e-12 and st.gmres_iters > 0
+    assert oracle.berr(a, X2.cpu().numpy().T, rhs.T) <= 1e-12
+
+
+def test_gmres_refinement_several_rhs_and_starting_iterate(rcp, handle):
+    a, rhs, A64, A, Dd, Ds, perm, Bv = _mixed_system(rcp, handle, 700, 6.0, "f16x3", nrhs=3)
+    X = torch.zeros_like(Bv)
+    code, st = rcp.rcp_refine_gmres(handle, A64, A, Dd, Ds, perm, "f16x3", Bv, X, tol=1e-12, max_outer=10,
+                                    restart=8)
+    assert code == 0
+    assert oracle.berr(a, X.cpu().numpy().T, rhs.T) <= 1e-12
+    # from a converged iterate nothing is left to do
+    code, st = rcp.rcp_refine_gmres(handle, A64, A, Dd, Ds, perm, "f16x3", Bv, X, tol=1e-12, use_x=True)
+    assert code == 0 and st.refine_iters == 0 and st.gmres_iters == 0
+
+
+@pytest.mark.parametrize("kexp,gmres", [(4.0, False), (10.0, True)])
+def test_sysv_falls_back_to_gmres_refinement(rcp, handle, kexp, gmres):
+    n = 2000
+    a = inputs.spectrum(n, seed=3, kexp=kexp, nrefl=16)
+    x = inputs.x_true(n, 1, seed=3)
+    rhs = inputs.rhs_for(a, x)
+    A64 = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    Bv = torch.from_numpy(rhs.copy()).to(DEV)
+    X = torch.zeros_like(Bv)
+    code, st = rcp.rcp_sysv(handle, A64, Bv, X, rcp.make_opts(b=64, d=80, seed=1, prec="f16x3"), tol=1e-12,
+                            max_iter=10)
+    assert code == 0 and st.berr <= 1e-12
+    assert (st.gmres_iters > 0) == gmres
+    assert oracle.berr(a, X.cpu().numpy().T, rhs.T) <= 1e-12
+
+
 # ------------------------------------------------------------------------------------------
 # full sizes, in the bench's launch configuration: sampled entries of P^T A P - L D L^T (each
 # computed in FP64 from one row of L), and the FP64 backward error of the refined solution
