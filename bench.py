@@ -241,6 +241,8 @@ def run_ours(a, rank, world, local_rank):
     step()
     phases = rcp.rcp_profile_read(h)
     rcp.rcp_profile(h, False)
+    # latency floor of a pivot step: the panel's grid-wide key exchange alone, on its grid
+    exchange_us = rcp.rcp_exchange_latency(h, 0, 20000, stream=stream)
 
     # the FP64 path on the same system
     fp64 = None
@@ -313,6 +315,11 @@ def run_ours(a, rank, world, local_rank):
         "speedup_vs_fp64": (fp64["ms_per_step"] / ms_step) if fp64 else None,
         "phases_ms": {k: round(v[0], 3) for k, v in phases.items()},
         "panel_us_per_pivot_step": 1e3 * pan_ms / max(1, n - st.n_2x2),
+        "panel_latency": {"exchange_floor_us": round(exchange_us, 3),
+                          "us_per_pivot_step": round(1e3 * pan_ms / max(1, n - st.n_2x2), 3),
+                          "floor_over_step": round(exchange_us / (1e3 * pan_ms / max(1, n - st.n_2x2)), 3),
+                          "note": "one grid-wide red.max + barrier + read-back per step is the floor of "
+                                  "the latency-bound panel (152 CTAs x 512 threads)"},
         "roofline": roofline,
         "clocks": clk.summary(),
         "e2e": e2e,

@@ -226,6 +226,14 @@ rcp_status rcp_profile(rcp_handle *h, int enable);
  * another position or a point was not reached) of the last such factorization. */
 rcp_status rcp_panel_trace(rcp_handle *h, unsigned long long *out, int cap);
 
+/* Latency floor of the FP32 panel's pivot step: `rounds` rounds of its grid-wide exchange
+ * (each CTA adds a packed key to a ring slot by red.max, grid barrier, read-back) on `grid`
+ * cooperative CTAs of the panel's 512 threads (0 = one per SM), without the step's arithmetic,
+ * timed with CUDA events on `stream` after a short warm-up; *us = microseconds per round.
+ * Uses the handle's barrier and key buffers (not while a factorization runs on the handle);
+ * synchronizes the stream. */
+rcp_status rcp_exchange_latency(rcp_handle *h, int grid, int rounds, rcp_stream_t stream, double *us);
+
 /* Number of kernels this library has launched in the process so far (all handles). */
 long long rcp_kernel_launches(void);
 rcp_status rcp_profile_read(rcp_handle *h, double *ms, int *launches, int nphase);

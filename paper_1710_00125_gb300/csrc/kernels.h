@@ -108,6 +108,12 @@ cudaError_t launch_factor_finish(const FactorWork<T> &w, cudaStream_t s);
 template <typename T>
 int panel_max_grid(int d, int bw, int chunk_cap, int spec);
 
+// Latency probe of the FP32 panel's per-step grid exchange (red.max of a key, grid barrier,
+// read-back) on `grid` CTAs of the panel's size; bar and the key ring must be zero at launch.
+int exchange_probe_grid();
+cudaError_t launch_exchange_probe(unsigned *bar, unsigned long long *keys, int *status, int grid, int rounds,
+                                  cudaStream_t s);
+
 // Solves and refinement.  `work` holds solve_work_bytes<T>(n, nrhs) bytes.
 template <typename T>
 size_t solve_work_bytes(int n, int nrhs);

@@ -1065,6 +1065,48 @@ int panel_max_grid(int d, int bw, int chunk_cap, int spec) {
     return per * sms;
 }
 
+// The panel's grid-wide exchange without its arithmetic, for a latency floor of the pivot
+// step: per round every CTA's thread 0 adds a packed key to a ring slot by red.max, the CTA
+// arrives at the grid barrier and waits, thread 0 reads the slot back, and CTA 0 clears the slot
+// half a ring ahead (as the FP32 panel does once per pivot step in its speculative path).
+__global__ void __launch_bounds__(PANEL_THREADS, 1) exchange_probe_kernel(unsigned *bar, unsigned long long *keys,
+                                                                          int *status, int rounds) {
+    __shared__ unsigned s_base;
+    const unsigned G = gridDim.x;
+    if (threadIdx.x == 0) s_base = barrier_base(bar, G);
+    __syncthreads();
+    const unsigned base = s_base;
+    unsigned long long acc = 0ull;
+    for (int r = 0; r < rounds; ++r) {
+        if (threadIdx.x == 0)
+            red_max_u64(keys + (r % KEY_RING), make_key((float)(blockIdx.x + 1), r & 0xFFFF, (int)blockIdx.x));
+        if (!grid_barrier(bar, base + (unsigned)(r + 1) * G, status)) return;
+        if (threadIdx.x == 0) {
+            acc += ld_key(keys + (r % KEY_RING)) & 0xFFFFull;   // the winning CTA of the round
+            if (blockIdx.x == 0) keys[(r + KEY_RING / 2) % KEY_RING] = 0ull;
+        }
+        __syncthreads();
+    }
+    // every round is won by the last CTA: a wrong exchange shows up in the status word
+    if (threadIdx.x == 0 && acc != (unsigned long long)rounds * (G - 1)) atomicOr(status, ST_INTERNAL);
+}
+
+int exchange_probe_grid() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, exchange_probe_kernel, PANEL_THREADS, 0) != cudaSuccess)
+        return 0;
+    return per * sms;
+}
+
+cudaError_t launch_exchange_probe(unsigned *bar, unsigned long long *keys, int *status, int grid, int rounds,
+                                  cudaStream_t s) {
+    void *args[] = {&bar, &keys, &status, &rounds};
+    count_launches(1);
+    return cudaLaunchCooperativeKernel((const void *)exchange_probe_kernel, dim3(grid), dim3(PANEL_THREADS), args, 0, s);
+}
+
 template size_t panel_smem_bytes<double>(int, int, int, int);
 template size_t panel_smem_bytes<float>(int, int, int, int);
 template cudaError_t launch_panel<double>(const FactorWork<double> &, cudaStream_t);

@@ -800,12 +800,12 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
     rcp_stats gst;
     std::memset(&gst, 0, sizeof gst);
     bool used_gmres = false;
-    {
+    if (max_iter > 0 && !(host.berr <= tol)) {
         FactorState fs0;
         int bits0 = 0;
         CU_TRY(cudaMemcpy(&fs0, h->state.p, sizeof fs0, cudaMemcpyDeviceToHost));
         CU_TRY(cudaMemcpy(&bits0, h->status.p, sizeof bits0, cudaMemcpyDeviceToHost));
-        if (max_iter > 0 && !(host.berr <= tol) && bits0 == 0 && fs0.info == 0) {
+        if (bits0 == 0 && fs0.info == 0) {
             rcp_status gs = rcp_refine_gmres(h, n, nrhs, dA, dlda, h->F.p, n, (double *)h->Dd.p, (double *)h->Ds.p,
                                              (int *)h->perm.p, r.prec, dB, dldb, dX, dldx, tol, max_iter, 0, 1, stream,
                                              &gst);
@@ -1023,6 +1023,51 @@ rcp_status rcp_panel_trace(rcp_handle *h, unsigned long long *out, int cap) {
 }
 
 long long rcp_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+rcp_status rcp_exchange_latency(rcp_handle *h, int grid, int rounds, rcp_stream_t stream, double *us) {
+    if (!h || !us || rounds < 1 || grid < 0) return RCP_EINVAL;
+    *us = 0.0;
+    const int maxg = exchange_probe_grid();
+    if (grid == 0) grid = sm_count();
+    if (maxg <= 0 || grid > maxg) return RCP_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    RCP_TRY(ensure_small(h));
+    RCP_TRY(grow(h->keys, PANEL_KEY_WORDS * sizeof(unsigned long long)));
+    unsigned *bar = (unsigned *)h->bar.p;
+    unsigned long long *keys = (unsigned long long *)h->keys.p;
+    int *status = (int *)h->status.p;
+    auto reset = [&]() -> rcp_status {
+        CU_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
+        CU_TRY(cudaMemsetAsync(keys, 0, PANEL_KEY_WORDS * sizeof(unsigned long long), s));
+        return RCP_OK;
+    };
+    CU_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    RCP_TRY(reset());
+    CU_TRY(launch_exchange_probe(bar, keys, status, grid, std::min(rounds, 64), s));   // warm-up
+    RCP_TRY(reset());
+    cudaEvent_t e0, e1;
+    CU_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return RCP_ECUDA;
+    }
+    cudaError_t ce = cudaEventRecord(e0, s);
+    if (ce == cudaSuccess) ce = launch_exchange_probe(bar, keys, status, grid, rounds, s);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CU_TRY(ce);
+    RCP_TRY(reset());
+    int bits = 0;
+    CU_TRY(cudaMemcpyAsync(&bits, status, sizeof bits, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    if (bits) return status_from_bits(bits);
+    *us = 1e3 * (double)ms / rounds;
+    return RCP_OK;
+}
 
 rcp_status rcp_omega(int d, int n, uint64_t seed, double *omega, rcp_stream_t stream) {
     if (d < 1 || n < 0 || (n > 0 && !omega)) return RCP_EINVAL;

@@ -76,6 +76,7 @@ def lib():
         L.rcp_factor.argtypes = [P, I, P, I, P, P, P, ctypes.POINTER(Opts), P, ctypes.POINTER(Stats)]
         L.rcp_solve.argtypes = [P, I, I, P, I, P, P, P, I, P, I, P]
         L.rcp_refine.argtypes = [P, I, I, P, I, P, I, P, P, P, I, P, I, P, I, D, I, P, ctypes.POINTER(Stats)]
+        L.rcp_exchange_latency.argtypes = [P, I, I, P, ctypes.POINTER(D)]
         L.rcp_refine_gmres.argtypes = [P, I, I, P, I, P, I, P, P, P, I, P, I, P, I, D, I, I, I, P,
                                        ctypes.POINTER(Stats)]
         L.rcp_sysv.argtypes = [P, I, I, P, I, P, I, P, I, ctypes.POINTER(Opts), D, I, I, P, ctypes.POINTER(Stats)]
@@ -252,6 +253,14 @@ PHASES = ("sketch", "panel", "interchange", "trailing", "solve", "residual")
 def rcp_profile(h: Handle, enable=True) -> None:
     """0/False: off; 1/True: per-phase events; 2: events plus per-step panel timestamps."""
     _check(lib().rcp_profile(h.h, int(enable)), "rcp_profile")
+
+
+def rcp_exchange_latency(h: Handle, grid: int = 0, rounds: int = 20000, stream=None) -> float:
+    """Microseconds per round of the panel's grid-wide key exchange (latency floor of a pivot step)."""
+    us = ctypes.c_double()
+    _check(lib().rcp_exchange_latency(h.h, int(grid), int(rounds), _stream(stream), ctypes.byref(us)),
+           "rcp_exchange_latency")
+    return us.value
 
 
 def rcp_panel_trace(h: Handle, n: int):

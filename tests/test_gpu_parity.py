@@ -410,6 +410,22 @@ def test_qb_mixed_gaussian_ragged_blocks(rcp, handle, prec, n):
     assert abs(st.n_2x2 - ref["n_2x2"]) <= 0.1 * ref["n_2x2"] + 3
 
 
+def test_exchange_latency_probe(rcp, handle):
+    # the panel's per-step grid exchange alone: a positive, finite time per round, and the
+    # handle factors normally afterwards (barrier counter and key ring left zeroed)
+    us = rcp.rcp_exchange_latency(handle, 0, 2000)
+    assert 0.05 < us < 100.0
+    us8 = rcp.rcp_exchange_latency(handle, 8, 2000)
+    assert 0.0 < us8 < 100.0
+    a = inputs.gaussian_sym(300, seed=1)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, 64, 40, 5, prec="fp32")
+    assert code == 0
+    L = _unit_lower(A)
+    D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
+    p = perm.cpu().numpy()
+    assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() / np.abs(a).max() < 2e-5 * max(1.0, st.growth_D)
+
+
 def _mixed_system(rcp, handle, n, kexp, prec, seed=7, nrhs=1):
     a = inputs.spectrum(n, seed=seed, kexp=kexp, nrefl=16)
     x = inputs.x_true(n, nrhs, seed=seed)
