@@ -35,7 +35,28 @@ def flops(n: int, nrhs: int) -> float:
     return n ** 3 / 3.0 + 2.0 * n * n * nrhs
 
 
-def parse():
+# ---- replicas (N > 1): the host logic, kept apart so that it runs on CPU ranks too ----
+def rank_seed(rank: int) -> int:
+    """Each replica solves its own seeded system (weak scaling: fixed work per GPU)."""
+    return 1000 * rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value, on every rank: the job takes as long as its slowest replica."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -56,7 +77,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=4096, help="systems of the batched ragged workload (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=5)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def workload_name(a):
@@ -194,7 +215,7 @@ def run_ours(a, rank, world, local_rank):
             dist.barrier()
 
     n, nrhs = a.n, a.nrhs
-    seed = 1000 * rank
+    seed = rank_seed(rank)
     A64 = inputs.spectrum(n, seed=seed, kexp=a.kexp, nrefl=64, device=dev)
     xt = torch.from_numpy(inputs.x_true(n, nrhs, seed=seed)).to(dev)
     Bv = (A64 @ xt.T).T.contiguous()
@@ -223,13 +244,9 @@ def run_ours(a, rank, world, local_rank):
         torch.cuda.synchronize()
     barrier()
     launches = (rcp.rcp_kernel_launches() - launches0) // max(1, a.steps)
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_step = ms / a.steps
-    value = world * flops(n, nrhs) / (ms_step * 1e-3) / 1e12
+    value = job_throughput(world, flops(n, nrhs), ms_step * 1e-3) / 1e12
     code, st = stats[-1]
     # independent check of the backward error with torch FP64 (cuBLAS) on the final solution
     r = Bv - (A64 @ X.T).T
@@ -273,12 +290,8 @@ def run_ours(a, rank, world, local_rank):
         for _ in range(a.e2e_steps):
             ce, se = rcp.rcp_sysv(h, Ah, Bh, Xh, opts, tol=a.tol, max_iter=a.max_iter, host_buffers=True)
         torch.cuda.synchronize()
-        el = (time.perf_counter() - t0) / a.e2e_steps
-        if dist is not None:
-            t = torch.tensor([el], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": world * flops(n, nrhs) / el / 1e12, "unit": UNIT,
+        el = max_over_ranks((time.perf_counter() - t0) / a.e2e_steps, dist, dev)
+        e2e = {"value": job_throughput(world, flops(n, nrhs), el) / 1e12, "unit": UNIT,
                "h2d_bytes_per_step": host_copy_bytes(n) + n * nrhs * 8, "d2h_bytes_per_step": n * nrhs * 8,
                "ms_per_step": el * 1e3, "berr": se.berr}
         del Ah, Bh, Xh
@@ -376,11 +389,7 @@ def run_batched(a, dev, stream, rank, world, dist):
         g.replay()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / a.batch_steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / a.batch_steps, dist, dev)
     # the two phases separately (eager calls, one each)
     f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     f0.record(stream)
@@ -403,8 +412,8 @@ def run_batched(a, dev, stream, rank, world, dist):
             "unit": "TFLOP/s", "frac": ach / 1.25, "traffic": None,
             "peak_note": "nominal FP64 rate of GB300 (no measured FP64 peak on this pool); the FP32 solves "
                          "inside the same kernel count as overhead"}
-    return {"workload": batched_workload_name(a), "metric": "systems/s", "value": world * a.batch / (ms * 1e-3),
-            "unit": "systems/s", "ms_per_step": ms, "tflops": world * fl / (ms * 1e-3) / 1e12,
+    return {"workload": batched_workload_name(a), "metric": "systems/s", "value": job_throughput(world, a.batch, ms * 1e-3),
+            "unit": "systems/s", "ms_per_step": ms, "tflops": job_throughput(world, fl, ms * 1e-3) / 1e12,
             "factor_ms": f0.elapsed_time(f1), "refine_ms": ref_ms,
             "berr_max": float(berr.max()), "all_berr_le_tol": bool((berr <= a.tol).all()),
             "info_nonzero": int((info != 0).sum()), "refine_iters_hist": np.bincount(iters).tolist(),
