@@ -57,7 +57,8 @@ def _load():
             lib.oracle_omega.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, P]
             lib.oracle_sketch.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P]
             lib.oracle_rcp.argtypes = [ctypes.c_int, P, ctypes.c_int, P, ctypes.c_double, ctypes.c_int,
-                                       ctypes.c_int, P, P, P, P, P, P, P, P, P, P]
+                                       ctypes.c_int, P, P, P, P, P, P, P, P, P, P,
+                                       ctypes.c_int, ctypes.c_double, ctypes.c_uint64, P]
             lib.oracle_rcp.restype = ctypes.c_int
             for f in (lib.oracle_bk, lib.oracle_bp):
                 f.argtypes = [ctypes.c_int, P, ctypes.c_double, P, P, P, P, P]
@@ -107,14 +108,17 @@ def sketch(om: np.ndarray, a: np.ndarray) -> np.ndarray:
 
 
 def rcp(a, om, alpha: float = SQRT2_OVER_2, q_mode: int = 1, block: int = 64,
-        record: bool = True, snapshots: bool = False) -> dict:
+        record: bool = True, snapshots: bool = False, guard_r: int = 0, guard_eps: float = 0.0,
+        seed: int = 0) -> dict:
     """RCP factorization (Algorithm 1, eager Schur complement).
 
     ``q_mode=1``: one sketch pivot per step; ``q_mode=2``: q = b (partial QRCP per block of
     ``block`` columns and one block sketch update per block).
     Returns L, Dd, Ds, perm, info, the per-step record and rho_elem, n_2x2, min sketch-norm
     ratio and max|L| (``stats``).  ``snapshots`` (tiny n only) adds the sketch B and the
-    Schur-complement array after every step.
+    Schur-complement array after every step.  ``guard_r`` > 0 adds the safeguard of
+    Algorithm 2 (q = 1; recomputed sketches drawn with ``seed``, Philox streams 1, 2, ...);
+    ``rank`` and ``resketches`` report where it stopped and how often it recomputed.
     """
     lib = _load()
     a = _f64(a).copy(order="F")
@@ -128,6 +132,7 @@ def rcp(a, om, alpha: float = SQRT2_OVER_2, q_mode: int = 1, block: int = 64,
     steps = (_Step * max(n, 1))()
     nsteps = ctypes.c_int(0)
     stats = np.zeros(4)
+    gout = np.zeros(2, dtype=np.int32)
     sb = np.zeros((max(n, 1), d, n), dtype=np.float64) if snapshots else None
     sa = np.zeros((max(n, 1), n, n), dtype=np.float64) if snapshots else None
     sp = np.zeros((max(n, 1), n), dtype=np.int32) if snapshots else None
@@ -135,10 +140,11 @@ def rcp(a, om, alpha: float = SQRT2_OVER_2, q_mode: int = 1, block: int = 64,
                           _ptr(L), _ptr(Dd), _ptr(Ds), _ptr(perm),
                           ctypes.cast(steps, ctypes.c_void_p), ctypes.byref(nsteps),
                           _ptr(sb) if snapshots else None, _ptr(sa) if snapshots else None,
-                          _ptr(sp) if snapshots else None, _ptr(stats))
+                          _ptr(sp) if snapshots else None, _ptr(stats),
+                          int(guard_r), float(guard_eps), ctypes.c_uint64(seed), _ptr(gout))
     out = dict(L=L, Dd=Dd, Ds=Ds, perm=perm.astype(np.int64), info=int(info),
                rho_elem=float(stats[0]), n_2x2=int(stats[1]), min_sketch_ratio=float(stats[2]),
-               max_abs_L=float(stats[3]))
+               max_abs_L=float(stats[3]), rank=int(gout[0]), resketches=int(gout[1]))
     if record:
         out["steps"] = [dict(k=s.k, pi=s.pi, r=s.r, kase=s.kase, s=s.s, norm2=s.norm2, lam=s.lam)
                         for s in steps[: nsteps.value]]
@@ -176,7 +182,8 @@ def bp(a, alpha: float = BK_ALPHA) -> dict:
 
 
 def ldlt_solve(L, Dd, Ds, perm, rhs) -> np.ndarray:
-    """x = Pi L^{-T} D^{-1} L^{-1} Pi^T b for one or several right-hand sides."""
+    """x = Pi L^{-T} D^+ L^{-1} Pi^T b for one or several right-hand sides (D^+: a zero 1x1 block
+    contributes 0)."""
     lib = _load()
     L = _f64(L)
     n = L.shape[0]

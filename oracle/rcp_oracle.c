@@ -283,12 +283,23 @@ static void partial_qrcp_select(int n, int d, int k, int q, double *a, double *b
  *               Schur-complement array and of perm after each step (tiny n only; else NULL)
  * stats [4]   : rho_elem (max over all Schur complements / max|A|), number of 2x2
  *               blocks, min over steps of ||B(:,pi)|| / ||B||_{1,2}, max|L_ij| (i > j)
+ * guard_r, guard_eps, seed, guard_out [2] : the safeguard of Algorithm 2 (q = 1 only;
+ *               guard_r = 0: off).  With beta = ||B^(1)||_{1,2} and delta = (j + 1) / r after j
+ *               recomputations of the sketch, the pivot of step k > 0 (already interchanged to
+ *               position k, a symmetric permutation of the unfactored part) is accepted when its
+ *               sketch column norm t >= eps^delta beta.  Otherwise, while j + 1 < r, a new
+ *               Omega' (d x (n-k), Philox stream j + 1, columns indexed from position k) gives
+ *               B(:, k:n) = Omega' S_k for the current Schur complement S_k, delta grows by 1/r
+ *               and the argmax and interchange are taken again; if t is still below
+ *               eps^delta beta (or no recomputation is left) the Schur complement counts as
+ *               zero: the factorization stops with D(k:n, k:n) = 0, L(k:n, k:n) = I and
+ *               info = k + 1.  guard_out = (rank k at the stop, or n; recomputations made).
  * Returns info.
  */
 int oracle_rcp(int n, double *a, int d, const double *om, double alpha, int q_mode, int bsize,
                double *l, double *dd, double *ds, int *perm,
                oracle_step *steps, int *nsteps, double *snap_b, double *snap_a, int *snap_perm,
-               double *stats)
+               double *stats, int guard_r, double guard_eps, uint64_t seed, int *guard_out)
 {
     int info = 0, ns = 0, n2 = 0;
     double *b = (double *)malloc(sizeof(double) * (size_t)d * (size_t)(n > 0 ? n : 1));
@@ -306,6 +317,7 @@ int oracle_rcp(int n, double *a, int d, const double *om, double alpha, int q_mo
 
     int k = 0;
     int blk_start = 0, blk_cols = 0, blk_len = 0;   /* q = b bookkeeping */
+    int nresk = 0, stopped = 0;                      /* Algorithm 2 */
     while (k < n - 1) {
         oracle_step st;
         memset(&st, 0, sizeof st);
@@ -320,10 +332,37 @@ int oracle_rcp(int n, double *a, int d, const double *om, double alpha, int q_mo
                 for (int r = 0; r < d; ++r) s2 += b[(size_t)r + (size_t)j * d] * b[(size_t)r + (size_t)j * d];
                 if (s2 > best) { best = s2; pi = j; }
             }
+            interchange(n, k, k, pi, a, d, b, l, perm);
+            if (guard_r > 0 && k > 0) {
+                /* Algorithm 2: t^2 against (eps^delta beta)^2 (beta holds ||B^(1)||_{1,2}^2) */
+                double thr2 = beta * pow(guard_eps, 2.0 * (double)(nresk + 1) / (double)guard_r);
+                if (best < thr2 && nresk + 1 < guard_r) {
+                    ++nresk;
+                    int m = n - k;
+                    double *om2 = (double *)malloc(sizeof(double) * (size_t)d * (size_t)m);
+                    oracle_omega(seed, (uint64_t)nresk, d, m, om2);
+                    for (int jj = 0; jj < m; ++jj)
+                        for (int r = 0; r < d; ++r) {
+                            double v = 0.0;
+                            for (int ii = 0; ii < m; ++ii) v += om2[(size_t)r + (size_t)ii * d] * AT(a, n, k + ii, k + jj);
+                            b[(size_t)r + (size_t)(k + jj) * d] = v;
+                        }
+                    free(om2);
+                    pi = k;
+                    best = -1.0;
+                    for (int j = k; j < n; ++j) {
+                        double s2 = 0.0;
+                        for (int r = 0; r < d; ++r) s2 += b[(size_t)r + (size_t)j * d] * b[(size_t)r + (size_t)j * d];
+                        if (s2 > best) { best = s2; pi = j; }
+                    }
+                    interchange(n, k, k, pi, a, d, b, l, perm);
+                    thr2 = beta * pow(guard_eps, 2.0 * (double)(nresk + 1) / (double)guard_r);
+                }
+                if (best < thr2) { stopped = 1; break; }
+            }
             st.pi = pi;
             st.norm2 = best;
             if (beta > 0.0 && sqrt(best / beta) < min_ratio) min_ratio = sqrt(best / beta);
-            interchange(n, k, k, pi, a, d, b, l, perm);
         } else if (blk_cols == 0) {
             /* first step of a block: b-step partial QRCP on B(:, k:n); the candidates are
              * interchanged to positions k..k+b-1 */
@@ -374,7 +413,15 @@ int oracle_rcp(int n, double *a, int d, const double *om, double alpha, int q_mo
         ++ns;
         k += s;
     }
-    if (k == n - 1) {
+    if (stopped) {
+        /* Algorithm 2: the Schur complement of order n - k counts as zero */
+        for (int i = k; i < n; ++i) {
+            dd[i] = 0.0;
+            ds[i] = 0.0;
+            for (int j = k; j < n; ++j) AT(l, n, i, j) = i == j ? 1.0 : 0.0;
+        }
+        if (info == 0) info = k + 1;
+    } else if (k == n - 1) {
         /* last position: D(n, n) = A(n, n) */
         dd[k] = AT(a, n, k, k);
         ds[k] = 0.0;
@@ -382,6 +429,7 @@ int oracle_rcp(int n, double *a, int d, const double *om, double alpha, int q_mo
         if (dd[k] == 0.0 && info == 0) info = k + 1;
     }
     free(b);
+    if (guard_out) { guard_out[0] = stopped ? k : n; guard_out[1] = nresk; }
     if (nsteps) *nsteps = ns;
     if (stats) {
         double lmax = 0.0;
@@ -498,7 +546,10 @@ int oracle_bp(int n, double *a, double alpha, double *l, double *dd, double *ds,
 /* ------------------------------------------------------------------------------ */
 
 /* Solution phase (Table "operation counts", solution row): with A(perm, perm) = L D L^T,
- * x(perm) = L^{-T} D^{-1} L^{-1} b(perm).  x [n*nrhs] holds b on entry, x on exit. */
+ * x(perm) = L^{-T} D^+ L^{-1} b(perm), D^+ the pseudo-inverse of D: a zero 1x1 block (an
+ * exactly singular pivot, or the zero Schur complement where Algorithm 2 stopped) contributes
+ * 0, which gives the basic solution of a rank-deficient factorization.  x [n*nrhs] holds b on
+ * entry, x on exit. */
 void oracle_ldlt_solve(int n, int nrhs, const double *l, const double *dd, const double *ds,
                        const int *perm, double *x)
 {
@@ -517,7 +568,7 @@ void oracle_ldlt_solve(int n, int nrhs, const double *l, const double *dd, const
                 y[i + 1] = (a11 * z2 - a21 * z1) / det;
                 ++i;
             } else {
-                y[i] /= dd[i];
+                y[i] = dd[i] != 0.0 ? y[i] / dd[i] : 0.0;
             }
         }
         for (int i = n - 1; i >= 0; --i)                 /* L^T v = w */

@@ -295,3 +295,78 @@ def test_generators_are_symmetric_and_seeded():
     assert np.array_equal(inputs.gaussian_sym(10, 3), inputs.gaussian_sym(10, 3))
     ev = np.abs(np.linalg.eigvalsh(inputs.spectrum(64, 2, 4.0, 16)))
     assert 1e3 < ev.max() / ev.min() <= 1e4 * 1.0001
+
+
+# ------------------------------------------------------------------------------------------
+# Algorithm 2 (safeguard): threshold eps^delta * beta on the pivot's sketch column norm
+# ------------------------------------------------------------------------------------------
+
+def _exact_rank_matrix(n, rho, seed):
+    # integer V (n x rho) and D = diag(+-1): A = V D V^T has exact rank rho
+    rng = np.random.default_rng(seed)
+    V = rng.integers(-3, 4, size=(n, rho)).astype(np.float64)
+    D = np.diag(rng.choice([-1.0, 1.0], size=rho))
+    return V @ D @ V.T
+
+
+def test_guard_stops_at_the_exact_rank():
+    n, rho, d = 24, 7, 12
+    a = _exact_rank_matrix(n, rho, 5)
+    assert np.linalg.matrix_rank(a) == rho
+    r = oracle.rcp(a, oracle.omega(3, d, n), guard_r=1, guard_eps=1e-8, seed=3)
+    assert r["rank"] == rho and r["resketches"] == 0
+    assert r["info"] == rho + 1
+    assert np.all(r["Dd"][rho:] == 0.0) and np.all(r["Ds"][rho - 1:] == 0.0)
+    L, p = r["L"], r["perm"]
+    assert np.array_equal(L[rho:, rho:], np.eye(n - rho))
+    D = oracle.block_d(r["Dd"], r["Ds"])
+    assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_guard_recomputes_once_then_stops():
+    n, rho, d = 24, 7, 12
+    a = _exact_rank_matrix(n, rho, 6)
+    # delta = 1/2 then 1: both thresholds sit far above the rounding-level Schur complement
+    r = oracle.rcp(a, oracle.omega(3, d, n), guard_r=2, guard_eps=1e-8, seed=3)
+    assert r["rank"] == rho and r["resketches"] == 1
+
+
+def test_guard_recomputation_can_accept_a_small_but_real_schur_complement():
+    # full rank with a block 1e-6 times smaller: sqrt(eps) * beta (eps = 1e-10) flags it, the
+    # recomputed sketch is checked against eps * beta and accepted
+    n, d = 20, 10
+    rng = np.random.default_rng(8)
+    g = rng.standard_normal((n, n))
+    q, _ = np.linalg.qr(g)
+    lam = np.concatenate([rng.uniform(1, 2, 12) * rng.choice([-1, 1], 12), 1e-6 * rng.uniform(1, 2, 8)])
+    a = (q * lam) @ q.T
+    a = 0.5 * (a + a.T)
+    r = oracle.rcp(a, oracle.omega(2, d, n), guard_r=2, guard_eps=1e-10, seed=2)
+    assert r["rank"] == n and r["resketches"] == 1 and r["info"] == 0
+    D = oracle.block_d(r["Dd"], r["Ds"])
+    p = r["perm"]
+    assert np.abs(a[np.ix_(p, p)] - r["L"] @ D @ r["L"].T).max() <= 1e-13 * np.abs(a).max()
+
+
+def test_guard_that_never_fires_changes_nothing():
+    a = inputs.gaussian_sym(40, seed=4)
+    om = oracle.omega(1, 12, 40)
+    r0 = oracle.rcp(a, om)
+    r1 = oracle.rcp(a, om, guard_r=3, guard_eps=1e-300, seed=1)
+    assert np.array_equal(r0["perm"], r1["perm"]) and np.array_equal(r0["L"], r1["L"])
+    assert r1["rank"] == 40 and r1["resketches"] == 0
+
+
+def test_pseudo_inverse_solve_and_basic_solution():
+    # D = diag(2, 0, 4), L = I, perm = id: x = (b0 / 2, 0, b2 / 4)
+    L = np.eye(3)
+    x = oracle.ldlt_solve(L, np.array([2.0, 0.0, 4.0]), np.zeros(3), np.arange(3), np.array([[6.0, 5.0, 8.0]]).T)
+    assert np.array_equal(x.ravel(), [3.0, 0.0, 2.0])
+    # a consistent rank-deficient system: the basic solution has a small backward error
+    n, rho = 24, 7
+    a = _exact_rank_matrix(n, rho, 9)
+    r = oracle.rcp(a, oracle.omega(3, 12, n), guard_r=1, guard_eps=1e-8, seed=3)
+    xt = np.random.default_rng(1).standard_normal((n, 1))
+    b = a @ xt
+    x = oracle.ldlt_solve(r["L"], r["Dd"], r["Ds"], r["perm"], b.copy())
+    assert oracle.berr(a, x, b) <= 1e-13
