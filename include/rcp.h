@@ -76,6 +76,18 @@ typedef struct {
     const void *omega;  /* optional device d x n Omega (ld = d) in the factor precision;     */
                         /* NULL = draw it from Philox(seed)                                  */
     int grid;           /* CTAs of the persistent panel kernel; 0 = automatic                */
+    int guard_r;        /* Algorithm 2 safeguard, q = 1 only (0 = off, Algorithm 1 as is):   */
+                        /* with beta = ||B^(1)||_{1,2} and delta = (j+1)/r after j sketch    */
+                        /* recomputations, a pivot whose sketch column norm t falls below   */
+                        /* eps^delta beta ends the panel; while j + 1 < r a fresh Omega'    */
+                        /* (Philox stream j + 1 of seed, d x (n-k)) re-sketches the Schur     */
+                        /* complement and the check is repeated with the larger delta; else  */
+                        /* the factorization stops: the Schur complement counts as zero      */
+                        /* (D(k:n) = 0, L(k:n, k:n) = I, info = k + 1, stats->rank = k).     */
+                        /* The host reads the state after every panel: the call synchronizes */
+                        /* once per panel and cannot be captured in a graph.  1 <= r <= 64.  */
+    double guard_eps;   /* eps of the safeguard; 0 = machine epsilon of the factor (2^-52    */
+                        /* FP64, 2^-23 otherwise)                                             */
 } rcp_opts;
 
 typedef struct {
@@ -90,6 +102,9 @@ typedef struct {
     double anorm;             /* ||A||_inf of the original matrix (rcp_refine)              */
     int gmres_iters;          /* GMRES iterations (applications of M^{-1} A) of              */
                               /* rcp_refine_gmres, or of rcp_sysv's fallback to it          */
+    int rank;                 /* rcp_factor with the safeguard: columns eliminated before a  */
+                              /* rank-deficiency stop (n when it did not stop)               */
+    int resketches;           /* rcp_factor with the safeguard: sketch recomputations        */
 } rcp_stats;
 
 typedef struct rcp_handle rcp_handle;
@@ -132,7 +147,8 @@ rcp_status rcp_factor(rcp_handle *h, int n, void *A, int lda, double *Dd, double
 
 /*
  * rcp_solve -- solution phase (operation-count table, "solution phase"):
- * X <- Pi L^{-T} D^{-1} L^{-1} Pi^T X for nrhs right-hand sides.
+ * X <- Pi L^{-T} D^+ L^{-1} Pi^T X for nrhs right-hand sides, D^+ the pseudo-inverse of D (a
+ * zero 1x1 block contributes 0: the basic solution when D is singular).
  *   LA, lda      device factor from rcp_factor (double* for RCP_FP64, float* otherwise)
  *   Dd, Ds, perm device, from rcp_factor
  *   prec         the precision the factor was computed in

@@ -760,7 +760,7 @@ __device__ void bt_dinv(int n, const double *Dd, const double *Ds, TL *e, TL *f,
             kind[i] = 1;
             kind[i + 1] = 2;
         } else {
-            e[i] = (TL)(1.0 / Dd[i]);
+            e[i] = (TL)(Dd[i] != 0.0 ? 1.0 / Dd[i] : 0.0);   // zero 1x1 block: pseudo-inverse 0
             f[i] = TL(0);
             kind[i] = 0;
         }

@@ -27,7 +27,8 @@ struct FactorState {
     int info;        // 1 + first zero pivot, 0 if none
     int n2x2;        // 2x2 blocks so far
     int n_moved;     // entries in the moved list of the current panel
-    int pad[2];
+    int guard_req;   // Algorithm 2, set by the panel: 1 recompute the sketch at guard_k, 2 stop there
+    int guard_k;     // position where the panel stopped for the safeguard
     double beta2;           // ||B^(1)||_{1,2}^2 (largest initial sketch column norm^2)
     double min_ratio;       // min over steps of ||B(:, pi)|| / sqrt(beta2)
     unsigned long long maxD_bits;   // max |D_ij| as ordered bits of a non-negative double
@@ -35,6 +36,8 @@ struct FactorState {
     unsigned long long maxA_bits;   // max |A_ij| of the input
     unsigned long long tcW_bits;    // max |W| over the current panel's trailing rows (FP16 split
     unsigned long long tcL_bits;    //   update) and max |L21|; ordered bits of non-negative doubles
+    int nresk;              // Algorithm 2: sketch recomputations so far
+    int rank;               // Algorithm 2: columns eliminated before a rank-deficiency stop (n if none)
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {

@@ -285,6 +285,7 @@ __global__ void factor_init_kernel(FactorWork<T> w) {
         st->next = 0; st->k0 = 0; st->kend = 0; st->info = 0; st->n2x2 = 0; st->n_moved = 0;
         st->beta2 = 0.0; st->min_ratio = 1.0;
         st->maxD_bits = 0ull; st->maxL_bits = 0ull; st->maxA_bits = 0ull;
+        st->guard_req = 0; st->guard_k = n; st->nresk = 0; st->rank = n;
     }
     for (int i = tid; i < n; i += gridDim.x * blockDim.x) {
         w.perm[i] = i;
@@ -309,6 +310,17 @@ __global__ void factor_finish_kernel(FactorWork<T> w) {
     const int n = w.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         w.A[(size_t)i + (size_t)i * w.lda] = (T)w.Dd[i];
+}
+
+template <typename T>
+__global__ void guard_zero_kernel(int n, int k, T *A, int lda, double *Dd, double *Ds) {
+    for (int j = k + blockIdx.x; j < n; j += gridDim.x) {
+        for (int i = j + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i + (size_t)j * lda] = T(0);
+        if (threadIdx.x == 0) {
+            Dd[j] = 0.0;
+            Ds[j] = 0.0;
+        }
+    }
 }
 
 // perm and the panel bounds after panel blk (after its interchange kernels)
@@ -471,6 +483,17 @@ cudaError_t launch_factor_finish(const FactorWork<T> &w, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_guard_zero(int n, int k, T *A, int lda, double *Dd, double *Ds, cudaStream_t s) {
+    if (k >= n) return cudaSuccess;
+    const int grid = n - k < 1024 ? n - k : 1024;
+    guard_zero_kernel<T><<<grid, 256, 0, s>>>(n, k, A, lda, Dd, Ds);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_guard_zero<double>(int, int, double *, int, double *, double *, cudaStream_t);
+template cudaError_t launch_guard_zero<float>(int, int, float *, int, double *, double *, cudaStream_t);
 template cudaError_t launch_interchange<double>(const FactorWork<double> &, cudaStream_t);
 template cudaError_t launch_interchange<float>(const FactorWork<float> &, cudaStream_t);
 template cudaError_t launch_panel_record<double>(const FactorWork<double> &, int, cudaStream_t);

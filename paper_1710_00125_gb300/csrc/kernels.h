@@ -15,8 +15,9 @@ constexpr int PANEL_TRACE_SLOTS = 16;
 // panel's clearing (the block QRCP) zeroes all of them.
 constexpr int PANEL_KEY_WORDS = 32;
 
+// Omega (d x n) from Philox counter (j, t, stream, 0) and key (seed, 0)
 template <typename T>
-cudaError_t launch_omega(int d, int n, uint64_t seed, T *om, cudaStream_t s);
+cudaError_t launch_omega(int d, int n, uint64_t seed, T *om, cudaStream_t s, uint64_t stream = 0);
 
 // B = Omega A (d x n).  In FP32, `part` (nullable, part_elems elements) holds the partial sums
 // of a split over K; sketch_scratch_floats(n, d) elements allow the full split.
@@ -65,6 +66,8 @@ struct FactorWork {
     int qb;                      // Algorithm 1 with q = b: the pivot of step k is the column at
                                  // position k (candidates chosen by the block QRCP); no per-step
                                  // sketch update (the block update follows the panel)
+    int guard_r;                 // Algorithm 2 safeguard: r (0 = off)
+    double guard_eps;            //   and its eps
 };
 
 template <typename T>
@@ -104,6 +107,11 @@ cudaError_t launch_lrows_permute(const FactorWork<T> &w, int npanels, cudaStream
 
 template <typename T>
 cudaError_t launch_factor_finish(const FactorWork<T> &w, cudaStream_t s);
+
+// Algorithm 2 stop at position k: the Schur complement counts as zero (lower triangle of
+// A(k:n, k:n) and D(k:n) set to zero)
+template <typename T>
+cudaError_t launch_guard_zero(int n, int k, T *A, int lda, double *Dd, double *Ds, cudaStream_t s);
 
 template <typename T>
 int panel_max_grid(int d, int bw, int chunk_cap, int spec);

@@ -423,6 +423,14 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     T *spec_pay = w.pay + (size_t)2 * G * ps;                 // [2][G][d], by barrier parity
     double *spec_rec = w.s3v;                                  // [2][G][4]
     bool have_next = false;
+    // Algorithm 2: the pivot's squared sketch norm against (eps^delta beta)^2 with
+    // delta = (recomputations + 1) / r; beta^2 is the first pivot's squared norm
+    double gfac = 0.0, gthr2 = 0.0;
+    if (w.guard_r > 0) {
+        gfac = pow(w.guard_eps, 2.0 * (double)(ldcg(&w.st->nresk) + 1) / (double)w.guard_r);
+        gthr2 = ldcg(&w.st->beta2) * gfac;
+    }
+    int gstop = 0;
     int run1 = 2;   // consecutive case-(0)/(1) steps; speculate when >= 2
     T preA0 = T(0), preA1 = T(0);   // next pivot's column of A, loaded during a commit
     __syncthreads();
@@ -505,6 +513,13 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             // ended with a CTA barrier)
         const int P = s_i[1], gP = s_i[3];
         if (P < 0 || !isfinite(s_x[0])) { fail = ST_NONFINITE; break; }
+        if (w.guard_r > 0) {
+            // the panel ends before step k (whose interchange only permuted the unfactored
+            // part); the host recomputes the sketch or stops
+            const double t2 = (double)s_x[0];
+            if (k > 0 && t2 < gthr2) { gstop = 1; break; }
+            if (k == 0) gthr2 = t2 * gfac;
+        }
         // where step (1) published P's sketch column and a_kk (read only without a committed
         // speculation, whose commit already loaded them)
         const T *payP = pay1 + (size_t)gP * ps;
@@ -1015,6 +1030,8 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         w.st->k0 = k0;
         w.st->kend = k;
         w.st->n2x2 += n2;
+        w.st->guard_req = gstop ? (ldcg(&w.st->nresk) + 1 < w.guard_r ? 1 : 2) : 0;
+        if (gstop) w.st->guard_k = k;
         if (info && w.st->info == 0) w.st->info = info;
         if (beta2 > 0.0 && minnorm2 < INFINITY) {
             const double ratio = sqrt(minnorm2 / beta2);

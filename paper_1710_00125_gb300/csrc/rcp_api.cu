@@ -138,6 +138,8 @@ rcp_status ensure_small(rcp_handle *h) {
 
 struct Resolved {
     int b, d, grid, chunk_cap, bw, maxmoved, spec, qb;
+    int guard_r;           // Algorithm 2 (0 = off)
+    double guard_eps;
     double alpha;
     rcp_prec prec;
     uint64_t seed;
@@ -163,6 +165,12 @@ rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
     if (!(r.alpha < 1.0)) return RCP_EINVAL;
     r.seed = o ? o->seed : 0;
     r.omega = o ? o->omega : nullptr;
+    r.guard_r = o ? o->guard_r : 0;
+    if (r.guard_r < 0 || r.guard_r > 64) return RCP_EINVAL;
+    r.guard_eps = (o && o->guard_eps > 0.0) ? o->guard_eps
+                                            : (r.prec == RCP_FP64 ? 0x1.0p-52 : 0x1.0p-23);   // machine epsilon
+    if (!(r.guard_eps < 1.0)) return RCP_EINVAL;
+    if (r.guard_r > 0 && r.qb) return RCP_EUNSUPPORTED;   // the safeguard is defined for q = 1
     r.bw = r.b + 1;
     // each pivot column costs at most two transpositions, and each moves two indices
     r.maxmoved = 4 * (r.b + 2);
@@ -223,7 +231,8 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->tmpA, (size_t)r.maxmoved * NT * sizeof(T)));
     RCP_TRY(grow(h->tmpL, (size_t)r.maxmoved * NT * sizeof(T)));
     RCP_TRY(grow(h->tmpP, (size_t)r.maxmoved * sizeof(int)));
-    const size_t npan = (N + r.b - 1) / r.b;
+    // each safeguard event ends a panel early: at most guard_r panels more
+    const size_t npan = (N + r.b - 1) / r.b + (size_t)r.guard_r;
     RCP_TRY(grow(h->psnap, npan * N * sizeof(int)));
     RCP_TRY(grow(h->pinv, npan * N * sizeof(int)));
     RCP_TRY(grow(h->pbounds, 2 * npan * sizeof(int)));
@@ -251,6 +260,8 @@ FactorWork<T> make_work(rcp_handle *h, int n, T *A, int lda, double *Dd, double 
     w.keys = (unsigned long long *)h->keys.p;
     w.spec = r.spec;
     w.qb = r.qb;
+    w.guard_r = r.guard_r;
+    w.guard_eps = r.guard_eps;
     w.psnap = (int *)h->psnap.p;
     w.pinv = (int *)h->pinv.p;
     w.pbounds = (int *)h->pbounds.p;
@@ -333,7 +344,61 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
         CU_TRY((launch_sketch<T, T>(n, r.d, A, lda, om, w.B, (T *)h->skp.p, h->skp.bytes / sizeof(T), s)));
     }
     const int nblk = (n + r.b - 1) / r.b;
-    for (int blk = 0; blk < nblk; ++blk) {
+    int npanels = nblk;
+    if (r.guard_r > 0) {
+        // Algorithm 2: its decisions change where panels end, so the host reads the state after
+        // every block; a request either recomputes the sketch of the Schur complement (a fresh
+        // Omega' from Philox stream = recomputation number, d x (n - k)) or stops the
+        // factorization at k (the Schur complement counts as zero)
+        auto set_int = [&](size_t off, int v) -> cudaError_t {
+            return cudaMemcpyAsync((char *)h->state.p + off, &v, sizeof v, cudaMemcpyHostToDevice, s);
+        };
+        const int maxpan = nblk + r.guard_r;
+        int blk = 0, k0h = 0;
+        while (k0h < n) {
+            if (blk >= maxpan) return RCP_ECUDA;   // cannot happen: each request ends one panel early
+            {
+                PhaseScope ps(h, s, PH_PANEL);
+                CU_TRY(launch_panel<T>(w, s));
+            }
+            {
+                PhaseScope ps(h, s, PH_INTERCHANGE);
+                CU_TRY(launch_interchange<T>(w, s));
+                CU_TRY(launch_panel_record<T>(w, blk, s));
+            }
+            {
+                PhaseScope ps(h, s, PH_TRAILING);
+                CU_TRY(launch_trailing<T>(w, k0h, (int)r.prec, s));   // the panel ends at or after k0h
+            }
+            ++blk;
+            FactorState st;
+            int bits = 0;
+            CU_TRY(cudaMemcpyAsync(&st, h->state.p, sizeof st, cudaMemcpyDeviceToHost, s));
+            CU_TRY(cudaMemcpyAsync(&bits, h->status.p, sizeof bits, cudaMemcpyDeviceToHost, s));
+            CU_TRY(cudaStreamSynchronize(s));
+            if (bits) break;
+            if (st.guard_req == 1) {
+                const int k = st.guard_k, m = n - k, q = st.nresk + 1;
+                PhaseScope ps(h, s, PH_SKETCH);
+                CU_TRY(launch_omega<T>(r.d, m, r.seed, (T *)h->om.p, s, (uint64_t)q));
+                CU_TRY((launch_sketch<T, T>(m, r.d, A + (size_t)k + (size_t)k * lda, lda, (const T *)h->om.p,
+                                            w.B + (size_t)k * r.d, (T *)h->skp.p, h->skp.bytes / sizeof(T), s)));
+                CU_TRY(set_int(offsetof(FactorState, nresk), q));
+                CU_TRY(set_int(offsetof(FactorState, guard_req), 0));
+            } else if (st.guard_req == 2) {
+                const int k = st.guard_k;
+                CU_TRY(launch_guard_zero<T>(n, k, A, lda, Dd, Ds, s));
+                CU_TRY(set_int(offsetof(FactorState, rank), k));
+                CU_TRY(set_int(offsetof(FactorState, next), n));
+                if (st.info == 0) CU_TRY(set_int(offsetof(FactorState, info), k + 1));
+                CU_TRY(set_int(offsetof(FactorState, guard_req), 0));
+                break;
+            }
+            k0h = st.next;
+        }
+        npanels = blk;
+    }
+    for (int blk = 0; blk < (r.guard_r > 0 ? 0 : nblk); ++blk) {
         if (r.qb) {
             // q = b: the block's candidates from a partial QRCP of the sketch, interchanged to
             // the first positions of the block before the panel
@@ -361,7 +426,7 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
     }
     {
         PhaseScope ps(h, s, PH_INTERCHANGE);
-        CU_TRY(launch_lrows_permute<T>(w, nblk, s));
+        CU_TRY(launch_lrows_permute<T>(w, npanels, s));
     }
     CU_TRY(launch_factor_finish<T>(w, s));
     if (!stats) return RCP_OK;
@@ -377,6 +442,8 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
     stats->n_2x2 = st.n2x2;
     stats->info = st.info;
     stats->device_flags = bits;
+    stats->rank = st.rank;
+    stats->resketches = st.nresk;
     rcp_status e = status_from_bits(bits);
     if (e != RCP_OK) return e;
     return st.info > 0 ? (rcp_status)st.info : RCP_OK;
@@ -834,6 +901,8 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
     stats->anorm = host.anorm;
     stats->refine_iters = host.iters + gst.refine_iters;
     stats->gmres_iters = gst.gmres_iters;
+    stats->rank = st.rank;
+    stats->resketches = st.nresk;
     (void)rst;
     const double berr_final = stats->berr;
     rcp_status e = status_from_bits(bits);

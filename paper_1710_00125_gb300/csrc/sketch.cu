@@ -26,14 +26,14 @@ __device__ __forceinline__ void philox4x64_10(uint64_t x[4], uint64_t k0, uint64
     }
 }
 
-// One thread per pair (2t, 2t+1) of column j: counter (j, t, 0, 0), key (seed, 0).
+// One thread per pair (2t, 2t+1) of column j: counter (j, t, stream, 0), key (seed, 0).
 template <typename T>
-__global__ void omega_kernel(int d, int n, uint64_t seed, T *__restrict__ om) {
+__global__ void omega_kernel(int d, int n, uint64_t seed, uint64_t stream, T *__restrict__ om) {
     const int half = (d + 1) / 2;
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)half * n) return;
     int j = (int)(idx / half), t = (int)(idx % half);
-    uint64_t x[4] = {(uint64_t)j, (uint64_t)t, 0ull, 0ull};
+    uint64_t x[4] = {(uint64_t)j, (uint64_t)t, stream, 0ull};
     philox4x64_10(x, seed, 0ull);
     double u1 = ((double)(x[0] >> 11) + 1.0) * 0x1.0p-53;
     double u2 = (double)(x[1] >> 11) * 0x1.0p-53;
@@ -316,11 +316,11 @@ cudaError_t launch_sketch_cols_f32(int n, int d, const float *A, int lda, const 
 }
 
 template <typename T>
-cudaError_t launch_omega(int d, int n, uint64_t seed, T *om, cudaStream_t s) {
+cudaError_t launch_omega(int d, int n, uint64_t seed, T *om, cudaStream_t s, uint64_t stream) {
     long long total = (long long)((d + 1) / 2) * n;
     if (total == 0) return cudaSuccess;
     int blocks = (int)((total + 255) / 256);
-    omega_kernel<T><<<blocks, 256, 0, s>>>(d, n, seed, om);
+    omega_kernel<T><<<blocks, 256, 0, s>>>(d, n, seed, stream, om);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -350,8 +350,8 @@ cudaError_t launch_sketch(int n, int d, const TA *A, int lda, const TC *om, TC *
     return launch_sketch_rpt<TA, TC>(n, d, A, lda, om, B, nullptr, 0, s);
 }
 
-template cudaError_t launch_omega<double>(int, int, uint64_t, double *, cudaStream_t);
-template cudaError_t launch_omega<float>(int, int, uint64_t, float *, cudaStream_t);
+template cudaError_t launch_omega<double>(int, int, uint64_t, double *, cudaStream_t, uint64_t);
+template cudaError_t launch_omega<float>(int, int, uint64_t, float *, cudaStream_t, uint64_t);
 template cudaError_t launch_sketch<double, double>(int, int, const double *, int, const double *, double *,
                                                    double *, size_t, cudaStream_t);
 template cudaError_t launch_sketch<float, float>(int, int, const float *, int, const float *, float *, float *,

@@ -292,8 +292,11 @@ __global__ void dsolve_kernel(int n, int nrhs, const double *__restrict__ Dd, co
                 y[i + 1] = (T)((a * y2 - y1) / den);
             }
         } else {
+            // a zero 1x1 block (exact singularity, or the Schur complement where the safeguard
+            // stopped) contributes 0: the pseudo-inverse of D, i.e. the basic solution
             const double dv = Dd[i];
-            for (int k = 0; k < nrhs; ++k) Y[(size_t)i + (size_t)k * n] = (T)((double)Y[(size_t)i + (size_t)k * n] / dv);
+            for (int k = 0; k < nrhs; ++k)
+                Y[(size_t)i + (size_t)k * n] = (T)(dv != 0.0 ? (double)Y[(size_t)i + (size_t)k * n] / dv : 0.0);
         }
     }
 }
@@ -524,8 +527,8 @@ __global__ void dsolve_words_kernel(int n, int nrhs, const double *__restrict__ 
                 W[(size_t)i + 1 + (size_t)k * n] = (float)((a * y2 - y1) / den);
             }
         } else {
-            const double dv = Dd[i];
-            for (int k = 0; k < nrhs; ++k) W[(size_t)i + (size_t)k * n] = (float)(yv(i, k) / dv);
+            const double dv = Dd[i];   // zero 1x1 block: pseudo-inverse 0
+            for (int k = 0; k < nrhs; ++k) W[(size_t)i + (size_t)k * n] = (float)(dv != 0.0 ? yv(i, k) / dv : 0.0);
         }
     }
 }

@@ -40,14 +40,15 @@ class RcpError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("b", ctypes.c_int), ("d", ctypes.c_int), ("q_mode", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("prec", ctypes.c_int), ("alpha", ctypes.c_double), ("omega", ctypes.c_void_p),
-                ("grid", ctypes.c_int)]
+                ("grid", ctypes.c_int), ("guard_r", ctypes.c_int), ("guard_eps", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("growth_D", ctypes.c_double), ("max_abs_L", ctypes.c_double),
                 ("min_sketch_ratio", ctypes.c_double), ("n_2x2", ctypes.c_int), ("info", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("device_flags", ctypes.c_int), ("berr", ctypes.c_double),
-                ("anorm", ctypes.c_double), ("gmres_iters", ctypes.c_int)]
+                ("anorm", ctypes.c_double), ("gmres_iters", ctypes.c_int), ("rank", ctypes.c_int),
+                ("resketches", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -119,12 +120,14 @@ def _check(code, where, allow_info=False):
     return code
 
 
-def make_opts(b=64, d=None, seed=0, prec=RCP_FP64, alpha=None, omega=None, grid=0, q_mode=1) -> Opts:
+def make_opts(b=64, d=None, seed=0, prec=RCP_FP64, alpha=None, omega=None, grid=0, q_mode=1, guard_r=0,
+              guard_eps=0.0) -> Opts:
     if isinstance(prec, str):
         prec = PREC_NAMES[prec]
     return Opts(b=b, d=(min(b + 16, 128) if d is None else d), q_mode=q_mode, seed=seed, prec=prec,
                 alpha=(math.sqrt(2.0) / 2.0 if alpha is None else alpha),
-                omega=(omega.data_ptr() if omega is not None else None), grid=grid)
+                omega=(omega.data_ptr() if omega is not None else None), grid=grid, guard_r=guard_r,
+                guard_eps=guard_eps)
 
 
 class Handle:

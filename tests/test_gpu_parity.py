@@ -410,6 +410,116 @@ def test_qb_mixed_gaussian_ragged_blocks(rcp, handle, prec, n):
     assert abs(st.n_2x2 - ref["n_2x2"]) <= 0.1 * ref["n_2x2"] + 3
 
 
+# ------------------------------------------------------------------------------------------
+# Algorithm 2 (safeguard)
+# ------------------------------------------------------------------------------------------
+
+def _exact_rank_matrix(n, rho, seed):
+    rng = np.random.default_rng(seed)
+    V = rng.integers(-3, 4, size=(n, rho)).astype(np.float64)
+    return V @ np.diag(rng.choice([-1.0, 1.0], size=rho)) @ V.T
+
+
+def _guarded(rcp, handle, a, b, d, seed, prec, r, eps):
+    n = a.shape[0]
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    A = torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(dt)
+    Dd = torch.zeros(n, dtype=torch.float64, device=DEV)
+    Ds = torch.zeros_like(Dd)
+    perm = torch.zeros(n, dtype=torch.int32, device=DEV)
+    code, st = rcp.rcp_factor(handle, A, Dd, Ds, perm,
+                              rcp.make_opts(b=b, d=d, seed=seed, prec=prec, guard_r=r, guard_eps=eps))
+    return code, st, A, Dd, Ds, perm
+
+
+@pytest.mark.parametrize("n,rho,b", [(300, 40, 64), (400, 150, 64)])
+def test_guard_fp64_stops_at_the_rank_like_the_oracle(rcp, handle, n, rho, b):
+    a = _exact_rank_matrix(n, rho, n + rho)
+    ref = oracle.rcp(a, oracle.omega(7, 40, n), record=False, guard_r=1, guard_eps=1e-8, seed=7)
+    assert ref["rank"] == rho
+    code, st, A, Dd, Ds, perm = _guarded(rcp, handle, a, b, 40, 7, "fp64", 1, 1e-8)
+    assert code == rho + 1 and st.info == rho + 1
+    assert st.rank == rho and st.resketches == 0
+    p = perm.cpu().numpy()
+    assert np.array_equal(p[:rho], ref["perm"][:rho])
+    assert sorted(p.tolist()) == list(range(n))
+    L = _unit_lower(A)
+    # the eliminated columns of L and D agree with the oracle's; rows are matched by original
+    # index (the order of the tail, the zero Schur complement, may differ)
+    rows = {int(v): i for i, v in enumerate(ref["perm"])}
+    Lr = ref["L"][[rows[int(v)] for v in p], :rho]
+    assert np.abs(L[:, :rho] - Lr).max() <= 1e-10
+    assert np.allclose(Dd.cpu().numpy()[:rho], ref["Dd"][:rho], rtol=1e-11, atol=1e-11 * np.abs(a).max())
+    assert np.all(Dd.cpu().numpy()[rho:] == 0.0) and np.all(Ds.cpu().numpy()[rho:] == 0.0)
+    D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
+    assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_guard_fp64_recomputes_the_sketch_like_the_oracle(rcp, handle):
+    # full rank, 80 of 200 eigenvalues near 1e-6: sqrt(eps) beta flags the small block, the
+    # recomputed sketch passes eps beta (r = 2, eps = 1e-10)
+    n, d = 200, 40
+    rng = np.random.default_rng(8)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([rng.uniform(1, 2, 120) * rng.choice([-1, 1], 120), 1e-6 * rng.uniform(1, 2, 80)])
+    a = (q * lam) @ q.T
+    a = 0.5 * (a + a.T)
+    ref = oracle.rcp(a, oracle.omega(5, d, n), record=False, guard_r=2, guard_eps=1e-10, seed=5)
+    assert ref["resketches"] == 1 and ref["rank"] == n
+    code, st, A, Dd, Ds, perm = _guarded(rcp, handle, a, 64, d, 5, "fp64", 2, 1e-10)
+    assert code == 0 and st.resketches == 1 and st.rank == n
+    p = perm.cpu().numpy()
+    assert np.array_equal(p[:120], ref["perm"][:120])
+    L = _unit_lower(A)
+    D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
+    assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() <= 1e-13 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_guard_that_never_fires_changes_nothing_on_the_gpu(rcp, handle, prec):
+    a = inputs.gaussian_sym(300, seed=4)
+    c0, s0, A0, Dd0, Ds0, p0 = _guarded(rcp, handle, a, 64, 40, 3, prec, 0, 0.0)
+    c1, s1, A1, Dd1, Ds1, p1 = _guarded(rcp, handle, a, 64, 40, 3, prec, 3, 1e-300)
+    assert c0 == c1 == 0 and s1.rank == 300 and s1.resketches == 0
+    assert torch.equal(p0, p1) and torch.equal(A0, A1) and torch.equal(Dd0, Dd1)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_guard_fp32_stops_at_the_rank(rcp, handle, prec):
+    n, rho = 500, 40
+    a = _exact_rank_matrix(n, rho, 11)
+    code, st, A, Dd, Ds, perm = _guarded(rcp, handle, a, 64, 80, 2, prec, 1, 1e-4)
+    assert st.rank == rho and code == rho + 1
+    L = _unit_lower(A)
+    D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
+    p = perm.cpu().numpy()
+    assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() <= 1e-5 * max(1.0, st.growth_D) * np.abs(a).max()
+
+
+def test_guard_sysv_basic_solution_of_a_consistent_rank_deficient_system(rcp, handle):
+    n, rho = 400, 60
+    a = _exact_rank_matrix(n, rho, 12)
+    x = inputs.x_true(n, 1, seed=12)
+    rhs = inputs.rhs_for(a, x)
+    A64 = torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    Bv = torch.from_numpy(rhs.copy()).to(DEV)
+    X = torch.zeros_like(Bv)
+    code, st = rcp.rcp_sysv(handle, A64, Bv, X, rcp.make_opts(b=64, d=80, seed=3, prec="fp64", guard_r=1,
+                                                              guard_eps=1e-8), tol=1e-12, max_iter=5)
+    assert st.rank == rho and code == rho + 1   # info > 0: D is singular, x is the basic solution
+    assert np.all(np.isfinite(X.cpu().numpy()))
+    assert oracle.berr(a, X.cpu().numpy().T, rhs.T) <= 1e-12
+
+
+def test_guard_option_checks(rcp, handle):
+    a = inputs.gaussian_sym(100, seed=1)
+    with pytest.raises(rcp.RcpError):
+        A = torch.from_numpy(a).to(DEV)
+        rcp.rcp_factor(handle, A, torch.zeros(100, dtype=torch.float64, device=DEV),
+                       torch.zeros(100, dtype=torch.float64, device=DEV), torch.zeros(100, dtype=torch.int32, device=DEV),
+                       rcp.make_opts(b=32, d=40, prec="fp64", q_mode=2, guard_r=1))
+
+
 def test_exchange_latency_probe(rcp, handle):
     # the panel's per-step grid exchange alone: a positive, finite time per round, and the
     # handle factors normally afterwards (barrier counter and key ring left zeroed)
