@@ -250,6 +250,14 @@ rcp_status rcp_panel_trace(rcp_handle *h, unsigned long long *out, int cap);
  * synchronizes the stream. */
 rcp_status rcp_exchange_latency(rcp_handle *h, int grid, int rounds, rcp_stream_t stream, double *us);
 
+/* Stability diagnostics of a factor (the paper's experiments report them per matrix type):
+ * *norm1_L = ||L||_1 exactly (unit lower L from rcp_factor: LA's strictly lower triangle, unit
+ * diagonal), *norm1_Linv = an estimate of ||L^{-1}||_1 by Higham's 1-norm estimator (1988; a
+ * lower bound, usually exact), from at most six solves with L and L^T.  prec: the precision of
+ * LA.  Synchronizes the stream. */
+rcp_status rcp_l_norms(rcp_handle *h, int n, const void *LA, int lda, rcp_prec prec, rcp_stream_t stream,
+                       double *norm1_L, double *norm1_Linv);
+
 /* Number of kernels this library has launched in the process so far (all handles). */
 long long rcp_kernel_launches(void);
 rcp_status rcp_profile_read(rcp_handle *h, double *ms, int *launches, int nphase);

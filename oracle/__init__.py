@@ -206,6 +206,18 @@ def berr(a, x, rhs) -> float:
     return float(lib.oracle_berr(n, x.shape[1], _ptr(a), _ptr(x), _ptr(rhs)))
 
 
+def l_norms(L) -> tuple:
+    """||L||_1 and ||L^{-1}||_1 of a unit lower triangular L (the stability diagnostics the
+    paper's experiments report beside the growth factor), by their definitions: the largest
+    column sum of |L| and of |L^{-1}|, L^{-1} from forward substitution against the identity."""
+    L = np.asarray(L, dtype=np.float64)
+    n = L.shape[0]
+    Li = np.eye(n)
+    for i in range(n):
+        Li[i] -= L[i, :i] @ Li[:i]
+    return float(np.abs(L).sum(axis=0).max()), float(np.abs(Li).sum(axis=0).max())
+
+
 def block_d(Dd, Ds) -> np.ndarray:
     """The block-diagonal D as a dense matrix."""
     n = len(Dd)

@@ -130,6 +130,16 @@ cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd,
                          const int *perm, double *X, int ldx, T *work, int *flags, int *status,
                          const int *skip, cudaStream_t s);
 
+// One triangle of the solve (unit lower L, one right-hand side, iperm = identity): mode 0
+// x <- L^{-1} x, mode 1 x <- L^{-T} x; work / flags as for launch_solve with nrhs = 1
+template <typename T>
+cudaError_t launch_tri_solve(int n, const T *L, int lda, const int *iperm, double *x, T *work, int *flags,
+                             int *status, int mode, cudaStream_t s);
+cudaError_t launch_iota(int n, int *p, cudaStream_t s);
+// ||L||_1 (unit diagonal implied) as ordered bits of a non-negative double
+template <typename T>
+cudaError_t launch_l_norm1(int n, const T *L, int lda, unsigned long long *out, cudaStream_t s);
+
 size_t symv_part_doubles(int n, int nrhs);
 cudaError_t launch_symv_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx,
                                  const double *Bv, int ldb, double *R, int ldr, double *part,

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -62,6 +63,7 @@ struct rcp_handle {
     cudaStream_t copy_stream = nullptr;            // rcp_sysv with host buffers: block copies of A
     std::vector<cudaEvent_t> copy_events;          //   one per block, and one for the start
     Buf gmV, gmZ, gmP, gmH;                        // GMRES refinement: basis, zero vector, partial sums, scalars
+    Buf iperm;                                     // identity permutation (one-triangle solves)
 };
 
 namespace {
@@ -451,9 +453,9 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
 
 int solve_nb(int n) { return (n + 63) / 64; }
 
+// Workspace of the solves (work area and flags) for n x nrhs.
 template <typename T>
-rcp_status solve_impl(rcp_handle *h, int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
-                      const int *perm, double *X, int ldx, const int *skip, cudaStream_t s) {
+rcp_status prepare_solve_ws(rcp_handle *h, int n, int nrhs, cudaStream_t s) {
     RCP_TRY(ensure_small(h));
     RCP_TRY(grow_zeroed(h->Y, solve_work_bytes<T>(n, nrhs), s, false));
     // the FP32 solves take a 64-bit word of the work area as published once its high half is the
@@ -467,6 +469,13 @@ rcp_status solve_impl(rcp_handle *h, int n, int nrhs, const T *L, int lda, const
     bool fresh = h->flags.bytes < (size_t)(2 * nb + 2) * sizeof(int);
     RCP_TRY(grow(h->flags, (size_t)(2 * nb + 2) * sizeof(int)));
     if (fresh) CU_TRY(cudaMemsetAsync(h->flags.p, 0, h->flags.bytes, s));
+    return RCP_OK;
+}
+
+template <typename T>
+rcp_status solve_impl(rcp_handle *h, int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
+                      const int *perm, double *X, int ldx, const int *skip, cudaStream_t s) {
+    RCP_TRY(prepare_solve_ws<T>(h, n, nrhs, s));
     PhaseScope ps(h, s, PH_SOLVE);
     CU_TRY(launch_solve<T>(n, nrhs, L, lda, Dd, Ds, perm, X, ldx, (T *)h->Y.p, (int *)h->flags.p,
                            (int *)h->status.p, skip, s));
@@ -474,6 +483,72 @@ rcp_status solve_impl(rcp_handle *h, int n, int nrhs, const T *L, int lda, const
 }
 
 bool valid_prec(rcp_prec p) { return p >= RCP_FP64 && p <= RCP_F16X3; }
+
+// ||L||_1 exactly and ||L^{-1}||_1 by Higham's estimator ("FORTRAN codes for estimating the
+// one-norm of a real or complex matrix", ACM TOMS 14 (1988), Algorithm 4.1, after Hager, 1984):
+// a few products with L^{-1} and L^{-T} steer a unit vector towards a column of L^{-1} of
+// largest 1-norm; every value it returns is ||L^{-1} x||_1 / ||x||_1 for some x, a lower bound.
+template <typename T>
+rcp_status l_norms_impl(rcp_handle *h, int n, const T *L, int lda, cudaStream_t s, double *nL, double *nLinv) {
+    RCP_TRY(prepare_solve_ws<T>(h, n, 1, s));
+    RCP_TRY(grow(h->iperm, (size_t)n * sizeof(int)));
+    RCP_TRY(grow(h->gmZ, (size_t)n * sizeof(double)));
+    CU_TRY(launch_iota(n, (int *)h->iperm.p, s));
+    RefineScalars *sc = (RefineScalars *)h->scal.p;
+    CU_TRY(launch_l_norm1<T>(n, L, lda, &sc->mx[0], s));
+    unsigned long long bits = 0;
+    CU_TRY(cudaMemcpyAsync(&bits, &sc->mx[0], sizeof bits, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    *nL = bits_to_double(bits);
+    double *dv = (double *)h->gmZ.p;
+    std::vector<double> x((size_t)n), y((size_t)n), xi((size_t)n), z((size_t)n);
+    // v <- L^{-1} v (mode 0) or L^{-T} v (mode 1) through the device
+    auto apply = [&](int mode, const std::vector<double> &in, std::vector<double> &out) -> rcp_status {
+        CU_TRY(cudaMemcpyAsync(dv, in.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CU_TRY(launch_tri_solve<T>(n, L, lda, (const int *)h->iperm.p, dv, (T *)h->Y.p, (int *)h->flags.p,
+                                   (int *)h->status.p, mode, s));
+        CU_TRY(cudaMemcpyAsync(out.data(), dv, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaStreamSynchronize(s));
+        int st = 0;
+        CU_TRY(cudaMemcpy(&st, h->status.p, sizeof st, cudaMemcpyDeviceToHost));
+        return st ? status_from_bits(st) : RCP_OK;
+    };
+    auto norm1 = [&](const std::vector<double> &v) { double t = 0.0; for (double a : v) t += std::fabs(a); return t; };
+    auto amax = [&](const std::vector<double> &v) {
+        int j = 0;
+        for (int i = 1; i < n; ++i) if (std::fabs(v[i]) > std::fabs(v[j])) j = i;
+        return j;
+    };
+    for (int i = 0; i < n; ++i) x[i] = 1.0 / n;
+    RCP_TRY(apply(0, x, y));
+    double est = norm1(y);
+    if (n > 1) {
+        for (int i = 0; i < n; ++i) xi[i] = y[i] >= 0.0 ? 1.0 : -1.0;
+        RCP_TRY(apply(1, xi, z));
+        int j = amax(z);
+        for (int iter = 2; iter <= 5; ++iter) {
+            std::fill(x.begin(), x.end(), 0.0);
+            x[j] = 1.0;
+            RCP_TRY(apply(0, x, y));
+            const double old = est;
+            est = norm1(y);
+            bool same = true;
+            for (int i = 0; i < n && same; ++i) same = (y[i] >= 0.0 ? 1.0 : -1.0) == xi[i];
+            if (same || est <= old) { est = std::max(est, old); break; }
+            for (int i = 0; i < n; ++i) xi[i] = y[i] >= 0.0 ? 1.0 : -1.0;
+            RCP_TRY(apply(1, xi, z));
+            const int jlast = j;
+            j = amax(z);
+            if (std::fabs(z[jlast]) == std::fabs(z[j])) break;   // no column promises more
+        }
+        // the alternative vector x_i = (-1)^i (1 + i / (n - 1)), ||x||_1 = 3n/2
+        for (int i = 0; i < n; ++i) x[i] = (i % 2 ? -1.0 : 1.0) * (1.0 + (double)i / (n - 1));
+        RCP_TRY(apply(0, x, y));
+        est = std::max(est, 2.0 * norm1(y) / (3.0 * n));
+    }
+    *nLinv = est;
+    return RCP_OK;
+}
 
 }  // namespace
 
@@ -492,7 +567,7 @@ void rcp_destroy(rcp_handle *h) {
     Buf *all[] = {&h->psnap, &h->pinv, &h->pbounds, &h->bord, &h->bom, &h->bticket, &h->bscr, &h->tcops, &h->keys, &h->skp, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
                   &h->s1v, &h->s2v, &h->s3v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
                   &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm,
-                  &h->gmV, &h->gmZ, &h->gmP, &h->gmH};
+                  &h->gmV, &h->gmZ, &h->gmP, &h->gmH, &h->iperm};
     for (Buf *b : all)
         if (b->p) cudaFree(b->p);
     for (auto &e : h->events) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -1092,6 +1167,17 @@ rcp_status rcp_panel_trace(rcp_handle *h, unsigned long long *out, int cap) {
 }
 
 long long rcp_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+rcp_status rcp_l_norms(rcp_handle *h, int n, const void *LA, int lda, rcp_prec prec, rcp_stream_t stream,
+                       double *norm1_L, double *norm1_Linv) {
+    if (!h || n < 0 || !valid_prec(prec) || !norm1_L || !norm1_Linv || (n > 0 && (!LA || lda < n))) return RCP_EINVAL;
+    *norm1_L = n > 0 ? 1.0 : 0.0;
+    *norm1_Linv = *norm1_L;
+    if (n == 0) return RCP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == RCP_FP64) return l_norms_impl<double>(h, n, (const double *)LA, lda, s, norm1_L, norm1_Linv);
+    return l_norms_impl<float>(h, n, (const float *)LA, lda, s, norm1_L, norm1_Linv);
+}
 
 rcp_status rcp_exchange_latency(rcp_handle *h, int grid, int rounds, rcp_stream_t stream, double *us) {
     if (!h || !us || rounds < 1 || grid < 0) return RCP_EINVAL;

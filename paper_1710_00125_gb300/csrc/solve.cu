@@ -619,6 +619,15 @@ bwd_words_kernel(int n, int nrhs, const float *__restrict__ L, int lda, const fl
 // u64 Yp[n * nrhs], u64 Vp[n * nrhs], float W[n * nrhs] (rounded up to 256 bytes), then
 // float Linv[nb * NB * NB]; of the flags only the two tickets are used.  The caller zeroes the
 // work area when it is allocated.
+// Epoch of a solve launch: the flags and published words of the work area carry it, so every
+// launcher that uses the area takes it from this one counter (a reused value would make stale
+// entries look current).
+static int next_solve_epoch() {
+    static int epoch = 0;
+    epoch = epoch % 1000000000 + 1;
+    return epoch;
+}
+
 template <typename T>
 static size_t solve_vec_bytes(int n, int nrhs) {
     const size_t v = ((size_t)n * nrhs * sizeof(T) + 255) / 256 * 256;
@@ -638,8 +647,7 @@ cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd,
                          const int *perm, double *X, int ldx, T *work, int *flags, int *status,
                          const int *skip, cudaStream_t s) {
     if (n == 0 || nrhs == 0) return cudaSuccess;
-    static int epoch = 0;
-    epoch = epoch % 1000000000 + 1;
+    const int epoch = next_solve_epoch();
     const int nb = (n + SV_NB - 1) / SV_NB;
     int *tickets = flags + 2 * nb;
     T *Linv = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(work) + solve_vec_bytes<T>(n, nrhs));
@@ -680,6 +688,110 @@ cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd,
     return cudaGetLastError();
 }
 
+// ---- one triangle of the solve on its own (1-norm estimate of L^{-1}) ----
+__global__ void words_to_double_kernel(int n, const unsigned long long *Yp, double *x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] = (double)__uint_as_float((unsigned)ldcg(Yp + i));
+}
+
+__global__ void double_to_float_kernel(int n, const double *x, float *w) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] = (float)x[i];
+}
+
+__global__ void iota_kernel(int n, int *p) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
+}
+
+cudaError_t launch_iota(int n, int *p, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    iota_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, s>>>(n, p);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tri_solve(int n, const T *L, int lda, const int *iperm, double *x, T *work, int *flags,
+                             int *status, int mode, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int epoch = next_solve_epoch();
+    const int nb = (n + SV_NB - 1) / SV_NB;
+    int *tickets = flags + 2 * nb;
+    T *Linv = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(work) + solve_vec_bytes<T>(n, 1));
+    cudaError_t e = cudaMemsetAsync(tickets, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = nb < sms ? nb : sms, vgrid = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
+    if constexpr (std::is_same<T, float>::value) {
+        float *Mneg = Linv + (size_t)nb * SV_NB * SV_NB, *Nneg = Mneg + (size_t)nb * SV_NB * SV_NB;
+        inv_diag_kernel<T><<<nb, SV_NB, 0, s>>>(n, L, lda, Linv, status, nullptr, Mneg, Nneg);
+        unsigned long long *Yp = reinterpret_cast<unsigned long long *>(work);
+        unsigned long long *Vp = Yp + (size_t)n;
+        float *W = reinterpret_cast<float *>(Vp + (size_t)n);
+        if (mode == 0) {
+            fwd_words_kernel<<<grid, SV_THREADS, 0, s>>>(n, 1, L, lda, Linv, Mneg, iperm, x, n, Yp, epoch, tickets,
+                                                         status, nullptr);
+            words_to_double_kernel<<<vgrid, 256, 0, s>>>(n, Yp, x);
+        } else {
+            double_to_float_kernel<<<vgrid, 256, 0, s>>>(n, x, W);
+            bwd_words_kernel<<<grid, SV_THREADS, 0, s>>>(n, 1, L, lda, Linv, Nneg, iperm, x, n, W, Vp, epoch,
+                                                         tickets + 1, status, nullptr);
+        }
+        count_launches(3);
+    } else {
+        inv_diag_kernel<T><<<nb, SV_NB, 0, s>>>(n, L, lda, Linv, status, nullptr);
+        T *Y = work;
+        if (mode == 0) {
+            fwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, 1, L, lda, Linv, iperm, x, n, Y, flags, epoch, tickets, status,
+                                                      nullptr);
+            e = cudaMemcpyAsync(x, Y, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        } else {
+            e = cudaMemcpyAsync(Y, x, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+            bwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, 1, L, lda, Linv, iperm, x, n, Y, flags + nb, epoch,
+                                                      tickets + 1, status, nullptr);
+        }
+        count_launches(2);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+// ||L||_1 of the unit lower L: max over columns of 1 + sum_{i > j} |L(i, j)|
+template <typename T>
+__global__ void __launch_bounds__(256) l_norm1_kernel(int n, const T *__restrict__ L, int lda, unsigned long long *out) {
+    __shared__ double red[8];
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        double s = 0.0;
+        for (int i = j + 1 + (int)threadIdx.x; i < n; i += 256) s += fabs((double)L[(size_t)i + (size_t)j * lda]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 1.0;
+            for (int q = 0; q < 8; ++q) t += red[q];
+            atomic_max_nonneg(out, t);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t launch_l_norm1(int n, const T *L, int lda, unsigned long long *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n <= 0) return e;
+    l_norm1_kernel<T><<<n < 1216 ? n : 1216, 256, 0, s>>>(n, L, lda, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_tri_solve<double>(int, const double *, int, const int *, double *, double *, int *, int *,
+                                              int, cudaStream_t);
+template cudaError_t launch_tri_solve<float>(int, const float *, int, const int *, double *, float *, int *, int *,
+                                             int, cudaStream_t);
+template cudaError_t launch_l_norm1<double>(int, const double *, int, unsigned long long *, cudaStream_t);
+template cudaError_t launch_l_norm1<float>(int, const float *, int, unsigned long long *, cudaStream_t);
 template size_t solve_work_bytes<double>(int, int);
 template size_t solve_work_bytes<float>(int, int);
 template cudaError_t launch_solve<double>(int, int, const double *, int, const double *, const double *, const int *,

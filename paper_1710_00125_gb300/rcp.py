@@ -78,6 +78,7 @@ def lib():
         L.rcp_solve.argtypes = [P, I, I, P, I, P, P, P, I, P, I, P]
         L.rcp_refine.argtypes = [P, I, I, P, I, P, I, P, P, P, I, P, I, P, I, D, I, P, ctypes.POINTER(Stats)]
         L.rcp_exchange_latency.argtypes = [P, I, I, P, ctypes.POINTER(D)]
+        L.rcp_l_norms.argtypes = [P, I, P, I, I, P, ctypes.POINTER(D), ctypes.POINTER(D)]
         L.rcp_refine_gmres.argtypes = [P, I, I, P, I, P, I, P, P, P, I, P, I, P, I, D, I, I, I, P,
                                        ctypes.POINTER(Stats)]
         L.rcp_sysv.argtypes = [P, I, I, P, I, P, I, P, I, ctypes.POINTER(Opts), D, I, I, P, ctypes.POINTER(Stats)]
@@ -256,6 +257,17 @@ PHASES = ("sketch", "panel", "interchange", "trailing", "solve", "residual")
 def rcp_profile(h: Handle, enable=True) -> None:
     """0/False: off; 1/True: per-phase events; 2: events plus per-step panel timestamps."""
     _check(lib().rcp_profile(h.h, int(enable)), "rcp_profile")
+
+
+def rcp_l_norms(h: Handle, LA: torch.Tensor, prec, stream=None):
+    """(||L||_1, estimate of ||L^{-1}||_1) of the factor ``LA`` from rcp_factor."""
+    if isinstance(prec, str):
+        prec = PREC_NAMES[prec]
+    nl, ni = ctypes.c_double(), ctypes.c_double()
+    n = LA.shape[0]
+    _check(lib().rcp_l_norms(h.h, n, _ptr(LA), n, prec, _stream(stream), ctypes.byref(nl), ctypes.byref(ni)),
+           "rcp_l_norms")
+    return nl.value, ni.value
 
 
 def rcp_exchange_latency(h: Handle, grid: int = 0, rounds: int = 20000, stream=None) -> float:

@@ -520,6 +520,31 @@ def test_guard_option_checks(rcp, handle):
                        rcp.make_opts(b=32, d=40, prec="fp64", q_mode=2, guard_r=1))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_l_norms_of_a_factor(rcp, handle, prec):
+    n = 500
+    a = inputs.gaussian_sym(n, seed=21)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, 64, 40, 3, prec=prec)
+    assert code == 0
+    nl, ni = rcp.rcp_l_norms(handle, A, prec)
+    L = _unit_lower(A)   # the factor's own values, in FP64
+    el, ei = oracle.l_norms(L)
+    assert nl == pytest.approx(el, rel=1e-12)
+    # Higham's estimate: a lower bound (up to the solve's rounding), and close on random factors
+    assert ei * 0.3 <= ni <= ei * (1 + (1e-10 if prec == "fp64" else 1e-4))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_l_norms_closed_form(rcp, handle, prec):
+    # L = I - subdiagonal: ||L||_1 = 2 and ||L^{-1}||_1 = n (the lower triangle of ones)
+    n = 777
+    L = torch.zeros((n, n), dtype=torch.float64 if prec == "fp64" else torch.float32, device=DEV)
+    idx = torch.arange(n - 1, device=DEV)
+    L[idx, idx + 1] = -1.0    # column-major storage of the subdiagonal (the row-major transpose)
+    nl, ni = rcp.rcp_l_norms(handle, L, prec)
+    assert nl == 2.0 and ni == float(n)
+
+
 def test_exchange_latency_probe(rcp, handle):
     # the panel's per-step grid exchange alone: a positive, finite time per round, and the
     # handle factors normally afterwards (barrier counter and key ring left zeroed)

@@ -370,3 +370,19 @@ def test_pseudo_inverse_solve_and_basic_solution():
     b = a @ xt
     x = oracle.ldlt_solve(r["L"], r["Dd"], r["Ds"], r["perm"], b.copy())
     assert oracle.berr(a, x, b) <= 1e-13
+
+
+def test_l_norms_closed_forms():
+    # L = I - (subdiagonal of ones): L^{-1} is the lower triangle of ones, ||L^{-1}||_1 = n
+    n = 9
+    L = np.eye(n) - np.eye(n, k=-1)
+    assert oracle.l_norms(L) == (2.0, float(n))
+    # [[1, 0], [e, 1]]: both norms 1 + |e|
+    e = -0.375
+    assert oracle.l_norms(np.array([[1.0, 0.0], [e, 1.0]])) == (1.0 + abs(e), 1.0 + abs(e))
+    # against numpy's inverse on a random unit lower triangle
+    rng = np.random.default_rng(2)
+    L = np.tril(rng.uniform(-1, 1, (30, 30)), -1) + np.eye(30)
+    nl, ni = oracle.l_norms(L)
+    assert nl == pytest.approx(np.abs(L).sum(0).max())
+    assert ni == pytest.approx(np.abs(np.linalg.inv(L)).sum(0).max(), rel=1e-8)
