@@ -77,6 +77,10 @@ def parse(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=4096, help="systems of the batched ragged workload (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--stability", action="store_true",
+                    help="instead of timing: the stability diagnostics of the GPU factor for each synthetic "
+                         "matrix type of the experiments section (growth, berr, ||L||_1, ||L^-1||_1)")
+    ap.add_argument("--stability-n", type=int, default=2048)
     return ap.parse_args(argv)
 
 
@@ -461,6 +465,45 @@ def roofline_for(name, ms, launches, a, hbm_peak, peaks, peak_src):
             "traffic": None}
 
 
+def run_stability(a, local_rank):
+    """Per matrix type (Types 1, 3, 4, 5, 6, 7, 8, 10; Type 9 is a dataset not in this container):
+    the FP64 factor with the paper's sampling dimension p = 5 (d = 5, b = 64), its growth factor,
+    2x2 count, ||L||_1 and estimated ||L^{-1}||_1, and the backward error of the plain solve."""
+    import numpy as np
+    import torch
+
+    from paper_1710_00125_gb300 import inputs, rcp
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    h = rcp.rcp_create()
+    n = a.stability_n
+    types = {"1 (BK worst case)": lambda: inputs.bk_worst(n), "3 (Hankel)": lambda: inputs.hankel(n, 1),
+             "4 (DST)": lambda: inputs.dst(n), "5 (DCT-I)": lambda: inputs.dct(n),
+             "6 (Gaussian)": lambda: inputs.gaussian_sym(n, 1),
+             "7 (KKT)": lambda: inputs.kkt(2 * n // 3, n - 2 * n // 3, seed=1),
+             "8 (augmented)": lambda: inputs.augmented(2 * n // 3, n - 2 * n // 3, 1),
+             "10 (rank deficient)": lambda: inputs.rank_deficient(n, 1)}
+    for name, make in types.items():
+        mat = np.ascontiguousarray(make())
+        m = mat.shape[0]
+        A64 = torch.from_numpy(mat).to(dev)
+        A = A64.clone()
+        Dd = torch.zeros(m, dtype=torch.float64, device=dev)
+        Ds = torch.zeros_like(Dd)
+        perm = torch.zeros(m, dtype=torch.int32, device=dev)
+        code, st = rcp.rcp_factor(h, A, Dd, Ds, perm, rcp.make_opts(b=64, d=5, seed=1, prec="fp64"))
+        nl, ni = rcp.rcp_l_norms(h, A, "fp64")
+        xt = torch.from_numpy(inputs.x_true(m, 1, seed=1)).to(dev)
+        Bv = (A64 @ xt.T).T.contiguous()
+        X = Bv.clone()
+        rcp.rcp_solve(h, A, Dd, Ds, perm, "fp64", X)
+        r = Bv - (A64 @ X.T).T
+        berr = float(r.abs().amax() / (A64.abs().sum(1).amax() * X.abs().amax()))
+        print(json.dumps({"type": name, "n": m, "d": 5, "b": 64, "prec": "fp64", "info": int(st.info),
+                          "growth_D": st.growth_D, "n_2x2": st.n_2x2, "max_abs_L": st.max_abs_L,
+                          "norm1_L": nl, "norm1_Linv_est": ni, "berr_solve": berr}), flush=True)
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -468,6 +511,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         run_reference(a, rank, world)
+        return
+    if a.stability:
+        if rank == 0:
+            run_stability(a, local_rank)
         return
     run_ours(a, rank, world, local_rank)
 
