@@ -69,7 +69,7 @@ typedef struct {
                         /* sketch picks each block's candidates, the block's steps take them */
                         /* in order (SBKP may still bring in other columns), and the sketch  */
                         /* is updated once per block, B(:, k1:n) -= B_blk L11^{-T} L21^T.    */
-                        /* rcp_factor_batched supports q = 1 only.                            */
+                        /* rcp_factor_batched supports q = 1 only, without the safeguard.     */
     uint64_t seed;      /* Philox key of the sketch matrix Omega                             */
     rcp_prec prec;      /* arithmetic of the factor                                          */
     double alpha;       /* SBKP threshold; 0 = default sqrt(2)/2                             */

@@ -1017,6 +1017,7 @@ rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, 
         for (const auto &t : h->tuned)
             if (t.nmax == nmax && t.d == d && t.f64 == (int)f64) b = t.b;   // the autotuned width
     if (opts && opts->q_mode != 0 && opts->q_mode != 1) return RCP_EUNSUPPORTED;
+    if (opts && opts->guard_r != 0) return RCP_EUNSUPPORTED;   // the safeguard is host-driven per system
     if (b > 512 || d > 128) return RCP_EUNSUPPORTED;
     const double alpha = (opts && opts->alpha > 0.0) ? opts->alpha : std::sqrt(2.0) / 2.0;
     if (!(alpha < 1.0)) return RCP_EINVAL;

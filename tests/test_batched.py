@@ -246,6 +246,12 @@ def test_batched_invalid_arguments(rcp, handle):
         rcp.rcp_factor_batched(handle, 2, 20, bt.n, None, None, bt.p_F, bt.ld, bt.p_Dd, bt.p_Ds, bt.p_perm,
                                _opts(rcp, "fp64", b=32, d=129), bt.info)
     assert e.value.code == -7
+    with pytest.raises(rcp.RcpError) as e:
+        # the Algorithm 2 safeguard is not offered on the batched path
+        o = _opts(rcp, "fp64")
+        o.guard_r = 1
+        rcp.rcp_factor_batched(handle, 2, 20, bt.n, None, None, bt.p_F, bt.ld, bt.p_Dd, bt.p_Ds, bt.p_perm, o, bt.info)
+    assert e.value.code == -7
 
 
 def test_batched_autotuner(rcp, handle):
