@@ -85,13 +85,13 @@ def parse(argv=None):
 
 
 def workload_name(a):
-    return (f"C3: n={a.n} A = Q diag(lam) Q^T (64 seeded Householder reflectors, |lam| log-uniform "
+    return (f"n={a.n} A = Q diag(lam) Q^T (64 seeded Householder reflectors, |lam| log-uniform "
             f"over 1..1e{a.kexp:g}, random signs), {a.nrhs} RHS b = A x_true; FP32 factor ({a.prec}, b={a.b}, "
             f"d={a.d}) + FP64 refinement to berr<={a.tol:g}")
 
 
 def batched_workload_name(a):
-    return (f"C5: {a.batch} systems, n_i ~ U{{32..512}} (seeded), A_i = (G_i + G_i^T)/2 with G_i N(0,1), "
+    return (f"{a.batch} systems, n_i ~ U{{32..512}} (seeded), A_i = (G_i + G_i^T)/2 with G_i N(0,1), "
             f"16 RHS b_i = A_i x_i; FP32 factor (d=40, panel width autotuned) + FP64 refinement to berr<={a.tol:g}, "
             f"one persistent launch per phase, replayed from a CUDA graph")
 
