@@ -83,20 +83,25 @@ __global__ void __launch_bounds__(QR_THREADS, 1) qrcp_kernel(FactorWork<T> w, in
     double *rec = w.s1v;               // per CTA: residual norm^2, position (as double)
     T *pay = w.pay;                    // per CTA: the candidate's residual rows
     const int steps = min(min(steps_max, m), d);
+    // The per-column work (residual norms, the reflection's dot products) runs in the factor's
+    // type: FP32 factors take their QRCP decisions on FP32 values, as their panels do (and FP64
+    // runs at 1/64 of the FP32 rate on this part); the few scalars of the reflection stay FP64.
+    using R = T;
     for (int t = 0; t < steps; ++t) {
         // ---- the local candidate: largest residual norm over rows t..d-1 ----
         double bv = -1.0;
         int bp = INT_MAX, bj = -1;
         for (int jl = warp; jl < cnt; jl += QR_WARPS) {
             if (chosen[jl]) continue;
-            double s2 = 0.0;
+            R s2 = R(0);
             for (int r = t + lane; r < d; r += 32) {
-                const double x = (double)Wk[(size_t)jl * d + r];
+                const R x = (R)Wk[(size_t)jl * d + r];
                 s2 += x * x;
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-            if (s2 > bv || (s2 == bv && cur[jl] < bp)) { bv = s2; bp = cur[jl]; bj = jl; }
+            const double s2d = (double)s2;
+            if (s2d > bv || (s2d == bv && cur[jl] < bp)) { bv = s2d; bp = cur[jl]; bj = jl; }
         }
         if (lane == 0) { s_wv[warp] = bv; s_wp[warp] = bp; s_wj[warp] = bj; }
         __syncthreads();
@@ -160,7 +165,10 @@ __global__ void __launch_bounds__(QR_THREADS, 1) qrcp_kernel(FactorWork<T> w, in
             for (int r = t + lane; r < d; r += 32) vv += (double)s_v[r] * (double)s_v[r];
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, off);
-            if (lane == 0) s_sc[2] = vv;
+            if (lane == 0) {
+                s_sc[2] = vv;
+                s_sc[3] = vv > 0.0 ? 2.0 / vv : 0.0;
+            }
         }
         __syncthreads();
         if (s_sc[0] != 0.0 && s_sc[2] > 0.0) {
@@ -168,11 +176,13 @@ __global__ void __launch_bounds__(QR_THREADS, 1) qrcp_kernel(FactorWork<T> w, in
             for (int jl = warp; jl < cnt; jl += QR_WARPS) {
                 if (chosen[jl]) continue;
                 T *col = Wk + (size_t)jl * d;
-                double dot = 0.0;
-                for (int r = t + lane; r < d; r += 32) dot += (double)s_v[r] * (double)col[r];
+                R dot = R(0);
+                for (int r = t + lane; r < d; r += 32) dot += (R)s_v[r] * (R)col[r];
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
-                const T f = (T)(2.0 * dot / vv);
+                T f;
+                if constexpr (sizeof(T) == sizeof(double)) f = (T)(2.0 * dot / vv);
+                else f = dot * (T)s_sc[3];   // 2 / v^T v, formed once per step
                 for (int r = t + lane; r < d; r += 32) col[r] -= f * s_v[r];
             }
         }
