@@ -475,6 +475,26 @@ def test_guard_fp64_recomputes_the_sketch_like_the_oracle(rcp, handle):
     assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() <= 1e-13 * np.abs(a).max()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+def test_guard_fp32_recomputes_the_sketch(rcp, handle, prec):
+    # the FP32 re-sketch of the trailing submatrix (split-K sketch at an offset): 500 of 1200
+    # eigenvalues near 1e-3, well above the FP32 rounding level of the Schur complement (~1e-5),
+    # are flagged by sqrt(eps) beta = 1e-2 beta and accepted against eps beta after one recomputation
+    n, d = 1200, 80
+    rng = np.random.default_rng(9)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([rng.uniform(1, 2, 700) * rng.choice([-1, 1], 700), 1e-3 * rng.uniform(1, 2, 500)])
+    a = (q * lam) @ q.T
+    a = 0.5 * (a + a.T)
+    code, st, A, Dd, Ds, perm = _guarded(rcp, handle, a, 64, d, 5, prec, 2, 1e-4)
+    assert code == 0 and st.resketches == 1 and st.rank == n
+    L = _unit_lower(A)
+    D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
+    p = perm.cpu().numpy()
+    assert sorted(p.tolist()) == list(range(n))
+    assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() <= 2e-5 * max(1.0, st.growth_D) * np.abs(a).max()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_guard_that_never_fires_changes_nothing_on_the_gpu(rcp, handle, prec):
     a = inputs.gaussian_sym(300, seed=4)
