@@ -99,3 +99,29 @@ def test_gmres_lsq_rejects_bad_arguments(clib):
     assert clib.rcp_gmres_lsq(-1, H.ctypes.data, 3, 1.0, y.ctypes.data, ctypes.byref(res)) == -1
     # k = 0: the residual is beta
     assert clib.rcp_gmres_lsq(0, None, 1, 3.0, None, ctypes.byref(res)) == 0 and res.value == 3.0
+
+
+def test_product_path_fails_loudly_without_a_gpu_or_library(monkeypatch, tmp_path):
+    # no CPU fallback: the binding raises instead of computing anything on the host
+    import torch
+
+    from paper_1710_00125_gb300 import rcp
+    monkeypatch.setattr(rcp, "_lib", None)
+    monkeypatch.setattr(rcp, "_LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        rcp.lib()
+    if not torch.cuda.is_available():
+        from paper_1710_00125_gb300 import build
+        monkeypatch.setattr(rcp, "_LIB_PATH", build.build())
+        with pytest.raises(RuntimeError, match="CUDA device"):
+            rcp.lib()
+
+
+def test_package_never_imports_the_oracle():
+    # the oracle is test infrastructure: no module of the package names it in an import
+    pkg = os.path.join(ROOT, "paper_1710_00125_gb300")
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            src = open(os.path.join(pkg, name)).read()
+            assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), name
+            assert "import oracle" not in src and "from oracle" not in src, name
