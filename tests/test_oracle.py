@@ -272,6 +272,22 @@ def test_q_equals_b_mode():
     assert checked >= 3
 
 
+def test_qb_block_candidates_match_lapack_qrcp():
+    # the partial QRCP of the sketch picks the same columns as LAPACK's ?geqp3 (Businger-Golub
+    # pivoting); on a strongly diagonal SPD matrix SBKP keeps case (1), so positions 0..b-1 after
+    # the first step hold the candidates in QRCP order
+    sl = pytest.importorskip("scipy.linalg")
+    n, d, blk = 60, 16, 8
+    rng = np.random.default_rng(11)
+    g = rng.standard_normal((n, n))
+    a = g @ g.T / n + 4.0 * np.eye(n)
+    om = oracle.omega(4, d, n)
+    r = oracle.rcp(a, om, q_mode=2, block=blk, snapshots=True)
+    assert all(st["kase"] == 1 for st in r["steps"][:blk])
+    _, _, piv = sl.qr(om @ a, pivoting=True, mode="economic")
+    assert np.array_equal(r["snap_perm"][0][:blk], piv[:blk])
+
+
 def test_paper_p_bound_example():
     g = json.load(open(GOLDEN))["p_bound_example"]
     assert oracle.p_bound(g["n"], g["eps"], g["delta"]) == g["p"]
