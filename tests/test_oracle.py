@@ -272,6 +272,23 @@ def test_q_equals_b_mode():
     assert checked >= 3
 
 
+def test_argmax_ties_go_to_the_smallest_position():
+    # Omega = I (d = n): B = A, and columns 0 and 1 have equal norms; the pivot is column 0
+    a = np.array([[2.0, 0.0, 0.5], [0.0, 2.0, 0.5], [0.5, 0.5, 1.0]])
+    r = oracle.rcp(a, np.eye(3))
+    assert r["steps"][0]["pi"] == 0 and r["perm"][0] == 0
+
+
+def test_sbkp_lambda_is_the_off_diagonal_maximum_of_the_pivot_column():
+    # step 0 (nothing eliminated yet): lambda = max_{i != pi} |A(i, pi)| of the input itself
+    for seed in range(5):
+        a = inputs.gaussian_sym(12, seed=20 + seed)
+        a[np.diag_indices(12)] *= 8.0   # diagonals larger than the column's other entries
+        st0 = oracle.rcp(a, oracle.omega(seed, 6, 12))["steps"][0]
+        col = np.delete(a[:, st0["pi"]], st0["pi"])
+        assert st0["lam"] == np.abs(col).max()
+
+
 def test_qb_block_candidates_match_lapack_qrcp():
     # the partial QRCP of the sketch picks the same columns as LAPACK's ?geqp3 (Businger-Golub
     # pivoting); on a strongly diagonal SPD matrix SBKP keeps case (1), so positions 0..b-1 after
