@@ -187,6 +187,17 @@ def test_bunch_kaufman_matches_lapack_sytrf():
         assert _recon_err(a, r) < 1e-13
 
 
+def test_bunch_kaufman_sigma_excludes_the_diagonal():
+    # lambda = |a_10| = 1 (r = 1), sigma = the largest off-diagonal |a_i1| = 1: case (3) takes a_11
+    # = 1000 as the first pivot (an interchange); counting a_11 in sigma would accept a_00 = 1e-3
+    a = np.array([[1e-3, 1.0, 0.0], [1.0, 1000.0, 0.1], [0.0, 0.1, 1.0]])
+    r = oracle.bk(a)
+    assert r["perm"][0] == 1 and r["Dd"][0] == 1000.0
+    sl = pytest.importorskip("scipy.linalg")
+    _, d_lapack, _ = sl.ldl(a, lower=True)
+    assert np.isclose(np.abs(np.diag(d_lapack)).max(), 1000.0)
+
+
 def test_bunch_parlett_first_pivot_is_global():
     # complete pivoting: the first pivot is the largest diagonal (1x1) or the largest
     # off-diagonal pair (2x2), found by brute force
