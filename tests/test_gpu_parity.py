@@ -469,7 +469,9 @@ def test_guard_fp64_recomputes_the_sketch_like_the_oracle(rcp, handle):
     code, st, A, Dd, Ds, perm = _guarded(rcp, handle, a, 64, d, 5, "fp64", 2, 1e-10)
     assert code == 0 and st.resketches == 1 and st.rank == n
     p = perm.cpu().numpy()
-    assert np.array_equal(p[:120], ref["perm"][:120])
+    # the whole pivot sequence, including the steps that follow the recomputed sketch (Omega'
+    # drawn from Philox stream 1 on both sides, then a fresh argmax)
+    assert np.array_equal(p, ref["perm"])
     L = _unit_lower(A)
     D = oracle.block_d(Dd.cpu().numpy(), Ds.cpu().numpy())
     assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() <= 1e-13 * np.abs(a).max()
