@@ -521,9 +521,8 @@ int oracle_bp(int n, double *a, double alpha, double *l, double *dd, double *ds,
             interchange(n, k, k, t, a, 0, NULL, l, perm);
         } else {
             s = 2;
-            /* move q0 to k, then p0 (which may have moved if p0 == k) to k+1 */
+            /* move q0 to k, then p0 to k+1 (p0 > q0 >= k: the first swap leaves p0 in place) */
             interchange(n, k, k, q0, a, 0, NULL, l, perm);
-            if (p0 == k) p0 = q0;
             interchange(n, k, k + 1, p0, a, 0, NULL, l, perm);
         }
         if (eliminate(n, k, s, a, l, dd, ds) && info == 0) info = k + 1;
