@@ -17,7 +17,10 @@
  *     cudaMalloc on first use and grown when a larger problem arrives; it is freed by
  *     rcp_destroy.  One handle serves one stream at a time.
  *   - Every call is asynchronous on the given stream unless it fills a host rcp_stats,
- *     in which case it synchronizes that stream before returning.
+ *     in which case it synchronizes that stream before returning.  The host-driven calls
+ *     synchronize always (and cannot be captured in a graph): rcp_refine_gmres, rcp_factor
+ *     and rcp_sysv with the Algorithm 2 safeguard (opts->guard_r > 0, once per panel),
+ *     rcp_l_norms and rcp_exchange_latency.
  *
  * Errors: a negative rcp_status is returned before anything is launched when an argument
  * is invalid.  Numerical faults found on the device (non-finite values, a bounded wait
