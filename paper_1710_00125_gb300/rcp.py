@@ -168,7 +168,7 @@ def rcp_factor(h: Handle, A: torch.Tensor, Dd: torch.Tensor, Ds: torch.Tensor, p
     n = A.shape[0]
     assert A.is_cuda and A.is_contiguous() and A.shape == (n, n)
     st = Stats()
-    code = lib().rcp_factor(h.h, n, _ptr(A), n, _ptr(Dd), _ptr(Ds), _ptr(perm),
+    code = lib().rcp_factor(h.h, n, _ptr(A), max(n, 1), _ptr(Dd), _ptr(Ds), _ptr(perm),
                             ctypes.byref(opts) if opts else None, _stream(stream),
                             ctypes.byref(st) if stats else None)
     _check(code, "rcp_factor", allow_info=True)

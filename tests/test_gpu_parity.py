@@ -130,6 +130,19 @@ def test_fp64_structured_families(rcp, handle, name):
         assert np.array_equal(p, ref["perm"])
 
 
+def test_empty_system(rcp, handle):
+    # n = 0: nothing to factor, solve or refine; every call succeeds without launching work
+    e = torch.empty((0, 0), dtype=torch.float64, device=DEV)
+    v = torch.empty(0, dtype=torch.float64, device=DEV)
+    p = torch.empty(0, dtype=torch.int32, device=DEV)
+    code, st = rcp.rcp_factor(handle, e, v, v, p, rcp.make_opts(b=64, d=80, prec="fp64"))
+    assert code == 0 and st.info == 0
+    rcp.rcp_solve(handle, e, v, v, p, "fp64", torch.empty((1, 0), dtype=torch.float64, device=DEV))
+    code, st = rcp.rcp_sysv(handle, e, torch.empty((1, 0), dtype=torch.float64, device=DEV),
+                            torch.empty((1, 0), dtype=torch.float64, device=DEV), rcp.make_opts(prec="f16x3"))
+    assert code == 0
+
+
 def test_degenerate_inputs(rcp, handle):
     # zero matrix: every pivot is a zero 1x1 (SBKP case 0); info reports the first
     code, st, A, Dd, Ds, perm = _factor(rcp, handle, np.zeros((5, 5)), 4, 3, 0)
