@@ -1,5 +1,7 @@
 // interchange.cu -- applies one panel's symmetric interchanges to the stored arrays and
-// performs the deferred trailing update of Algorithm 1 ("compute Schur complement").
+// performs the deferred trailing update of Algorithm 1 ("compute Schur complement"); also the
+// start and end of a factorization, and the zero fill of the Schur complement where the
+// Algorithm 2 safeguard stops.
 //
 // After a panel, position p >= k0 holds the block-start index phi(p); only a few indices
 // moved (at most twice the panel width).  For each moved index j with new position

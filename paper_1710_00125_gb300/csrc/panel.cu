@@ -8,7 +8,9 @@
 // of the Schur complement.  An interchange therefore moves no data during the panel; it only
 // relabels positions (lp[] per owned index, and a small window table of which index sits at
 // the positions k0 .. k0+b+2 the panel can fill).  The data are moved once per panel by the
-// interchange kernels (interchange.cu).
+// interchange kernels (interchange.cu).  With the Algorithm 2 safeguard on, a step whose
+// pivot's sketch norm falls below eps^delta beta ends the panel before that step, and the host
+// recomputes the sketch or stops.
 //
 // Per pivot step (Section 3, Figure SBKP, Eq. "Update matrix B"):
 //   (1) argmax of ||B(:, j)||^2 over the remaining indices (ties: smallest position)  -> P

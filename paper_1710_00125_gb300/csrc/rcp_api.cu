@@ -1,7 +1,10 @@
 // rcp_api.cu -- the C ABI declared in include/rcp.h: handle, workspace and the host-side
-// orchestration of the kernels on one CUDA stream.  All loop control that depends on data
-// (panel widths, refinement convergence) stays on the device, so the launch sequence of a
-// call depends only on its arguments.
+// orchestration of the kernels on one CUDA stream.  In the factorization, the solves and the
+// classic refinement, loop control that depends on data (panel widths, refinement convergence)
+// stays on the device, so the launch sequence of a call depends only on its arguments.  The
+// host-driven calls read device scalars between launches: GMRES-based refinement (the Krylov
+// least-squares problem), the factorization with the Algorithm 2 safeguard (one state read per
+// panel) and the 1-norm estimator of rcp_l_norms.
 #include <cmath>
 #include <cstdlib>
 #include <cstring>

@@ -1,7 +1,9 @@
-// solve.cu -- the solution phase (x = Pi L^{-T} D^{-1} L^{-1} Pi^T b, the operation-count
-// table's "solution phase"), and the FP64 pieces of iterative refinement: the residual
-// r = b - A x with the lower-stored original A, ||A||_inf, and the normwise backward error
-// ||r||_inf / (||A||_inf ||x||_inf) of the experiments section.
+// solve.cu -- the solution phase (x = Pi L^{-T} D^+ L^{-1} Pi^T b, the operation-count
+// table's "solution phase"; D^+ the pseudo-inverse of D: a zero 1x1 block contributes 0), and
+// the FP64 pieces of iterative refinement: the residual r = b - A x with the lower-stored
+// original A, ||A||_inf, and the normwise backward error ||r||_inf / (||A||_inf ||x||_inf) of
+// the experiments section.  Also one triangle of the solve on its own and ||L||_1, for the
+// stability diagnostics (||L||_1, an estimate of ||L^{-1}||_1).
 //
 // Triangular solves: one persistent launch per triangle.  Row blocks of SV_NB rows are
 // handed out in dependency order through an atomic ticket; a block waits (bounded) on the
