@@ -1,7 +1,8 @@
 // gmres.cu -- FP64 vector kernels of GMRES-based iterative refinement.
 //
-// The refinement of Section "Numerical experiments" (x += solve(r)) converges only while the
-// factor's error times the condition number stays below one.  For harder systems the
+// Classic iterative refinement (x += solve(r), with the backward error of the experiments
+// section as its stopping test) converges only while the factor's error times the condition
+// number stays below one.  For harder systems the
 // correction equation A d = r is solved instead by GMRES (Saad and Schultz, 1986) on the
 // preconditioned operator M^{-1} A, M = the computed L D L^T (Carson and Higham, 2017/2018:
 // "GMRES-based iterative refinement").  Every vector of that iteration is FP64 and
