@@ -437,10 +437,17 @@ def roofline_for(name, ms, launches, a, hbm_peak, peaks, peak_src):
     per_launch_ms = ms / max(1, launches)
     if name == "trailing":
         # lower-triangle update per panel: (n-k)^2 flops-pairs * 2 * width, summed ~ n^3/3
+        # (the algorithmic flops: the split products' three tensor products count once)
         fl = n ** 3 / 3.0 / npan
+        ach = fl / (per_launch_ms * 1e-3) / 1e12
+        if a.prec in ("f16x3", "tf32x3") and "bf16_tflops" in peaks:
+            # tcgen05: FP16 runs at the bf16 rate, TF32 at half of it (nominal ratio)
+            peak = peaks["bf16_tflops"] * (1.0 if a.prec == "f16x3" else 0.5)
+            return {"kernel": "tc_trailing_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_note": "of measured (bf16 burst" + (")" if a.prec == "f16x3" else " x 1/2 for TF32)")}
         # FP32 CUDA-core FMA peak: 152 SMs x 128 lanes x 2 flop x max clock
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        ach = fl / (per_launch_ms * 1e-3) / 1e12
         return {"kernel": "trailing_simt_kernel<float>", "bound": "alu", "achieved": ach, "peak": peak,
                 "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x sm_max_mhz"}
@@ -460,7 +467,6 @@ def roofline_for(name, ms, launches, a, hbm_peak, peaks, peak_src):
                 "unit": "GB/s", "frac": ach / hbm_peak, "traffic": traffic, "peak_note": peak_src,
                 "note": "latency-bound: per pivot step one grid barrier (two on the non-speculative path) "
                         "and dependent L2/HBM round trips for the keys and the next pivot's column"}
-    byts = 0
     return {"kernel": name, "bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s", "frac": None,
             "traffic": None}
 
