@@ -125,3 +125,45 @@ def test_package_never_imports_the_oracle():
             src = open(os.path.join(pkg, name)).read()
             assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), name
             assert "import oracle" not in src and "from oracle" not in src, name
+
+
+def test_plain_c_program_compiles_links_and_calls_the_abi(clib, tmp_path):
+    # a C (not C++) consumer of include/rcp.h: the header is valid C, the library links, and the
+    # host-only entry points answer (no device work)
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_1710_00125_gb300 import build
+    lib = build.build()
+    src = tmp_path / "abi.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "rcp.h"
+int main(void) {
+    double H[6] = {2.0, 1.0, 0.0, 1.0, 3.0, 1.0};   /* 3 x 2 Hessenberg, column-major */
+    double y[2], res = -1.0;
+    rcp_opts o = {0};
+    rcp_stats st = {0};
+    (void)o; (void)st;
+    if (rcp_gmres_lsq(2, H, 3, 1.0, y, &res) != RCP_OK) return 2;
+    if (rcp_factor(NULL, 4, NULL, 4, NULL, NULL, NULL, NULL, NULL, NULL) != RCP_EINVAL) return 3;
+    printf("%s|%.17g\n", rcp_status_string(RCP_EUNSUPPORTED), res);
+    return 0;
+}
+""")
+    exe = tmp_path / "abi"
+    inc = os.path.join(ROOT, "include")
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-I", inc, str(src), lib, "-o", str(exe),
+                        "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    msg, res = out.stdout.strip().split("|")
+    assert msg == "unsupported size or option"
+    # the least-squares residual of the 3 x 2 Hessenberg problem, by numpy
+    Hm = np.array([[2.0, 1.0], [1.0, 3.0], [0.0, 1.0]])
+    e1 = np.array([1.0, 0.0, 0.0])
+    yref = np.linalg.lstsq(Hm, e1, rcond=None)[0]
+    assert float(res) == pytest.approx(np.linalg.norm(e1 - Hm @ yref), rel=1e-12)
