@@ -12,6 +12,11 @@ solve, and FP64 refinement until the normwise backward error is <= 1e-12.
 N > 1 (torchrun): every rank solves its own independent system (replicas; the path has no
 data exchange), value = all ranks' flops / the slowest rank's time.  ``--impl reference``
 times the CPU oracle (plain C, FP64, one thread) on a bounded sample of the same workload.
+
+Besides the contract's keys the line carries the FP64 path on the same system
+(``speedup_vs_fp64``), per-phase CUDA-event times (``phases_ms``), the panel's time per pivot
+step beside the latency floor of its grid exchange (``panel_latency``), and the batched ragged
+workload (``batched``).  ``--stability`` prints per-type stability diagnostics instead of timing.
 """
 from __future__ import annotations
 
