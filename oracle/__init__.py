@@ -44,7 +44,9 @@ def build(force: bool = False) -> str:
 class _Step(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("pi", ctypes.c_int), ("r", ctypes.c_int),
                 ("kase", ctypes.c_int), ("s", ctypes.c_int),
-                ("norm2", ctypes.c_double), ("lam", ctypes.c_double)]
+                ("norm2", ctypes.c_double), ("lam", ctypes.c_double),
+                ("norm2_next", ctypes.c_double), ("lam_next", ctypes.c_double),
+                ("akk", ctypes.c_double), ("arr", ctypes.c_double)]
 
 
 def _load():
@@ -146,7 +148,8 @@ def rcp(a, om, alpha: float = SQRT2_OVER_2, q_mode: int = 1, block: int = 64,
                rho_elem=float(stats[0]), n_2x2=int(stats[1]), min_sketch_ratio=float(stats[2]),
                max_abs_L=float(stats[3]), rank=int(gout[0]), resketches=int(gout[1]))
     if record:
-        out["steps"] = [dict(k=s.k, pi=s.pi, r=s.r, kase=s.kase, s=s.s, norm2=s.norm2, lam=s.lam)
+        out["steps"] = [dict(k=s.k, pi=s.pi, r=s.r, kase=s.kase, s=s.s, norm2=s.norm2, lam=s.lam,
+                             norm2_next=s.norm2_next, lam_next=s.lam_next, akk=s.akk, arr=s.arr)
                         for s in steps[: nsteps.value]]
     if snapshots:
         # snapshot arrays are C-ordered stacks of column-major d x n and n x n matrices

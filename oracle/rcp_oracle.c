@@ -184,12 +184,17 @@ typedef struct {
     int s;          /* pivot size                                                     */
     double norm2;   /* ||B(:, pi)||_2^2                                                */
     double lambda;  /* SBKP lambda                                                    */
+    /* margins of the step's decisions (diagnostics; no decision reads them):           */
+    double norm2_next;  /* second largest ||B(:, j)||_2^2 over the candidates (-1: none) */
+    double lam_next;    /* second largest |a_ik| over i > k (-1: none)                  */
+    double akk;         /* |a_kk| compared with alpha lambda                            */
+    double arr;         /* |a_rr| compared with alpha lambda (cases 2/3), else -1       */
 } oracle_step;
 
 /* Simplified Bunch-Kaufman pivoting (Figure "SBKP") on column k of the current
  * Schur complement.  Performs the interchange it prescribes and returns s. */
 static int sbkp(int n, int k, double alpha, double *a, int d, double *b, double *l, int *perm,
-                int *kase_out, int *r_out, double *lam_out)
+                int *kase_out, int *r_out, double *lam_out, oracle_step *rec)
 {
     double lam = 0.0;
     int r = -1;
@@ -197,6 +202,11 @@ static int sbkp(int n, int k, double alpha, double *a, int d, double *b, double 
         if (fabs(AT(a, n, i, k)) > lam) { lam = fabs(AT(a, n, i, k)); r = i; }
     *lam_out = lam;
     *r_out = r;
+    rec->lam_next = -1.0;
+    for (int i = k + 1; i < n; ++i)
+        if (i != r && fabs(AT(a, n, i, k)) > rec->lam_next) rec->lam_next = fabs(AT(a, n, i, k));
+    rec->akk = fabs(AT(a, n, k, k));
+    rec->arr = r >= 0 ? fabs(AT(a, n, r, r)) : -1.0;
     if (lam == 0.0) { *kase_out = 0; return 1; }
     if (fabs(AT(a, n, k, k)) >= alpha * lam) { *kase_out = 1; return 1; }
     if (fabs(AT(a, n, r, r)) >= alpha * lam) {
@@ -326,12 +336,14 @@ int oracle_rcp(int n, double *a, int d, const double *om, double alpha, int q_mo
             /* pi_k = argmax_{k <= j < n} ||B(:, j)||_2 (squared norms compared; ties to the
              * smallest position), then the interchange k <-> pi_k */
             int pi = k;
-            double best = -1.0;
+            double best = -1.0, second = -1.0;
             for (int j = k; j < n; ++j) {
                 double s2 = 0.0;
                 for (int r = 0; r < d; ++r) s2 += b[(size_t)r + (size_t)j * d] * b[(size_t)r + (size_t)j * d];
-                if (s2 > best) { best = s2; pi = j; }
+                if (s2 > best) { second = best; best = s2; pi = j; }
+                else if (s2 > second) second = s2;
             }
+            st.norm2_next = second;
             interchange(n, k, k, pi, a, d, b, l, perm);
             if (guard_r > 0 && k > 0) {
                 /* Algorithm 2: t^2 against (eps^delta beta)^2 (beta holds ||B^(1)||_{1,2}^2) */
@@ -373,7 +385,7 @@ int oracle_rcp(int n, double *a, int d, const double *om, double alpha, int q_mo
         }
         int kase, r;
         double lam;
-        int s = sbkp(n, k, alpha, a, d, b, l, perm, &kase, &r, &lam);
+        int s = sbkp(n, k, alpha, a, d, b, l, perm, &kase, &r, &lam, &st);
         st.kase = kase; st.r = r; st.lambda = lam; st.s = s;
         if (eliminate(n, k, s, a, l, dd, ds) && info == 0) info = k + 1;
         if (s == 2) ++n2;

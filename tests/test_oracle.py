@@ -430,3 +430,41 @@ def test_l_norms_closed_forms():
     nl, ni = oracle.l_norms(L)
     assert nl == pytest.approx(np.abs(L).sum(0).max())
     assert ni == pytest.approx(np.abs(np.linalg.inv(L)).sum(0).max(), rel=1e-8)
+
+
+# ---------------------------------------------------------------------------------------------
+# The growth factor rho = max|D_ij| / max|A_ij| (experiments section, Eq. "growth")
+# ---------------------------------------------------------------------------------------------
+
+def test_growth_closed_form_one_by_one_pivots():
+    # A = [[1, t], [t, 1]], t = 1.2: lambda = t and |a_kk| = 1 >= alpha t, so a 1x1 pivot,
+    # D = diag(1, 1 - t^2) whichever column the sketch picks; max|A| = t sits off the diagonal
+    t = 1.2
+    a = np.array([[1.0, t], [t, 1.0]])
+    r = oracle.rcp(a, oracle.omega(0, 2, 2), record=False)
+    assert r["n_2x2"] == 0
+    assert oracle.growth_d(r["Dd"], r["Ds"], a) == pytest.approx(1.0 / t, rel=1e-15)
+
+
+def test_growth_closed_form_largest_entry_in_a_2x2_block():
+    # the 5 couples two small diagonal entries: SBKP case (3) takes the whole 2x2 block, so the
+    # largest entry of D is its off-diagonal 5 = max|A| and rho = 1 (without D's sub-diagonal the
+    # ratio would be 0.2 / 5)
+    a = np.array([[0.1, 5.0, 0.0], [5.0, 0.2, 0.0], [0.0, 0.0, 1.0]])
+    for seed in range(4):
+        r = oracle.rcp(a, oracle.omega(seed, 3, 3), record=False)
+        assert r["n_2x2"] == 1
+        assert oracle.growth_d(r["Dd"], r["Ds"], a) == pytest.approx(1.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("n,seed", [(60, 0), (61, 3), (90, 7)])
+def test_growth_equals_the_largest_entry_of_the_reconstructed_d(n, seed):
+    # D rebuilt without Dd/Ds: L^{-1} (P A P^T) L^{-T} from the factor's L and the input alone
+    a = inputs.gaussian_sym(n, seed=seed)
+    r = oracle.rcp(a, oracle.omega(seed, 12, n), record=False)
+    assert r["n_2x2"] > 0
+    p = r["perm"]
+    Li = scipy.linalg.solve_triangular(r["L"], np.eye(n), lower=True, unit_diagonal=True)
+    d_full = Li @ a[np.ix_(p, p)] @ Li.T
+    rho = np.max(np.abs(d_full)) / np.max(np.abs(a))
+    assert oracle.growth_d(r["Dd"], r["Ds"], a) == pytest.approx(rho, rel=1e-10)
