@@ -1,16 +1,17 @@
 // noalloc.cu -- rcp_solve_noalloc: the solution phase without any device allocation.
 //
-// Some callers cannot allocate device memory at the moment they need a solve: code that runs
-// while a stream is being captured into a CUDA graph (cudaMalloc is not allowed there), hard
-// real-time loops that must never block in the allocator, and programs whose device memory is
-// entirely owned by another allocator (a framework's pool).  For them this entry point runs the
-// same forward / block-diagonal / backward kernels as rcp_solve, but takes its scratch (the
-// work vector, the row-block flags, the tickets and a status word) from one statically sized
-// __device__ array instead of a handle's cudaMalloc'ed workspace.
+// Some callers cannot allocate device memory at the moment they need a solve: hard real-time
+// loops that must never block in the allocator, and programs whose device memory is entirely
+// owned by another allocator (a framework's pool, an embedding application with a fixed
+// budget).  For them this entry point runs the same forward / block-diagonal / backward kernels
+// as rcp_solve, but takes its scratch (the work vector, the row-block flags, the tickets and a
+// status word) from one statically sized __device__ array instead of a handle's cudaMalloc'ed
+// workspace.
 //
 // That array lives in every GPU that loads this library until the process exits.  All calls
 // share it: two calls whose kernels overlap on the GPU (different streams, or different host
 // threads on one stream without ordering) race on it and give wrong results.
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/rcp.h"
@@ -18,9 +19,11 @@
 
 namespace {
 
-// 16 MiB of scratch: the solve's work area (the work vector, n * nrhs entries of the factor
-// type, and the inverses of the 64 x 64 diagonal blocks of L), then 2 * ceil(n / 64) + 2
-// flag/ticket words and one status word.
+// 16 MiB of scratch: the solve's work area, then 2 * ceil(n / 64) + 2 flag/ticket words and one
+// status word.  Work area (nb = ceil(n / 64)): FP64 factors, the work vector (8 n nrhs bytes,
+// rounded up to 256) and the inverted 64 x 64 diagonal blocks of L (8 * 4096 nb bytes); FP32
+// factors, two arrays of 64-bit (epoch, value) words (16 n nrhs bytes), an FP32 vector (4 n nrhs
+// bytes, rounded up to 256) and three 64 x 64 FP32 matrices per row block (12 * 4096 nb bytes).
 constexpr size_t kScratchBytes = 16u << 20;
 static __device__ __align__(256) unsigned char g_solve_scratch[kScratchBytes];
 
@@ -61,6 +64,18 @@ size_t scratch_needed(int n, int nrhs, bool f64) {
     return work_bytes(n, nrhs, f64) + (2 * nb + 2 + 1) * sizeof(int);
 }
 
+// A solve whose device status word is set (a bounded wait that ran out, a non-finite diagonal
+// block) has no valid result: its solutions are overwritten with NaN, so that the failure is
+// visible in X (this entry point has no handle to report it through).
+__global__ void poison_on_status_kernel(int n, int nrhs, double *X, int ldx, const int *status) {
+    if (*(volatile const int *)status == 0) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    const long long total = (long long)n * nrhs;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        X[(size_t)(e % n) + (size_t)(e / n) * ldx] = nan;
+}
+
 }  // namespace
 
 extern "C" rcp_status rcp_solve_noalloc(int n, int nrhs, const void *LA, int lda, const double *Dd,
@@ -84,6 +99,13 @@ extern "C" rcp_status rcp_solve_noalloc(int n, int nrhs, const void *LA, int lda
         cudaGetLastError();
         return RCP_ECUDA;
     }
+    // FP32 factors: a reader takes a 64-bit word of the two word arrays as published once its
+    // high half equals the call's epoch.  Whatever an earlier call left there (words of another
+    // size, doubles of an FP64 solve) could match by chance, so the word arrays start at zero.
+    if (!f64 && cudaMemsetAsync(base, 0, 2 * (size_t)n * nrhs * sizeof(unsigned long long), s) != cudaSuccess) {
+        cudaGetLastError();
+        return RCP_ECUDA;
+    }
     cudaError_t e;
     if (prec == RCP_FP64)
         e = rcpk::launch_solve<double>(n, nrhs, (const double *)LA, lda, Dd, Ds, perm, X, ldx,
@@ -95,5 +117,10 @@ extern "C" rcp_status rcp_solve_noalloc(int n, int nrhs, const void *LA, int lda
         cudaGetLastError();
         return RCP_ECUDA;
     }
+    const long long total = (long long)n * nrhs;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 1024);
+    poison_on_status_kernel<<<blocks, 256, 0, s>>>(n, nrhs, X, ldx, status);
+    rcpk::count_launches(1);
+    if (cudaGetLastError() != cudaSuccess) return RCP_ECUDA;
     return RCP_OK;
 }
