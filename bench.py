@@ -285,6 +285,20 @@ def run_ours(a, rank, world, local_rank):
         torch.cuda.synchronize()
         fp64 = {"ms_per_step": e0.elapsed_time(e1) / a.fp64_steps, "berr": s64.berr,
                 "growth_D": s64.growth_D, "refine_iters": s64.refine_iters}
+        # its phases (one profiled step), the trailing update's rate and cuBLAS DGEMM beside it
+        rcp.rcp_profile(h, True)
+        rcp.rcp_sysv(h, A64, Bv, X64, o64, tol=a.tol, max_iter=a.max_iter)
+        ph64 = rcp.rcp_profile_read(h)
+        rcp.rcp_profile(h, False)
+        tr_ms = ph64["trailing"][0]
+        tr_fl = trailing_flops(n, 64)
+        dgemm = dgemm_tflops(dev, stream)
+        fp64.update({"phases_ms": {k: round(v[0], 3) for k, v in ph64.items() if k != "h2d"},
+                     "trailing_flops": tr_fl, "trailing_tflops": tr_fl / (tr_ms * 1e-3) / 1e12 if tr_ms > 0 else None,
+                     "dgemm_tflops": dgemm,
+                     "dgemm_note": "torch.matmul FP64 8192^3 (cuBLAS), best of 3, same process"})
+        if fp64["trailing_tflops"] and dgemm:
+            fp64["trailing_frac_of_dgemm"] = fp64["trailing_tflops"] / dgemm
 
     # end to end through the same call with host (pinned) buffers
     e2e = None
@@ -300,9 +314,24 @@ def run_ours(a, rank, world, local_rank):
             ce, se = rcp.rcp_sysv(h, Ah, Bh, Xh, opts, tol=a.tol, max_iter=a.max_iter, host_buffers=True)
         torch.cuda.synchronize()
         el = max_over_ranks((time.perf_counter() - t0) / a.e2e_steps, dist, dev)
+        h2d_bytes = host_copy_bytes(n) + n * nrhs * 8
         e2e = {"value": job_throughput(world, flops(n, nrhs), el) / 1e12, "unit": UNIT,
-               "h2d_bytes_per_step": host_copy_bytes(n) + n * nrhs * 8, "d2h_bytes_per_step": n * nrhs * 8,
+               "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": n * nrhs * 8,
                "ms_per_step": el * 1e3, "berr": se.berr}
+        # where the time goes: one profiled host-buffer step (the copies run on a second stream,
+        # overlapped with the FP32 rounding and the sketch), and the link's rate for a plain copy
+        rcp.rcp_profile(h, True)
+        tp0 = time.perf_counter()
+        rcp.rcp_sysv(h, Ah, Bh, Xh, opts, tol=a.tol, max_iter=a.max_iter, host_buffers=True)
+        torch.cuda.synchronize()
+        tp1 = time.perf_counter()
+        phe = rcp.rcp_profile_read(h)
+        rcp.rcp_profile(h, False)
+        h2d_ms = phe["h2d"][0]
+        e2e.update({"h2d_ms": round(h2d_ms, 3), "h2d_gbs": h2d_bytes / (h2d_ms * 1e-3) / 1e9 if h2d_ms > 0 else None,
+                    "profiled_step_ms": round(1e3 * (tp1 - tp0), 3),
+                    "phases_ms": {k: round(v[0], 3) for k, v in phe.items()},
+                    "link_gbs": pinned_copy_gbs(Ah, dev, stream)})
         del Ah, Bh, Xh
 
     batched = run_batched(a, dev, stream, rank, world, dist) if a.batch > 0 else None
@@ -320,7 +349,7 @@ def run_ours(a, rank, world, local_rank):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
     # dominant kernel by time in the profiled step
-    dom = max(phases.items(), key=lambda kv: kv[1][0])
+    dom = max(((k, v) for k, v in phases.items() if k != "h2d"), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_launches) = dom
     roofline = roofline_for(dom_name, dom_ms, dom_launches, a, hbm_peak, peaks, peak_src)
     pan_ms, pan_launch = phases["panel"]
@@ -335,7 +364,7 @@ def run_ours(a, rank, world, local_rank):
         "n_2x2": st.n_2x2, "ok": bool(ok),
         "fp64": fp64,
         "speedup_vs_fp64": (fp64["ms_per_step"] / ms_step) if fp64 else None,
-        "phases_ms": {k: round(v[0], 3) for k, v in phases.items()},
+        "phases_ms": {k: round(v[0], 3) for k, v in phases.items() if k != "h2d"},
         "panel_us_per_pivot_step": 1e3 * pan_ms / max(1, n - st.n_2x2),
         "panel_latency": {"exchange_floor_us": round(exchange_us, 3),
                           "us_per_pivot_step": round(1e3 * pan_ms / max(1, n - st.n_2x2), 3),
@@ -429,6 +458,56 @@ def run_batched(a, dev, stream, rank, world, dist):
             "gpu_launches_per_replay": 2, "steps": a.batch_steps, "tuned_b": tuned_b, "roofline": roof}
 
 
+def trailing_flops(n, b):
+    """Flops of the deferred trailing updates A22 -= W L21^T on the lower triangle (diagonal
+    included) at the nominal panel boundaries k0 = 0, b, 2b, ...: 2 N (N + 1) / 2 K per panel,
+    N = n - kend the trailing order and K = kend - k0 the panel width (about n^3 / 3)."""
+    fl = 0.0
+    for k0 in range(0, n, b):
+        kend = min(n, k0 + b)
+        N = n - kend
+        fl += N * (N + 1) * (kend - k0)
+    return fl
+
+
+def dgemm_tflops(dev, stream, m=8192, reps=3):
+    """cuBLAS FP64 GEMM rate on this GPU (torch.matmul, m^3, best of reps): the yardstick of the
+    FP64 trailing update."""
+    import torch
+    x = torch.randn(m, m, dtype=torch.float64, device=dev)
+    y = torch.randn(m, m, dtype=torch.float64, device=dev)
+    z = x @ y
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.matmul(x, y, out=z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    del x, y, z
+    return 2.0 * m ** 3 / (best * 1e-3) / 1e12
+
+
+def pinned_copy_gbs(host, dev, stream, reps=3):
+    """Host-to-device rate of one contiguous copy of a pinned host tensor (best of reps)."""
+    import torch
+    d = torch.empty_like(host, device=dev)
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d.copy_(host, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    nbytes = host.numel() * host.element_size()
+    del d
+    return nbytes / (best * 1e-3) / 1e9
+
+
 def host_copy_bytes(n, cols=256):
     """Bytes of A the library copies to the device with host buffers: the lower triangle, as
     rectangles of `cols` columns from each block's diagonal down."""
@@ -462,14 +541,9 @@ def roofline_for(name, ms, launches, a, hbm_peak, peaks, peak_src):
         m_avg = n / 2.0
         byts = (2 * d * m_avg + b * m_avg * 1.5 + 2 * b * m_avg) * 4
         ach = byts / (per_launch_ms * 1e-3) / 1e9
-        # DRAM bytes of one launch from ncu (profiles/panel_kernel_f32_n16384.md: the third panel at
-        # n = 16384, b = 256, d = 80 moved 257 MB over 15872 remaining columns), scaled to the
-        # average launch (n / 2 remaining columns); only for that configuration
-        traffic = None
-        if (n, b, d) == (16384, 256, 80) and a.prec in ("f16x3", "tf32x3"):
-            traffic = 257.0e6 * (n / 2.0) / 15872.0
+        # DRAM traffic needs a profiler capture, which this timed run does not take: null here
         return {"kernel": "panel_kernel<float>", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
-                "unit": "GB/s", "frac": ach / hbm_peak, "traffic": traffic, "peak_note": peak_src,
+                "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None, "peak_note": peak_src,
                 "note": "latency-bound: per pivot step one grid barrier (two on the non-speculative path) "
                         "and dependent L2/HBM round trips for the keys and the next pivot's column"}
     return {"kernel": name, "bound": "hbm", "achieved": None, "peak": hbm_peak, "unit": "GB/s", "frac": None,

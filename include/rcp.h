@@ -20,7 +20,7 @@
  *     in which case it synchronizes that stream before returning.  The host-driven calls
  *     synchronize always (and cannot be captured in a graph): rcp_refine_gmres, rcp_factor
  *     and rcp_sysv with the Algorithm 2 safeguard (opts->guard_r > 0, once per panel),
- *     rcp_l_norms and rcp_exchange_latency.
+ *     rcp_l_norms, rcp_exchange_latency and rcp_wait_expiry.
  *
  * Errors: a negative rcp_status is returned before anything is launched when an argument
  * is invalid.  Numerical faults found on the device (non-finite values, a bounded wait
@@ -232,8 +232,10 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
  * launches with two CUDA events on its stream; rcp_profile_read waits for them and returns,
  * per phase, the summed milliseconds and the number of bracketed stretches since the last
  * read.  Phases: 0 sketch (Omega + B = Omega A), 1 panel, 2 interchange, 3 trailing update,
- * 4 solve (forward, D, backward), 5 residual (refinement).  Profiling adds event records
- * between launches, so time calls with it off.
+ * 4 solve (forward, D, backward), 5 residual (refinement), 6 the host-to-device copies of
+ * rcp_sysv with host buffers (on the stream that issues them; for FP32 factors a second stream,
+ * where they overlap phase 0).  Profiling adds event records between launches, so time calls
+ * with it off.
  */
 rcp_status rcp_profile(rcp_handle *h, int enable);
 
@@ -252,6 +254,16 @@ rcp_status rcp_panel_trace(rcp_handle *h, unsigned long long *out, int cap);
  * Uses the handle's barrier and key buffers (not while a factorization runs on the handle);
  * synchronizes the stream. */
 rcp_status rcp_exchange_latency(rcp_handle *h, int grid, int rounds, rcp_stream_t stream, double *us);
+
+/* Failure path of the bounded device waits: one cooperative launch of `grid` CTAs of the panel's
+ * 512 threads (0 = one per SM) in which every CTA waits at a grid barrier for one arrival more
+ * than the launch has CTAs, so that no wait can complete.  Each CTA gives up after limit_us
+ * microseconds (1 .. 2000000; the library's own waits give up after 2 s), records a timeout in
+ * the handle's status word and returns: no kernel hangs or traps.  *waited_us = how long the
+ * first CTA waited.  Synchronizes the stream and returns what rcp_sync then reports, i.e.
+ * RCP_ETIMEOUT; the status word stays set until a call that starts a factorization clears it,
+ * and the handle remains usable. */
+rcp_status rcp_wait_expiry(rcp_handle *h, int grid, int limit_us, rcp_stream_t stream, double *waited_us);
 
 /* Stability diagnostics of a factor (the paper's experiments report them per matrix type):
  * *norm1_L = ||L||_1 exactly (unit lower L from rcp_factor: LA's strictly lower triangle, unit
@@ -346,22 +358,25 @@ rcp_status rcp_sketch(int n, int d, const void *A, int lda, rcp_prec prec, uint6
 
 /*
  * rcp_solve_noalloc -- the same solve as rcp_solve for callers that cannot allocate device
- * memory when they solve: code running while a stream is captured into a CUDA graph (where
- * cudaMalloc is not allowed), real-time loops that must never block in the allocator, or
- * programs whose device memory belongs to another allocator.  It takes no handle and calls no
- * cudaMalloc, cudaFree or allocating library routine; its scratch is one 16 MiB array in
- * device memory that every GPU loading this library keeps until the process exits.
+ * memory when they solve: hard real-time loops that must never block in the allocator, and
+ * programs whose device memory belongs to another allocator (a framework's pool, an embedding
+ * application with a fixed memory budget).  It takes no handle and calls no cudaMalloc,
+ * cudaFree or allocating library routine; its scratch is one 16 MiB array in device memory
+ * that every GPU loading this library keeps until the process exits.
  * (The paper has no counterpart to this entry point; it is a deployment convenience.)
  *   Arguments, layout and results are those of rcp_solve.
- *   Limit: w * (n * nrhs + 64 * 64 * ceil(n / 64)) + 4 * (2 * ceil(n / 64) + 3) bytes (plus
- *          alignment padding), w = 8 for RCP_FP64 and 4 otherwise, must fit in 16 MiB (for
- *          example n = 16384 with nrhs <= 64 for an FP64 factor); larger problems return
- *          RCP_EUNSUPPORTED before anything is launched.
+ *   Limit, with nb = ceil(n / 64), sizes in bytes, each term rounded up to 256:
+ *     FP64 factor:  8 n nrhs + 32768 nb + 4 (2 nb + 3)             <= 16 MiB
+ *     FP32 factors: 16 n nrhs + 4 n nrhs + 49152 nb + 4 (2 nb + 3) <= 16 MiB
+ *   e.g. n = 16384: nrhs <= 63 for an FP64 factor, nrhs <= 12 for an FP32 one.  Larger problems
+ *   return RCP_EUNSUPPORTED before anything is launched.
  *   The first call on each device looks up the array's device address (cudaGetSymbolAddress,
  *   not stream-ordered): make that first call before any stream capture.
- *   All calls share the array: calls whose kernels can overlap on the GPU (different streams,
- *   or unsynchronized host threads) race and give wrong results.  Each call clears the parts
- *   that must start at zero.  The call is asynchronous and reports only argument errors.
+ *   All calls share the array and it keeps the last call's contents: each call clears, on its
+ *   stream, the parts that must start at zero.  Calls whose kernels can overlap on the GPU
+ *   (different streams, or unsynchronized host threads) race and give wrong results.
+ *   The call is asynchronous and returns only argument and launch errors.  A failure found on
+ *   the device (a bounded wait that ran out, a non-finite diagonal block of L) fills X with NaN.
  */
 rcp_status rcp_solve_noalloc(int n, int nrhs, const void *LA, int lda, const double *Dd, const double *Ds,
                              const int *perm, rcp_prec prec, double *X, int ldx, rcp_stream_t stream);

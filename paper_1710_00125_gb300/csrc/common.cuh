@@ -72,9 +72,10 @@ template <typename T> __device__ __forceinline__ void stcg(T *p, T v) { __stcg(p
 
 // Grid-wide barrier for a cooperative launch.  `bar` counts arrivals; the barrier with
 // sequence number `seq` (1, 2, ...) completes when bar >= base + seq * nblocks.  The wait is
-// bounded by kWaitLimitNs; on expiry ST_TIMEOUT is set and false is returned to every
-// thread of the CTA.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *status) {
+// bounded by limit_ns (kWaitLimitNs unless a caller asks for less); on expiry ST_TIMEOUT is
+// set and false is returned to every thread of the CTA.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *status,
+                                             unsigned long long limit_ns = kWaitLimitNs) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -85,7 +86,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int
             unsigned long long t0 = global_ns();
             unsigned spins = 0;
             while (ld_acquire_u32(bar) < target) {
-                if ((++spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+                if ((++spins & 255u) == 0 && global_ns() - t0 > limit_ns) {
                     ok = 0;
                     atomicOr(status, ST_TIMEOUT);
                     break;

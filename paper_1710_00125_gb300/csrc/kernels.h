@@ -121,6 +121,10 @@ int panel_max_grid(int d, int bw, int chunk_cap, int spec);
 int exchange_probe_grid();
 cudaError_t launch_exchange_probe(unsigned *bar, unsigned long long *keys, int *status, int grid, int rounds,
                                   cudaStream_t s);
+// Failure path of the bounded waits: a grid barrier that cannot complete on `grid` cooperative
+// CTAs, each giving up after limit_ns (ST_TIMEOUT); CTA 0 writes its wait's duration
+cudaError_t launch_wait_expiry(unsigned *bar, int *status, int grid, unsigned long long limit_ns,
+                               unsigned long long *elapsed_ns, cudaStream_t s);
 
 // Solves and refinement.  `work` holds solve_work_bytes<T>(n, nrhs) bytes.
 template <typename T>

@@ -1110,6 +1110,31 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) exchange_probe_kernel(unsign
     if (threadIdx.x == 0 && acc != (unsigned long long)rounds * (G - 1)) atomicOr(status, ST_INTERNAL);
 }
 
+// Failure path of the bounded waits: every CTA arrives once at a grid barrier whose target is
+// one arrival more than the launch has CTAs, so no wait can complete; each CTA gives up after
+// limit_ns, sets ST_TIMEOUT and returns.  CTA 0 records how long its wait lasted.
+__global__ void __launch_bounds__(PANEL_THREADS, 1) wait_expiry_kernel(unsigned *bar, int *status,
+                                                                        unsigned long long limit_ns,
+                                                                        unsigned long long *elapsed_ns) {
+    __shared__ unsigned s_base;
+    const unsigned G = gridDim.x;
+    if (threadIdx.x == 0) s_base = barrier_base(bar, G);
+    __syncthreads();
+    const unsigned long long t0 = global_ns();
+    const bool ok = grid_barrier(bar, s_base + G + 1u, status, limit_ns);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *elapsed_ns = global_ns() - t0;
+        if (ok) atomicOr(status, ST_INTERNAL);   // a barrier nobody can complete did complete
+    }
+}
+
+cudaError_t launch_wait_expiry(unsigned *bar, int *status, int grid, unsigned long long limit_ns,
+                               unsigned long long *elapsed_ns, cudaStream_t s) {
+    void *args[] = {&bar, &status, &limit_ns, &elapsed_ns};
+    count_launches(1);
+    return cudaLaunchCooperativeKernel((const void *)wait_expiry_kernel, dim3(grid), dim3(PANEL_THREADS), args, 0, s);
+}
+
 int exchange_probe_grid() {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);

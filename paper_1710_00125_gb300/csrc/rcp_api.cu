@@ -32,7 +32,9 @@ struct Buf {
 
 }  // namespace
 
-enum Phase { PH_SKETCH = 0, PH_PANEL, PH_INTERCHANGE, PH_TRAILING, PH_SOLVE, PH_RESIDUAL, PH_OTHER, PH_COUNT };
+// PH_H2D: rcp_sysv's host-to-device copies with host buffers, bracketed on the stream that
+// issues them (the copy stream for FP32 factors, where they overlap the sketch)
+enum Phase { PH_SKETCH = 0, PH_PANEL, PH_INTERCHANGE, PH_TRAILING, PH_SOLVE, PH_RESIDUAL, PH_H2D, PH_COUNT };
 
 struct EventPair {
     int phase;
@@ -895,6 +897,11 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
             CU_TRY(cudaStreamWaitEvent(h->copy_stream, h->copy_events[nblk], 0));
         }
         cudaStream_t cs = overlap ? h->copy_stream : s;
+        cudaEvent_t h2d_a = nullptr;
+        if (h->profiling) {
+            h2d_a = take_event(h);
+            CU_TRY(cudaEventRecord(h2d_a, cs));
+        }
         // only the lower triangle is read: copy it as rectangles of kHostCopyCols columns from
         // each block's diagonal down (half the bytes of the full matrix)
         for (int b = 0; b < nblk; ++b) {
@@ -906,6 +913,12 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
         }
         CU_TRY(cudaMemcpy2DAsync(h->Bh.p, (size_t)n * sizeof(double), Bv, (size_t)ldb * sizeof(double),
                                  (size_t)n * sizeof(double), nrhs, cudaMemcpyHostToDevice, cs));
+        if (h2d_a) {
+            cudaEvent_t h2d_b = take_event(h);
+            CU_TRY(cudaEventRecord(h2d_b, cs));
+            h->events.push_back({PH_H2D, h2d_a, h2d_b});
+            h->launches[PH_H2D] += 1;
+        }
         if (overlap) {
             const float *om = (const float *)r.omega;
             if (!om) {
@@ -1226,6 +1239,30 @@ rcp_status rcp_exchange_latency(rcp_handle *h, int grid, int rounds, rcp_stream_
     if (bits) return status_from_bits(bits);
     *us = 1e3 * (double)ms / rounds;
     return RCP_OK;
+}
+
+rcp_status rcp_wait_expiry(rcp_handle *h, int grid, int limit_us, rcp_stream_t stream, double *waited_us) {
+    if (!h || !waited_us || grid < 0 || limit_us < 1 || limit_us > 2000000) return RCP_EINVAL;
+    *waited_us = 0.0;
+    const int maxg = exchange_probe_grid();
+    if (grid == 0) grid = sm_count();
+    if (maxg <= 0 || grid > maxg) return RCP_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    RCP_TRY(ensure_small(h));
+    unsigned *bar = (unsigned *)h->bar.p;
+    int *status = (int *)h->status.p;
+    // the elapsed time goes to the refinement scalars' first word (not in use between calls)
+    unsigned long long *el = (unsigned long long *)&((RefineScalars *)h->scal.p)->mx[0];
+    CU_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    CU_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
+    CU_TRY(cudaMemsetAsync(el, 0, sizeof *el, s));
+    CU_TRY(launch_wait_expiry(bar, status, grid, (unsigned long long)limit_us * 1000ull, el, s));
+    unsigned long long ns = 0;
+    CU_TRY(cudaMemcpyAsync(&ns, el, sizeof ns, cudaMemcpyDeviceToHost, s));
+    CU_TRY(cudaStreamSynchronize(s));
+    CU_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
+    *waited_us = 1e-3 * (double)ns;
+    return rcp_sync(h, stream);
 }
 
 rcp_status rcp_omega(int d, int n, uint64_t seed, double *omega, rcp_stream_t stream) {

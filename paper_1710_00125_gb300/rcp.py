@@ -78,6 +78,8 @@ def lib():
         L.rcp_solve.argtypes = [P, I, I, P, I, P, P, P, I, P, I, P]
         L.rcp_refine.argtypes = [P, I, I, P, I, P, I, P, P, P, I, P, I, P, I, D, I, P, ctypes.POINTER(Stats)]
         L.rcp_exchange_latency.argtypes = [P, I, I, P, ctypes.POINTER(D)]
+        L.rcp_wait_expiry.argtypes = [P, I, I, P, ctypes.POINTER(D)]
+        L.rcp_wait_expiry.restype = ctypes.c_int
         L.rcp_l_norms.argtypes = [P, I, P, I, I, P, ctypes.POINTER(D), ctypes.POINTER(D)]
         L.rcp_refine_gmres.argtypes = [P, I, I, P, I, P, I, P, P, P, I, P, I, P, I, D, I, I, I, P,
                                        ctypes.POINTER(Stats)]
@@ -193,8 +195,9 @@ def rcp_solve(h: Handle, LA: torch.Tensor, Dd, Ds, perm, prec, X: torch.Tensor, 
 
 
 def rcp_solve_noalloc(LA: torch.Tensor, Dd, Ds, perm, prec, X: torch.Tensor, stream=None) -> None:
-    """rcp_solve without any device allocation (for callers that cannot allocate, e.g. inside
-    stream capture): scratch comes from a fixed 16 MiB device array shared by all calls."""
+    """rcp_solve without any device allocation, for callers that cannot allocate when they
+    solve (real-time loops, memory owned by another allocator): scratch comes from a fixed
+    16 MiB device array shared by all calls."""
     n = LA.shape[0]
     nrhs, ldx = _rhs_view(X, n)
     if isinstance(prec, str):
@@ -251,7 +254,7 @@ def rcp_sysv(h: Handle, A64, Bv, X, opts: Opts | None = None, tol=1e-12, max_ite
     return code, st
 
 
-PHASES = ("sketch", "panel", "interchange", "trailing", "solve", "residual")
+PHASES = ("sketch", "panel", "interchange", "trailing", "solve", "residual", "h2d")
 
 
 def rcp_profile(h: Handle, enable=True) -> None:
@@ -276,6 +279,14 @@ def rcp_exchange_latency(h: Handle, grid: int = 0, rounds: int = 20000, stream=N
     _check(lib().rcp_exchange_latency(h.h, int(grid), int(rounds), _stream(stream), ctypes.byref(us)),
            "rcp_exchange_latency")
     return us.value
+
+
+def rcp_wait_expiry(h: Handle, limit_us: int, grid: int = 0, stream=None):
+    """Run a grid barrier that cannot complete, every wait bounded by limit_us: returns the
+    status code (RCP_ETIMEOUT = -5 expected) and how long the first CTA waited (microseconds)."""
+    us = ctypes.c_double()
+    code = lib().rcp_wait_expiry(h.h, int(grid), int(limit_us), _stream(stream), ctypes.byref(us))
+    return code, us.value
 
 
 def rcp_panel_trace(h: Handle, n: int):

@@ -43,9 +43,8 @@ def test_panel_roofline_record():
     m = 16384 / 2.0
     byts = (2 * 80 * m + 256 * m * 1.5 + 2 * 256 * m) * 4
     assert r["achieved"] == pytest.approx(byts / (76.0 / 64 * 1e-3) / 1e9)
-    assert r["traffic"] == pytest.approx(257.0e6 * m / 15872.0)
-    # the ncu traffic belongs to that configuration only
-    assert bench.roofline_for("panel", 76.0, 64, _args(b=128), 6685.5, {}, "")["traffic"] is None
+    # DRAM traffic needs a profiler capture; the timed run reports none
+    assert r["traffic"] is None
 
 
 def test_trailing_roofline_record():
@@ -55,3 +54,20 @@ def test_trailing_roofline_record():
     assert r["achieved"] == pytest.approx(16384 ** 3 / 3 / 64 / (10.0 / 64 * 1e-3) / 1e12)
     assert bench.roofline_for("trailing", 10.0, 64, _args(prec="tf32x3"), 6685.5, peaks, "")["peak"] == 972.0
     assert bench.roofline_for("trailing", 10.0, 64, _args(prec="fp32"), 6685.5, peaks, "")["bound"] == "alu"
+
+
+@pytest.mark.parametrize("n,b", [(1, 64), (7, 3), (64, 64), (300, 64), (513, 32)])
+def test_trailing_flops_count_the_lower_triangle_updates(n, b):
+    # brute force: for every panel, every lower entry (i >= j) of the trailing block gets one
+    # multiply and one add per panel column
+    fl = 0
+    for k0 in range(0, n, b):
+        kend = min(n, k0 + b)
+        for j in range(kend, n):
+            fl += 2 * (n - j) * (kend - k0)
+    assert bench.trailing_flops(n, b) == fl
+
+
+def test_trailing_flops_approach_n_cubed_over_three():
+    n = 16384
+    assert bench.trailing_flops(n, 64) == pytest.approx(n ** 3 / 3, rel=0.01)

@@ -596,6 +596,25 @@ def test_exchange_latency_probe(rcp, handle):
     assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() / np.abs(a).max() < 2e-5 * max(1.0, st.growth_D)
 
 
+@pytest.mark.parametrize("grid,limit_us", [(0, 2000), (8, 20000)])
+def test_bounded_wait_runs_out_and_the_handle_recovers(rcp, grid, limit_us):
+    # a grid barrier that no launch can complete: every CTA gives up after the limit, records the
+    # timeout and returns (no hang, no trap); the handle then reports RCP_ETIMEOUT until the next
+    # factorization clears the status word, and that factorization matches the oracle exactly
+    h = rcp.rcp_create()
+    code, waited = rcp.rcp_wait_expiry(h, limit_us, grid=grid)
+    assert code == -5, rcp.STATUS.get(code, code)
+    assert limit_us <= waited < limit_us + 200000
+    assert rcp.lib().rcp_sync(h.h, None) == -5
+    n, b, d, seed = 200, 32, 40, 4
+    a = inputs.gaussian_sym(n, seed=seed)
+    code, st, A, Dd, Ds, perm = _factor(rcp, h, a, b, d, seed)
+    assert code == 0 and st.device_flags == 0
+    ref = oracle.rcp(a, oracle.omega(seed, d, n), record=False)
+    assert np.array_equal(perm.cpu().numpy(), ref["perm"])
+    assert rcp.lib().rcp_sync(h.h, None) == 0
+
+
 def _mixed_system(rcp, handle, n, kexp, prec, seed=7, nrhs=1):
     a = inputs.spectrum(n, seed=seed, kexp=kexp, nrefl=16)
     x = inputs.x_true(n, nrhs, seed=seed)
