@@ -56,10 +56,12 @@ typedef enum {
     RCP_FP64 = 0,           /* everything in FP64 (CUDA cores)                             */
     RCP_FP32 = 1,           /* FP32 factor; FP32 trailing update on CUDA cores                  */
     RCP_TF32 = 2,           /* reserved: currently runs as RCP_FP32                              */
-    RCP_TF32X3 = 3,         /* FP32 factor; trailing update on tcgen05 tensor cores with split  */
-                            /* TF32 operands (hi*hi + hi*lo + lo*hi, FP32 accumulation)        */
-    RCP_F16X3 = 4           /* as RCP_TF32X3 with the split in FP16 (the same 11 significant    */
-                            /* bits per part): W and L21 are scaled by powers of two so that    */
+    RCP_TF32X3 = 3,         /* FP32 factor; sketch B = Omega A and trailing update on tcgen05   */
+                            /* tensor cores with split TF32 operands (hi*hi + hi*lo + lo*hi,    */
+                            /* FP32 accumulation)                                               */
+    RCP_F16X3 = 4           /* as RCP_TF32X3, the trailing update's split in FP16 (the same 11  */
+                            /* significant bits per part; the sketch keeps split TF32, which    */
+                            /* needs no scaling): W and L21 are scaled by powers of two so that */
                             /* their panel maxima sit below 2^15, the three products run at the */
                             /* FP16 tensor rate and move half the operand bytes of TF32         */
 } rcp_prec;
@@ -351,6 +353,9 @@ rcp_status rcp_refine_batched(rcp_handle *h, int batch, int nmax, int nrhs, cons
  *             (u1 = (w0 >> 11 + 1) 2^-53, u2 = (w1 >> 11) 2^-53).  Section 3, "draw Omega".
  * rcp_sketch: B = Omega A (d x n, ld d, device, precision prec) for the lower-stored
  *             symmetric A; Omega drawn from seed unless omega != NULL.  Section 3, B = Omega A.
+ *             RCP_FP64 and RCP_FP32 run on the CUDA cores; RCP_TF32X3 and RCP_F16X3 on the
+ *             tcgen05 tensor cores with split TF32 operands (hi*hi + hi*lo + lo*hi, FP32
+ *             accumulation), as rcp_factor forms the sketch in those precisions.
  */
 rcp_status rcp_omega(int d, int n, uint64_t seed, double *omega, rcp_stream_t stream);
 rcp_status rcp_sketch(int n, int d, const void *A, int lda, rcp_prec prec, uint64_t seed,

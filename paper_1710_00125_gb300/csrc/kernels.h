@@ -25,6 +25,20 @@ template <typename TA, typename TC>
 cudaError_t launch_sketch(int n, int d, const TA *A, int lda, const TC *om, TC *B, TC *part, size_t part_elems,
                           cudaStream_t s);
 size_t sketch_scratch_floats(int n, int d);
+// B(:, c0:c1) = sum over S slices of part (slice order), count = d (c1 - c0)
+cudaError_t launch_sketch_reduce(size_t count, int S, const float *part, float *B, cudaStream_t s);
+
+// Tensor-core sketch (split TF32 on tcgen05) for the FP32 factors of RCP_TF32X3 / RCP_F16X3:
+// Omega is first split into swizzled tiles (sketch_tc_omega_floats(n, d) floats), then columns
+// c0 .. c1-1 of B = Omega A are formed (A must hold its final values in columns < c1); `part`
+// holds sketch_tc_scratch_floats(n, d) floats of slice partial sums; a bounded wait that runs
+// out sets ST_TIMEOUT in *status.
+int sketch_tc_slices(int n);
+size_t sketch_tc_omega_floats(int n, int d);
+size_t sketch_tc_scratch_floats(int n, int d);
+cudaError_t launch_omega_split(int n, int d, const float *om, float *omt, cudaStream_t s);
+cudaError_t launch_sketch_tc(int n, int d, const float *A, int lda, const float *omt, float *B, float *part,
+                             size_t part_floats, int c0, int c1, int *status, cudaStream_t s);
 
 // Per-factorization workspace pointers used by the panel / interchange / trailing kernels.
 template <typename T>

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/rcp.h"
@@ -55,6 +56,7 @@ struct rcp_handle {
     Buf psnap, pinv, pbounds;                      // deferred L-row interchanges
     Buf keys;                                      // packed argmax keys of the FP32 panel
     Buf skp;                                       // partial sums of the FP32 sketch
+    Buf omt;                                       // Omega split into TF32 tiles (tensor-core sketch)
     Buf tcops;                                     // tensor-core operand tiles
     int trace_n = 0;
     int y_words = -1;                              // solve work last used by: 1 FP32 (epoch words), 0 FP64
@@ -143,6 +145,8 @@ rcp_status ensure_small(rcp_handle *h) {
     return RCP_OK;
 }
 
+bool tc_prec(rcp_prec p) { return p == RCP_TF32X3 || p == RCP_F16X3; }
+
 struct Resolved {
     int b, d, grid, chunk_cap, bw, maxmoved, spec, qb;
     int guard_r;           // Algorithm 2 (0 = off)
@@ -227,7 +231,9 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->s1v, 4 * (size_t)r.grid * sizeof(double)));
     RCP_TRY(grow(h->s2v, 4 * (size_t)r.grid * sizeof(double)));
     RCP_TRY(grow(h->keys, PANEL_KEY_WORDS * sizeof(unsigned long long)));
-    if (sizeof(T) == sizeof(float)) RCP_TRY(grow(h->skp, sketch_scratch_floats(n, r.d) * sizeof(float)));
+    if (sizeof(T) == sizeof(float))
+        RCP_TRY(grow(h->skp, std::max(sketch_scratch_floats(n, r.d), sketch_tc_scratch_floats(n, r.d)) * sizeof(float)));
+    if (tc_prec(r.prec)) RCP_TRY(grow(h->omt, sketch_tc_omega_floats(n, r.d) * sizeof(float)));
     if (r.prec == RCP_TF32X3 || r.prec == RCP_F16X3) RCP_TRY(grow(h->tcops, tc_ops_floats(n, r.b) * sizeof(float)));
     RCP_TRY(grow(h->s1i, 2 * (size_t)r.grid * sizeof(int)));
     RCP_TRY(grow(h->s2i, 2 * (size_t)r.grid * sizeof(int)));
@@ -332,6 +338,21 @@ double bits_to_double(unsigned long long b) {
     return v;
 }
 
+// B = Omega A (d x n) of the order-n matrix A in the factor's arithmetic: FP64 or FP32 on the
+// CUDA cores, the tensor-core precisions by the split-TF32 tcgen05 sketch
+template <typename T>
+cudaError_t sketch_for(rcp_handle *h, const Resolved &r, int n, const T *A, int lda, const T *om, T *B, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (tc_prec(r.prec)) {
+            cudaError_t e = launch_omega_split(n, r.d, om, (float *)h->omt.p, s);
+            if (e != cudaSuccess) return e;
+            return launch_sketch_tc(n, r.d, A, lda, (const float *)h->omt.p, B, (float *)h->skp.p,
+                                    h->skp.bytes / sizeof(float), 0, n, (int *)h->status.p, s);
+        }
+    }
+    return launch_sketch<T, T>(n, r.d, A, lda, om, B, (T *)h->skp.p, h->skp.bytes / sizeof(T), s);
+}
+
 template <typename T>
 rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *Ds, int *perm, const Resolved &r,
                        cudaStream_t s, rcp_stats *stats, bool presketched = false) {
@@ -348,7 +369,7 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
             CU_TRY(launch_omega<T>(r.d, n, r.seed, (T *)h->om.p, s));
             om = (const T *)h->om.p;
         }
-        CU_TRY((launch_sketch<T, T>(n, r.d, A, lda, om, w.B, (T *)h->skp.p, h->skp.bytes / sizeof(T), s)));
+        CU_TRY(sketch_for<T>(h, r, n, A, lda, om, w.B, s));
     }
     const int nblk = (n + r.b - 1) / r.b;
     int npanels = nblk;
@@ -388,8 +409,8 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
                 const int k = st.guard_k, m = n - k, q = st.nresk + 1;
                 PhaseScope ps(h, s, PH_SKETCH);
                 CU_TRY(launch_omega<T>(r.d, m, r.seed, (T *)h->om.p, s, (uint64_t)q));
-                CU_TRY((launch_sketch<T, T>(m, r.d, A + (size_t)k + (size_t)k * lda, lda, (const T *)h->om.p,
-                                            w.B + (size_t)k * r.d, (T *)h->skp.p, h->skp.bytes / sizeof(T), s)));
+                CU_TRY(sketch_for<T>(h, r, m, A + (size_t)k + (size_t)k * lda, lda, (const T *)h->om.p,
+                                     w.B + (size_t)k * r.d, s));
                 CU_TRY(set_int(offsetof(FactorState, nresk), q));
                 CU_TRY(set_int(offsetof(FactorState, guard_req), 0));
             } else if (st.guard_req == 2) {
@@ -569,7 +590,7 @@ rcp_status rcp_create(rcp_handle **h) {
 
 void rcp_destroy(rcp_handle *h) {
     if (!h) return;
-    Buf *all[] = {&h->psnap, &h->pinv, &h->pbounds, &h->bord, &h->bom, &h->bticket, &h->bscr, &h->tcops, &h->keys, &h->skp, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
+    Buf *all[] = {&h->psnap, &h->pinv, &h->pbounds, &h->bord, &h->bom, &h->bticket, &h->bscr, &h->tcops, &h->keys, &h->skp, &h->omt, &h->trace, &h->status, &h->state, &h->bar, &h->scal, &h->om, &h->B, &h->Wbuf, &h->Lc, &h->Lg, &h->lpos, &h->moved,
                   &h->s1v, &h->s2v, &h->s3v, &h->s1i, &h->s2i, &h->pay, &h->tmpA, &h->tmpL, &h->tmpP, &h->Y, &h->flags,
                   &h->R, &h->Dc, &h->part, &h->A64, &h->F, &h->Bh, &h->Xh, &h->Dd, &h->Ds, &h->perm,
                   &h->gmV, &h->gmZ, &h->gmP, &h->gmH, &h->iperm};
@@ -925,12 +946,18 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
                 CU_TRY(launch_omega<float>(r.d, n, r.seed, (float *)h->om.p, s));
                 om = (const float *)h->om.p;
             }
+            if (tc_prec(r.prec)) CU_TRY(launch_omega_split(n, r.d, om, (float *)h->omt.p, s));
             for (int b = 0; b < nblk; ++b) {
                 const int j0 = b * kHostCopyCols, j1 = std::min(n, j0 + kHostCopyCols);
                 CU_TRY(cudaStreamWaitEvent(s, h->copy_events[b], 0));
                 CU_TRY(launch_copy_lower_f64(n, dA, dlda, h->F.p, n, 1, s, j0, j1));
-                CU_TRY(launch_sketch_cols_f32(n, r.d, (const float *)h->F.p, n, om, (float *)h->B.p, (float *)h->skp.p,
-                                              h->skp.bytes / sizeof(float), j0, j1, s));
+                if (tc_prec(r.prec))
+                    CU_TRY(launch_sketch_tc(n, r.d, (const float *)h->F.p, n, (const float *)h->omt.p, (float *)h->B.p,
+                                            (float *)h->skp.p, h->skp.bytes / sizeof(float), j0, j1,
+                                            (int *)h->status.p, s));
+                else
+                    CU_TRY(launch_sketch_cols_f32(n, r.d, (const float *)h->F.p, n, om, (float *)h->B.p,
+                                                  (float *)h->skp.p, h->skp.bytes / sizeof(float), j0, j1, s));
             }
             // the right-hand sides (last on the copy stream) before the refinement
             CU_TRY(cudaEventRecord(h->copy_events[nblk], cs));
@@ -1295,16 +1322,29 @@ rcp_status rcp_sketch(int n, int d, const void *A, int lda, rcp_prec prec, uint6
             CU_TRY(launch_omega<float>(d, n, seed, tmp, s));
             om = tmp;
         }
-        float *part = nullptr;
-        const size_t pf = sketch_scratch_floats(n, d);
-        if (pf > 0 && cudaMallocAsync((void **)&part, pf * sizeof(float), s) != cudaSuccess) {
-            cudaGetLastError();
-            if (tmp) cudaFreeAsync(tmp, s);
-            return RCP_ENOMEM;
+        const bool tcs = tc_prec(prec);
+        float *part = nullptr, *omt = nullptr;
+        int *st = nullptr;
+        const size_t pf = tcs ? sketch_tc_scratch_floats(n, d) : sketch_scratch_floats(n, d);
+        bool ok = !(pf > 0 && cudaMallocAsync((void **)&part, pf * sizeof(float), s) != cudaSuccess);
+        if (ok && tcs)
+            ok = cudaMallocAsync((void **)&omt, sketch_tc_omega_floats(n, d) * sizeof(float), s) == cudaSuccess &&
+                 cudaMallocAsync((void **)&st, sizeof(int), s) == cudaSuccess &&
+                 cudaMemsetAsync(st, 0, sizeof(int), s) == cudaSuccess;
+        cudaError_t e = cudaSuccess;
+        if (ok && tcs) {
+            e = launch_omega_split(n, d, om, omt, s);
+            if (e == cudaSuccess)
+                e = launch_sketch_tc(n, d, (const float *)A, lda, omt, (float *)B, part, part ? pf : 0, 0, n, st, s);
+        } else if (ok) {
+            e = launch_sketch<float, float>(n, d, (const float *)A, lda, om, (float *)B, part, part ? pf : 0, s);
         }
-        cudaError_t e = launch_sketch<float, float>(n, d, (const float *)A, lda, om, (float *)B, part, part ? pf : 0, s);
+        if (!ok) cudaGetLastError();
+        if (st) cudaFreeAsync(st, s);
+        if (omt) cudaFreeAsync(omt, s);
         if (part) cudaFreeAsync(part, s);
         if (tmp) cudaFreeAsync(tmp, s);
+        if (!ok) return RCP_ENOMEM;
         CU_TRY(e);
     }
     return RCP_OK;

@@ -251,6 +251,14 @@ __global__ void sketch_reduce_kernel(size_t count, int S, const float *__restric
     }
 }
 
+cudaError_t launch_sketch_reduce(size_t count, int S, const float *part, float *B, cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    const int blocks = (int)std::min<size_t>((count + 255) / 256, 4096);
+    sketch_reduce_kernel<<<blocks, 256, 0, s>>>(count, S, part, B);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <int RPT>
 static int sketch_f32_grid() {
     static int g = 0;
@@ -299,13 +307,10 @@ static cudaError_t launch_sketch_f32(int n, int d, const float *A, int lda, cons
 #undef SKF_CASE
     }
     count_launches(1);
-    if (S > 1) {
-        const size_t count = (size_t)d * nc;
-        const int blocks = (int)std::min<size_t>((count + 255) / 256, 4096);
-        sketch_reduce_kernel<<<blocks, 256, 0, s>>>(count, S, part, B + (size_t)c0 * d);
-        count_launches(1);
-    }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (S > 1) return launch_sketch_reduce((size_t)d * nc, S, part, B + (size_t)c0 * d, s);
+    return cudaSuccess;
 }
 
 cudaError_t launch_sketch_cols_f32(int n, int d, const float *A, int lda, const float *om, float *B, float *part,

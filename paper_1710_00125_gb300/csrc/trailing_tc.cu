@@ -35,6 +35,7 @@
 #include <cstdint>
 
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace rcpk {
 
@@ -47,18 +48,6 @@ constexpr uint32_t STAGE_BYTES = 4u * TILE_FLOATS * 4u;   // W_hi, W_lo, L_hi, L
 // K chunk: one 128-byte swizzle row, 32 TF32 or 64 FP16 values
 template <bool F16> constexpr int KC = F16 ? 64 : 32;
 
-// Offset (in elements) of element (m, k) of a 128-row K-major tile in the 128-byte swizzle
-// image: 8-row groups of 1024 bytes, rows of 128 bytes, 16-byte chunks xor-ed with row % 8
-// (4 FP32/TF32 or 8 FP16 values per chunk).
-__host__ __device__ __forceinline__ int swz(int m, int k) {
-    const int r = m & 7;
-    return (m >> 3) * 256 + r * 32 + (((k >> 2) ^ r) << 2) + (k & 3);
-}
-__host__ __device__ __forceinline__ int swz16(int m, int k) {
-    const int r = m & 7;
-    return (m >> 3) * 512 + r * 64 + (((k >> 3) ^ r) << 3) + (k & 7);
-}
-
 // Scale exponent for the FP16 split: the largest e with bound * 2^e < 2^15 (0 for a zero or
 // non-finite bound), from the bits of a non-negative double; clamped to the FP32 range.
 __device__ __forceinline__ int f16_scale_exp(unsigned long long bits) {
@@ -67,90 +56,6 @@ __device__ __forceinline__ int f16_scale_exp(unsigned long long bits) {
     const int e = ef == 0 ? -1022 : ef - 1022;
     const int s = 15 - e;
     return s < -126 ? -126 : (s > 126 ? 126 : s);
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t y;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-    return __uint_as_float(y);
-}
-
-// ---- shared-memory / tensor-memory primitives ------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Bounded wait for the phase with parity `phase` to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
-    const uint32_t a = smem_u32(bar);
-    uint32_t done = 0;
-    unsigned long long t0 = 0;
-    for (unsigned spins = 0;; ++spins) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(phase)
-            : "memory");
-        if (done) return true;
-        if (spins == 0) t0 = global_ns();
-        else if ((spins & 63u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
-    }
-}
-
-// L2 eviction policies: the operand tiles are read by many tiles of the panel and should stay
-// in L2 while the trailing block A22 (up to a few GB per panel) streams through it once.
-__device__ __forceinline__ uint64_t policy_evict_last() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ float ld_stream(const float *a, uint64_t pol) {
-    float v;
-    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ void st_stream(float *a, float v, uint64_t pol) {
-    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" :: "l"(a), "f"(v), "l"(pol) : "memory");
-}
-__device__ __forceinline__ void st_keep_v4(float4 *a, float4 v, uint64_t pol) {
-    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
-                 :: "l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
-        :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle layout, 8-row
-// groups 1024 bytes apart (stride byte offset), descriptor version 1, base offset 0 (every
-// tile starts on a 1024-byte boundary).
-__device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);           // start address
-    d |= (uint64_t)1u << 16;                              // leading byte offset (unused here)
-    d |= (uint64_t)(1024u >> 4) << 32;                    // stride byte offset
-    d |= (uint64_t)1u << 46;                              // version
-    d |= (uint64_t)2u << 61;                              // 128-byte swizzle
-    return d;
 }
 
 // Instruction descriptors: D = F32, A = B = TF32 (kind::tf32) or F16 (kind::f16), both
@@ -175,24 +80,6 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bd
             :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(IDESC_TF32), "r"(accumulate)
             : "memory");
 }
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 :: "r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 }  // namespace tc
 
@@ -284,9 +171,6 @@ constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_EPI_COLS = tc::TM * 4 / TC_EPI_WARPS;   // columns per epilogue warp
 constexpr int TC_THREADS = 32 * (1 + TC_EPI_WARPS);
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_u32(bar)) : "memory");
-}
 
 __device__ __forceinline__ void tile_ij(long long tile, int *I, int *J) {
     // FP32 estimate, corrected in integers (no FP64 on this part's slow FP64 pipe)
@@ -484,7 +368,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
             finish16(c1v, 48, taddr);
             tc::tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[a]);   // the accumulator may be reused
+            if (lane == 0) tc::mbar_arrive(&acce[a]);   // the accumulator may be reused
         }
     }
     tc::tc_fence_before();
