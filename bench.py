@@ -82,6 +82,8 @@ def parse(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=4096, help="systems of the batched ragged workload (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--no-qcompare", action="store_true", help="skip the q = b versus q = 1 comparison")
+    ap.add_argument("--no-kkt", action="store_true", help="skip the n = 12288 saddle-point system")
     ap.add_argument("--stability", action="store_true",
                     help="instead of timing: the stability diagnostics of the GPU factor for each synthetic "
                          "matrix type of the experiments section (growth, berr, ||L||_1, ||L^-1||_1)")
@@ -309,15 +311,24 @@ def run_ours(a, rank, world, local_rank):
         rcp.rcp_sysv(h, Ah, Bh, Xh, opts, tol=a.tol, max_iter=a.max_iter, host_buffers=True)
         torch.cuda.synchronize()
         barrier()
+        walls, gpus = [], []
         t0 = time.perf_counter()
         for _ in range(a.e2e_steps):
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ts = time.perf_counter()
+            g0.record(stream)
             ce, se = rcp.rcp_sysv(h, Ah, Bh, Xh, opts, tol=a.tol, max_iter=a.max_iter, host_buffers=True)
+            g1.record(stream)
+            walls.append(time.perf_counter() - ts)
+            gpus.append((g0, g1))
         torch.cuda.synchronize()
         el = max_over_ranks((time.perf_counter() - t0) / a.e2e_steps, dist, dev)
         h2d_bytes = host_copy_bytes(n) + n * nrhs * 8
         e2e = {"value": job_throughput(world, flops(n, nrhs), el) / 1e12, "unit": UNIT,
                "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": n * nrhs * 8,
-               "ms_per_step": el * 1e3, "berr": se.berr}
+               "ms_per_step": el * 1e3, "berr": se.berr,
+               "steps_wall_ms": [round(1e3 * w, 3) for w in walls],
+               "steps_stream_ms": [round(g0.elapsed_time(g1), 3) for g0, g1 in gpus]}
         # where the time goes: one profiled host-buffer step (the copies run on a second stream,
         # overlapped with the FP32 rounding and the sketch), and the link's rate for a plain copy
         rcp.rcp_profile(h, True)
@@ -335,6 +346,8 @@ def run_ours(a, rank, world, local_rank):
         del Ah, Bh, Xh
 
     batched = run_batched(a, dev, stream, rank, world, dist) if a.batch > 0 else None
+    qcmp = run_q_compare(a, dev, stream, A64, Bv, seed) if (not a.no_qcompare and rank == 0) else None
+    kkt = run_kkt(a, dev, stream) if (not a.no_kkt and rank == 0) else None
 
     if rank != 0:
         if dist is not None:
@@ -376,6 +389,8 @@ def run_ours(a, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "batched": batched,
+        "q_compare": qcmp,
+        "kkt": kkt,
     }
     if world == 1 and not a.no_cpu:
         times, be, _ = oracle_sample(a.cpu_n, a.kexp, 2)
@@ -456,6 +471,84 @@ def run_batched(a, dev, stream, rank, world, dist):
             "berr_max": float(berr.max()), "all_berr_le_tol": bool((berr <= a.tol).all()),
             "info_nonzero": int((info != 0).sum()), "refine_iters_hist": np.bincount(iters).tolist(),
             "gpu_launches_per_replay": 2, "steps": a.batch_steps, "tuned_b": tuned_b, "roofline": roof}
+
+
+def run_q_compare(a, dev, stream, A64, Bv, seed):
+    """The paper's choice of q (Section 3.1): Algorithm 1 with q = 1 (one sketch argmax and rank-1/2
+    sketch update per pivot step) against q = b (a b-step partial QRCP of the sketch per block and
+    one block sketch update B(:, k1:n) -= Y L21^T on the tensor cores), b = 64, d = 80: time to
+    solution of the timed system (same precision and refinement), and the growth of the FP64
+    factor on the Gaussian matrix (Type 6) at n = 4096."""
+    import torch
+
+    from paper_1710_00125_gb300 import inputs, rcp
+    h = rcp.rcp_create()
+    out = {"b": 64, "d": 80}
+    X = torch.zeros_like(Bv)
+    for q, name in ((1, "q1"), (2, "qb")):
+        o = rcp.make_opts(b=64, d=80, seed=seed, prec=a.prec, q_mode=q)
+        rcp.rcp_sysv(h, A64, Bv, X, o, tol=a.tol, max_iter=a.max_iter)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        code, st = rcp.rcp_sysv(h, A64, Bv, X, o, tol=a.tol, max_iter=a.max_iter)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rcp.rcp_profile(h, True)
+        rcp.rcp_sysv(h, A64, Bv, X, o, tol=a.tol, max_iter=a.max_iter)
+        ph = rcp.rcp_profile_read(h)
+        rcp.rcp_profile(h, False)
+        out[name] = {"ms": e0.elapsed_time(e1), "berr": st.berr, "growth_D": st.growth_D, "code": int(code),
+                     "phases_ms": {k: round(v[0], 3) for k, v in ph.items() if k != "h2d"}}
+    m = 4096
+    g = torch.from_numpy(inputs.gaussian_sym(m, seed=1)).to(dev)
+    for q, name in ((1, "type6_q1"), (2, "type6_qb")):
+        A = g.clone()
+        Dd = torch.zeros(m, dtype=torch.float64, device=dev)
+        Ds = torch.zeros_like(Dd)
+        perm = torch.zeros(m, dtype=torch.int32, device=dev)
+        code, st = rcp.rcp_factor(h, A, Dd, Ds, perm, rcp.make_opts(b=64, d=80, seed=1, prec="fp64", q_mode=q))
+        out[name] = {"n": m, "prec": "fp64", "growth_D": st.growth_D, "max_abs_L": st.max_abs_L, "n_2x2": st.n_2x2}
+    out["qb_over_q1_time"] = out["qb"]["ms"] / out["q1"]["ms"]
+    return out
+
+
+def run_kkt(a, dev, stream, n1=8192, n2=4096):
+    """The growth-stress saddle-point system of the experiments section (Type 7) at n = 12288:
+    [[H, W^T], [W, 0]], H = M M^T / 8192 + 1e-3 I (M 8192 x 8192), W 4096 x 8192, all N(0, 1).
+    The FP64 factor with a plain solve, and the FP32 (f16x3) factor with FP64 refinement to
+    berr <= tol, each timed once after a warm-up call, with growth and the backward error."""
+    import torch
+
+    from paper_1710_00125_gb300 import inputs, rcp
+    n = n1 + n2
+    A64 = inputs.kkt(n1, n2, m=8192, seed=4, device=dev)
+    xt = torch.from_numpy(inputs.x_true(n, 1, seed=4)).to(dev)
+    Bv = (A64 @ xt.T).T.contiguous()
+    h = rcp.rcp_create()
+    out = {"workload": f"KKT n={n} (H = M M^T/8192 + 1e-3 I, W {n2}x{n1}, N(0,1), seed 4), 1 RHS", "n": n}
+
+    def berr_of(X):
+        r = Bv - (A64 @ X.T).T
+        return float((r.abs().amax() / (A64.abs().sum(1).amax() * X.abs().amax())))
+
+    for prec, b, it in (("fp64", 64, 0), ("f16x3", 256, a.max_iter)):
+        o = rcp.make_opts(b=b, d=80, seed=4, prec=prec)
+        X = torch.zeros_like(Bv)
+        rcp.rcp_sysv(h, A64, Bv, X, o, tol=a.tol, max_iter=it)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        code, st = rcp.rcp_sysv(h, A64, Bv, X, o, tol=a.tol, max_iter=it)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[prec] = {"ms": ms, "tflops": flops(n, 1) / (ms * 1e-3) / 1e12, "code": int(code), "berr": berr_of(X),
+                     "refine_iters": st.refine_iters, "growth_D": st.growth_D, "max_abs_L": st.max_abs_L,
+                     "n_2x2": st.n_2x2, "b": b}
+    del A64, Bv
+    torch.cuda.empty_cache()
+    return out
 
 
 def trailing_flops(n, b):
@@ -584,9 +677,11 @@ def run_stability(a, local_rank):
         rcp.rcp_solve(h, A, Dd, Ds, perm, "fp64", X)
         r = Bv - (A64 @ X.T).T
         berr = float(r.abs().amax() / (A64.abs().sum(1).amax() * X.abs().amax()))
-        print(json.dumps({"type": name, "n": m, "d": 5, "b": 64, "prec": "fp64", "info": int(st.info),
-                          "growth_D": st.growth_D, "n_2x2": st.n_2x2, "max_abs_L": st.max_abs_L,
-                          "norm1_L": nl, "norm1_Linv_est": ni, "berr_solve": berr}), flush=True)
+        rec = {"type": name, "n": m, "d": 5, "b": 64, "prec": "fp64", "info": int(st.info),
+               "growth_D": st.growth_D, "n_2x2": st.n_2x2, "max_abs_L": st.max_abs_L,
+               "norm1_L": nl, "norm1_Linv_est": ni, "berr_solve": berr}
+        print(json.dumps(rec), flush=True)
+    print(json.dumps({"kkt": run_kkt(a, dev, torch.cuda.current_stream())}), flush=True)
 
 
 def main():

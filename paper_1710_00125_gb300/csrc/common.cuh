@@ -142,4 +142,37 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double 
 
 __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 
+
+// ---- packed 64-bit argmax keys (FP32 values) exchanged between the CTAs of a grid ----------
+// FP32 argmax key: larger key = larger value, then smaller position.  Needs n <= 65535.
+__device__ __forceinline__ unsigned long long make_key(float v, int lpos, int phys) {
+    return ((unsigned long long)__float_as_uint(v) << 32) | ((unsigned long long)(0xFFFFu - (unsigned)lpos) << 16) |
+           (unsigned long long)(unsigned)phys;
+}
+
+__device__ __forceinline__ void red_max_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+
+// Keys are read right after the grid barrier, whose acquire already orders these loads after
+// every CTA's red.max; a relaxed load suffices and lets independent key loads overlap.
+__device__ __forceinline__ unsigned long long ld_key(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Ring of key slots indexed by the grid-barrier generation; the slot of generation g + KEY_RING/2
+// is cleared (by one CTA) after the key of generation g is read, so a slot is zero when reused.
+constexpr int KEY_RING = 16;
+
+// Maximum of a packed key over the warp (the result in every lane): redux.sync on the high
+// words, then on the low words among the lanes holding the maximal high word.
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+    const unsigned m = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned l = __reduce_max_sync(0xffffffffu, hi == m ? lo : 0u);
+    return ((unsigned long long)m << 32) | l;
+}
+
 }  // namespace rcpk

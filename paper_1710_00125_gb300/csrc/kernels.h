@@ -95,6 +95,13 @@ template <typename T>
 cudaError_t launch_qrcp(const FactorWork<T> &w, int steps, cudaStream_t s);
 template <typename T>
 cudaError_t launch_block_sketch_update(const FactorWork<T> &w, T *ytmp, cudaStream_t s);
+// Y = B(:, k0:k1) L11^{-T} (d x nb, ld d) of the panel just done, into ytmp
+template <typename T>
+cudaError_t launch_bsk_y(const FactorWork<T> &w, T *ytmp, cudaStream_t s);
+// the block sketch update on tcgen05 (split TF32): Y, its tiles (block_update_tc_floats(bw, d)
+// floats in ytiles), then B(:, k1:n) -= Y L21^T
+size_t block_update_tc_floats(int bw, int d);
+cudaError_t launch_block_sketch_update_tc(const FactorWork<float> &w, float *ytmp, float *ytiles, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_panel(const FactorWork<T> &w, cudaStream_t s);

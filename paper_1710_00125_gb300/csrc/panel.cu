@@ -152,25 +152,6 @@ __device__ __forceinline__ SlotWin slot_reduce(const double *slots, int G) {
     return b;   // valid in lane 0
 }
 
-// FP32 argmax key: larger key = larger value, then smaller position.  Needs n <= 65535.
-__device__ __forceinline__ unsigned long long make_key(float v, int lpos, int phys) {
-    return ((unsigned long long)__float_as_uint(v) << 32) | ((unsigned long long)(0xFFFFu - (unsigned)lpos) << 16) |
-           (unsigned long long)(unsigned)phys;
-}
-
-__device__ __forceinline__ void red_max_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
-}
-
-// Keys are read right after the grid barrier, whose acquire already orders these loads after
-// every CTA's red.max; a relaxed load suffices and lets independent key loads overlap.
-__device__ __forceinline__ unsigned long long ld_key(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-constexpr int KEY_RING = 16;
 static_assert(2 * KEY_RING <= PANEL_KEY_WORDS, "the pivot and speculative key rings");
 
 // Block-wide maximum of two packed keys per thread (the result to every thread): per warp two
@@ -178,13 +159,6 @@ static_assert(2 * KEY_RING <= PANEL_KEY_WORDS, "the pivot and speculative key ri
 // high word), one shared slot per key and warp, and the same warp reduction over the slots.
 // Two slot sets are used in alternation (call counter `cnt`, uniform over the block): the set
 // of call c is rewritten at call c + 2, after the CTA barrier of call c + 1.
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
-    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
-    const unsigned m = __reduce_max_sync(FULL, hi);
-    const unsigned l = __reduce_max_sync(FULL, hi == m ? lo : 0u);
-    return ((unsigned long long)m << 32) | l;
-}
-
 constexpr int RED2_SLOTS = 4 * (PANEL_THREADS / 32);   // [2 sets][2 keys][warps]
 
 __device__ __forceinline__ void block_max2_u64(unsigned long long &a, unsigned long long &b, unsigned long long *red,

@@ -17,6 +17,8 @@
 // are written in the panel's format (lpos, moved list, an empty panel k0 = kend), so the
 // interchange kernels apply them to A, the earlier L rows and perm; the sketch columns are
 // moved here.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace rcpk {
@@ -223,6 +225,213 @@ __global__ void __launch_bounds__(QR_THREADS, 1) qrcp_kernel(FactorWork<T> w, in
     }
 }
 
+// The FP32 block QRCP, arranged around one exchange per step like the FP32 panel: the step's
+// reflection, the downdated residual norms (recomputed from the updated rows t+1..d-1) and the
+// CTA's next candidate come out of one pass over the owned columns, four threads per column (a
+// quad: rows t + sub, t + sub + 4, ...; two shuffles per reduction); the candidates meet in one
+// packed 64-bit key per CTA (norm bits, inverted position, CTA) folded by red.max into the
+// panel's key ring, and after the grid barrier a single key load names the winner, whose
+// residual rows the winning CTA published beside it.  The reflection's scalars are formed in
+// FP32, the factor's type (an FP32 factor takes its pivot decisions on FP32 values).
+__device__ __forceinline__ unsigned long long qr_block_max(unsigned long long v, unsigned long long *slots) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_max_u64(v);
+    if (lane == 0) slots[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long x = warp_max_u64(lane < QR_WARPS ? slots[lane] : 0ull);
+        if (lane == 0) slots[QR_WARPS] = x;
+    }
+    __syncthreads();
+    return slots[QR_WARPS];
+}
+
+__global__ void __launch_bounds__(QR_THREADS, 1) qrcp_keys_kernel(FactorWork<float> w, int steps_max) {
+    extern __shared__ __align__(16) unsigned char qr_smem[];
+    __shared__ unsigned long long s_slots[QR_WARPS + 1];
+    __shared__ float s_v[QR_DMAX];   // the Householder vector of the step (rows t..d-1)
+    __shared__ double s_sc[4];       // ||x||, alpha, v^T v, 2 / v^T v
+    __shared__ int s_i[4];
+    const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (ldcg(w.status) != 0) return;
+    const int n = w.n, d = w.d;
+    const int k0 = ldcg(&w.st->next);
+    if (k0 >= n) {
+        if (cta == 0 && tid == 0) {
+            w.st->n_moved = 0;
+            w.st->k0 = n;
+            w.st->kend = n;
+        }
+        return;
+    }
+    const int m = n - k0;
+    const int chunk = (m + G - 1) / G;
+    if (chunk > w.chunk_cap || d > QR_DMAX || G > 0xFFFF) {
+        if (tid == 0) atomicOr(w.status, ST_INTERNAL);
+        return;
+    }
+    const int j_lo = k0 + cta * chunk;
+    const int cnt = max(0, min(n, j_lo + chunk) - j_lo);
+    float *Wk = reinterpret_cast<float *>(qr_smem);                     // [cnt][d] working copy
+    int *cur = reinterpret_cast<int *>(Wk + (size_t)w.chunk_cap * d);   // current positions
+    int *chosen = cur + w.chunk_cap;
+    for (int e = tid; e < cnt * d; e += QR_THREADS) {
+        const int jl = e / d, r = e - jl * d;
+        Wk[e] = w.B[(size_t)r + (size_t)(j_lo + jl) * d];
+    }
+    for (int jl = tid; jl < cnt; jl += QR_THREADS) {
+        cur[jl] = j_lo + jl;
+        chosen[jl] = 0;
+    }
+    if (tid == 0) {
+        s_i[0] = (int)barrier_base(w.bar, (unsigned)G);
+        if (cta == 0) w.st->n_moved = 0;
+    }
+    __syncthreads();
+    const unsigned base = (unsigned)s_i[0];
+    const unsigned gbase = base / (unsigned)G;
+    unsigned nbar = 0;
+    float *pay = w.pay;   // per CTA: the candidate's residual rows
+    unsigned long long *keys = w.keys;
+    const int steps = min(min(steps_max, m), d);
+    // the CTA's candidate for step 0: largest ||B(:, j)||^2 (local key: norm bits, position, index)
+    constexpr int QUADS = QR_THREADS / 4;
+    const int quad = tid >> 2, sub = tid & 3;
+    unsigned long long key = 0ull;
+    for (int jl0 = 0; jl0 < cnt; jl0 += QUADS) {
+        const int jl = jl0 + quad;
+        float s2 = 0.f;
+        if (jl < cnt)
+            for (int r = sub; r < d; r += 4) {
+                const float x = Wk[(size_t)jl * d + r];
+                s2 = fmaf(x, x, s2);
+            }
+        s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+        if (jl < cnt && sub == 0) key = max(key, make_key(s2, cur[jl], jl));
+    }
+    for (int t = 0; t < steps; ++t) {
+        const unsigned long long kc = qr_block_max(key, s_slots);
+        const unsigned g = gbase + nbar + 1;
+        if (kc != 0ull) {
+            const int jc = (int)(kc & 0xFFFFull);
+            for (int r = t + tid; r < d; r += QR_THREADS) stcg(pay + (size_t)cta * d + r, Wk[(size_t)jc * d + r]);
+            if (tid == 0) red_max_u64(keys + (g % KEY_RING), (kc & ~0xFFFFull) | (unsigned long long)cta);
+        }
+        if (!grid_barrier(w.bar, base + (++nbar) * (unsigned)G, w.status)) return;
+        if (tid == 0) {
+            const unsigned long long kw = ld_key(keys + (g % KEY_RING));
+            if (cta == 0) keys[(g + KEY_RING / 2) % KEY_RING] = 0ull;
+            const float v = __uint_as_float((unsigned)(kw >> 32));
+            s_i[2] = kw != 0ull && isfinite(v) ? 0xFFFF - (int)((kw >> 16) & 0xFFFFull) : -1;
+            s_i[3] = (int)(kw & 0xFFFFull);
+        }
+        __syncthreads();
+        const int wpos = s_i[2], wcta = s_i[3];
+        if (wpos < k0 + t || wpos >= n || wcta >= G) {
+            // no finite residual norm left (NaN or Inf in the sketch)
+            if (tid == 0) atomicOr(w.status, ST_NONFINITE);
+            return;
+        }
+        for (int r = t + tid; r < d; r += QR_THREADS) s_v[r] = ldcg(pay + (size_t)wcta * d + r);
+        // ---- interchange k0 + t <-> wpos in the owned bookkeeping ----
+        for (int jl = tid; jl < cnt; jl += QR_THREADS) {
+            const int o = cur[jl];
+            if (o == wpos) { cur[jl] = k0 + t; chosen[jl] = 1; }
+            else if (o == k0 + t) cur[jl] = wpos;
+        }
+        __syncthreads();
+        // ---- the Householder reflection zeroing x(t+1:d) (same arithmetic in every CTA) ----
+        if (warp == 0) {
+            float s2 = 0.f;
+            for (int r = t + lane; r < d; r += 32) s2 = fmaf(s_v[r], s_v[r], s2);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+            const float nrm = sqrtf(s2), x0 = s_v[t];
+            const float alpha = x0 >= 0.f ? -nrm : nrm;
+            __syncwarp();
+            if (lane == 0) s_v[t] = x0 - alpha;
+            __syncwarp();
+            float vv = 0.f;
+            for (int r = t + lane; r < d; r += 32) vv = fmaf(s_v[r], s_v[r], vv);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, off);
+            if (lane == 0) {
+                s_sc[0] = nrm;
+                s_sc[2] = vv;
+                s_sc[3] = vv > 0.f ? 2.f / vv : 0.f;
+            }
+        }
+        __syncthreads();
+        // ---- the reflection on every owned column left, its residual norm over rows t+1..d-1
+        // and the CTA's candidate for the next step, in one pass (a quad per column) ----
+        const bool reflect = s_sc[0] != 0.0 && s_sc[2] > 0.0;
+        const float f2 = (float)s_sc[3];
+        key = 0ull;
+        for (int jl0 = 0; jl0 < cnt; jl0 += QUADS) {
+            const int jl = jl0 + quad;
+            const bool live = jl < cnt && !chosen[jl];
+            float *col = Wk + (size_t)(live ? jl : 0) * d;
+            float dot = 0.f;
+            if (live && reflect)
+                for (int r = t + sub; r < d; r += 4) dot = fmaf(s_v[r], col[r], dot);
+            dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+            dot += __shfl_xor_sync(0xffffffffu, dot, 2);
+            float s2 = 0.f;
+            if (live) {
+                const float f = dot * f2;
+                for (int r = t + sub; r < d; r += 4) {
+                    float x = col[r];
+                    if (reflect) {
+                        x = fmaf(-f, s_v[r], x);
+                        col[r] = x;
+                    }
+                    if (r > t) s2 = fmaf(x, x, s2);   // rows t+1.. are the next step's residual
+                }
+            }
+            s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+            if (live && sub == 0) key = max(key, make_key(s2, cur[jl], jl));
+        }
+        __syncthreads();
+    }
+    // ---- publish the interchanges in the panel's format; move the sketch columns ----
+    for (int jl = tid; jl < cnt; jl += QR_THREADS) {
+        const int j = j_lo + jl;
+        w.lpos[j] = cur[jl];
+        chosen[jl] = -1;
+        if (cur[jl] != j) {
+            const int idx = atomicAdd(&w.st->n_moved, 1);
+            if (idx < w.maxmoved) {
+                w.moved[idx] = j;
+                chosen[jl] = idx;
+            } else {
+                atomicOr(w.status, ST_INTERNAL);
+            }
+        }
+    }
+    __syncthreads();
+    for (int jl = warp; jl < cnt; jl += QR_WARPS) {
+        const int idx = chosen[jl];
+        if (idx < 0) continue;
+        for (int r = lane; r < d; r += 32) w.tmpA[(size_t)idx * d + r] = w.B[(size_t)r + (size_t)(j_lo + jl) * d];
+    }
+    {
+        const unsigned g = gbase + nbar + 1;
+        if (!grid_barrier(w.bar, base + (++nbar) * (unsigned)G, w.status)) return;
+        if (cta == 0 && tid == 0) keys[(g + KEY_RING / 2) % KEY_RING] = 0ull;   // the ring stays in step
+    }
+    for (int jl = warp; jl < cnt; jl += QR_WARPS) {
+        const int idx = chosen[jl];
+        if (idx < 0) continue;
+        for (int r = lane; r < d; r += 32) w.B[(size_t)r + (size_t)cur[jl] * d] = ldcg(w.tmpA + (size_t)idx * d + r);
+    }
+    if (cta == 0 && tid == 0) {
+        w.st->k0 = k0;
+        w.st->kend = k0;
+    }
+}
+
 // Y = B(:, k0:k1) L11^{-T} (Y L11^T = B(:, blk), column by column), one CTA; Y^T is kept in
 // shared memory as [c][r] and written to ytmp (d x nb, ld d).
 template <typename T>
@@ -286,9 +495,12 @@ __global__ void __launch_bounds__(128) bsk_update_kernel(FactorWork<T> w, const 
 template <typename T>
 cudaError_t launch_qrcp(const FactorWork<T> &w, int steps, cudaStream_t s) {
     const size_t smem = qrcp_smem_bytes<T>(w.d, w.chunk_cap);
+    // FP32: the key-exchange kernel (it keeps the panel's key ring in step, so the ring must
+    // have been zeroed at the start of the factorization, as factor_impl does)
+    const void *fn = std::is_same<T, float>::value ? (const void *)qrcp_keys_kernel : (const void *)qrcp_kernel<T>;
     static int attr_set = 0;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(qrcp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr_set = 1;
     }
@@ -297,7 +509,22 @@ cudaError_t launch_qrcp(const FactorWork<T> &w, int steps, cudaStream_t s) {
     int st = steps;
     void *args[] = {&arg, &st};
     count_launches(1);
-    return cudaLaunchCooperativeKernel((const void *)qrcp_kernel<T>, dim3(w.grid), dim3(QR_THREADS), args, smem, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(w.grid), dim3(QR_THREADS), args, smem, s);
+}
+
+template <typename T>
+cudaError_t launch_bsk_y(const FactorWork<T> &w, T *ytmp, cudaStream_t s) {
+    const size_t ysm = (size_t)w.bw * w.d * sizeof(T);
+    static int attr_set = 0;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(bsk_y_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = 1;
+    }
+    if (ysm > 200 * 1024) return cudaErrorInvalidValue;
+    bsk_y_kernel<T><<<1, 1024, ysm, s>>>(w, ytmp);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -326,6 +553,8 @@ template size_t qrcp_smem_bytes<double>(int, int);
 template size_t qrcp_smem_bytes<float>(int, int);
 template cudaError_t launch_qrcp<double>(const FactorWork<double> &, int, cudaStream_t);
 template cudaError_t launch_qrcp<float>(const FactorWork<float> &, int, cudaStream_t);
+template cudaError_t launch_bsk_y<double>(const FactorWork<double> &, double *, cudaStream_t);
+template cudaError_t launch_bsk_y<float>(const FactorWork<float> &, float *, cudaStream_t);
 template cudaError_t launch_block_sketch_update<double>(const FactorWork<double> &, double *, cudaStream_t);
 template cudaError_t launch_block_sketch_update<float>(const FactorWork<float> &, float *, cudaStream_t);
 

@@ -233,7 +233,8 @@ rcp_status ensure_factor_ws(rcp_handle *h, int n, const Resolved &r) {
     RCP_TRY(grow(h->keys, PANEL_KEY_WORDS * sizeof(unsigned long long)));
     if (sizeof(T) == sizeof(float))
         RCP_TRY(grow(h->skp, std::max(sketch_scratch_floats(n, r.d), sketch_tc_scratch_floats(n, r.d)) * sizeof(float)));
-    if (tc_prec(r.prec)) RCP_TRY(grow(h->omt, sketch_tc_omega_floats(n, r.d) * sizeof(float)));
+    if (tc_prec(r.prec))   // Omega's tiles for the sketch, later Y's for the q = b block update
+        RCP_TRY(grow(h->omt, std::max(sketch_tc_omega_floats(n, r.d), block_update_tc_floats(r.bw, r.d)) * sizeof(float)));
     if (r.prec == RCP_TF32X3 || r.prec == RCP_F16X3) RCP_TRY(grow(h->tcops, tc_ops_floats(n, r.b) * sizeof(float)));
     RCP_TRY(grow(h->s1i, 2 * (size_t)r.grid * sizeof(int)));
     RCP_TRY(grow(h->s2i, 2 * (size_t)r.grid * sizeof(int)));
@@ -449,7 +450,12 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
         }
         if (r.qb) {
             PhaseScope ps(h, s, PH_SKETCH);
-            CU_TRY(launch_block_sketch_update<T>(w, w.tmpL, s));
+            if constexpr (std::is_same<T, float>::value) {
+                if (tc_prec(r.prec)) CU_TRY(launch_block_sketch_update_tc(w, w.tmpL, (float *)h->omt.p, s));
+                else CU_TRY(launch_block_sketch_update<T>(w, w.tmpL, s));
+            } else {
+                CU_TRY(launch_block_sketch_update<T>(w, w.tmpL, s));
+            }
         }
     }
     {

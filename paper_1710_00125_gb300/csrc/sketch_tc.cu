@@ -68,8 +68,16 @@ size_t sketch_tc_scratch_floats(int n, int d) {
 }
 
 // Omega (d x n, ld d) as K-major swizzled tiles of np rows x 32 K values, TF32 hi and lo parts:
-// tile (c, q) at (2 c + q) np 32 floats; rows r >= d and columns k >= n are zero.
-__global__ void omega_split_kernel(int n, int d, int np, const float *__restrict__ om, float *__restrict__ out) {
+// tile (c, q) at (2 c + q) np 32 floats; rows r >= d and columns k >= n are zero.  With st
+// (the q = b block update), the matrix is Y = B_blk L11^{-T} (d x nb) of the panel just done,
+// nb = kend - k0 read from the device state.
+__global__ void omega_split_kernel(int n, int d, int np, const float *__restrict__ om, float *__restrict__ out,
+                                   const FactorState *st) {
+    if (st) {
+        const int nb = st->kend - st->k0;
+        if (nb <= 0 || st->kend >= n) return;
+        n = nb;
+    }
     const int nkc = (n + sktc::KC - 1) / sktc::KC;
     for (int c = blockIdx.x; c < nkc; c += gridDim.x) {
         float *hi = out + (size_t)(2 * c) * np * sktc::KC, *lo = hi + (size_t)np * sktc::KC;
@@ -112,10 +120,28 @@ __device__ __forceinline__ void sk_map(bool above, int lw, int lane, int u, int 
     }
 }
 
+// UPD = false: the sketch, columns c0 .. c1-1 of B (or of the slice partials).  UPD = true: the
+// q = b block sketch update B(:, k1:n) -= Y L21^T, i.e. B^T(j, :) -= sum_c L(j, k0 + c) Y(:, c)^T
+// for the rows j >= k1 of the panel's multipliers (A = Lc, position order, ld n; K = the panel's
+// nb columns), its geometry read from the device state, B updated in place.
+template <bool UPD>
 __global__ void __launch_bounds__(sktc::THREADS, 1)
 sketch_tc_kernel(int n, int d, int np, const float *__restrict__ A, int lda, const float *__restrict__ omt,
-                 float *__restrict__ out, int S, int Jb, int ksteps, int c0, int c1, int *status) {
+                 float *__restrict__ out, int S, int Jb, int ksteps, int c0, int c1, int *status,
+                 const FactorState *st) {
     using namespace sktc;
+    int kmax = n;   // K extent (rows of A, or the panel's columns)
+    if (UPD) {
+        if (ldcg(status) != 0) return;
+        const int k0 = st->k0, k1 = st->kend;
+        if (k1 - k0 <= 0 || k1 >= n) return;
+        kmax = k1 - k0;
+        c0 = k1;
+        c1 = n;
+        S = 1;
+        ksteps = (kmax + KC - 1) / KC;
+        Jb = (n - k1 + TM - 1) / TM;
+    }
     extern __shared__ __align__(1024) unsigned char sk_smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[STAGES];   // the stage's A parts stored (one arrival per loader warp)
     __shared__ __align__(8) uint64_t om_bar[STAGES];     // its Omega parts landed (transaction count)
@@ -214,14 +240,18 @@ sketch_tc_kernel(int n, int d, int np, const float *__restrict__ A, int lda, con
         float cur[PER], nxt[PER];
         auto load_chunk = [&](float (&v)[PER], int j0, int c) {
             const int k0 = c * KC;
-            const bool above = k0 + KC <= j0;
+            const bool above = UPD || k0 + KC <= j0;
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
                 int m, kk;
                 sk_map(above, lw, lane, u, &m, &kk);
                 const int j = j0 + m, k = k0 + kk;
                 float x = 0.f;
-                if (k < n && j < c1) x = k >= j ? A[(size_t)k + (size_t)j * lda] : A[(size_t)j + (size_t)k * lda];
+                if (UPD) {
+                    if (k < kmax && j < c1) x = A[(size_t)j + (size_t)k * lda];   // L(j, k0 + k)
+                } else if (k < n && j < c1) {
+                    x = k >= j ? A[(size_t)k + (size_t)j * lda] : A[(size_t)j + (size_t)k * lda];
+                }
                 v[u] = x;
             }
         };
@@ -261,7 +291,7 @@ sketch_tc_kernel(int n, int d, int np, const float *__restrict__ A, int lda, con
                 tc::bulk_g2s(st + 2 * A_FLOATS + np * KC, src + (size_t)np * KC, om_part_bytes, &om_bar[s], keep);
                 ++issued[s];
             }
-            const bool above = c * KC + KC <= x.j0;
+            const bool above = UPD || c * KC + KC <= x.j0;
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
                 int m, kk;
@@ -301,7 +331,7 @@ sketch_tc_kernel(int n, int d, int np, const float *__restrict__ A, int lda, con
             accf_ph ^= 1u << a;
             tc::tc_fence_after();
             const int j = x.j0 + q * 32 + lane;
-            float *dst = out + (size_t)x.sl * d * (c1 - c0) + (size_t)(j - c0) * d;
+            float *dst = UPD ? out + (size_t)j * d : out + (size_t)x.sl * d * (c1 - c0) + (size_t)(j - c0) * d;
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * TM);
             for (int cb = 0; cb < np; cb += 16) {
                 uint32_t r[16];
@@ -310,7 +340,10 @@ sketch_tc_kernel(int n, int d, int np, const float *__restrict__ A, int lda, con
                 if (j < c1) {
 #pragma unroll
                     for (int t = 0; t < 16; ++t)
-                        if (cb + t < d) dst[cb + t] = __uint_as_float(r[t]);
+                        if (cb + t < d) {
+                            if (UPD) dst[cb + t] -= __uint_as_float(r[t]);
+                            else dst[cb + t] = __uint_as_float(r[t]);
+                        }
                 }
             }
             tc::tc_fence_before();
@@ -325,11 +358,31 @@ sketch_tc_kernel(int n, int d, int np, const float *__restrict__ A, int lda, con
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
 }
 
+// SM count; the dynamic shared-memory limit of both kernel variants is raised once (for np = 128)
+static int sk_setup() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0, m = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+        const int want = (int)(sktc::STAGES * sktc::stage_floats(128) * sizeof(float) + 1024);
+        if (cudaFuncSetAttribute(sketch_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, want) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(sketch_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, want) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        sms = m;
+    }
+    return sms;
+}
+
 cudaError_t launch_omega_split(int n, int d, const float *om, float *omt, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     if (d < 1 || d > 128) return cudaErrorInvalidValue;
     const int nkc = (n + sktc::KC - 1) / sktc::KC;
-    omega_split_kernel<<<std::min(nkc, 4096), 256, 0, s>>>(n, d, sktc::npad(d), om, omt);
+    omega_split_kernel<<<std::min(nkc, 4096), 256, 0, s>>>(n, d, sktc::npad(d), om, omt, nullptr);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -341,31 +394,45 @@ cudaError_t launch_sketch_tc(int n, int d, const float *A, int lda, const float 
     if (d < 1 || d > 128 || c0 < 0 || c1 > n || !status) return cudaErrorInvalidValue;
     const int np = npad(d);
     const size_t smem = STAGES * stage_floats(np) * sizeof(float) + 1024;
-    static int sms = 0;
-    static size_t attr = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    if (attr < smem) {
-        const size_t want = STAGES * stage_floats(128) * sizeof(float) + 1024;   // the largest np
-        cudaError_t e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want);
-        if (e != cudaSuccess) return e;
-        attr = want;
-    }
+    const int sms = sk_setup();
+    if (sms <= 0) return cudaErrorInvalidValue;
     const int nc = c1 - c0;
     const int Jb = (nc + TM - 1) / TM, ksteps = (n + KC - 1) / KC;
     const int S = sketch_tc_slices(n);
     if (S > 1 && (!part || part_floats < (size_t)S * d * nc)) return cudaErrorInvalidValue;
     float *dst = S > 1 ? part : B + (size_t)c0 * d;
     const int grid = std::min(Jb * S, sms);
-    sketch_tc_kernel<<<grid, THREADS, smem, s>>>(n, d, np, A, lda, omt, dst, S, Jb, ksteps, c0, c1, status);
+    sketch_tc_kernel<false><<<grid, THREADS, smem, s>>>(n, d, np, A, lda, omt, dst, S, Jb, ksteps, c0, c1, status,
+                                                        nullptr);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (S > 1) return launch_sketch_reduce((size_t)d * nc, S, part, B + (size_t)c0 * d, s);
     return cudaSuccess;
+}
+
+size_t block_update_tc_floats(int bw, int d) {
+    const size_t nkc = ((size_t)bw + sktc::KC - 1) / sktc::KC;
+    return 2 * nkc * (size_t)sktc::npad(d) * sktc::KC;
+}
+
+cudaError_t launch_block_sketch_update_tc(const FactorWork<float> &w, float *ytmp, float *ytiles, cudaStream_t s) {
+    using namespace sktc;
+    if (w.d < 1 || w.d > 128) return cudaErrorInvalidValue;
+    cudaError_t e = launch_bsk_y<float>(w, ytmp, s);   // Y = B(:, k0:k1) L11^{-T} (CUDA cores, small)
+    if (e != cudaSuccess) return e;
+    const int np = npad(w.d);
+    const int nkc = (w.bw + KC - 1) / KC;
+    omega_split_kernel<<<nkc, 256, 0, s>>>(w.n, w.d, np, ytmp, ytiles, w.st);
+    count_launches(1);
+    const int sms = sk_setup();
+    if (sms <= 0) return cudaErrorInvalidValue;
+    const int grid = std::min((w.n + TM - 1) / TM, sms);
+    const size_t smem = STAGES * stage_floats(np) * sizeof(float) + 1024;
+    sketch_tc_kernel<true><<<grid, THREADS, smem, s>>>(w.n, w.d, np, w.Lc, w.n, ytiles, w.B, 1, 1, 1, 0, 0, w.status,
+                                                       w.st);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace rcpk

@@ -172,13 +172,22 @@ constexpr int TC_EPI_COLS = tc::TM * 4 / TC_EPI_WARPS;   // columns per epilogue
 constexpr int TC_THREADS = 32 * (1 + TC_EPI_WARPS);
 
 
-__device__ __forceinline__ void tile_ij(long long tile, int *I, int *J) {
-    // FP32 estimate, corrected in integers (no FP64 on this part's slow FP64 pipe)
-    int a = (int)((sqrtf(8.f * (float)tile + 1.f) - 1.f) * 0.5f);
-    while ((long long)a * (a + 1) / 2 > tile) --a;
-    while ((long long)(a + 1) * (a + 2) / 2 <= tile) ++a;
-    *I = a;
-    *J = (int)(tile - (long long)a * (a + 1) / 2);
+// Tile order: diagonal by diagonal (delta = I - J = 0, 1, ...; J ascending within a diagonal), so
+// that the ~152 tiles in flight at any time have distinct row blocks I and J: every operand tile
+// is read by one CTA at a time instead of one W tile by all of them at once (row by row order).
+// Diagonal delta holds nrb - delta tiles and starts at C(delta) = delta (2 nrb + 1 - delta) / 2.
+__device__ __forceinline__ void tile_ij(long long tile, int nrb, int *I, int *J) {
+    // FP32 estimate of the root of delta^2 - (2 nrb + 1) delta + 2 tile = 0, corrected in integers
+    // (no FP64 on this part's slow FP64 pipe)
+    const float b = 2.f * (float)nrb + 1.f;
+    const float disc = fmaxf(b * b - 8.f * (float)tile, 0.f);
+    int dl = (int)((b - sqrtf(disc)) * 0.5f);
+    dl = dl < 0 ? 0 : (dl > nrb - 1 ? nrb - 1 : dl);
+    auto start = [&](long long x) { return x * (2LL * nrb + 1 - x) / 2; };
+    while (dl > 0 && start(dl) > tile) --dl;
+    while (dl + 1 < nrb && start(dl + 1) <= tile) ++dl;
+    *J = (int)(tile - start(dl));
+    *I = *J + dl;
 }
 
 template <bool F16>
@@ -241,7 +250,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
             auto chunk_src = [&](int g, size_t *ti, size_t *tj) {
                 const int lt = g / nkc, c = g % nkc;
                 int I, J;
-                tile_ij(blockIdx.x + (long long)lt * gridDim.x, &I, &J);
+                tile_ij(blockIdx.x + (long long)lt * gridDim.x, nrb, &I, &J);
                 *ti = ((size_t)I * nkc + c) * tc::TILE_FLOATS;
                 *tj = ((size_t)J * nkc + c) * tc::TILE_FLOATS;
             };
@@ -320,7 +329,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
         for (int lt = 0; lt < ntiles; ++lt) {
             const int a = lt & 1;
             int I, J;
-            tile_ij(blockIdx.x + (long long)lt * gridDim.x, &I, &J);
+            tile_ij(blockIdx.x + (long long)lt * gridDim.x, nrb, &I, &J);
             const int p = kend + I * tc::TM + q * 32 + lane;
             const int q0 = kend + J * tc::TM + h * EC;
             // chunks 0 and 1 of the block of A this warp updates, loaded while the MMAs run

@@ -803,3 +803,63 @@ def test_full_size_fp64_n8192_matches_the_oracle(rcp, handle):
         torch.cuda.synchronize()
         be = oracle.berr(a, X.cpu().numpy().T, rhs.T)
         assert abs(be - g[name]) <= 1e-12 and be <= 1e-13, (name, be, g[name])
+
+
+# ------------------------------------------------------------------------------------------
+# Growth-stress and saddle-point systems (experiments section, Types 1 and 7)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("family", ["type1", "kkt"])
+def test_growth_stress_rcp_against_bunch_kaufman_and_bunch_parlett(rcp, handle, family):
+    # n = 2048 with the paper's sampling dimension p = 5: the GPU's growth equals the oracle's RCP
+    # with the same Omega (within 1%); Bunch-Kaufman's growth explodes on Type 1 and is far larger
+    # on the KKT system, while RCP stays within a small factor of Bunch-Parlett's complete pivoting
+    n, b, d, seed = 2048, 64, 5, 1
+    a = inputs.bk_worst(n) if family == "type1" else inputs.kkt(2 * n // 3, n - 2 * n // 3, seed=1)
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, b, d, seed)
+    assert code == 0
+    ref = oracle.rcp(a, oracle.omega(seed, d, n), record=False)
+    rho = oracle.growth_d(ref["Dd"], ref["Ds"], a)
+    assert abs(st.growth_D - rho) <= 0.01 * rho
+    bk, bp = oracle.bk(a), oracle.bp(a)
+    rho_bk = oracle.growth_d(bk["Dd"], bk["Ds"], a)
+    rho_bp = oracle.growth_d(bp["Dd"], bp["Ds"], a)
+    if family == "type1":
+        assert st.growth_D < 1e-3 * rho_bk and st.growth_D < 10.0
+    else:
+        assert st.growth_D < 0.1 * rho_bk
+    assert st.growth_D <= 10.0 * rho_bp
+
+
+def test_kkt_n12288_fp64_and_mixed(rcp, handle):
+    # the saddle-point system [[H, W^T], [W, 0]], H = M M^T / 8192 + 1e-3 I (M 8192 x 8192),
+    # W 4096 x 8192, all N(0, 1): the FP64 factor solves it to FP64 backward error, and the
+    # FP16-split factor with FP64 refinement reaches berr <= 1e-12
+    n1, n2 = 8192, 4096
+    n = n1 + n2
+    A64 = inputs.kkt(n1, n2, m=8192, seed=4, device=DEV)
+    xt = torch.from_numpy(inputs.x_true(n, 1, seed=4)).to(DEV)
+    Bv = (A64 @ xt.T).T.contiguous()
+    A = A64.clone()
+    Dd = torch.zeros(n, dtype=torch.float64, device=DEV)
+    Ds = torch.zeros_like(Dd)
+    perm = torch.zeros(n, dtype=torch.int32, device=DEV)
+    code, st = rcp.rcp_factor(handle, A, Dd, Ds, perm, rcp.make_opts(b=64, d=80, seed=4, prec="fp64"))
+    assert code == 0
+    assert torch.equal(torch.sort(perm.long())[0], torch.arange(n, device=DEV))
+    assert _sampled_reconstruction(A64, A, Dd, Ds, perm) < 1e-12 * max(1.0, st.growth_D) * n / 64
+    assert st.growth_D < 1e3 and st.max_abs_L < 50.0
+    X = Bv.clone()
+    rcp.rcp_solve(handle, A, Dd, Ds, perm, "fp64", X)
+    r = Bv - (A64 @ X.T).T
+    berr = float((r.abs().amax() / (A64.abs().sum(1).amax() * X.abs().amax())))
+    assert berr <= 1e-13
+    del A
+    X = torch.zeros_like(Bv)
+    code, st2 = rcp.rcp_sysv(handle, A64, Bv, X, rcp.make_opts(b=256, d=80, seed=4, prec="f16x3"), tol=1e-12,
+                             max_iter=10)
+    assert code == 0 and st2.berr <= 1e-12
+    r = Bv - (A64 @ X.T).T
+    assert float((r.abs().amax() / (A64.abs().sum(1).amax() * X.abs().amax()))) <= 4e-12
+    del A64, Bv, X, r
+    torch.cuda.empty_cache()
