@@ -78,6 +78,8 @@ def parse(argv=None):
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-n", type=int, default=2048, help="order of the oracle's CPU sample")
+    ap.add_argument("--cpu-scan", default="256,1024,2048",
+                    help="orders at which the oracle is timed once each for the CPU baseline's size scan")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=4096, help="systems of the batched ragged workload (0: skip)")
@@ -180,6 +182,35 @@ def oracle_sample(n: int, kexp: float, reps: int = 1):
         times.append(time.perf_counter() - t0)
         be = oracle.berr(a, xs, rhs.T)
     return times, be, np
+
+
+def host_info():
+    """The host the CPU numbers come from: core count and CPU model."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            low = line.lower()
+            if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
+
+
+def cpu_scan(a):
+    """The oracle (one thread) at several orders of the timed family, each once, with the time
+    extrapolated by n^3 to the timed order (marked as extrapolated)."""
+    out = []
+    for n in [int(x) for x in a.cpu_scan.split(",") if x]:
+        t, be, _ = oracle_sample(n, a.kexp, 1)
+        out.append({"n": n, "s": round(t[0], 3), "tflops": flops(n, 1) / t[0] / 1e12, "berr": be})
+    if out:
+        last = out[-1]
+        out.append({"n": a.n, "s_extrapolated": round(last["s"] * (a.n / last["n"]) ** 3, 1),
+                    "from_n": last["n"], "note": "extrapolated by n^3, not measured"})
+    return out
 
 
 def run_reference(a, rank, world):
@@ -397,7 +428,8 @@ def run_ours(a, rank, world, local_rank):
         v = flops(a.cpu_n, 1) * len(times) / sum(times) / 1e12
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"oracle RCP factor+solve (plain C, FP64, one thread) on the same matrix "
-                                          f"family at n={a.cpu_n}, 2 runs ({sum(times):.1f} s), berr={be:.1e}"}
+                                          f"family at n={a.cpu_n}, 2 runs ({sum(times):.1f} s), berr={be:.1e}",
+                                "host": host_info(), "scan": cpu_scan(a)}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
