@@ -86,6 +86,8 @@ def parse(argv=None):
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-qcompare", action="store_true", help="skip the q = b versus q = 1 comparison")
     ap.add_argument("--no-kkt", action="store_true", help="skip the n = 12288 saddle-point system")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the other conditionings (1e2, 1e6) at n and the n = 32768 system")
     ap.add_argument("--stability", action="store_true",
                     help="instead of timing: the stability diagnostics of the GPU factor for each synthetic "
                          "matrix type of the experiments section (growth, berr, ||L||_1, ||L^-1||_1)")
@@ -379,6 +381,7 @@ def run_ours(a, rank, world, local_rank):
     batched = run_batched(a, dev, stream, rank, world, dist) if a.batch > 0 else None
     qcmp = run_q_compare(a, dev, stream, A64, Bv, seed) if (not a.no_qcompare and rank == 0) else None
     kkt = run_kkt(a, dev, stream) if (not a.no_kkt and rank == 0) else None
+    c3 = run_conditionings(a, dev, stream) if (not a.no_c3 and rank == 0) else None
 
     if rank != 0:
         if dist is not None:
@@ -422,6 +425,7 @@ def run_ours(a, rank, world, local_rank):
         "batched": batched,
         "q_compare": qcmp,
         "kkt": kkt,
+        "conditionings": c3,
     }
     if world == 1 and not a.no_cpu:
         times, be, _ = oracle_sample(a.cpu_n, a.kexp, 2)
@@ -542,6 +546,40 @@ def run_q_compare(a, dev, stream, A64, Bv, seed):
         code, st = rcp.rcp_factor(h, A, Dd, Ds, perm, rcp.make_opts(b=64, d=80, seed=1, prec="fp64", q_mode=q))
         out[name] = {"n": m, "prec": "fp64", "growth_D": st.growth_D, "max_abs_L": st.max_abs_L, "n_2x2": st.n_2x2}
     out["qb_over_q1_time"] = out["qb"]["ms"] / out["q1"]["ms"]
+    return out
+
+
+def run_conditionings(a, dev, stream):
+    """The timed family at the other condition numbers (1e2, 1e6) at the timed order, and at
+    n = 32768 (1e4; b = 128, the widest panel whose W rows fit one CTA's shared memory there): one
+    rcp_sysv each after a warm-up call, time to solution, refinement steps and the backward error
+    checked with torch."""
+    import torch
+
+    from paper_1710_00125_gb300 import inputs, rcp
+    h = rcp.rcp_create()
+    out = []
+    for n, kexp, b in ((a.n, 2.0, a.b), (a.n, 6.0, a.b), (32768, 4.0, 128)):
+        A64 = inputs.spectrum(n, seed=7, kexp=kexp, nrefl=64, device=dev)
+        xt = torch.from_numpy(inputs.x_true(n, 1, seed=7)).to(dev)
+        Bv = (A64 @ xt.T).T.contiguous()
+        X = torch.zeros_like(Bv)
+        o = rcp.make_opts(b=b, d=a.d, seed=7, prec=a.prec)
+        rcp.rcp_sysv(h, A64, Bv, X, o, tol=a.tol, max_iter=a.max_iter)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        code, st = rcp.rcp_sysv(h, A64, Bv, X, o, tol=a.tol, max_iter=a.max_iter)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        r = Bv - (A64 @ X.T).T
+        berr = float((r.abs().amax() / (A64.abs().sum(1).amax() * X.abs().amax())))
+        out.append({"n": n, "kappa": 10 ** kexp, "b": b, "prec": a.prec, "ms": ms,
+                    "tflops": flops(n, 1) / (ms * 1e-3) / 1e12, "code": int(code), "berr": st.berr,
+                    "berr_torch_check": berr, "refine_iters": st.refine_iters, "gmres_iters": st.gmres_iters})
+        del A64, Bv, X, r
+        torch.cuda.empty_cache()
     return out
 
 

@@ -41,10 +41,11 @@ namespace rcpk {
 
 namespace tc {
 
-constexpr int TM = 128;              // tile rows (M) and columns (N)
+constexpr int TM = 128;              // tile rows (M); a super-tile has NT 128-column tiles (N = 128 NT)
 constexpr int TILE_FLOATS = 4096;    // one 128 x 128-byte tile = 16 KB
-constexpr int STAGES = 3;
-constexpr uint32_t STAGE_BYTES = 4u * TILE_FLOATS * 4u;   // W_hi, W_lo, L_hi, L_lo
+constexpr int NT = 2;                // 128 x 256 super-tiles: the W tile of a chunk serves two L tiles
+constexpr int STAGES = NT == 1 ? 3 : 2;
+constexpr uint32_t STAGE_BYTES = (2u + 2u * NT) * TILE_FLOATS * 4u;   // W_hi, W_lo, L_hi x NT, L_lo x NT
 // K chunk: one 128-byte swizzle row, 32 TF32 or 64 FP16 values
 template <bool F16> constexpr int KC = F16 ? 64 : 32;
 
@@ -59,9 +60,11 @@ __device__ __forceinline__ int f16_scale_exp(unsigned long long bits) {
 }
 
 // Instruction descriptors: D = F32, A = B = TF32 (kind::tf32) or F16 (kind::f16), both
-// K-major, N = 128, M = 128.
-constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-constexpr uint32_t IDESC_F16 = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(TM >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// K-major, M = 128, N = 128 NT.
+constexpr uint32_t IDESC_TF32 =
+    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)((TM * NT) >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t IDESC_F16 =
+    (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)((TM * NT) >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 template <bool F16>
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
@@ -168,14 +171,13 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(FactorWork<float> w, float
 //   acce[a]  : the epilogue has read accumulator a (one arrival per epilogue warp)
 // ------------------------------------------------------------------------------------------
 constexpr int TC_EPI_WARPS = 8;
-constexpr int TC_EPI_COLS = tc::TM * 4 / TC_EPI_WARPS;   // columns per epilogue warp
+constexpr int TC_EPI_COLS = tc::TM * tc::NT * 4 / TC_EPI_WARPS;   // columns per epilogue warp
 constexpr int TC_THREADS = 32 * (1 + TC_EPI_WARPS);
 
 
-// Tile order: diagonal by diagonal (delta = I - J = 0, 1, ...; J ascending within a diagonal), so
-// that the ~152 tiles in flight at any time have distinct row blocks I and J: every operand tile
-// is read by one CTA at a time instead of one W tile by all of them at once (row by row order).
-// Diagonal delta holds nrb - delta tiles and starts at C(delta) = delta (2 nrb + 1 - delta) / 2.
+// Tile order with NT = 1: diagonal by diagonal (delta = I - J = 0, 1, ...; J ascending within a
+// diagonal).  Diagonal delta holds nrb - delta tiles and starts at C(delta) = delta (2 nrb + 1 -
+// delta) / 2.
 __device__ __forceinline__ void tile_ij(long long tile, int nrb, int *I, int *J) {
     // FP32 estimate of the root of delta^2 - (2 nrb + 1) delta + 2 tile = 0, corrected in integers
     // (no FP64 on this part's slow FP64 pipe)
@@ -190,13 +192,40 @@ __device__ __forceinline__ void tile_ij(long long tile, int nrb, int *I, int *J)
     *I = *J + dl;
 }
 
+// Super-tiles of NT = 2 column tiles: row block I holds floor(I/2) + 1 of them, column tiles
+// (2 J2, 2 J2 + 1), J2 = 0..floor(I/2) (on even I the last one's second tile lies above the
+// diagonal: computed, never stored).  Rows come in pairs (2P, 2P+1) of P + 1 super-tiles each;
+// P(P + 1) super-tiles precede pair P.  Returns the row block and the first column tile.
+__device__ __forceinline__ void supertile_ij(long long t, int nrb, int *I, int *J0) {
+    if (tc::NT == 1) {
+        tile_ij(t, nrb, I, J0);
+        return;
+    }
+    int P = (int)((sqrtf(4.f * (float)t + 1.f) - 1.f) * 0.5f);
+    if (P < 0) P = 0;
+    while (P > 0 && (long long)P * (P + 1) > t) --P;
+    while ((long long)(P + 1) * (P + 2) <= t) ++P;
+    const int u = (int)(t - (long long)P * (P + 1));
+    const int second = u >= P + 1 ? 1 : 0;
+    *I = 2 * P + second;
+    *J0 = 2 * (u - second * (P + 1));
+}
+
+__host__ __device__ __forceinline__ long long supertile_count(long long nrb) {
+    if (tc::NT == 1) return nrb * (nrb + 1) / 2;
+    const long long m = nrb / 2;
+    return (nrb & 1) ? (m + 1) * (m + 1) : m * (m + 1);
+}
+
 template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<float> w, const float *ops, int nrb_cap,
                                                                     int nkc_cap) {
     constexpr int KC = tc::KC<F16>;
+    constexpr int NT = tc::NT, STAGES = tc::STAGES;
+    constexpr int SN = tc::TM * NT;   // columns of a super-tile (the MMA's N)
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[tc::STAGES];
-    __shared__ __align__(8) uint64_t free_bar[tc::STAGES];
+    __shared__ __align__(8) uint64_t full_bar[STAGES];
+    __shared__ __align__(8) uint64_t free_bar[STAGES];
     __shared__ __align__(8) uint64_t accf[2];
     __shared__ __align__(8) uint64_t acce[2];
     __shared__ uint32_t s_tmem;
@@ -209,24 +238,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
     if (K <= 0 || N <= 0) return;
     const int nrb = (N + tc::TM - 1) / tc::TM, nkc = (K + KC - 1) / KC;
     if (nrb > nrb_cap || nkc > nkc_cap) return;   // prep has flagged it
-    const long long total = (long long)nrb * (nrb + 1) / 2;
+    const long long total = supertile_count(nrb);
     if ((long long)blockIdx.x >= total) return;
-    const int ntiles = (int)((total - blockIdx.x + gridDim.x - 1) / gridDim.x);   // tiles of this CTA
+    const int ntiles = (int)((total - blockIdx.x + gridDim.x - 1) / gridDim.x);   // super-tiles of this CTA
 
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
     float *stage0 = reinterpret_cast<float *>(base);
 
     if (tid == 0) {
-        for (int s = 0; s < tc::STAGES; ++s) { tc::mbar_init(&full_bar[s], 1); tc::mbar_init(&free_bar[s], 1); }
+        for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full_bar[s], 1); tc::mbar_init(&free_bar[s], 1); }
         for (int a = 0; a < 2; ++a) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], TC_EPI_WARPS); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
     if (warp == 0) {
-        // 256 columns: two FP32 128 x 128 accumulators
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" :: "r"(tc::smem_u32(&s_tmem))
-                     : "memory");
+        // two FP32 128 x SN accumulators (2 SN <= 512 columns)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(tc::smem_u32(&s_tmem)), "r"(2 * SN) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc::tc_fence_before();
@@ -240,56 +269,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- producer + MMA issuer ----------------
-            uint32_t full_ph[tc::STAGES] = {0, 0, 0}, free_ph[tc::STAGES] = {0, 0, 0};
-            int used[tc::STAGES] = {0, 0, 0};        // stage has a commit not yet waited for
-            int loaded[tc::STAGES] = {0, 0, 0};      // stage has copies not yet waited for
+            uint32_t full_ph = 0, free_ph = 0;   // phase bit per stage
+            int used[STAGES] = {}, loaded[STAGES] = {};
             uint32_t acce_ph[2] = {0, 0};
-            const int nchunks = ntiles * nkc;          // every chunk of every tile, in order
+            const int nchunks = ntiles * nkc;          // every chunk of every super-tile, in order
             bool ok = true;
             const uint64_t keep = tc::policy_evict_last();
-            auto chunk_src = [&](int g, size_t *ti, size_t *tj) {
-                const int lt = g / nkc, c = g % nkc;
-                int I, J;
-                tile_ij(blockIdx.x + (long long)lt * gridDim.x, nrb, &I, &J);
-                *ti = ((size_t)I * nkc + c) * tc::TILE_FLOATS;
-                *tj = ((size_t)J * nkc + c) * tc::TILE_FLOATS;
-            };
             auto load = [&](int g) -> bool {
-                const int s = g % tc::STAGES;
+                const int s = g % STAGES;
                 if (used[s]) {
-                    if (!tc::mbar_wait(&free_bar[s], free_ph[s])) return false;
-                    free_ph[s] ^= 1u;
+                    if (!tc::mbar_wait(&free_bar[s], (free_ph >> s) & 1u)) return false;
+                    free_ph ^= 1u << s;
                     used[s] = 0;
                 }
-                size_t ti, tj;
-                chunk_src(g, &ti, &tj);
+                const int lt = g / nkc, c = g % nkc;
+                int I, J0;
+                supertile_ij(blockIdx.x + (long long)lt * gridDim.x, nrb, &I, &J0);
+                const size_t ti = ((size_t)I * nkc + c) * tc::TILE_FLOATS;
+                // column tiles past the last row block are not copied: their accumulator columns
+                // belong to columns >= n, which the epilogue never stores
+                const int nj = min(NT, nrb - J0);
                 float *dst = stage0 + (size_t)s * (tc::STAGE_BYTES / 4);
-                tc::mbar_expect_tx(&full_bar[s], tc::STAGE_BYTES);
+                tc::mbar_expect_tx(&full_bar[s], (uint32_t)(2 + 2 * nj) * tc::TILE_FLOATS * 4u);
                 tc::bulk_g2s(dst, whi + ti, tc::TILE_FLOATS * 4, &full_bar[s], keep);
                 tc::bulk_g2s(dst + tc::TILE_FLOATS, wlo + ti, tc::TILE_FLOATS * 4, &full_bar[s], keep);
-                tc::bulk_g2s(dst + 2 * tc::TILE_FLOATS, lhi + tj, tc::TILE_FLOATS * 4, &full_bar[s], keep);
-                tc::bulk_g2s(dst + 3 * tc::TILE_FLOATS, llo + tj, tc::TILE_FLOATS * 4, &full_bar[s], keep);
+                for (int u = 0; u < nj; ++u) {
+                    const size_t tj = ((size_t)(J0 + u) * nkc + c) * tc::TILE_FLOATS;
+                    tc::bulk_g2s(dst + (2 + u) * tc::TILE_FLOATS, lhi + tj, tc::TILE_FLOATS * 4, &full_bar[s], keep);
+                    tc::bulk_g2s(dst + (2 + NT + u) * tc::TILE_FLOATS, llo + tj, tc::TILE_FLOATS * 4, &full_bar[s],
+                                 keep);
+                }
                 loaded[s] = 1;
                 return true;
             };
-            for (int g = 0; g < nchunks && g < tc::STAGES && ok; ++g) ok = load(g);
+            for (int g = 0; g < nchunks && g < STAGES && ok; ++g) ok = load(g);
             for (int g = 0; g < nchunks && ok; ++g) {
                 const int lt = g / nkc, c = g % nkc, a = lt & 1;
-                const uint32_t dacc = tmem + (uint32_t)(a * tc::TM);
+                const uint32_t dacc = tmem + (uint32_t)(a * SN);
                 if (c == 0 && lt >= 2) {
-                    // accumulator a is free once the epilogue has read tile lt - 2
+                    // accumulator a is free once the epilogue has read super-tile lt - 2
                     if (!tc::mbar_wait(&acce[a], acce_ph[a])) { ok = false; break; }
                     acce_ph[a] ^= 1u;
                     tc::tc_fence_after();
                 }
-                const int s = g % tc::STAGES;
-                if (!tc::mbar_wait(&full_bar[s], full_ph[s])) { ok = false; break; }
-                full_ph[s] ^= 1u;
+                const int s = g % STAGES;
+                if (!tc::mbar_wait(&full_bar[s], (full_ph >> s) & 1u)) { ok = false; break; }
+                full_ph ^= 1u << s;
                 loaded[s] = 0;
                 tc::tc_fence_after();
                 const float *st = stage0 + (size_t)s * (tc::STAGE_BYTES / 4);
                 const uint32_t a_hi = tc::smem_u32(st), a_lo = tc::smem_u32(st + tc::TILE_FLOATS);
-                const uint32_t b_hi = tc::smem_u32(st + 2 * tc::TILE_FLOATS), b_lo = tc::smem_u32(st + 3 * tc::TILE_FLOATS);
+                const uint32_t b_hi = tc::smem_u32(st + 2 * tc::TILE_FLOATS);
+                const uint32_t b_lo = tc::smem_u32(st + (2 + NT) * tc::TILE_FLOATS);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const uint32_t off = kk * 32;   // one K-step (8 tf32 or 16 f16) = 32 bytes along the swizzled row
@@ -301,21 +332,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
                 used[s] = 1;
                 if (c == nkc - 1) tc::mma_commit(&accf[a]);
                 // refill the stage of the previous chunk (its MMAs were queued before these)
-                if (g >= 1 && g - 1 + tc::STAGES < nchunks) ok = load(g - 1 + tc::STAGES);
+                if (g >= 1 && g - 1 + STAGES < nchunks) ok = load(g - 1 + STAGES);
             }
             if (!ok) {
                 s_abort = 1;
                 atomicOr(w.status, ST_TIMEOUT);
             }
             // drain the ring before the CTA can leave
-            for (int s = 0; s < tc::STAGES; ++s) {
-                if (loaded[s]) tc::mbar_wait(&full_bar[s], full_ph[s]);
-                if (used[s]) tc::mbar_wait(&free_bar[s], free_ph[s]);
+            for (int s = 0; s < STAGES; ++s) {
+                if (loaded[s]) tc::mbar_wait(&full_bar[s], (full_ph >> s) & 1u);
+                if (used[s]) tc::mbar_wait(&free_bar[s], (free_ph >> s) & 1u);
             }
         }
     } else {
         // ---------------- epilogue warps: lane quarter q, columns h*EC .. h*EC+EC-1 ----------------
         constexpr int EC = TC_EPI_COLS;
+        static_assert(EC % 32 == 0, "pairs of 16-column chunks per epilogue warp");
         const int q = warp & 3, h = (warp - 1) >> 2;
         // FP16: the accumulator holds 2^(sw + sl) W L21^T
         float inv_w = 1.f, inv_l = 1.f;
@@ -328,11 +360,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
         const uint64_t stream = tc::policy_evict_first();   // A22 passes through L2 once per panel
         for (int lt = 0; lt < ntiles; ++lt) {
             const int a = lt & 1;
-            int I, J;
-            tile_ij(blockIdx.x + (long long)lt * gridDim.x, nrb, &I, &J);
+            int I, J0;
+            supertile_ij(blockIdx.x + (long long)lt * gridDim.x, nrb, &I, &J0);
             const int p = kend + I * tc::TM + q * 32 + lane;
-            const int q0 = kend + J * tc::TM + h * EC;
-            // chunks 0 and 1 of the block of A this warp updates, loaded while the MMAs run
+            const int q0 = kend + J0 * tc::TM + h * EC;
+            // the first two 16-column chunks of the block of A this warp updates, loaded while the
+            // MMAs run; every later chunk is loaded two chunks ahead of its use
             const bool rowok = p < n;
             float *blk = A + (size_t)(rowok ? p : 0) + (size_t)q0 * lda;
             float c0v[16], c1v[16];
@@ -367,14 +400,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
                 break;
             }
             tc::tc_fence_after();
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * tc::TM + h * EC);
-            static_assert(EC == 64, "four 16-column chunks per epilogue warp");
-            finish16(c0v, 0, taddr);
-            load16(c0v, 32);
-            finish16(c1v, 16, taddr);
-            load16(c1v, 48);
-            finish16(c0v, 32, taddr);
-            finish16(c1v, 48, taddr);
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * SN + h * EC);
+#pragma unroll 1
+            for (int cb = 0; cb < EC; cb += 32) {
+                finish16(c0v, cb, taddr);
+                if (cb + 32 < EC) load16(c0v, cb + 32);
+                finish16(c1v, cb + 16, taddr);
+                if (cb + 48 < EC) load16(c1v, cb + 48);
+            }
             tc::tc_fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acce[a]);   // the accumulator may be reused
@@ -384,7 +417,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
     __syncthreads();
     tc::tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" :: "r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * SN) : "memory");
 }
 
 size_t tc_ops_floats(int n, int bmax) {
@@ -416,7 +449,7 @@ static cudaError_t launch_trailing_tc_fmt(const FactorWork<float> &w, float *ops
     const long long nrb = rows > 0 ? (rows + tc::TM - 1) / tc::TM : 1;
     tc_prep_kernel<F16><<<8 * sms, 256, 0, s>>>(w, ops, nrb_cap, nkc_cap);
     count_launches(1);
-    const long long tiles = nrb * (nrb + 1) / 2;
+    const long long tiles = supertile_count(nrb);
     const int grid = (int)(tiles < sms ? tiles : sms);
     tc_trailing_kernel<F16><<<grid > 0 ? grid : 1, TC_THREADS, smem, s>>>(w, ops, nrb_cap, nkc_cap);
     count_launches(1);
