@@ -38,12 +38,12 @@ namespace sktc {
 constexpr int TM = 128;                          // columns of B per tile (MMA M)
 constexpr int KC = 32;                           // rows of A per chunk (one 128-byte TF32 row)
 constexpr int STAGES = 3;
-constexpr int LOAD_WARPS = 8, EPI_WARPS = 4;
+constexpr int LOAD_WARPS = 16, EPI_WARPS = 4;
 constexpr int THREADS = 32 * (1 + LOAD_WARPS + EPI_WARPS);
 constexpr int LOAD_THREADS = 32 * LOAD_WARPS;
 constexpr int A_FLOATS = TM * KC;                // one split part of an A chunk: 16 KB
 constexpr int PER = A_FLOATS / LOAD_THREADS;     // values per loader thread and chunk
-static_assert(PER == 16, "loader mapping");
+static_assert(PER == 8, "loader mapping");
 static_assert(EPI_WARPS == 4, "one epilogue warp per tensor-memory lane quarter");
 
 __host__ __device__ constexpr int npad(int d) { return (d + 15) / 16 * 16; }
@@ -107,15 +107,16 @@ __device__ __forceinline__ SkUnit sk_unit(int lu, int Jb, int S, int ksteps, int
     return x;
 }
 
-// Loader mapping of element u (0..15) of a chunk to (m, kk) = (column j0 + m, row k0 + kk).  Above
-// the diagonal block (k < j everywhere) A(k, j) is stored at j + k lda and the lanes run along j;
-// elsewhere the lanes run along k (stored at k + j lda below the diagonal, mixed on it).
+// Loader mapping of element u (0..7) of loader warp lw (0..15) to (m, kk) = (column j0 + m, row
+// k0 + kk) of a chunk.  Above the diagonal block (k < j everywhere) A(k, j) is stored at j + k lda
+// and the lanes run along j; elsewhere the lanes run along k (stored at k + j lda below the
+// diagonal, mixed on it).
 __device__ __forceinline__ void sk_map(bool above, int lw, int lane, int u, int *m, int *kk) {
     if (above) {
         *m = lane + 32 * (u & 3);
-        *kk = lw + 8 * (u >> 2);
+        *kk = lw + 16 * (u >> 2);
     } else {
-        *m = lw + 8 * u;
+        *m = lw + 16 * u;
         *kk = lane;
     }
 }
@@ -237,7 +238,7 @@ sketch_tc_kernel(int n, int d, int np, const float *__restrict__ A, int lda, con
         const int lt = tid - 32, lw = lt >> 5;
         uint32_t free_ph = 0;
         int issued[STAGES] = {0, 0, 0};   // Omega copies issued per stage (thread lt == 0)
-        float cur[PER], nxt[PER];
+        float bufa[PER], bufb[PER];
         auto load_chunk = [&](float (&v)[PER], int j0, int c) {
             const int k0 = c * KC;
             const bool above = UPD || k0 + KC <= j0;
@@ -255,61 +256,73 @@ sketch_tc_kernel(int n, int d, int np, const float *__restrict__ A, int lda, con
                 v[u] = x;
             }
         };
-        int lu = 0;
-        SkUnit x = sk_unit(0, Jb, S, ksteps, c0);
-        int c = x.kb;
-        load_chunk(cur, x.j0, c);
-        for (int g = 0;; ++g) {
-            // the next chunk's loads go out before this chunk's stores
-            int lu2 = lu, c2 = c + 1;
-            SkUnit x2 = x;
-            if (c2 >= x.ke) {
-                ++lu2;
-                if (lu2 < nunits) {
-                    x2 = sk_unit(lu2, Jb, S, ksteps, c0);
-                    c2 = x2.kb;
-                }
+        // two cursors over this CTA's (unit, chunk) sequence: the loads run two chunks ahead of
+        // the stores, alternating between two register buffers
+        struct Cursor {
+            int lu, c;
+            SkUnit x;
+            bool live;
+        };
+        auto first = [&]() { Cursor q{0, 0, sk_unit(0, Jb, S, ksteps, c0), nunits > 0}; q.c = q.x.kb; return q; };
+        auto step = [&](Cursor &q) {
+            if (++q.c < q.x.ke) return;
+            if (++q.lu < nunits) {
+                q.x = sk_unit(q.lu, Jb, S, ksteps, c0);
+                q.c = q.x.kb;
+            } else {
+                q.live = false;
             }
-            const bool more = lu2 < nunits;
-            if (more) load_chunk(nxt, x2.j0, c2);
+        };
+        Cursor ld = first(), pr = first();
+        // store the chunk of buffer v at the stage of chunk g (false: a wait ran out)
+        auto store_chunk = [&](const float (&v)[PER], int g) -> bool {
             const int s = g % STAGES;
             if (g >= STAGES) {
-                bool ok = !*abort_flag && tc::mbar_wait(&free_bar[s], (free_ph >> s) & 1u);
+                const bool ok = !*abort_flag && tc::mbar_wait(&free_bar[s], (free_ph >> s) & 1u);
                 if (!ok) {
                     *abort_flag = 1;
                     atomicOr(status, ST_TIMEOUT);
-                    break;
+                    return false;
                 }
                 free_ph ^= 1u << s;
             }
             float *st = base + (size_t)s * sf;
             if (lt == 0) {
-                const float *src = omt + (size_t)(2 * c) * np * KC;
+                const float *src = omt + (size_t)(2 * pr.c) * np * KC;
                 const uint64_t keep = tc::policy_evict_last();
                 tc::mbar_expect_tx(&om_bar[s], 2 * om_part_bytes);
                 tc::bulk_g2s(st + 2 * A_FLOATS, src, om_part_bytes, &om_bar[s], keep);
                 tc::bulk_g2s(st + 2 * A_FLOATS + np * KC, src + (size_t)np * KC, om_part_bytes, &om_bar[s], keep);
                 ++issued[s];
             }
-            const bool above = UPD || c * KC + KC <= x.j0;
+            const bool above = UPD || pr.c * KC + KC <= pr.x.j0;
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
                 int m, kk;
                 sk_map(above, lw, lane, u, &m, &kk);
                 const int o = tc::swz(m, kk);
-                const float h = tc::tf32_rna(cur[u]);
+                const float h = tc::tf32_rna(v[u]);
                 st[o] = h;
-                st[A_FLOATS + o] = tc::tf32_rna(cur[u] - h);
+                st[A_FLOATS + o] = tc::tf32_rna(v[u] - h);
             }
             tc::fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&full_bar[s]);
-            if (!more) break;
-#pragma unroll
-            for (int u = 0; u < PER; ++u) cur[u] = nxt[u];
-            lu = lu2;
-            x = x2;
-            c = c2;
+            step(pr);
+            return true;
+        };
+        bool fa = ld.live, fb = false;
+        if (fa) { load_chunk(bufa, ld.x.j0, ld.c); step(ld); }
+        fb = ld.live;
+        if (fb) { load_chunk(bufb, ld.x.j0, ld.c); step(ld); }
+        for (int g = 0; fa; g += 2) {
+            if (!store_chunk(bufa, g)) break;
+            fa = ld.live;
+            if (fa) { load_chunk(bufa, ld.x.j0, ld.c); step(ld); }
+            if (!fb) break;
+            if (!store_chunk(bufb, g + 1)) break;
+            fb = ld.live;
+            if (fb) { load_chunk(bufb, ld.x.j0, ld.c); step(ld); }
         }
         // no bulk copy may still be writing this CTA's shared memory when it returns
         if (lt == 0)
