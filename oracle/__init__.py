@@ -221,6 +221,28 @@ def l_norms(L) -> tuple:
     return float(np.abs(L).sum(axis=0).max()), float(np.abs(Li).sum(axis=0).max())
 
 
+def decision_margins(steps, alpha: float = SQRT2_OVER_2) -> list:
+    """(position, margin) of every step of an ``rcp`` record: the closest relative margin of the
+    step's decisions -- the gap between the two largest sketch norms, between the two largest
+    |a_ik| (lambda), and between |a_kk| (|a_rr| in cases 2/3) and alpha lambda.  A computation that
+    rounds differently can decide a step the other way only where its margin is of the order of
+    its rounding error."""
+    out = []
+    for st in steps:
+        m = []
+        if st["norm2"] > 0 and st["norm2_next"] >= 0:
+            m.append((st["norm2"] - st["norm2_next"]) / st["norm2"])
+        lam = st["lam"]
+        if lam > 0:
+            if st["lam_next"] >= 0:
+                m.append((lam - st["lam_next"]) / lam)
+            m.append(abs(st["akk"] - alpha * lam) / (alpha * lam))
+            if st["kase"] >= 2 and st["arr"] >= 0:
+                m.append(abs(st["arr"] - alpha * lam) / (alpha * lam))
+        out.append((st["k"], min(m) if m else float("inf")))
+    return out
+
+
 def block_d(Dd, Ds) -> np.ndarray:
     """The block-diagonal D as a dense matrix."""
     n = len(Dd)

@@ -42,24 +42,6 @@ N, D, SEED = 8192, 80, 0
 OUT = os.path.join(HERE, "c2_n8192.json")
 
 
-def margins(steps, alpha):
-    """Closest decision margin of every step (relative), with the step's position."""
-    out = []
-    for st in steps:
-        m = []
-        if st["norm2"] > 0 and st["norm2_next"] >= 0:
-            m.append((st["norm2"] - st["norm2_next"]) / st["norm2"])
-        lam = st["lam"]
-        if lam > 0:
-            if st["lam_next"] >= 0:
-                m.append((lam - st["lam_next"]) / lam)
-            m.append(abs(st["akk"] - alpha * lam) / (alpha * lam))
-            if st["kase"] >= 2 and st["arr"] >= 0:
-                m.append(abs(st["arr"] - alpha * lam) / (alpha * lam))
-        out.append((st["k"], min(m) if m else float("inf")))
-    return out
-
-
 def main(n=N, path=OUT):
     t0 = time.time()
     a = inputs.gaussian_sym(n, seed=SEED)
@@ -72,7 +54,7 @@ def main(n=N, path=OUT):
     for name, rhs in (("berr_1", rhs1), ("berr_32", rhs32)):
         x = oracle.ldlt_solve(r["L"], r["Dd"], r["Ds"], r["perm"], rhs.T)
         be[name] = oracle.berr(a, x, rhs.T)
-    ties = [[k, m] for k, m in margins(r["steps"], oracle.SQRT2_OVER_2) if m < 1e-6]
+    ties = [[k, m] for k, m in oracle.decision_margins(r["steps"]) if m < 1e-6]
     rec = {
         "_comment": "Written by tests/golden/make_c2_n8192.py from the CPU oracle only "
                     "(Algorithm 1, b = q = 1, eager Schur complement).",

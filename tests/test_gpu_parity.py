@@ -863,3 +863,30 @@ def test_kkt_n12288_fp64_and_mixed(rcp, handle):
     assert float((r.abs().amax() / (A64.abs().sum(1).amax() * X.abs().amax()))) <= 4e-12
     del A64, Bv, X, r
     torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------------------------------------
+# FP32 factors against the oracle, entry by entry, where every decision is well separated
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "f16x3"])
+@pytest.mark.parametrize("n,b,d,seed", [(200, 32, 40, 2), (513, 64, 80, 7)])
+def test_fp32_factor_matches_the_oracle_where_decisions_are_well_separated(rcp, handle, prec, n, b, d, seed):
+    # The FP32 factors take their decisions on FP32 values (rounding ~1e-6 relative here); on inputs
+    # whose every decision in the oracle clears its threshold by more than 2e-4 they must take the
+    # oracle's decisions: the same pivot sequence and 2x2 pattern, and L and D equal to the oracle's
+    # up to the FP32 arithmetic.
+    a = inputs.gaussian_sym(n, seed=seed)
+    ref = oracle.rcp(a, oracle.omega(seed, d, n), record=True)
+    assert min(m for _, m in oracle.decision_margins(ref["steps"])) > 2e-4
+    code, st, A, Dd, Ds, perm = _factor(rcp, handle, a, b, d, seed, prec=prec)
+    assert code == 0
+    assert np.array_equal(perm.cpu().numpy(), ref["perm"])
+    ds = Ds.cpu().numpy()
+    assert np.array_equal(ds != 0.0, ref["Ds"] != 0.0)
+    scale = np.abs(a).max() * max(1.0, st.growth_D)
+    assert np.abs(Dd.cpu().numpy() - ref["Dd"]).max() <= 1e-4 * scale
+    assert np.abs(ds - ref["Ds"]).max() <= 1e-4 * scale
+    assert np.abs(_unit_lower(A) - ref["L"]).max() <= 1e-4 * max(1.0, ref["max_abs_L"])
+    rho = oracle.growth_d(ref["Dd"], ref["Ds"], a)
+    assert abs(st.growth_D - rho) <= 0.01 * rho

@@ -468,3 +468,18 @@ def test_growth_equals_the_largest_entry_of_the_reconstructed_d(n, seed):
     d_full = Li @ a[np.ix_(p, p)] @ Li.T
     rho = np.max(np.abs(d_full)) / np.max(np.abs(a))
     assert oracle.growth_d(r["Dd"], r["Ds"], a) == pytest.approx(rho, rel=1e-10)
+
+
+def test_decision_margins_closed_forms():
+    # Omega = I: the sketch is A itself.  diag(2, 1): squared column norms 4 and 1, lambda = 0 at the
+    # first step, so the only decision is the argmax with relative gap (4 - 1) / 4
+    om = np.eye(2)
+    r = oracle.rcp(np.diag([2.0, 1.0]), om)
+    assert oracle.decision_margins(r["steps"])[0] == (0, pytest.approx(0.75, rel=1e-15))
+    # [[1, t], [t, 1]]: equal column norms (a tie, margin 0)
+    r = oracle.rcp(np.array([[1.0, 0.5], [0.5, 1.0]]), om)
+    assert oracle.decision_margins(r["steps"])[0][1] == 0.0
+    # [[3, 1], [1, 0.5]], Omega = I: norms^2 10 and 1.25; lambda = 1, |a_kk| = 3 against alpha
+    r = oracle.rcp(np.array([[3.0, 1.0], [1.0, 0.5]]), om)
+    want = min((10.0 - 1.25) / 10.0, abs(3.0 - oracle.SQRT2_OVER_2) / oracle.SQRT2_OVER_2)
+    assert oracle.decision_margins(r["steps"])[0][1] == pytest.approx(want, rel=1e-14)
