@@ -103,7 +103,7 @@ def workload_name(a):
 
 def batched_workload_name(a):
     return (f"{a.batch} systems, n_i ~ U{{32..512}} (seeded), A_i = (G_i + G_i^T)/2 with G_i N(0,1), "
-            f"16 RHS b_i = A_i x_i; FP32 factor (d=40, panel width autotuned) + FP64 refinement to berr<={a.tol:g}, "
+            f"16 RHS b_i = A_i x_i; FP32 factor (panel width b autotuned, d = b + 8) + FP64 refinement to berr<={a.tol:g}, "
             f"one persistent launch per phase, replayed from a CUDA graph")
 
 
@@ -457,9 +457,10 @@ def run_batched(a, dev, stream, rank, world, dist):
     inputs.fill_batched_gaussian_device(sizes, bt.off_sq, bt.A64_pool, seed=rank)
     inputs.fill_batched_rhs_device(sizes, bt.off_sq, bt.A64_pool, bt.off_rhs, bt.B_pool, nrhs, seed=rank)
     h = rcp.rcp_create()
-    # the autotuner picks the panel width on this batch; b = 0 then selects it
-    tuned_b, tuned_ms = bt.tune(h, rcp.make_opts(b=0, d=40, seed=rank, prec="fp32"))
-    opts = rcp.make_opts(b=0, d=40, seed=rank, prec="fp32")
+    # the autotuner picks the panel width b on this batch, with the sketch d = b + 8 following it;
+    # b = 0, d = 0 then select the pair
+    tuned_b, tuned_ms = bt.tune(h, rcp.make_opts(b=0, d=0, seed=rank, prec="fp32"))
+    opts = rcp.make_opts(b=0, d=0, seed=rank, prec="fp32")
     s = torch.cuda.Stream(device=dev)
     s.wait_stream(stream)
     with torch.cuda.stream(s):

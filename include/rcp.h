@@ -302,8 +302,8 @@ rcp_status rcp_profile_read(rcp_handle *h, double *ms, int *launches, int nphase
  *   A64     optional (NULL allowed) device array of pointers to FP64 originals (ld lda64[i]):
  *           their lower triangles are first copied (rounded) into A[i] by the same kernel.
  *   Dd, Ds, perm: per-system outputs with the meaning they have for rcp_factor.
- *   opts    b (0: the width chosen by rcp_tune_batched for this nmax/d/precision, else 32),
- *           d (default b + 8, at most 128), seed, alpha, omega as for
+ *   opts    b (0: the shape chosen by rcp_tune_batched for this nmax/d/precision, else 32),
+ *           d (0: b + 8, or the d tuned with b; at most 128), seed, alpha, omega as for
  *           rcp_factor; one Omega (d x nmax) serves every system, system i using its first
  *           n_i columns (the same columns a d x n_i draw with that seed gives).  q_mode 1 only.
  *   info    device [batch]: 0, or 1 + position of the first exactly-zero 1x1 pivot, or -4
@@ -330,11 +330,13 @@ rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, 
 /* rcp_tune_batched -- autotuner of the batched factor: times rcp_factor_batched on the caller's
  *   batch (A64 required: every trial re-copies the originals into A) for every panel width b in
  *   {8, 12, 16, 24, 32, 48, 64} whose per-system state fits one CTA's shared memory, and keeps
- *   the fastest for (nmax, d, FP64 or not) in the handle: later rcp_factor_batched calls with
- *   opts->b == 0 use it.  The width changes only the blocking of the deferred trailing update
- *   (with q = 1 the pivot sequence is the same in exact arithmetic).  Synchronizes the stream;
- *   not for use during stream capture.  best_b / best_ms (host, may be NULL) get the choice and
- *   its factor time. */
+ *   the fastest for (nmax, opts->d, FP64 or not) in the handle: later rcp_factor_batched calls
+ *   with opts->b == 0 and the same opts->d use it.  With opts->d > 0 the width changes only the
+ *   blocking of the deferred trailing update (with q = 1 the pivot sequence is the same in exact
+ *   arithmetic).  With opts->d == 0 the sketch follows the width, d = b + 8 (Algorithm 1's
+ *   d = b + p with oversampling p = 8), and the pair (b, d) is tuned together.  Synchronizes the
+ *   stream; not for use during stream capture.  best_b / best_ms (host, may be NULL) get the
+ *   chosen width and its factor time. */
 rcp_status rcp_tune_batched(rcp_handle *h, int batch, int nmax, const int *n, const double *const *A64,
                             const int *lda64, void *const *A, const int *lda, double *const *Dd,
                             double *const *Ds, int *const *perm, const rcp_opts *opts, int *info,

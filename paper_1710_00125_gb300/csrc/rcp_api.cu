@@ -65,8 +65,8 @@ struct rcp_handle {
     int bord_batch = -1, bord_nmax = -1;
     uint64_t bom_seed = 0;                         // (seed, d, nmax, fp64) of the drawn Omega
     int bom_d = -1, bom_nmax = -1, bom_f64 = -1;
-    struct Tuned { int nmax, d, f64, b; };
-    std::vector<Tuned> tuned;                      // batched panel widths chosen by rcp_tune_batched
+    struct Tuned { int nmax, dkey, f64, b, d; };   // dkey: the caller's d (0: d = b + 8 tuned with b)
+    std::vector<Tuned> tuned;                      // batched shapes chosen by rcp_tune_batched
     cudaStream_t copy_stream = nullptr;            // rcp_sysv with host buffers: block copies of A
     std::vector<cudaEvent_t> copy_events;          //   one per block, and one for the start
     Buf gmV, gmZ, gmP, gmH;                        // GMRES refinement: basis, zero vector, partial sums, scalars
@@ -1061,10 +1061,11 @@ rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, 
     if (!valid_prec(prec)) return RCP_EINVAL;
     const bool f64 = prec == RCP_FP64;
     int b = (opts && opts->b > 0) ? opts->b : 32;
-    const int d = (opts && opts->d > 0) ? opts->d : std::min(b + 8, 128);
+    const int dkey = (opts && opts->d > 0) ? opts->d : 0;
+    int d = dkey > 0 ? dkey : std::min(b + 8, 128);
     if (!(opts && opts->b > 0))
         for (const auto &t : h->tuned)
-            if (t.nmax == nmax && t.d == d && t.f64 == (int)f64) b = t.b;   // the autotuned width
+            if (t.nmax == nmax && t.dkey == dkey && t.f64 == (int)f64) { b = t.b; d = t.d; }   // the autotuned shape
     if (opts && opts->q_mode != 0 && opts->q_mode != 1) return RCP_EUNSUPPORTED;
     if (opts && opts->guard_r != 0) return RCP_EUNSUPPORTED;   // the safeguard is host-driven per system
     if (b > 512 || d > 128) return RCP_EUNSUPPORTED;
@@ -1111,22 +1112,23 @@ rcp_status rcp_tune_batched(rcp_handle *h, int batch, int nmax, const int *n, co
     const rcp_prec prec = opts ? opts->prec : RCP_FP64;
     if (!valid_prec(prec)) return RCP_EINVAL;
     const bool f64 = prec == RCP_FP64;
-    const int d = (opts && opts->d > 0) ? opts->d : 40;
+    const int dkey = (opts && opts->d > 0) ? opts->d : 0;   // 0: d = b + 8 follows each width
     cudaStream_t s = (cudaStream_t)stream;
     rcp_opts o = opts ? *opts : rcp_opts{};
-    o.d = d;
     o.prec = prec;
     static const int cand[] = {8, 12, 16, 24, 32, 48, 64};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CU_TRY(cudaEventCreate(&e0));
     CU_TRY(cudaEventCreate(&e1));
-    int bb = 0;
+    int bb = 0, bd = 0;
     float bms = 0.f;
     rcp_status err = RCP_OK;
     for (int b : cand) {
+        const int d = dkey > 0 ? dkey : std::min(b + 8, 128);
         const size_t smem = f64 ? batched_factor_smem<double>(d, b, nmax) : batched_factor_smem<float>(d, b, nmax);
         if (smem > batched_max_smem()) continue;
         o.b = b;
+        o.d = d;
         err = rcp_factor_batched(h, batch, nmax, n, A64, lda64, A, lda, Dd, Ds, perm, &o, info, stream);   // warm-up
         if (err != RCP_OK) break;
         if (cudaEventRecord(e0, s) != cudaSuccess) { err = RCP_ECUDA; break; }
@@ -1135,7 +1137,7 @@ rcp_status rcp_tune_batched(rcp_handle *h, int batch, int nmax, const int *n, co
         if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { err = RCP_ECUDA; break; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (bb == 0 || ms < bms) { bb = b; bms = ms; }
+        if (bb == 0 || ms < bms) { bb = b; bd = d; bms = ms; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1144,8 +1146,8 @@ rcp_status rcp_tune_batched(rcp_handle *h, int batch, int nmax, const int *n, co
     if (bb == 0) return RCP_EUNSUPPORTED;
     bool found = false;
     for (auto &t : h->tuned)
-        if (t.nmax == nmax && t.d == d && t.f64 == (int)f64) { t.b = bb; found = true; }
-    if (!found) h->tuned.push_back({nmax, d, (int)f64, bb});
+        if (t.nmax == nmax && t.dkey == dkey && t.f64 == (int)f64) { t.b = bb; t.d = bd; found = true; }
+    if (!found) h->tuned.push_back({nmax, dkey, (int)f64, bb, bd});
     if (best_b) *best_b = bb;
     if (best_ms) *best_ms = bms;
     return RCP_OK;

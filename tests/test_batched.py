@@ -254,16 +254,29 @@ def test_batched_invalid_arguments(rcp, handle):
     assert e.value.code == -7
 
 
-def test_batched_autotuner(rcp, handle):
+@pytest.mark.parametrize("d", [40, 0])
+def test_batched_autotuner(rcp, handle, d):
+    # d = 40: the width alone is tuned; d = 0: the sketch follows the width (d = b + 8)
     sizes = inputs.batched_sizes(20, 32, 300, seed=5).tolist()
     mats = inputs.batched_gaussian(sizes, seed=5)
     bt = rcp.Batch(sizes, 1, prec="fp32", device=DEV)
     _load(bt, mats)
-    b, ms = bt.tune(handle, rcp.make_opts(b=0, d=40, seed=2, prec="fp32"))
+    h = rcp.rcp_create()
+    b, ms = bt.tune(h, rcp.make_opts(b=0, d=d, seed=2, prec="fp32"))
     assert b in (8, 12, 16, 24, 32, 48, 64) and ms > 0
-    bt.factor(handle, rcp.make_opts(b=0, d=40, seed=2, prec="fp32"))   # uses the tuned width
+    # the explicit shape the tuner chose gives the same factorization as b = 0
+    _load(bt, mats)
+    bt.factor(h, rcp.make_opts(b=b, d=d if d else b + 8, seed=2, prec="fp32"))
+    torch.cuda.synchronize()
+    perms = [bt.perm(i).cpu().numpy().copy() for i in range(len(sizes))]
+    dds = [bt.dd(i).cpu().numpy().copy() for i in range(len(sizes))]
+    _load(bt, mats)
+    bt.factor(h, rcp.make_opts(b=0, d=d, seed=2, prec="fp32"))   # uses the tuned shape
     torch.cuda.synchronize()
     assert (bt.info == 0).all()
+    for i in range(len(sizes)):
+        assert np.array_equal(bt.perm(i).cpu().numpy(), perms[i]), i
+        assert np.array_equal(bt.dd(i).cpu().numpy(), dds[i]), i
     for i, a in enumerate(mats):
         n = a.shape[0]
         L = _unit_lower(bt.f(i))
