@@ -164,7 +164,14 @@ __device__ __forceinline__ unsigned long long ld_key(const unsigned long long *p
 
 // Ring of key slots indexed by the grid-barrier generation; the slot of generation g + KEY_RING/2
 // is cleared (by one CTA) after the key of generation g is read, so a slot is zero when reused.
+// Each slot has a 128-byte line of its own (KEY_STRIDE words), so that the clearing store and
+// the red.max of the current generation do not meet on one line.
 constexpr int KEY_RING = 16;
+constexpr int KEY_STRIDE = 16;
+
+__device__ __forceinline__ unsigned long long *key_slot(unsigned long long *ring, unsigned g) {
+    return ring + (size_t)(g % KEY_RING) * KEY_STRIDE;
+}
 
 // Maximum of a packed key over the warp (the result in every lane): redux.sync on the high
 // words, then on the low words among the lanes holding the maximal high word.

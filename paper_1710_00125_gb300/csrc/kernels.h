@@ -13,7 +13,7 @@ constexpr int PANEL_TRACE_SLOTS = 16;
 // slot is indexed by the grid-barrier generation and cleared half a ring ahead of its use, which
 // assumes consecutive generations: a cooperative kernel that advances the generation without the
 // panel's clearing (the block QRCP) zeroes all of them.
-constexpr int PANEL_KEY_WORDS = 32;
+constexpr int PANEL_KEY_WORDS = 512;   // two key rings of 16 slots, one 128-byte line per slot
 
 // Omega (d x n) from Philox counter (j, t, stream, 0) and key (seed, 0)
 template <typename T>

@@ -152,7 +152,7 @@ __device__ __forceinline__ SlotWin slot_reduce(const double *slots, int G) {
     return b;   // valid in lane 0
 }
 
-static_assert(2 * KEY_RING <= PANEL_KEY_WORDS, "the pivot and speculative key rings");
+static_assert(2 * KEY_RING * KEY_STRIDE <= PANEL_KEY_WORDS, "the pivot and speculative key rings");
 
 // Block-wide maximum of two packed keys per thread (the result to every thread): per warp two
 // 32-bit redux.sync per key (high word, then the low word among the lanes holding the maximal
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     double *rec1 = w.s1v, *rec2 = w.s2v;   // per-CTA records (4 doubles each)
     unsigned long long *keys = w.keys;
     // speculative case-(1) state (FP32 path with room for the shadow sketch)
-    unsigned long long *spec_keys = (KEYS && w.spec) ? w.keys + KEY_RING : nullptr;
+    unsigned long long *spec_keys = (KEYS && w.spec) ? w.keys + KEY_RING * KEY_STRIDE : nullptr;
     T *spec_pay = w.pay + (size_t)2 * G * ps;                 // [2][G][d], by barrier parity
     double *spec_rec = w.s3v;                                  // [2][G][4]
     bool have_next = false;
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             if (KEYS) {
                 if (c.phys >= 0) {
                     stcg(reinterpret_cast<T *>(rec1 + 4 * (size_t)cta), dg[c.phys - j_lo]);
-                    red_max_u64(keys + (g1 % KEY_RING), make_key((float)c.v, c.lpos, c.phys));
+                    red_max_u64(key_slot(keys, g1), make_key((float)c.v, c.lpos, c.phys));
                 }
             } else {
                 const double dgc = c.phys >= 0 ? (double)dg[c.phys - j_lo] : 0.0;
@@ -444,10 +444,10 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         PANEL_MARK(2);
         if (KEYS) {
             if (tid == 0) {
-                const unsigned long long key = ld_key(keys + (g1 % KEY_RING));
+                const unsigned long long key = ld_key(key_slot(keys, g1));
                 if (cta == 0) {
-                    keys[(g1 + KEY_RING / 2) % KEY_RING] = 0ull;
-                    if (spec_keys) spec_keys[(g1 + KEY_RING / 2) % KEY_RING] = 0ull;
+                    *key_slot(keys, g1 + KEY_RING / 2) = 0ull;
+                    if (spec_keys) *key_slot(spec_keys, g1 + KEY_RING / 2) = 0ull;
                 }
                 if (key != 0ull) {
                     s_i[1] = (int)(key & 0xFFFFull);
@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                     T *rp = reinterpret_cast<T *>(rec2 + 4 * (size_t)cta);
                     stcg(rp, c1[jc]);
                     stcg(rp + 1, dg[jc]);
-                    red_max_u64(keys + (g2 % KEY_RING), kl);
+                    red_max_u64(key_slot(keys, g2), kl);
                 }
             }
             if (ks != 0ull) {
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                     T *rp = reinterpret_cast<T *>(spec_rec + (size_t)(par * G + cta) * 4);
                     stcg(rp, dnew);
                     stcg(rp + 1, l1);
-                    red_max_u64(spec_keys + (g2 % KEY_RING), ks);
+                    red_max_u64(key_slot(spec_keys, g2), ks);
                 }
             }
         } else {
@@ -674,9 +674,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         PANEL_MARK(6);
         if (KEYS) {
             if (tid == 0) {
-                const unsigned long long key = ld_key(keys + (g2 % KEY_RING));
-                const unsigned long long key3 = spec ? ld_key(spec_keys + (g2 % KEY_RING)) : 0ull;
-                if (cta == 0) keys[(g2 + KEY_RING / 2) % KEY_RING] = 0ull;
+                const unsigned long long key = ld_key(key_slot(keys, g2));
+                const unsigned long long key3 = spec ? ld_key(key_slot(spec_keys, g2)) : 0ull;
+                if (cta == 0) *key_slot(keys, g2 + KEY_RING / 2) = 0ull;
                 int R = -1, LR = -1;
                 T lam = T(0);
                 if (key != 0ull) {
@@ -704,7 +704,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                     s_i[8] = akkT != T(0);
                 }
                 s_i[9] = 0;
-                if (spec_keys && cta == 0) spec_keys[(g2 + KEY_RING / 2) % KEY_RING] = 0ull;
+                if (spec_keys && cta == 0) *key_slot(spec_keys, g2 + KEY_RING / 2) = 0ull;
                 if (spec) {
                     if ((kase == 0 || kase == 1) && key3 != 0ull) {
                         s_i[9] = 1;   // commit the speculation
@@ -1072,11 +1072,11 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) exchange_probe_kernel(unsign
     unsigned long long acc = 0ull;
     for (int r = 0; r < rounds; ++r) {
         if (threadIdx.x == 0)
-            red_max_u64(keys + (r % KEY_RING), make_key((float)(blockIdx.x + 1), r & 0xFFFF, (int)blockIdx.x));
+            red_max_u64(key_slot(keys, (unsigned)r), make_key((float)(blockIdx.x + 1), r & 0xFFFF, (int)blockIdx.x));
         if (!grid_barrier(bar, base + (unsigned)(r + 1) * G, status)) return;
         if (threadIdx.x == 0) {
-            acc += ld_key(keys + (r % KEY_RING)) & 0xFFFFull;   // the winning CTA of the round
-            if (blockIdx.x == 0) keys[(r + KEY_RING / 2) % KEY_RING] = 0ull;
+            acc += ld_key(key_slot(keys, (unsigned)r)) & 0xFFFFull;   // the winning CTA of the round
+            if (blockIdx.x == 0) *key_slot(keys, (unsigned)(r + KEY_RING / 2)) = 0ull;
         }
         __syncthreads();
     }

@@ -316,12 +316,12 @@ __global__ void __launch_bounds__(QR_THREADS, 1) qrcp_keys_kernel(FactorWork<flo
         if (kc != 0ull) {
             const int jc = (int)(kc & 0xFFFFull);
             for (int r = t + tid; r < d; r += QR_THREADS) stcg(pay + (size_t)cta * d + r, Wk[(size_t)jc * d + r]);
-            if (tid == 0) red_max_u64(keys + (g % KEY_RING), (kc & ~0xFFFFull) | (unsigned long long)cta);
+            if (tid == 0) red_max_u64(key_slot(keys, g), (kc & ~0xFFFFull) | (unsigned long long)cta);
         }
         if (!grid_barrier(w.bar, base + (++nbar) * (unsigned)G, w.status)) return;
         if (tid == 0) {
-            const unsigned long long kw = ld_key(keys + (g % KEY_RING));
-            if (cta == 0) keys[(g + KEY_RING / 2) % KEY_RING] = 0ull;
+            const unsigned long long kw = ld_key(key_slot(keys, g));
+            if (cta == 0) *key_slot(keys, g + KEY_RING / 2) = 0ull;
             const float v = __uint_as_float((unsigned)(kw >> 32));
             s_i[2] = kw != 0ull && isfinite(v) ? 0xFFFF - (int)((kw >> 16) & 0xFFFFull) : -1;
             s_i[3] = (int)(kw & 0xFFFFull);
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(QR_THREADS, 1) qrcp_keys_kernel(FactorWork<flo
     {
         const unsigned g = gbase + nbar + 1;
         if (!grid_barrier(w.bar, base + (++nbar) * (unsigned)G, w.status)) return;
-        if (cta == 0 && tid == 0) keys[(g + KEY_RING / 2) % KEY_RING] = 0ull;   // the ring stays in step
+        if (cta == 0 && tid == 0) *key_slot(keys, g + KEY_RING / 2) = 0ull;   // the ring stays in step
     }
     for (int jl = warp; jl < cnt; jl += QR_WARPS) {
         const int idx = chosen[jl];
