@@ -957,13 +957,25 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         int jl = e / d, r = e - jl * d;
         if (alive[jl] || w.qb) w.B[(size_t)r + (size_t)lp[jl] * d] = Bs[(size_t)jl * ds + r];
     }
-    for (int jl = tid; jl < cnt; jl += PANEL_THREADS) {
-        int j = j_lo + jl;
-        w.lpos[j] = lp[jl];
-        if (lp[jl] != j) {
-            int idx = atomicAdd(&w.st->n_moved, 1);
-            if (idx < w.maxmoved) w.moved[idx] = j;
-            else atomicOr(w.status, ST_INTERNAL);
+    // the moved rows, appended with one atomic per warp (the CTAs that own the panel's
+    // positions move nearly every row)
+    for (int base = 0; base < cnt; base += PANEL_THREADS) {
+        const int jl = base + tid, j = j_lo + jl;
+        bool mv = false;
+        if (jl < cnt) {
+            w.lpos[j] = lp[jl];
+            mv = lp[jl] != j;
+        }
+        const unsigned bal = __ballot_sync(FULL, mv);
+        if (bal != 0u) {
+            int first = 0;
+            if (lane == 0) first = atomicAdd(&w.st->n_moved, __popc(bal));
+            first = __shfl_sync(FULL, first, 0);
+            if (mv) {
+                const int idx = first + __popc(bal & ((1u << lane) - 1u));
+                if (idx < w.maxmoved) w.moved[idx] = j;
+                else atomicOr(w.status, ST_INTERNAL);
+            }
         }
     }
     // per-CTA statistics
