@@ -241,6 +241,15 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
  */
 rcp_status rcp_profile(rcp_handle *h, int enable);
 
+/* How the FP32 panel speculates on SBKP case (1) of the next pivot step while it waits at a pivot
+ * step's grid barrier (an implementation choice; Algorithm 1 has no counterpart, and every mode
+ * gives bit-identical factors): -1 automatic (the default: with a shadow copy of the CTA's sketch
+ * columns when it fits in shared memory, else with the confirmed sketch update deferred to the next
+ * step's pass), 0 off (two grid exchanges per pivot step), 1 shadow copy, 2 deferred update.  A
+ * forced mode whose shared memory does not fit makes the factorization return RCP_EUNSUPPORTED.
+ * Applies to the handle's later FP32 factorizations with q = 1; RCP_EINVAL for other values. */
+rcp_status rcp_set_speculation(rcp_handle *h, int mode);
+
 /* With rcp_profile(h, 2), the next factorizations also record, for every pivot position k,
  * sixteen SM clock stamps (clock64 of one thread of the first CTA) at fixed points of the panel
  * step (top, before/after barrier 1, Schur column P, before/after barrier 2, decision, column r,

@@ -46,7 +46,8 @@ __host__ __device__ constexpr int quad_stride(int x) { return x + ((36 - (x % 32
 template <typename T>
 size_t panel_smem_bytes(int d, int bw, int chunk_cap, int spec) {
     size_t s = 0;
-    if (spec) s += (size_t)chunk_cap * (quad_stride(d) + 1) * sizeof(T) + 16;   // shadow sketch + norms
+    if (spec == 1) s += (size_t)chunk_cap * (quad_stride(d) + 1) * sizeof(T) + 16;   // shadow sketch + norms
+    if (spec == 2) s += ((size_t)2 * chunk_cap + d) * sizeof(T) + 16;   // deferred: norms, multipliers, pivot column
     s += (size_t)chunk_cap * sizeof(double);           // nrm (T, padded to 8 bytes)
     s += (size_t)chunk_cap * quad_stride(d) * sizeof(T);    // Bs
     s += (size_t)chunk_cap * quad_stride(bw) * sizeof(T);   // Ws
@@ -285,7 +286,9 @@ __device__ void sbkp_scalars(int kase, double akk, double lam, double ark, doubl
     s_i[8] = dpiv != 0.0;
 }
 
-template <typename T>
+// DEF: the speculative sketch update is deferred to the next step's pass (w.spec == 2, FP32 only);
+// a separate instantiation, so that the shadow-copy kernel carries none of its code.
+template <typename T, bool DEF>
 __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w) {
     constexpr bool KEYS = std::is_same<T, float>::value;   // packed-key argmax (FP32 values)
     extern __shared__ __align__(16) unsigned char smem[];
@@ -339,8 +342,15 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
     int *win = alive + cap;           // positions k0 .. k0 + bw + 2
     int *ckind = win + (bw + 3);      // per panel column: 0 zero, 1 scalar, 3/4 first/second of 2x2
     // shadow sketch columns and norms for the speculative case-(1) update (when w.spec)
+    // shadow sketch columns and norms for the speculative case-(1) update (w.spec == 1), or, when
+    // the shadow does not fit (w.spec == 2, deferred), only the norms, each row's multiplier of the
+    // speculative update (l1s) and the pivot's sketch column of a confirmed update not yet applied
     T *Bs2 = reinterpret_cast<T *>(ckind + bw);
-    T *nrm2 = Bs2 + (w.spec ? (size_t)cap * ds : 0);
+    T *nrm2 = Bs2 + (w.spec == 1 ? (size_t)cap * ds : 0);
+    T *l1s = nrm2 + cap;
+    T *bPd = l1s + cap;
+    constexpr bool deferred = KEYS && DEF;
+    bool pend = false;   // deferred: a confirmed speculative sketch update (bPd, l1s) awaits the next pass
     const int wsz = bw + 3;
 
     const T *__restrict__ A = w.A;
@@ -548,7 +558,41 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 if (sub == 0 && jl < cnt) c1[jl] = cv;
                 const bool live = in && j_lo + jl != P;
                 T sacc = T(0);
-                if (spec && live) {
+                if (deferred) {
+                    // the confirmed speculative update of the previous step, in place, on every live
+                    // row (with the operations the shadow sketch uses), then this step's speculative
+                    // update for its norm only; the row's multiplier is kept for the next pass
+                    const bool app = pend && in, sp = spec && live;
+                    const T l0 = app ? l1s[jl] : T(0);
+                    const T l1 = cv * f;
+                    __syncwarp();   // every lane of the quad has read l1s[jl] before it is rewritten
+                    if (app || sp) {
+                        T *col = Bs + (size_t)jl * ds;
+                        for (int r0 = sub; r0 < d; r0 += 20) {
+                            T v[5], pd[5], pb[5];
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) {
+                                const int r = r0 + 4 * q;
+                                v[q] = r < d ? col[r] : T(0);
+                                pd[q] = (app && r < d) ? bPd[r] : T(0);
+                                pb[q] = (sp && r < d) ? bP[r] : T(0);
+                            }
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) {
+                                const int r = r0 + 4 * q;
+                                if (app) {
+                                    v[q] = v[q] - pd[q] * l0;
+                                    if (r < d) col[r] = v[q];
+                                }
+                                if (sp) {
+                                    const T x = v[q] - pb[q] * l1;
+                                    sacc = fma(x, x, sacc);
+                                }
+                            }
+                        }
+                    }
+                    if (sp && sub == 0) l1s[jl] = l1;
+                } else if (spec && live) {
                     const T l1 = cv * f;
                     const T *col = Bs + (size_t)jl * ds;
                     T *col2 = Bs2 + (size_t)jl * ds;
@@ -583,6 +627,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                     }
                 }
             }
+            pend = false;   // (deferred) applied to every live row above
         } else {
             schur_column<T>(A, lda, j_lo, cnt, P, i, ws, Ws, payP, bP, w.Lg + (size_t)P * bw, lP, d,
                             alive, c1, recP, s_x + 8, 0, NoHook{}, false, T(0), T(0));
@@ -611,7 +656,8 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 const int jc = (int)(ks & 0xFFFFull) - j_lo;
                 T *dst = spec_pay + (size_t)(par * G + cta) * ps;
                 const int r = tid - 256;
-                if (r >= 0 && r < d) stcg(dst + r, Bs2[(size_t)jc * ds + r]);
+                if (r >= 0 && r < d)
+                    stcg(dst + r, deferred ? (T)(Bs[(size_t)jc * ds + r] - bP[r] * l1s[jc]) : Bs2[(size_t)jc * ds + r]);
                 if (tid == 384) {
                     const T cv = c1[jc], l1 = cv * fk;
                     const T dnew = fma(-cv, l1, dg[jc]);
@@ -757,7 +803,13 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             PANEL_MARK(13);
             for (int jl = tid; jl < cnt; jl += PANEL_THREADS)
                 if (j_lo + jl == P) alive[jl] = 0;
-            { T *t = Bs; Bs = Bs2; Bs2 = t; t = nrm; nrm = nrm2; nrm2 = t; t = dg; dg = dg2; dg2 = t; }
+            if (deferred) {
+                // the sketch update stays pending (bPd, l1s) until the next pass
+                T *t = nrm; nrm = nrm2; nrm2 = t; t = dg; dg = dg2; dg2 = t;
+                pend = true;
+            } else {
+                T *t = Bs; Bs = Bs2; Bs2 = t; t = nrm; nrm = nrm2; nrm2 = t; t = dg; dg = dg2; dg2 = t;
+            }
             if (tid == 0) {
                 ckind[i] = (kase == 0 || !s_i[8]) ? 0 : 1;
                 cs0[i] = s_t[6];
@@ -779,7 +831,10 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
                 s_x[8] = prec_d;            // a_kk of P2 after this step
                 lP[i] = prec_l;             // L(P2, k)
             }
-            if (tid < d) bP[tid] = pb;
+            if (tid < d) {
+                if (deferred) bPd[tid] = bP[tid];   // the committed pivot's sketch column
+                bP[tid] = pb;
+            }
             if (tid < i) lP[tid] = pl;
             have_next = true;
             ++run1;
@@ -941,6 +996,14 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
 
     // ---------------- epilogue: publish the panel in logical order ----------------
     __syncthreads();
+    if (pend) {
+        // deferred: a confirmed speculative update that no later pass applied (the loop ended)
+        for (int e = tid; e < cnt * d; e += PANEL_THREADS) {
+            const int jl = e / d, r = e - jl * d;
+            if (alive[jl]) Bs[(size_t)jl * ds + r] = Bs[(size_t)jl * ds + r] - bPd[r] * l1s[jl];
+        }
+        __syncthreads();
+    }
     T amw = T(0), aml = T(0);   // max |W| and |L| over the rows left for the trailing update
     for (int e = tid; e < cnt * i; e += PANEL_THREADS) {
         int t = e / cnt, jl = e - t * cnt;
@@ -1031,7 +1094,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
 
 // Largest dynamic shared memory the panel kernel may request (opt-in limit minus its static
 // shared memory); the attribute is set once per instantiation.
-template <typename T>
+template <typename T, bool DEF>
 static size_t panel_dyn_limit() {
     static size_t limit = 0;
     if (limit == 0) {
@@ -1039,9 +1102,9 @@ static size_t panel_dyn_limit() {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, panel_kernel<T>) != cudaSuccess) return 0;
+        if (cudaFuncGetAttributes(&fa, panel_kernel<T, DEF>) != cudaSuccess) return 0;
         size_t lim = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
-        if (cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim) != cudaSuccess)
+        if (cudaFuncSetAttribute(panel_kernel<T, DEF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim) != cudaSuccess)
             return 0;
         limit = lim;
     }
@@ -1051,11 +1114,19 @@ static size_t panel_dyn_limit() {
 template <typename T>
 cudaError_t launch_panel(const FactorWork<T> &w, cudaStream_t s) {
     size_t smem = panel_smem_bytes<T>(w.d, w.bw, w.chunk_cap, w.spec);
-    if (smem > panel_dyn_limit<T>()) return cudaErrorInvalidValue;
     FactorWork<T> arg = w;
     void *args[] = {&arg};
+    if constexpr (std::is_same<T, float>::value) {
+        if (w.spec == 2) {
+            if (smem > panel_dyn_limit<T, true>()) return cudaErrorInvalidValue;
+            count_launches(1);
+            return cudaLaunchCooperativeKernel((const void *)panel_kernel<T, true>, dim3(w.grid), dim3(PANEL_THREADS), args,
+                                               smem, s);
+        }
+    }
+    if (smem > panel_dyn_limit<T, false>()) return cudaErrorInvalidValue;
     count_launches(1);
-    return cudaLaunchCooperativeKernel((const void *)panel_kernel<T>, dim3(w.grid), dim3(PANEL_THREADS), args, smem, s);
+    return cudaLaunchCooperativeKernel((const void *)panel_kernel<T, false>, dim3(w.grid), dim3(PANEL_THREADS), args, smem, s);
 }
 
 // Largest cooperative grid for the given per-CTA workspace (0 if it does not fit).
@@ -1065,8 +1136,17 @@ int panel_max_grid(int d, int bw, int chunk_cap, int spec) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     size_t smem = panel_smem_bytes<T>(d, bw, chunk_cap, spec);
-    if (smem > panel_dyn_limit<T>()) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_kernel<T>, PANEL_THREADS, smem) != cudaSuccess) return 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (spec == 2) {
+            if (smem > panel_dyn_limit<T, true>()) return 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_kernel<T, true>, PANEL_THREADS, smem) != cudaSuccess)
+                return 0;
+            return per * sms;
+        }
+    }
+    if (smem > panel_dyn_limit<T, false>()) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, panel_kernel<T, false>, PANEL_THREADS, smem) != cudaSuccess)
+        return 0;
     return per * sms;
 }
 

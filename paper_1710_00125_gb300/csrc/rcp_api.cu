@@ -45,6 +45,7 @@ struct EventPair {
 struct rcp_handle {
     int device = 0;
     int profiling = 0;
+    int spec_mode = -1;                            // FP32 panel speculation (rcp_set_speculation)
     std::vector<EventPair> events;      // recorded pairs of the calls since the last read
     std::vector<cudaEvent_t> pool;      // free events
     int launches[PH_COUNT] = {0};
@@ -164,7 +165,7 @@ int sm_count() {
     return sms > 0 ? sms : 1;
 }
 
-rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
+rcp_status resolve(int n, const rcp_opts *o, Resolved &r, int spec_mode = -1) {
     r.prec = o ? o->prec : RCP_FP64;
     if (r.prec < RCP_FP64 || r.prec > RCP_F16X3) return RCP_EINVAL;
     r.b = (o && o->b > 0) ? o->b : 64;
@@ -194,7 +195,8 @@ rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
     g = std::max(1, g);
     r.chunk_cap = (n + g - 1) / g;
     if (r.chunk_cap > 1024) return RCP_EUNSUPPORTED;
-    // the FP32 panel speculates on SBKP case (1) when its shadow norms fit in shared memory
+    // the FP32 panel speculates on SBKP case (1): with a shadow copy of its sketch columns when that
+    // fits in shared memory, else with the sketch update deferred to the next step's pass
     r.spec = 0;
     if (r.qb) {
         // q = b: the block QRCP keeps its chunk of the sketch in shared memory, and the block
@@ -208,9 +210,20 @@ rcp_status resolve(int n, const rcp_opts *o, Resolved &r) {
     } else if (f64) {
         maxg = panel_max_grid<double>(r.d, r.bw, r.chunk_cap, 0);
     } else {
-        maxg = panel_max_grid<float>(r.d, r.bw, r.chunk_cap, 1);
-        if (maxg >= g) r.spec = 1;
-        else maxg = panel_max_grid<float>(r.d, r.bw, r.chunk_cap, 0);
+        // speculation with the shadow sketch (1), else with the deferred sketch update (2), else
+        // none; spec_mode forces one of them (-1: this order)
+        if (spec_mode == -1 || spec_mode == 1) {
+            const int m1 = panel_max_grid<float>(r.d, r.bw, r.chunk_cap, 1);
+            if (m1 >= g) { r.spec = 1; maxg = m1; }
+        }
+        if (r.spec == 0 && (spec_mode == -1 || spec_mode == 2)) {
+            const int m2 = panel_max_grid<float>(r.d, r.bw, r.chunk_cap, 2);
+            if (m2 >= g) { r.spec = 2; maxg = m2; }
+        }
+        if (r.spec == 0) {
+            if (spec_mode == 1 || spec_mode == 2) return RCP_EUNSUPPORTED;
+            maxg = panel_max_grid<float>(r.d, r.bw, r.chunk_cap, 0);
+        }
     }
     if (maxg <= 0 || g > maxg) return RCP_EUNSUPPORTED;
     r.grid = g;
@@ -635,7 +648,7 @@ rcp_status rcp_sync(rcp_handle *h, rcp_stream_t stream) {
 rcp_status rcp_reserve(rcp_handle *h, int n, int nrhs, const rcp_opts *opts) {
     if (!h || n < 0 || nrhs < 0) return RCP_EINVAL;
     Resolved r;
-    RCP_TRY(resolve(n, opts, r));
+    RCP_TRY(resolve(n, opts, r, h->spec_mode));
     if (r.prec == RCP_FP64) RCP_TRY(ensure_factor_ws<double>(h, n, r));
     else RCP_TRY(ensure_factor_ws<float>(h, n, r));
     RCP_TRY(grow_zeroed(h->Y,
@@ -654,7 +667,7 @@ rcp_status rcp_factor(rcp_handle *h, int n, void *A, int lda, double *Dd, double
     if (stats) std::memset(stats, 0, sizeof *stats);
     if (n == 0) return RCP_OK;
     Resolved r;
-    RCP_TRY(resolve(n, opts, r));
+    RCP_TRY(resolve(n, opts, r, h->spec_mode));
     cudaStream_t s = (cudaStream_t)stream;
     if (r.prec == RCP_FP64) return factor_impl<double>(h, n, (double *)A, lda, Dd, Ds, perm, r, s, stats);
     return factor_impl<float>(h, n, (float *)A, lda, Dd, Ds, perm, r, s, stats);
@@ -888,7 +901,7 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
     if (n == 0 || nrhs == 0) return RCP_OK;
     if (!A64 || !Bv || !X || lda < n || ldb < n || ldx < n) return RCP_EINVAL;
     Resolved r;
-    RCP_TRY(resolve(n, opts, r));
+    RCP_TRY(resolve(n, opts, r, h->spec_mode));
     cudaStream_t s = (cudaStream_t)stream;
     RCP_TRY(ensure_small(h));
     const double *dA = A64, *dB = Bv;
@@ -1178,6 +1191,12 @@ rcp_status rcp_refine_batched(rcp_handle *h, int batch, int nmax, int nrhs, cons
         CU_TRY(launch_batched_refine<float>(batch, nrhs, nmax, max_iter, tol, n, (const float *const *)LA, ldla, Dd,
                                             Ds, perm, A64, lda64, Bv, ldb, X, ldx, berr, iters,
                                             (const int *)h->bord.p, (int *)h->bticket.p, s));
+    return RCP_OK;
+}
+
+rcp_status rcp_set_speculation(rcp_handle *h, int mode) {
+    if (!h || mode < -1 || mode > 2) return RCP_EINVAL;
+    h->spec_mode = mode;
     return RCP_OK;
 }
 

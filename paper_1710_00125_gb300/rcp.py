@@ -87,6 +87,7 @@ def lib():
         L.rcp_omega.argtypes = [I, I, ctypes.c_uint64, P, P]
         L.rcp_sketch.argtypes = [I, I, P, I, I, ctypes.c_uint64, P, P, P]
         L.rcp_profile.argtypes = [P, I]
+        L.rcp_set_speculation.argtypes = [P, I]
         L.rcp_profile_read.argtypes = [P, P, P, I]
         L.rcp_solve_noalloc.argtypes = [I, I, P, I, P, P, P, I, P, I, P]
         L.rcp_solve_noalloc.restype = ctypes.c_int
@@ -101,7 +102,7 @@ def lib():
                                        ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]
         L.rcp_tune_batched.restype = ctypes.c_int
         L.rcp_refine_batched.restype = ctypes.c_int
-        for name in ("rcp_profile", "rcp_profile_read", "rcp_create", "rcp_sync", "rcp_reserve", "rcp_factor", "rcp_solve", "rcp_refine", "rcp_sysv",
+        for name in ("rcp_profile", "rcp_profile_read", "rcp_set_speculation", "rcp_create", "rcp_sync", "rcp_reserve", "rcp_factor", "rcp_solve", "rcp_refine", "rcp_sysv",
                      "rcp_omega", "rcp_sketch"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -260,6 +261,11 @@ PHASES = ("sketch", "panel", "interchange", "trailing", "solve", "residual", "h2
 def rcp_profile(h: Handle, enable=True) -> None:
     """0/False: off; 1/True: per-phase events; 2: events plus per-step panel timestamps."""
     _check(lib().rcp_profile(h.h, int(enable)), "rcp_profile")
+
+
+def rcp_set_speculation(h: Handle, mode: int) -> None:
+    """FP32 panel speculation: -1 automatic, 0 off, 1 shadow sketch copy, 2 deferred update."""
+    _check(lib().rcp_set_speculation(h.h, int(mode)), "rcp_set_speculation")
 
 
 def rcp_l_norms(h: Handle, LA: torch.Tensor, prec, stream=None):

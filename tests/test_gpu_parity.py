@@ -320,6 +320,37 @@ def test_fp32_panel_many_rows_per_cta(rcp, handle, prec, n, grid):
     assert abs(st.n_2x2 - st2.n_2x2) <= max(3, 0.05 * st2.n_2x2)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "f16x3"])
+@pytest.mark.parametrize("n,grid", [(1000, 0), (2000, 8), (1200, 4)])
+def test_speculation_modes_give_identical_factors(rcp, prec, n, grid):
+    # The FP32 panel's ways of preparing the next pivot step while it waits at a step's grid
+    # barrier (a shadow copy of the sketch columns, the confirmed sketch update deferred to the next
+    # step's pass, or no speculation) apply the same operations to every value: the pivot sequence,
+    # D and L agree bit for bit.  300 rows per CTA (n = 1200 on 4 CTAs): the shadow copy does not
+    # fit and is refused.
+    a = inputs.gaussian_sym(n, seed=77 + n)
+    h = rcp.rcp_create()
+    got = {}
+    for mode in (1, 2, 0, -1):
+        rcp.rcp_set_speculation(h, mode)
+        if mode == 1 and n == 1200:
+            with pytest.raises(rcp.RcpError):
+                _factor(rcp, h, a, 64, 40, 5, prec=prec, grid=grid)
+            continue
+        code, st, A, Dd, Ds, perm = _factor(rcp, h, a, 64, 40, 5, prec=prec, grid=grid)
+        assert code == 0
+        got[mode] = (perm.cpu().numpy(), Dd.cpu().numpy(), Ds.cpu().numpy(), A.cpu().numpy(), st.n_2x2)
+    rcp.rcp_set_speculation(h, -1)
+    ref = got[0]
+    for mode, r in got.items():
+        assert np.array_equal(r[0], ref[0]), mode
+        for x, y in zip(r[1:4], ref[1:4]):
+            assert np.array_equal(x, y), mode
+        assert r[4] == ref[4]
+    with pytest.raises(rcp.RcpError):
+        rcp.rcp_set_speculation(h, 3)
+
+
 @pytest.mark.parametrize("prec", ["tf32x3", "f16x3"])
 @pytest.mark.parametrize("kexp", [2.0, 4.0, 6.0])
 def test_tf32x3_refine_reaches_fp64_backward_error(rcp, handle, kexp, prec):
