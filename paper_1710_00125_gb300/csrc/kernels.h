@@ -147,13 +147,15 @@ cudaError_t launch_exchange_probe(unsigned *bar, unsigned long long *keys, int *
 cudaError_t launch_wait_expiry(unsigned *bar, int *status, int grid, unsigned long long limit_ns,
                                unsigned long long *elapsed_ns, cudaStream_t s);
 
-// Solves and refinement.  `work` holds solve_work_bytes<T>(n, nrhs) bytes.
+// Solves and refinement.  `work` holds solve_work_bytes<T>(n, nrhs) bytes.  reuse_inv: the
+// inverted diagonal blocks (and FP32 couplings) in `work` are those of this L, n and nrhs from an
+// earlier call (the solves of one refinement), so they are not recomputed.
 template <typename T>
 size_t solve_work_bytes(int n, int nrhs);
 template <typename T>
 cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
                          const int *perm, double *X, int ldx, T *work, int *flags, int *status,
-                         const int *skip, cudaStream_t s);
+                         const int *skip, cudaStream_t s, bool reuse_inv = false);
 
 // One triangle of the solve (unit lower L, one right-hand side, iperm = identity): mode 0
 // x <- L^{-1} x, mode 1 x <- L^{-T} x; work / flags as for launch_solve with nrhs = 1

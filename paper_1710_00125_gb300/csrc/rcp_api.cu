@@ -517,13 +517,18 @@ rcp_status prepare_solve_ws(rcp_handle *h, int n, int nrhs, cudaStream_t s) {
     return RCP_OK;
 }
 
+// reuse_inv: a later solve of the same refinement (same factor, n and nrhs, workspace untouched
+// since): the inverted diagonal blocks of the first solve are used again.
 template <typename T>
 rcp_status solve_impl(rcp_handle *h, int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
-                      const int *perm, double *X, int ldx, const int *skip, cudaStream_t s) {
+                      const int *perm, double *X, int ldx, const int *skip, cudaStream_t s, bool reuse_inv = false) {
+    const void *y0 = h->Y.p;
+    const size_t y0b = h->Y.bytes;
     RCP_TRY(prepare_solve_ws<T>(h, n, nrhs, s));
+    if (h->Y.p != y0 || h->Y.bytes != y0b) reuse_inv = false;   // the workspace was reallocated
     PhaseScope ps(h, s, PH_SOLVE);
     CU_TRY(launch_solve<T>(n, nrhs, L, lda, Dd, Ds, perm, X, ldx, (T *)h->Y.p, (int *)h->flags.p,
-                           (int *)h->status.p, skip, s));
+                           (int *)h->status.p, skip, s, reuse_inv));
     return RCP_OK;
 }
 
@@ -701,11 +706,15 @@ rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda
     CU_TRY(launch_anorm(n, A64, lda, part, &sc->anorm, s));
     CU_TRY(cudaMemcpy2DAsync(X, (size_t)ldx * sizeof(double), Bv, (size_t)ldb * sizeof(double), (size_t)n * sizeof(double),
                              nrhs, cudaMemcpyDeviceToDevice, s));
-    auto do_solve = [&](double *rhs, const int *skip) -> rcp_status {
-        if (prec == RCP_FP64) return solve_impl<double>(h, n, nrhs, (const double *)LA, ldla, Dd, Ds, perm, rhs, rhs == X ? ldx : n, skip, s);
-        return solve_impl<float>(h, n, nrhs, (const float *)LA, ldla, Dd, Ds, perm, rhs, rhs == X ? ldx : n, skip, s);
+    // the corrections' solves reuse the first solve's inverted diagonal blocks (same factor)
+    auto do_solve = [&](double *rhs, const int *skip, bool reuse) -> rcp_status {
+        if (prec == RCP_FP64)
+            return solve_impl<double>(h, n, nrhs, (const double *)LA, ldla, Dd, Ds, perm, rhs, rhs == X ? ldx : n, skip, s,
+                                      reuse);
+        return solve_impl<float>(h, n, nrhs, (const float *)LA, ldla, Dd, Ds, perm, rhs, rhs == X ? ldx : n, skip, s,
+                                 reuse);
     };
-    RCP_TRY(do_solve(X, nullptr));
+    RCP_TRY(do_solve(X, nullptr, false));
     for (int it = 0; it <= max_iter; ++it) {
         {
             PhaseScope ps(h, s, PH_RESIDUAL);
@@ -715,7 +724,7 @@ rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda
                                    it < max_iter, s));
         if (it == max_iter) break;
         CU_TRY(cudaMemcpyAsync(Dc, R, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        RCP_TRY(do_solve(Dc, &sc->conv));
+        RCP_TRY(do_solve(Dc, &sc->conv, true));
         CU_TRY(launch_axpy_update(n, nrhs, X, ldx, Dc, n, &sc->conv, s));
     }
     if (!stats) return RCP_OK;

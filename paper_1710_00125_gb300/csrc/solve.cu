@@ -647,7 +647,7 @@ size_t solve_work_bytes(int n, int nrhs) {
 template <typename T>
 cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd, const double *Ds,
                          const int *perm, double *X, int ldx, T *work, int *flags, int *status,
-                         const int *skip, cudaStream_t s) {
+                         const int *skip, cudaStream_t s, bool reuse_inv) {
     if (n == 0 || nrhs == 0) return cudaSuccess;
     const int epoch = next_solve_epoch();
     const int nb = (n + SV_NB - 1) / SV_NB;
@@ -661,8 +661,10 @@ cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd,
     const int grid = nb < sms ? nb : sms;
     if constexpr (std::is_same<T, float>::value) {
         float *Mneg = Linv + (size_t)nb * SV_NB * SV_NB, *Nneg = Mneg + (size_t)nb * SV_NB * SV_NB;
-        inv_diag_kernel<T><<<nb, SV_NB, 0, s>>>(n, L, lda, Linv, status, skip, Mneg, Nneg);
-        count_launches(1);
+        if (!reuse_inv) {
+            inv_diag_kernel<T><<<nb, SV_NB, 0, s>>>(n, L, lda, Linv, status, skip, Mneg, Nneg);
+            count_launches(1);
+        }
         unsigned long long *Yp = reinterpret_cast<unsigned long long *>(work);
         unsigned long long *Vp = Yp + (size_t)n * nrhs;
         float *W = reinterpret_cast<float *>(Vp + (size_t)n * nrhs);
@@ -675,8 +677,10 @@ cudaError_t launch_solve(int n, int nrhs, const T *L, int lda, const double *Dd,
                                                      tickets + 1, status, skip);
         count_launches(1);
     } else {
-        inv_diag_kernel<T><<<nb, SV_NB, 0, s>>>(n, L, lda, Linv, status, skip);
-        count_launches(1);
+        if (!reuse_inv) {
+            inv_diag_kernel<T><<<nb, SV_NB, 0, s>>>(n, L, lda, Linv, status, skip);
+            count_launches(1);
+        }
         T *Y = work;
         fwd_kernel<T><<<grid, SV_THREADS, 0, s>>>(n, nrhs, L, lda, Linv, perm, X, ldx, Y, flags, epoch, tickets, status,
                                                   skip);
@@ -797,9 +801,9 @@ template cudaError_t launch_l_norm1<float>(int, const float *, int, unsigned lon
 template size_t solve_work_bytes<double>(int, int);
 template size_t solve_work_bytes<float>(int, int);
 template cudaError_t launch_solve<double>(int, int, const double *, int, const double *, const double *, const int *,
-                                          double *, int, double *, int *, int *, const int *, cudaStream_t);
+                                          double *, int, double *, int *, int *, const int *, cudaStream_t, bool);
 template cudaError_t launch_solve<float>(int, int, const float *, int, const double *, const double *, const int *,
-                                         double *, int, float *, int *, int *, const int *, cudaStream_t);
+                                         double *, int, float *, int *, int *, const int *, cudaStream_t, bool);
 
 // ------------------------------------------------------------------------------------------
 // Refinement pieces (FP64).
