@@ -376,7 +376,7 @@ __global__ void lrows_permute_kernel(FactorWork<T> w, int npanels) {
 // LP_COLS of its columns); the map q -> pinv_J[perm[q]] of the rows kend..n-1 and one column
 // segment at a time sit in shared memory (dynamic: (n - kend) ints + (n - kend) values), so the
 // column is read and written in coalesced runs.
-constexpr int LP_COLS = 16, LP_THREADS = 512;
+constexpr int LP_COLS = 16, LP_THREADS = 512, LP_DEPTH = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(LP_THREADS) lrows_permute_smem_kernel(FactorWork<T> w, int npanels) {
@@ -408,7 +408,20 @@ __global__ void __launch_bounds__(LP_THREADS) lrows_permute_smem_kernel(FactorWo
         const int c_lo = k0 + (u - ubase) * LP_COLS, c_hi = min(kend, c_lo + LP_COLS);
         for (int c = c_lo; c < c_hi; ++c) {
             T *col = w.A + (size_t)kend + (size_t)c * lda;
-            for (int q = threadIdx.x; q < m; q += LP_THREADS) seg[q] = col[q];
+            // LP_DEPTH loads of a thread in flight together before their shared-memory stores
+            for (int q0 = threadIdx.x; q0 < m; q0 += LP_THREADS * LP_DEPTH) {
+                T v[LP_DEPTH];
+#pragma unroll
+                for (int u = 0; u < LP_DEPTH; ++u) {
+                    const int q = q0 + u * LP_THREADS;
+                    v[u] = q < m ? col[q] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < LP_DEPTH; ++u) {
+                    const int q = q0 + u * LP_THREADS;
+                    if (q < m) seg[q] = v[u];
+                }
+            }
             __syncthreads();
             for (int q = threadIdx.x; q < m; q += LP_THREADS) col[q] = seg[map[q]];
             __syncthreads();
