@@ -297,14 +297,28 @@ __global__ void factor_init_kernel(FactorWork<T> w) {
     }
 }
 
+// max |A_ij| over the lower triangle, in the matrix's own type (the maximum of FP32 magnitudes is
+// exact in FP32; converting every entry to FP64 would run the pass on the slow FP64 pipe), four
+// loads of a thread in flight together
 template <typename T>
 __global__ void maxabs_lower_kernel(FactorWork<T> w) {
     const int n = w.n, lda = w.lda;
-    double m = 0.0;
-    for (int j = blockIdx.x; j < n; j += gridDim.x)
-        for (int i = j + threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs((double)w.A[(size_t)i + (size_t)j * lda]));
+    T m = T(0);
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const T *col = w.A + (size_t)j * lda;
+        for (int i0 = j + threadIdx.x; i0 < n; i0 += 4 * blockDim.x) {
+            T v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * blockDim.x;
+                v[u] = i < n ? col[i] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) m = fmax(m, fabs(v[u]));
+        }
+    }
     for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_nonneg(&w.st->maxA_bits, m);
+    if ((threadIdx.x & 31) == 0 && m > T(0)) atomic_max_nonneg(&w.st->maxA_bits, (double)m);
 }
 
 template <typename T>
