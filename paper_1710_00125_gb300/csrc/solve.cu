@@ -989,12 +989,26 @@ cudaError_t launch_axpy_update(int n, int nrhs, double *X, int ldx, const double
 // Copy of the lower triangle of an FP64 matrix (columns c0 .. c1-1), optionally rounded to FP32.
 __global__ void copy_lower_kernel(int n, const double *__restrict__ src, int lds, void *dst, int ldd, int to_f32, int c0,
                                   int c1) {
-    for (int j = c0 + blockIdx.x; j < c1; j += gridDim.x)
-        for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
-            double v = src[(size_t)i + (size_t)j * lds];
-            if (to_f32) static_cast<float *>(dst)[(size_t)i + (size_t)j * ldd] = (float)v;
-            else static_cast<double *>(dst)[(size_t)i + (size_t)j * ldd] = v;
+    // four loads of a thread in flight together before their stores
+    for (int j = c0 + blockIdx.x; j < c1; j += gridDim.x) {
+        const double *sc = src + (size_t)j * lds;
+        for (int i0 = j + threadIdx.x; i0 < n; i0 += 4 * blockDim.x) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * blockDim.x;
+                v[u] = i < n ? sc[i] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * blockDim.x;
+                if (i < n) {
+                    if (to_f32) static_cast<float *>(dst)[(size_t)i + (size_t)j * ldd] = (float)v[u];
+                    else static_cast<double *>(dst)[(size_t)i + (size_t)j * ldd] = v[u];
+                }
+            }
         }
+    }
 }
 
 cudaError_t launch_copy_lower_f64(int n, const double *src, int lds, void *dst, int ldd, int to_f32, cudaStream_t s,
