@@ -218,11 +218,15 @@ trailing_simt_kernel(FactorWork<T> w) {
     }
 }
 
+// marked: the panel kernel already wrote the position marks and saved permutation entries of
+// its moved indices (the block QRCP's moved list needs mark_kernel)
 template <typename T>
-cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s) {
+cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s, bool marked) {
     int *phi = w.moved + w.n;   // second half of the moved buffer holds the position marks
-    mark_kernel<T><<<1, 256, 0, s>>>(w, phi);
-    count_launches(1);
+    if (!marked) {
+        mark_kernel<T><<<1, 256, 0, s>>>(w, phi);
+        count_launches(1);
+    }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -523,8 +527,8 @@ cudaError_t launch_guard_zero(int n, int k, T *A, int lda, double *Dd, double *D
 
 template cudaError_t launch_guard_zero<double>(int, int, double *, int, double *, double *, cudaStream_t);
 template cudaError_t launch_guard_zero<float>(int, int, float *, int, double *, double *, cudaStream_t);
-template cudaError_t launch_interchange<double>(const FactorWork<double> &, cudaStream_t);
-template cudaError_t launch_interchange<float>(const FactorWork<float> &, cudaStream_t);
+template cudaError_t launch_interchange<double>(const FactorWork<double> &, cudaStream_t, bool);
+template cudaError_t launch_interchange<float>(const FactorWork<float> &, cudaStream_t, bool);
 template cudaError_t launch_panel_record<double>(const FactorWork<double> &, int, cudaStream_t);
 template cudaError_t launch_panel_record<float>(const FactorWork<float> &, int, cudaStream_t);
 template cudaError_t launch_lrows_permute<double>(const FactorWork<double> &, int, cudaStream_t);

@@ -107,7 +107,7 @@ template <typename T>
 cudaError_t launch_panel(const FactorWork<T> &w, cudaStream_t s);
 
 template <typename T>
-cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s);
+cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s, bool marked = false);
 
 template <typename T>
 cudaError_t launch_trailing(const FactorWork<T> &w, int kmin, int mode, cudaStream_t s);

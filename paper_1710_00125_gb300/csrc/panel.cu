@@ -1021,7 +1021,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
         if (alive[jl] || w.qb) w.B[(size_t)r + (size_t)lp[jl] * d] = Bs[(size_t)jl * ds + r];
     }
     // the moved rows, appended with one atomic per warp (the CTAs that own the panel's
-    // positions move nearly every row)
+    // positions move nearly every row), with their position marks and saved permutation entries
+    // for the interchange kernels (phi: second half of the moved buffer)
+    int *const phi = w.moved + n;
     for (int base = 0; base < cnt; base += PANEL_THREADS) {
         const int jl = base + tid, j = j_lo + jl;
         bool mv = false;
@@ -1036,8 +1038,13 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_kernel(FactorWork<T> w
             first = __shfl_sync(FULL, first, 0);
             if (mv) {
                 const int idx = first + __popc(bal & ((1u << lane) - 1u));
-                if (idx < w.maxmoved) w.moved[idx] = j;
-                else atomicOr(w.status, ST_INTERNAL);
+                if (idx < w.maxmoved) {
+                    w.moved[idx] = j;
+                    phi[lp[jl]] = j;
+                    w.tmpP[idx] = w.perm[j];
+                } else {
+                    atomicOr(w.status, ST_INTERNAL);
+                }
             }
         }
     }

@@ -405,7 +405,7 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
             }
             {
                 PhaseScope ps(h, s, PH_INTERCHANGE);
-                CU_TRY(launch_interchange<T>(w, s));
+                CU_TRY(launch_interchange<T>(w, s, true));   // the panel marked its moved indices
                 CU_TRY(launch_panel_record<T>(w, blk, s));
             }
             {
@@ -454,7 +454,7 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
         }
         {
             PhaseScope ps(h, s, PH_INTERCHANGE);
-            CU_TRY(launch_interchange<T>(w, s));
+            CU_TRY(launch_interchange<T>(w, s, true));   // the panel marked its moved indices
             CU_TRY(launch_panel_record<T>(w, blk, s));
         }
         {
