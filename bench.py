@@ -103,7 +103,8 @@ def workload_name(a):
 
 def batched_workload_name(a):
     return (f"{a.batch} systems, n_i ~ U{{32..512}} (seeded), A_i = (G_i + G_i^T)/2 with G_i N(0,1), "
-            f"16 RHS b_i = A_i x_i; FP32 factor (panel width b autotuned, d = b + 8) + FP64 refinement to berr<={a.tol:g}, "
+            f"16 RHS b_i = A_i x_i; FP32 factor (panel width b and CTA schedule autotuned, d = b + 8) + FP64 refinement "
+            f"to berr<={a.tol:g}, "
             f"one persistent launch per phase, replayed from a CUDA graph")
 
 
@@ -458,9 +459,11 @@ def run_batched(a, dev, stream, rank, world, dist, fp64_peak=None):
     inputs.fill_batched_gaussian_device(sizes, bt.off_sq, bt.A64_pool, seed=rank)
     inputs.fill_batched_rhs_device(sizes, bt.off_sq, bt.A64_pool, bt.off_rhs, bt.B_pool, nrhs, seed=rank)
     h = rcp.rcp_create()
-    # the autotuner picks the panel width b on this batch, with the sketch d = b + 8 following it;
-    # b = 0, d = 0 then select the pair
+    # the autotuner picks the panel width b on this batch, with the sketch d = b + 8 following it,
+    # and the CTA schedule (512- or 256-thread CTAs, or the small systems in a second launch of
+    # 256-thread CTAs); b = 0, d = 0 then select them
     tuned_b, tuned_ms = bt.tune(h, rcp.make_opts(b=0, d=0, seed=rank, prec="fp32"))
+    sched = rcp.rcp_get_batched_schedule(h, bt.nmax, 0, "fp32")
     opts = rcp.make_opts(b=0, d=0, seed=rank, prec="fp32")
     s = torch.cuda.Stream(device=dev)
     s.wait_stream(stream)
@@ -516,7 +519,8 @@ def run_batched(a, dev, stream, rank, world, dist, fp64_peak=None):
             "factor_ms": f0.elapsed_time(f1), "refine_ms": ref_ms,
             "berr_max": float(berr.max()), "all_berr_le_tol": bool((berr <= a.tol).all()),
             "info_nonzero": int((info != 0).sum()), "refine_iters_hist": np.bincount(iters).tolist(),
-            "gpu_launches_per_replay": 2, "steps": a.batch_steps, "tuned_b": tuned_b, "roofline": roof}
+            "gpu_launches_per_replay": 3 if sched["split"] else 2, "steps": a.batch_steps, "tuned_b": tuned_b,
+            "schedule": sched, "roofline": roof}
 
 
 def run_q_compare(a, dev, stream, A64, Bv, seed):

@@ -65,7 +65,8 @@ struct BtShared {
     int s_idx;
 };
 
-// FP64: warp shuffles, then every thread reduces the eight warp candidates.
+// FP64: warp shuffles, then every thread reduces the NW warp candidates.
+template <int NW>
 __device__ __forceinline__ BtCand<double> bt_argmax(BtCand<double> c, BtShared<double> &sh, int &cnt) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, buf = cnt & 1;
 #pragma unroll
@@ -78,7 +79,7 @@ __device__ __forceinline__ BtCand<double> bt_argmax(BtCand<double> c, BtShared<d
     __syncthreads();
     BtCand<double> r = sh.red[buf][0];
 #pragma unroll
-    for (int w2 = 1; w2 < bt::WARPS; ++w2) {
+    for (int w2 = 1; w2 < NW; ++w2) {
         const BtCand<double> x = sh.red[buf][w2];
         if (bt_better(x.v, x.j, r.v, r.j)) r = x;
     }
@@ -90,6 +91,7 @@ __device__ __forceinline__ BtCand<double> bt_argmax(BtCand<double> c, BtShared<d
 // warp takes its maximum with two redux.sync, the block with one shared 64-bit atomicMax.
 // Slot cnt % 3 serves this call; the slot of the next call, last read two barriers ago, is
 // cleared here.  A NaN value wins (its bits exceed those of +Inf), so the caller sees it.
+template <int NW>
 __device__ __forceinline__ BtCand<float> bt_argmax(BtCand<float> c, BtShared<float> &sh, int &cnt) {
     const bool has = c.j != INT_MAX;
     const unsigned hi = has ? __float_as_uint(c.v) : 0u, lo = has ? ~(unsigned)c.j : 0u;
@@ -135,6 +137,7 @@ struct BtFactorArgs {
     const int *order;           // processing order (largest first)
     int *ticket;
     int *pscr;                  // per CTA: panel bounds and the permutation after every panel
+    const int *first, *last;    // device: the range of order[] this launch takes (NULL: 0, batch)
 };
 
 // panels of one system: widths b or b + 1, so at most nmax / b + 1 of them
@@ -161,9 +164,9 @@ size_t batched_factor_smem(int d, int b, int nmax) {
     return bt_factor_elems(d, b, nmax) * sizeof(T);
 }
 
-// DR > 0: thread j keeps the sketch column of position j in registers (n <= THREADS, dp <= DR,
+// DR > 0: thread j keeps the sketch column of position j in registers (n <= NT, dp <= DR,
 // FP32 only); DR == 0: the sketch stays in shared memory.
-template <typename T, int DR>
+template <typename T, int DR, int NT>
 __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared<T> &sh, int &cnt) {
     static_assert(DR == 0 || (sizeof(T) == 4 && DR % 4 == 0), "register sketch: FP32, whole float4s");
     constexpr int DR4 = DR > 0 ? DR / 4 : 1;
@@ -196,12 +199,12 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
     if (a.A64) {
         const double *S = a.A64[sys];
         const int lds = a.lda64[sys];
-        for (int e = tid; e < n * n; e += bt::THREADS) {
+        for (int e = tid; e < n * n; e += NT) {
             const int i = e % n, j = e / n;
             if (i >= j) A[(size_t)i + (size_t)j * lda] = (T)S[(size_t)i + (size_t)j * lds];
         }
     }
-    for (int x = tid; x < n; x += bt::THREADS) perm[x] = x;
+    for (int x = tid; x < n; x += NT) perm[x] = x;
     __syncthreads();
 
     // ---- B = Omega(:, 0:n) A by 32 x 32 tiles of A (the sketch region aliases the panels) ----
@@ -210,11 +213,11 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
         T *Os = W + bt::TILE * (bt::TILE + 1);         // [d][33]:  Os[r][i] = Omega(r, i0 + i)
         const int jj = tid & 31, r0 = tid >> 5;
         for (int j0 = 0; j0 < n; j0 += bt::TILE) {
-            T acc[bt::MR];
+            T acc[(4096 / NT)];
 #pragma unroll
-            for (int m = 0; m < bt::MR; ++m) acc[m] = T(0);
+            for (int m = 0; m < (4096 / NT); ++m) acc[m] = T(0);
             for (int i0 = 0; i0 < n; i0 += bt::TILE) {
-                for (int e = tid; e < bt::TILE * bt::TILE; e += bt::THREADS) {
+                for (int e = tid; e < bt::TILE * bt::TILE; e += NT) {
                     const int lo = e & 31, hi = e >> 5;
                     if (i0 > j0) {          // A(i0 + lo, j0 + hi): column j0 + hi, coalesced
                         const int i = i0 + lo, j = j0 + hi;
@@ -227,7 +230,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                         As[lo * (bt::TILE + 1) + hi] = (i < n && j < n) ? a_sym(A, lda, i, j) : T(0);
                     }
                 }
-                for (int e = tid; e < d * bt::TILE; e += bt::THREADS) {
+                for (int e = tid; e < d * bt::TILE; e += NT) {
                     const int r = e % d, i = e / d;
                     Os[r * (bt::TILE + 1) + i] = (i0 + i < n) ? a.om[(size_t)r + (size_t)(i0 + i) * d] : T(0);
                 }
@@ -236,16 +239,16 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                 for (int i = 0; i < bt::TILE; ++i) {
                     const T av = As[i * (bt::TILE + 1) + jj];
 #pragma unroll
-                    for (int m = 0; m < bt::MR; ++m) {
-                        const int r = r0 + bt::WARPS * m;
+                    for (int m = 0; m < (4096 / NT); ++m) {
+                        const int r = r0 + (NT / 32) * m;
                         if (r < d) acc[m] += Os[r * (bt::TILE + 1) + i] * av;
                     }
                 }
                 __syncthreads();
             }
 #pragma unroll
-            for (int m = 0; m < bt::MR; ++m) {
-                const int r = r0 + bt::WARPS * m;
+            for (int m = 0; m < (4096 / NT); ++m) {
+                const int r = r0 + (NT / 32) * m;
                 if (r < dp && j0 + jj < n) Bs[(size_t)(j0 + jj) * dp + r] = r < d ? acc[m] : T(0);
             }
         }
@@ -267,13 +270,13 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
             cand = BtCand<T>{(T)(s0 + s1), tid};
         }
     } else {
-        for (int j = tid; j < n; j += bt::THREADS) {
+        for (int j = tid; j < n; j += NT) {
             T s = T(0);
             for (int r = 0; r < d; ++r) { const T v = Bs[(size_t)j * dp + r]; s += v * v; }
             if (bt_better(s, j, cand.v, cand.j)) cand = BtCand<T>{s, j};
         }
     }
-    cand = bt_argmax(cand, sh, cnt);
+    cand = bt_argmax<NT / 32>(cand, sh, cnt);
 
     int info = 0, k = 0, np = 0;
     bool bad = false;
@@ -287,7 +290,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
             // ---- phase A: k <-> P in the trailing part of A; Schur column k in the new labels
             //      (W, Lp and Bs are still in the old labels: position x came from sigma(x)) ----
             BtCand<T> lc{T(-1), INT_MAX};
-            for (int x = k + tid; x < n; x += bt::THREADS) {
+            for (int x = k + tid; x < n; x += NT) {
                 T av;
                 if (x == k) {
                     av = A[(size_t)P + (size_t)P * lda];
@@ -328,12 +331,12 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                     }
                 }
             } else {
-                for (int e = tid; e < 2 * dp; e += bt::THREADS) {
+                for (int e = tid; e < 2 * dp; e += NT) {
                     const int r = e < dp ? e : e - dp;
                     stg[e < dp ? r : 2 * dp + r] = Bs[(size_t)(e < dp ? k : P) * dp + r];
                 }
             }
-            lc = bt_argmax(lc, sh, cnt);
+            lc = bt_argmax<NT / 32>(lc, sh, cnt);
             // ---- SBKP decision (every thread, in the factor's type) ----
             const int R = lc.j < n ? lc.j : -1;     // new label
             const T lam = R >= 0 ? lc.v : T(0);
@@ -346,7 +349,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
             const int sR = R < 0 ? -1 : (R == P ? k : R);   // old label of R
             if (kase == 4) {
                 // ---- phase R: Schur column R (new labels), decision, 2x2 inverse, staging ----
-                for (int x = k + tid; x < n; x += bt::THREADS) {
+                for (int x = k + tid; x < n; x += NT) {
                     T av = a_sym(A, lda, x, R);
                     const int sx = x == k ? P : (x == P ? k : x);
                     T cs = T(0);
@@ -387,7 +390,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                         }
                     }
                 } else {
-                    for (int e = tid; e < 2 * dp; e += bt::THREADS) {
+                    for (int e = tid; e < 2 * dp; e += NT) {
                         const int r = e < dp ? e : e - dp;
                         stg[e < dp ? dp + r : 3 * dp + r] = Bs[(size_t)(e < dp ? k + 1 : sR) * dp + r];
                     }
@@ -479,7 +482,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                     nc = BtCand<T>{(T)(n0 + n1), j};
                 }
             } else {
-                for (int j = k + s + tid; j < n; j += bt::THREADS) {
+                for (int j = k + s + tid; j < n; j += NT) {
                     const int u = j == Rm ? tgt : j;                   // label after the first interchange
                     const int o = u == k ? P : (u == P ? k : u);         // label before the step
                     const T *src = o == j ? Bs + (size_t)j * dp
@@ -542,7 +545,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                 }
             }
             // the interchanges of the panel rows: new row q of W and Lp is old row sigma(tau(q))
-            for (int e = tid; e < 2 * i; e += bt::THREADS) {
+            for (int e = tid; e < 2 * i; e += NT) {
                 T *rowp = (e < i ? W : Lp) + (size_t)(e < i ? e : e - i) * nmax;
                 const int q4[4] = {k, P, k + 1 < n ? k + 1 : k, Rm >= 0 ? Rm : k};
                 T v4[4];
@@ -562,24 +565,24 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
             if (s == 2 && tid == 0) Lp[(size_t)i * nmax + k + 1] = T(0);   // L(k+1, k) of a 2x2 block
             if (mdst) *mdst = mv;
             if (Rm >= 0) {
-                for (int x = k + s + tid + bt::THREADS; x < n; x += bt::THREADS) {
+                for (int x = k + s + tid + NT; x < n; x += NT) {
                     if (x == Rm) A[(size_t)Rm + (size_t)Rm * lda] = A[(size_t)tgt + (size_t)tgt * lda];
                     else if (x > Rm) A[(size_t)x + (size_t)Rm * lda] = A[(size_t)x + (size_t)tgt * lda];
                     else A[(size_t)Rm + (size_t)x * lda] = A[(size_t)x + (size_t)tgt * lda];
                 }
             }
-            cand = bt_argmax(nc, sh, cnt);
+            cand = bt_argmax<NT / 32>(nc, sh, cnt);
             k += s;
             i += s;
         }
         if (bad) break;
         // ---- end of the panel: multipliers into A, the permutation so far, A22 -= W Lp^T ----
-        for (int e = tid; e < i * (n - k0); e += bt::THREADS) {
+        for (int e = tid; e < i * (n - k0); e += NT) {
             const int t = e / (n - k0), p = k0 + e % (n - k0);
             if (p > k0 + t) A[(size_t)p + (size_t)(k0 + t) * lda] = Lp[(size_t)t * nmax + p];
         }
         if (k < n) {
-            for (int x = tid; x < n; x += bt::THREADS) psnap[(size_t)np * a.nmax + x] = perm[x];
+            for (int x = tid; x < n; x += NT) psnap[(size_t)np * a.nmax + x] = perm[x];
             if (tid == 0) pbound[np] = k;
             ++np;
         }
@@ -588,7 +591,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
             // (I, J), I >= J, enumerated so that consecutive threads take consecutive row tiles
             // of one column tile (coalesced columns of A)
             const int kA = k & ~3, nt = (n - kA + 3) >> 2, ntri = nt * (nt + 1) / 2;
-            for (int tt = tid; tt < ntri; tt += bt::THREADS) {
+            for (int tt = tid; tt < ntri; tt += NT) {
                 int ra = (int)((sqrtf(8.f * (float)tt + 1.f) - 1.f) * 0.5f);
                 while (ra * (ra + 1) / 2 > tt) --ra;
                 while ((ra + 1) * (ra + 2) / 2 <= tt) ++ra;
@@ -634,7 +637,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
         __syncthreads();
     }
     if (bad) {
-        for (int x = tid; x < n; x += bt::THREADS) perm_out[x] = perm[x];
+        for (int x = tid; x < n; x += NT) perm_out[x] = perm[x];
         if (tid == 0) a.info[sys] = BT_INFO_NONFINITE;
         __syncthreads();
         return;
@@ -644,21 +647,21 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
     {
         int *pf = reinterpret_cast<int *>(W);          // final permutation
         int *inv = pf + nmax;                          // inverse of the panel's permutation
-        for (int x = tid; x < n; x += bt::THREADS) pf[x] = perm[x];
+        for (int x = tid; x < n; x += NT) pf[x] = perm[x];
         int c0 = 0;
         for (int J = 0; J < np; ++J) {
             const int kend = pbound[J];
             __syncthreads();
-            for (int x = tid; x < n; x += bt::THREADS) inv[psnap[(size_t)J * a.nmax + x]] = x;
+            for (int x = tid; x < n; x += NT) inv[psnap[(size_t)J * a.nmax + x]] = x;
             for (int cb = c0; cb < kend; cb += d) {
                 const int cw = min(d, kend - cb), rows = n - kend;
                 __syncthreads();
-                for (int e = tid; e < cw * rows; e += bt::THREADS) {
+                for (int e = tid; e < cw * rows; e += NT) {
                     const int q = kend + e % rows, c = cb + e / rows;
                     Bs[(size_t)(e / rows) * nmax + q] = A[(size_t)q + (size_t)c * lda];
                 }
                 __syncthreads();
-                for (int e = tid; e < cw * rows; e += bt::THREADS) {
+                for (int e = tid; e < cw * rows; e += NT) {
                     const int q = kend + e % rows, c = cb + e / rows;
                     A[(size_t)q + (size_t)c * lda] = Bs[(size_t)(e / rows) * nmax + inv[pf[q]]];
                 }
@@ -666,7 +669,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
             c0 = kend;
         }
     }
-    for (int x = tid; x < n; x += bt::THREADS) {
+    for (int x = tid; x < n; x += NT) {
         A[(size_t)x + (size_t)x * lda] = (T)Dd[x];
         perm_out[x] = perm[x];
     }
@@ -674,19 +677,24 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
     __syncthreads();
 }
 
-template <typename T, int DR>
-__global__ void __launch_bounds__(bt::THREADS, 1) batched_factor_kernel(BtFactorArgs<T> a) {
+// NT threads per CTA: 512 (one CTA per SM) or 256 (two per SM where the shared memory allows).
+// The CTAs take the systems order[first .. last) (first and last read from device memory when
+// given, else 0 and batch).
+template <typename T, int DR, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) batched_factor_kernel(BtFactorArgs<T> a) {
+    static_assert(NT == 256 || NT == 512, "CTA size");
     extern __shared__ __align__(16) unsigned char bt_raw[];
     __shared__ BtShared<T> sh;
     int cnt = 0;
     if (threadIdx.x == 0) { sh.key[0] = sh.key[1] = sh.key[2] = 0ull; }
+    const int first = a.first ? *a.first : 0, last = a.last ? *a.last : a.batch;
     for (;;) {
-        if (threadIdx.x == 0) sh.s_idx = atomicAdd(a.ticket, 1);
+        if (threadIdx.x == 0) sh.s_idx = first + atomicAdd(a.ticket, 1);
         __syncthreads();
         const int idx = sh.s_idx;
         __syncthreads();
-        if (idx >= a.batch) return;
-        bt_factor_one<T, DR>(a, a.order[idx], reinterpret_cast<T *>(bt_raw), sh, cnt);
+        if (idx >= last) return;
+        bt_factor_one<T, DR, NT>(a, a.order[idx], reinterpret_cast<T *>(bt_raw), sh, cnt);
     }
 }
 
@@ -1053,7 +1061,9 @@ __global__ void __launch_bounds__(bt::THREADS, 1) batched_refine_kernel(BtRefine
 // ---------------------------------------------------------------------------------------------
 // order: systems by decreasing n (counting sort in one CTA), and the launchers
 // ---------------------------------------------------------------------------------------------
-__global__ void batched_order_kernel(int batch, int nmax, const int *n, int *order) {
+// above[v] (v = 0..nmax, when given) = the number of systems with n > v: order[0 .. above[v])
+// are those systems, order[above[v] .. batch) the others.
+__global__ void batched_order_kernel(int batch, int nmax, const int *n, int *order, int *above) {
     extern __shared__ int cnt[];   // nmax + 1 counters
     for (int v = threadIdx.x; v <= nmax; v += blockDim.x) cnt[v] = 0;
     __syncthreads();
@@ -1063,6 +1073,10 @@ __global__ void batched_order_kernel(int batch, int nmax, const int *n, int *ord
         int run = 0;
         for (int v = 0; v <= nmax; ++v) { const int c = cnt[v]; cnt[v] = run; run += c; }
     }
+    __syncthreads();
+    // cnt[u] now counts the systems with nmax - n < u, i.e. n > nmax - u
+    if (above)
+        for (int v = threadIdx.x; v <= nmax; v += blockDim.x) above[v] = cnt[nmax - v];
     __syncthreads();
     for (int s = threadIdx.x; s < batch; s += blockDim.x)
         order[atomicAdd(&cnt[nmax - min(max(n[s], 0), nmax)], 1)] = s;
@@ -1077,8 +1091,8 @@ static int bt_grid(const void *fn, size_t smem, int batch) {
     return (int)(g < batch ? g : batch);
 }
 
-cudaError_t launch_batched_order(int batch, int nmax, const int *n, int *order, cudaStream_t s) {
-    batched_order_kernel<<<1, 1024, (size_t)(nmax + 1) * sizeof(int), s>>>(batch, nmax, n, order);
+cudaError_t launch_batched_order(int batch, int nmax, const int *n, int *order, int *above, cudaStream_t s) {
+    batched_order_kernel<<<1, 1024, (size_t)(nmax + 1) * sizeof(int), s>>>(batch, nmax, n, order, above);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1090,30 +1104,33 @@ size_t batched_max_smem() {
     return (size_t)v > 1024 ? (size_t)v - 1024 : 0;   // room for the kernels' static shared memory
 }
 
-// the factor kernel for a shape: the register sketch when it fits (FP32, d <= 48, nmax <= THREADS)
+// the factor kernel for a shape and CTA size: the register sketch when it fits (FP32, d <= 48,
+// nmax <= threads)
 constexpr int BT_DR = 48;
 template <typename T>
-static void (*bt_factor_fn(int d, int nmax))(BtFactorArgs<T>) {
+static void (*bt_factor_fn(int d, int nmax, int nt))(BtFactorArgs<T>) {
     if constexpr (sizeof(T) == 4) {
-        if (bt_stride(d) <= BT_DR && nmax <= bt::THREADS) return batched_factor_kernel<T, BT_DR>;
+        if (bt_stride(d) <= BT_DR && nmax <= nt)
+            return nt == 256 ? batched_factor_kernel<T, BT_DR, 256> : batched_factor_kernel<T, BT_DR, 512>;
     }
     (void)d;
     (void)nmax;
-    return batched_factor_kernel<T, 0>;
+    return nt == 256 ? batched_factor_kernel<T, 0, 256> : batched_factor_kernel<T, 0, 512>;
 }
 
 template <typename T>
-int batched_factor_grid(int d, int b, int nmax) {
+int batched_factor_grid(int d, int b, int nmax, int nt) {
+    if (nt != 256 && nt != 512) return 0;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = batched_factor_smem<T>(d, b, nmax);
-    void (*fn)(BtFactorArgs<T>) = bt_factor_fn<T>(d, nmax);
+    void (*fn)(BtFactorArgs<T>) = bt_factor_fn<T>(d, nmax, nt);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, bt::THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, nt, smem);
     return sms * (per > 0 ? per : 1);
 }
 
@@ -1121,15 +1138,18 @@ template <typename T>
 cudaError_t launch_batched_factor(int batch, int d, int b, int nmax, const int *n, const double *const *A64,
                                   const int *lda64, T *const *A, const int *lda, double *const *Dd, double *const *Ds,
                                   int *const *perm, const T *om, double alpha, int *info, const int *order,
-                                  int *ticket, int *pscr, int grid, cudaStream_t s) {
-    BtFactorArgs<T> a{batch, d, b, nmax, n, A64, lda64, A, lda, Dd, Ds, perm, om, alpha, info, order, ticket, pscr};
+                                  int *ticket, int *pscr, int grid, int nt, const int *first, const int *last,
+                                  cudaStream_t s) {
+    if (nt != 256 && nt != 512) return cudaErrorInvalidValue;
+    BtFactorArgs<T> a{batch, d, b, nmax, n, A64, lda64, A, lda, Dd, Ds, perm, om, alpha, info, order, ticket, pscr,
+                      first, last};
     const size_t smem = batched_factor_smem<T>(d, b, nmax);
-    void (*fn)(BtFactorArgs<T>) = bt_factor_fn<T>(d, nmax);
+    void (*fn)(BtFactorArgs<T>) = bt_factor_fn<T>(d, nmax, nt);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(ticket, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    fn<<<grid < batch ? grid : batch, bt::THREADS, smem, s>>>(a);
+    fn<<<grid < batch ? grid : batch, nt, smem, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1156,11 +1176,11 @@ cudaError_t launch_batched_refine(int batch, int nrhs, int nmax, int max_iter, d
 #define BT_INST(T)                                                                                                   \
     template size_t batched_factor_smem<T>(int, int, int);                                                           \
     template size_t batched_refine_smem<T>(int, int);                                                                \
-    template int batched_factor_grid<T>(int, int, int);                                                             \
+    template int batched_factor_grid<T>(int, int, int, int);                                                         \
     template cudaError_t launch_batched_factor<T>(int, int, int, int, const int *, const double *const *, const int *, \
                                                   T *const *, const int *, double *const *, double *const *,          \
                                                   int *const *, const T *, double, int *, const int *, int *, int *,  \
-                                                  int, cudaStream_t);                                                \
+                                                  int, int, const int *, const int *, cudaStream_t);                 \
     template cudaError_t launch_batched_refine<T>(int, int, int, int, double, const int *, const T *const *,          \
                                                   const int *, const double *const *, const double *const *,          \
                                                   const int *const *, const double *const *, const int *,             \

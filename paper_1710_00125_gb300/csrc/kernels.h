@@ -203,15 +203,19 @@ template <typename T>
 size_t batched_factor_smem(int d, int b, int nmax);
 template <typename TL>
 size_t batched_refine_smem(int nrhs, int nmax);
-cudaError_t launch_batched_order(int batch, int nmax, const int *n, int *order, cudaStream_t s);
+// order: systems by decreasing n; above (nmax + 1 ints, may be NULL): above[v] = systems with n > v
+cudaError_t launch_batched_order(int batch, int nmax, const int *n, int *order, int *above, cudaStream_t s);
 size_t batched_factor_scratch_ints(int b, int nmax);   // per CTA
+// resident CTAs of the factor kernel with nt (256 or 512) threads per CTA (0: error)
 template <typename T>
-int batched_factor_grid(int d, int b, int nmax);        // resident CTAs of the factor kernel (0: error)
+int batched_factor_grid(int d, int b, int nmax, int nt);
+// one launch over order[*first .. *last) (NULL: 0 and batch) with nt threads per CTA
 template <typename T>
 cudaError_t launch_batched_factor(int batch, int d, int b, int nmax, const int *n, const double *const *A64,
                                   const int *lda64, T *const *A, const int *lda, double *const *Dd, double *const *Ds,
                                   int *const *perm, const T *om, double alpha, int *info, const int *order,
-                                  int *ticket, int *pscr, int grid, cudaStream_t s);
+                                  int *ticket, int *pscr, int grid, int nt, const int *first, const int *last,
+                                  cudaStream_t s);
 template <typename TL>
 cudaError_t launch_batched_refine(int batch, int nrhs, int nmax, int max_iter, double tol, const int *n,
                                   const TL *const *LA, const int *ldla, const double *const *Dd,

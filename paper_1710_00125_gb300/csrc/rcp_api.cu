@@ -66,8 +66,9 @@ struct rcp_handle {
     int bord_batch = -1, bord_nmax = -1;
     uint64_t bom_seed = 0;                         // (seed, d, nmax, fp64) of the drawn Omega
     int bom_d = -1, bom_nmax = -1, bom_f64 = -1;
-    struct Tuned { int nmax, dkey, f64, b, d; };   // dkey: the caller's d (0: d = b + 8 tuned with b)
+    struct Tuned { int nmax, dkey, f64, b, d, nt, split; };   // dkey: the caller's d (0: d = b + 8 tuned with b)
     std::vector<Tuned> tuned;                      // batched shapes chosen by rcp_tune_batched
+    int bt_nt = 0, bt_split = 0;                   // rcp_set_batched_schedule (0, 0: tuned or default)
     cudaStream_t copy_stream = nullptr;            // rcp_sysv with host buffers: block copies of A
     std::vector<cudaEvent_t> copy_events;          //   one per block, and one for the start
     Buf gmV, gmZ, gmP, gmH;                        // GMRES refinement: basis, zero vector, partial sums, scalars
@@ -1060,12 +1061,13 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
 
 // ---- batched ragged systems ----
 
+// order[batch] (largest systems first), then above[nmax + 1] (above[v]: systems with n > v)
 static rcp_status batched_order(rcp_handle *h, int batch, int nmax, const int *n, cudaStream_t s) {
-    RCP_TRY(grow(h->bord, (size_t)batch * sizeof(int)));
+    RCP_TRY(grow(h->bord, ((size_t)batch + nmax + 1) * sizeof(int)));
     RCP_TRY(grow(h->bticket, 64));
     if (h->bord_n == n && h->bord_batch == batch && h->bord_nmax == nmax) return RCP_OK;
     // any permutation of the systems gives the same results; this one is for load balance
-    CU_TRY(launch_batched_order(batch, nmax, n, (int *)h->bord.p, s));
+    CU_TRY(launch_batched_order(batch, nmax, n, (int *)h->bord.p, (int *)h->bord.p + batch, s));
     h->bord_n = n;
     h->bord_batch = batch;
     h->bord_nmax = nmax;
@@ -1085,9 +1087,17 @@ rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, 
     int b = (opts && opts->b > 0) ? opts->b : 32;
     const int dkey = (opts && opts->d > 0) ? opts->d : 0;
     int d = dkey > 0 ? dkey : std::min(b + 8, 128);
+    int nt = 512, split = 0;   // CTA size; split > 0: systems with n <= split in a second launch
     if (!(opts && opts->b > 0))
         for (const auto &t : h->tuned)
-            if (t.nmax == nmax && t.dkey == dkey && t.f64 == (int)f64) { b = t.b; d = t.d; }   // the autotuned shape
+            if (t.nmax == nmax && t.dkey == dkey && t.f64 == (int)f64) {   // the autotuned shape
+                b = t.b; d = t.d; nt = t.nt; split = t.split;
+            }
+    if (h->bt_nt > 0 || h->bt_split > 0) {   // the schedule set on the handle
+        nt = h->bt_nt > 0 ? h->bt_nt : 512;
+        split = h->bt_split;
+    }
+    if (split >= nmax) split = 0;
     if (opts && opts->q_mode != 0 && opts->q_mode != 1) return RCP_EUNSUPPORTED;
     if (opts && opts->guard_r != 0) return RCP_EUNSUPPORTED;   // the safeguard is host-driven per system
     if (b > 512 || d > 128) return RCP_EUNSUPPORTED;
@@ -1111,18 +1121,68 @@ rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, 
         }
         om = h->bom.p;
     }
-    const int grid = f64 ? batched_factor_grid<double>(d, b, nmax) : batched_factor_grid<float>(d, b, nmax);
-    if (grid <= 0) return RCP_ECUDA;
-    RCP_TRY(grow(h->bscr, batched_factor_scratch_ints(b, nmax) * sizeof(int) * (size_t)grid));
+    // launches: {CTA size, order of the shared arrays, range of order[]}; with a split the systems
+    // with n > split come first (512 threads), the others after (256 threads, arrays of order split)
+    struct Leg { int nt, nm; const int *first, *last; int grid; };
+    const int *above = (const int *)h->bord.p + batch;
+    Leg legs[2];
+    int nlegs = 0;
+    if (split > 0) {
+        legs[nlegs++] = {512, nmax, nullptr, above + split, 0};
+        legs[nlegs++] = {256, split, above + split, nullptr, 0};
+    } else {
+        legs[nlegs++] = {nt, nmax, nullptr, nullptr, 0};
+    }
+    size_t scr = 0;
+    for (int l = 0; l < nlegs; ++l) {
+        Leg &g = legs[l];
+        const size_t sm = f64 ? batched_factor_smem<double>(d, b, g.nm) : batched_factor_smem<float>(d, b, g.nm);
+        if (sm > batched_max_smem()) return RCP_EUNSUPPORTED;
+        g.grid = f64 ? batched_factor_grid<double>(d, b, g.nm, g.nt) : batched_factor_grid<float>(d, b, g.nm, g.nt);
+        if (g.grid <= 0) return RCP_ECUDA;
+        scr = std::max(scr, batched_factor_scratch_ints(b, g.nm) * (size_t)g.grid);
+    }
+    RCP_TRY(grow(h->bscr, scr * sizeof(int)));
     PhaseScope ps(h, s, PH_PANEL);
-    if (f64)
-        CU_TRY(launch_batched_factor<double>(batch, d, b, nmax, n, A64, lda64, (double *const *)A, lda, Dd, Ds, perm,
-                                             (const double *)om, alpha, info, (const int *)h->bord.p,
-                                             (int *)h->bticket.p, (int *)h->bscr.p, grid, s));
-    else
-        CU_TRY(launch_batched_factor<float>(batch, d, b, nmax, n, A64, lda64, (float *const *)A, lda, Dd, Ds, perm,
-                                            (const float *)om, alpha, info, (const int *)h->bord.p,
-                                            (int *)h->bticket.p, (int *)h->bscr.p, grid, s));
+    for (int l = 0; l < nlegs; ++l) {
+        const Leg &g = legs[l];
+        if (f64)
+            CU_TRY(launch_batched_factor<double>(batch, d, b, g.nm, n, A64, lda64, (double *const *)A, lda, Dd, Ds, perm,
+                                                 (const double *)om, alpha, info, (const int *)h->bord.p,
+                                                 (int *)h->bticket.p, (int *)h->bscr.p, g.grid, g.nt, g.first, g.last,
+                                                 s));
+        else
+            CU_TRY(launch_batched_factor<float>(batch, d, b, g.nm, n, A64, lda64, (float *const *)A, lda, Dd, Ds, perm,
+                                                (const float *)om, alpha, info, (const int *)h->bord.p,
+                                                (int *)h->bticket.p, (int *)h->bscr.p, g.grid, g.nt, g.first, g.last,
+                                                s));
+    }
+    return RCP_OK;
+}
+
+rcp_status rcp_set_batched_schedule(rcp_handle *h, int threads, int split) {
+    if (!h || (threads != 0 && threads != 256 && threads != 512) || split < 0 || split > 65535) return RCP_EINVAL;
+    if (split > 0 && threads == 256) return RCP_EINVAL;   // a split runs the large systems with 512 threads
+    h->bt_nt = threads;
+    h->bt_split = split;
+    return RCP_OK;
+}
+
+rcp_status rcp_get_batched_schedule(rcp_handle *h, int nmax, int d, rcp_prec prec, int *b, int *d_out,
+                                    int *threads, int *split) {
+    if (!h || !valid_prec(prec)) return RCP_EINVAL;
+    const int dkey = d > 0 ? d : 0, f64 = prec == RCP_FP64;
+    int tb = 32, td = dkey > 0 ? dkey : std::min(32 + 8, 128), tn = 512, ts = 0;
+    for (const auto &t : h->tuned)
+        if (t.nmax == nmax && t.dkey == dkey && t.f64 == f64) { tb = t.b; td = t.d; tn = t.nt; ts = t.split; }
+    if (h->bt_nt > 0 || h->bt_split > 0) {
+        tn = h->bt_nt > 0 ? h->bt_nt : 512;
+        ts = h->bt_split;
+    }
+    if (b) *b = tb;
+    if (d_out) *d_out = td;
+    if (threads) *threads = tn;
+    if (split) *split = ts >= nmax ? 0 : ts;
     return RCP_OK;
 }
 
@@ -1139,28 +1199,48 @@ rcp_status rcp_tune_batched(rcp_handle *h, int batch, int nmax, const int *n, co
     rcp_opts o = opts ? *opts : rcp_opts{};
     o.prec = prec;
     static const int cand[] = {8, 12, 16, 24, 32, 48, 64};
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // schedules: {threads, split}: one launch of 512-thread CTAs; one of 256-thread CTAs (tried
+    // where two fit an SM); the systems of order <= split in a second launch of 256-thread CTAs
+    const int sp = std::min(256, nmax / 2) & ~3;
+    const int sched[3][2] = {{512, 0}, {256, 0}, {512, sp}};
+    const int keep_nt = h->bt_nt, keep_split = h->bt_split;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CU_TRY(cudaEventCreate(&e0));
     CU_TRY(cudaEventCreate(&e1));
-    int bb = 0, bd = 0;
+    int bb = 0, bd = 0, bnt = 512, bsp = 0;
     float bms = 0.f;
     rcp_status err = RCP_OK;
     for (int b : cand) {
         const int d = dkey > 0 ? dkey : std::min(b + 8, 128);
         const size_t smem = f64 ? batched_factor_smem<double>(d, b, nmax) : batched_factor_smem<float>(d, b, nmax);
         if (smem > batched_max_smem()) continue;
-        o.b = b;
-        o.d = d;
-        err = rcp_factor_batched(h, batch, nmax, n, A64, lda64, A, lda, Dd, Ds, perm, &o, info, stream);   // warm-up
+        for (const auto &sc : sched) {
+            if (sc[0] == 256 && sc[1] == 0) {
+                const int g = f64 ? batched_factor_grid<double>(d, b, nmax, 256) : batched_factor_grid<float>(d, b, nmax, 256);
+                if (g < 2 * sms) continue;
+            }
+            if (sc[1] > 0 && (sc[1] < 32 || sc[1] >= nmax)) continue;
+            h->bt_nt = sc[0];
+            h->bt_split = sc[1];
+            o.b = b;
+            o.d = d;
+            err = rcp_factor_batched(h, batch, nmax, n, A64, lda64, A, lda, Dd, Ds, perm, &o, info, stream);   // warm-up
+            if (err != RCP_OK) break;
+            if (cudaEventRecord(e0, s) != cudaSuccess) { err = RCP_ECUDA; break; }
+            err = rcp_factor_batched(h, batch, nmax, n, A64, lda64, A, lda, Dd, Ds, perm, &o, info, stream);
+            if (err != RCP_OK) break;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { err = RCP_ECUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (bb == 0 || ms < bms) { bb = b; bd = d; bnt = sc[0]; bsp = sc[1]; bms = ms; }
+        }
         if (err != RCP_OK) break;
-        if (cudaEventRecord(e0, s) != cudaSuccess) { err = RCP_ECUDA; break; }
-        err = rcp_factor_batched(h, batch, nmax, n, A64, lda64, A, lda, Dd, Ds, perm, &o, info, stream);
-        if (err != RCP_OK) break;
-        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { err = RCP_ECUDA; break; }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (bb == 0 || ms < bms) { bb = b; bd = d; bms = ms; }
     }
+    h->bt_nt = keep_nt;
+    h->bt_split = keep_split;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaGetLastError();
@@ -1168,8 +1248,10 @@ rcp_status rcp_tune_batched(rcp_handle *h, int batch, int nmax, const int *n, co
     if (bb == 0) return RCP_EUNSUPPORTED;
     bool found = false;
     for (auto &t : h->tuned)
-        if (t.nmax == nmax && t.dkey == dkey && t.f64 == (int)f64) { t.b = bb; t.d = bd; found = true; }
-    if (!found) h->tuned.push_back({nmax, dkey, (int)f64, bb, bd});
+        if (t.nmax == nmax && t.dkey == dkey && t.f64 == (int)f64) {
+            t.b = bb; t.d = bd; t.nt = bnt; t.split = bsp; found = true;
+        }
+    if (!found) h->tuned.push_back({nmax, dkey, (int)f64, bb, bd, bnt, bsp});
     if (best_b) *best_b = bb;
     if (best_ms) *best_ms = bms;
     return RCP_OK;

@@ -102,6 +102,11 @@ def lib():
                                        ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float)]
         L.rcp_tune_batched.restype = ctypes.c_int
         L.rcp_refine_batched.restype = ctypes.c_int
+        L.rcp_set_batched_schedule.argtypes = [P, I, I]
+        L.rcp_set_batched_schedule.restype = ctypes.c_int
+        L.rcp_get_batched_schedule.argtypes = [P, I, I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                               ctypes.POINTER(I)]
+        L.rcp_get_batched_schedule.restype = ctypes.c_int
         for name in ("rcp_profile", "rcp_profile_read", "rcp_set_speculation", "rcp_create", "rcp_sync", "rcp_reserve", "rcp_factor", "rcp_solve", "rcp_refine", "rcp_sysv",
                      "rcp_omega", "rcp_sketch"):
             getattr(L, name).restype = ctypes.c_int
@@ -377,6 +382,21 @@ def rcp_refine_batched(h: Handle, batch: int, nmax: int, nrhs: int, n, A64, lda6
                                     _ptr(LA), _ptr(ldla), _ptr(Dd), _ptr(Ds), _ptr(perm), int(prec), _ptr(Bv),
                                     _ptr(ldb), _ptr(X), _ptr(ldx), float(tol), int(max_iter), _ptr(berr),
                                     _ptr(iters), _stream(stream)), "rcp_refine_batched")
+
+
+def rcp_set_batched_schedule(h: Handle, threads: int = 0, split: int = 0) -> None:
+    """One-to-one call of ``rcp_set_batched_schedule`` (0, 0: the tuned or default schedule)."""
+    _check(lib().rcp_set_batched_schedule(h.h, int(threads), int(split)), "rcp_set_batched_schedule")
+
+
+def rcp_get_batched_schedule(h: Handle, nmax: int, d: int = 0, prec="fp32") -> dict:
+    """``rcp_get_batched_schedule``: the shape and CTA schedule rcp_factor_batched would use."""
+    if isinstance(prec, str):
+        prec = PREC_NAMES[prec]
+    b, dd, t, sp = (ctypes.c_int(0) for _ in range(4))
+    _check(lib().rcp_get_batched_schedule(h.h, int(nmax), int(d), int(prec), ctypes.byref(b), ctypes.byref(dd),
+                                          ctypes.byref(t), ctypes.byref(sp)), "rcp_get_batched_schedule")
+    return {"b": b.value, "d": dd.value, "threads": t.value, "split": sp.value}
 
 
 class Batch:

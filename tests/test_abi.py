@@ -167,3 +167,35 @@ int main(void) {
     e1 = np.array([1.0, 0.0, 0.0])
     yref = np.linalg.lstsq(Hm, e1, rcond=None)[0]
     assert float(res) == pytest.approx(np.linalg.norm(e1 - Hm @ yref), rel=1e-12)
+
+
+def test_batched_schedule_setter_and_getter_on_the_host(clib):
+    # the schedule lives in the handle: no device work, so this runs without a GPU
+    P, I = ctypes.c_void_p, ctypes.c_int
+    clib.rcp_create.argtypes = [ctypes.POINTER(P)]
+    clib.rcp_destroy.argtypes = [P]
+    clib.rcp_set_batched_schedule.argtypes = [P, I, I]
+    clib.rcp_get_batched_schedule.argtypes = [P, I, I, I] + [ctypes.POINTER(I)] * 4
+    h = P()
+    assert clib.rcp_create(ctypes.byref(h)) == 0
+
+    def get(nmax, d=0, prec=1):
+        out = [I(-1) for _ in range(4)]
+        assert clib.rcp_get_batched_schedule(h, nmax, d, prec, *[ctypes.byref(o) for o in out]) == 0
+        return tuple(o.value for o in out)
+
+    try:
+        assert get(512) == (32, 40, 512, 0)              # default shape and schedule
+        assert get(512, 24) == (32, 24, 512, 0)
+        for bad in ((128, 0), (-1, 0), (512, -1), (256, 100), (1024, 0)):
+            assert clib.rcp_set_batched_schedule(h, *bad) == -1, bad
+        assert clib.rcp_set_batched_schedule(h, 256, 0) == 0
+        assert get(512)[2:] == (256, 0)
+        assert clib.rcp_set_batched_schedule(h, 0, 200) == 0
+        assert get(512)[2:] == (512, 200)
+        assert get(200)[2:] == (512, 0)                  # a split at or above nmax is no split
+        assert clib.rcp_set_batched_schedule(h, 0, 0) == 0
+        assert get(512)[2:] == (512, 0)
+        assert clib.rcp_set_batched_schedule(None, 0, 0) == -1
+    finally:
+        clib.rcp_destroy(h)

@@ -264,10 +264,15 @@ def test_batched_autotuner(rcp, handle, d):
     h = rcp.rcp_create()
     b, ms = bt.tune(h, rcp.make_opts(b=0, d=d, seed=2, prec="fp32"))
     assert b in (8, 12, 16, 24, 32, 48, 64) and ms > 0
-    # the explicit shape the tuner chose gives the same factorization as b = 0
+    sch = rcp.rcp_get_batched_schedule(h, bt.nmax, d, "fp32")
+    assert sch["b"] == b and sch["d"] == (d if d else b + 8)
+    assert (sch["threads"], sch["split"]) in ((512, 0), (256, 0), (512, min(256, bt.nmax // 2) & ~3))
+    # the explicit shape and schedule the tuner chose give the same factorization as b = 0
+    rcp.rcp_set_batched_schedule(h, sch["threads"], sch["split"])
     _load(bt, mats)
     bt.factor(h, rcp.make_opts(b=b, d=d if d else b + 8, seed=2, prec="fp32"))
     torch.cuda.synchronize()
+    rcp.rcp_set_batched_schedule(h, 0, 0)
     perms = [bt.perm(i).cpu().numpy().copy() for i in range(len(sizes))]
     dds = [bt.dd(i).cpu().numpy().copy() for i in range(len(sizes))]
     _load(bt, mats)
@@ -284,3 +289,113 @@ def test_batched_autotuner(rcp, handle, d):
         p = bt.perm(i).cpu().numpy()
         growth = oracle.growth_d(bt.dd(i).cpu().numpy(), bt.ds(i).cpu().numpy(), a)
         assert np.abs(a[np.ix_(p, p)] - L @ D @ L.T).max() / np.abs(a).max() < 2e-5 * max(1.0, growth)
+
+
+# ------------------------------------------------------------------------------------------
+# CTA schedules: 256-thread CTAs (two per SM) and the split by system order
+# ------------------------------------------------------------------------------------------
+
+def _factor_with(rcp, h, bt, mats, opts, threads, split):
+    rcp.rcp_set_batched_schedule(h, threads, split)
+    try:
+        _load(bt, mats)
+        bt.factor(h, opts)
+        torch.cuda.synchronize()
+    finally:
+        rcp.rcp_set_batched_schedule(h, 0, 0)
+    return ([bt.perm(i).cpu().numpy().copy() for i in range(bt.batch)],
+            [bt.dd(i).cpu().numpy().copy() for i in range(bt.batch)],
+            [bt.ds(i).cpu().numpy().copy() for i in range(bt.batch)],
+            [bt.f(i).cpu().numpy().copy() for i in range(bt.batch)],
+            bt.info.cpu().numpy().copy())
+
+
+def _same(x, y):
+    for u, v in zip(x[:4], y[:4]):
+        for i, (p, q) in enumerate(zip(u, v)):
+            assert np.array_equal(p, q), i
+    assert np.array_equal(x[4], y[4])
+
+
+@pytest.mark.parametrize("threads,split", [(256, 0), (512, 160), (0, 97)])
+def test_batched_fp64_schedules_give_identical_factors(rcp, threads, split):
+    # FP64 has one code path for every CTA size: the schedule moves work between threads only
+    sizes = [300, 0, 1, 2, 97, 98, 160, 161, 33, 250, 5, 64]
+    mats = [inputs.gaussian_sym(n, seed=700 + i) for i, n in enumerate(sizes)]
+    bt = rcp.Batch(sizes, 1, prec="fp64", device=DEV)
+    h = rcp.rcp_create()
+    opts = _opts(rcp, "fp64", 16, 24, seed=4)
+    ref = _factor_with(rcp, h, bt, mats, opts, 512, 0)
+    got = _factor_with(rcp, h, bt, mats, opts, threads, split)
+    _same(ref, got)
+    for i, a in enumerate(mats):
+        if a.shape[0]:
+            _check_against_oracle(bt, i, a, 4, 24, 1e-11)
+
+
+def test_batched_fp32_split_schedule_gives_identical_factors(rcp):
+    # d <= 48: both launches keep the sketch in registers (the second one's order is 256), as the
+    # single 512-thread launch does, so the factors are bit for bit the same
+    sizes = inputs.batched_sizes(300, 32, 512, seed=9).tolist() + [256, 257, 1, 0]
+    mats = inputs.batched_gaussian(sizes, seed=9)
+    bt = rcp.Batch(sizes, 1, prec="fp32", device=DEV)
+    h = rcp.rcp_create()
+    opts = _opts(rcp, "fp32", 16, 24, seed=6)
+    ref = _factor_with(rcp, h, bt, mats, opts, 512, 0)
+    got = _factor_with(rcp, h, bt, mats, opts, 512, 256)
+    _same(ref, got)
+    assert (got[4] == 0).all()
+
+
+@pytest.mark.parametrize("b,d", [(8, 16), (16, 24), (32, 40)])
+def test_batched_fp32_256_thread_ctas_refine_to_fp64_backward_error(rcp, b, d):
+    # 256-thread CTAs over systems up to order 512: the sketch stays in shared memory
+    sizes = inputs.batched_sizes(200, 32, 512, seed=b).tolist()
+    mats = inputs.batched_gaussian(sizes, seed=b)
+    bt = rcp.Batch(sizes, 16, prec="fp32", device=DEV)
+    h = rcp.rcp_create()
+    rcp.rcp_set_batched_schedule(h, 256, 0)
+    try:
+        rhs = _load(bt, mats, nrhs=16, seed=b)
+        bt.factor(h, _opts(rcp, "fp32", b, d, seed=1))
+        bt.refine(h, tol=1e-12, max_iter=10)
+        torch.cuda.synchronize()
+    finally:
+        rcp.rcp_set_batched_schedule(h, 0, 0)
+    assert (bt.info.cpu().numpy() == 0).all()
+    for i, a in enumerate(mats):
+        be = oracle.berr(a, bt.x(i).cpu().numpy().T, rhs[i].T)
+        assert be <= 1e-12, (i, a.shape[0], be)
+
+
+def test_batched_schedule_graph_replay(rcp):
+    # the split schedule's two launches replay from a CUDA graph with the same results
+    sizes = inputs.batched_sizes(120, 32, 400, seed=12).tolist()
+    mats = inputs.batched_gaussian(sizes, seed=12)
+    bt = rcp.Batch(sizes, 1, prec="fp32", device=DEV)
+    h = rcp.rcp_create()
+    opts = _opts(rcp, "fp32", 16, 24, seed=8)
+    ref = _factor_with(rcp, h, bt, mats, opts, 512, 200)
+    rcp.rcp_set_batched_schedule(h, 512, 200)
+    try:
+        _load(bt, mats)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            bt.factor(h, opts, stream=s)   # warm-up: workspace and order array
+            s.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                bt.factor(h, opts, stream=s)
+        for _ in range(2):
+            _load(bt, mats)
+            g.replay()
+            torch.cuda.synchronize()
+            got = ([bt.perm(i).cpu().numpy().copy() for i in range(bt.batch)],
+                   [bt.dd(i).cpu().numpy().copy() for i in range(bt.batch)],
+                   [bt.ds(i).cpu().numpy().copy() for i in range(bt.batch)],
+                   [bt.f(i).cpu().numpy().copy() for i in range(bt.batch)],
+                   bt.info.cpu().numpy().copy())
+            _same(ref, got)
+    finally:
+        rcp.rcp_set_batched_schedule(h, 0, 0)
