@@ -76,7 +76,7 @@ def parse(argv=None):
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--max-iter", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-n", type=int, default=2048, help="order of the oracle's CPU sample")
     ap.add_argument("--cpu-scan", default="256,1024,2048",
                     help="orders at which the oracle is timed once each for the CPU baseline's size scan")
@@ -344,6 +344,7 @@ def run_ours(a, rank, world, local_rank):
         Xh = torch.zeros_like(Bh).pin_memory()
         rcp.rcp_sysv(h, Ah, Bh, Xh, opts, tol=a.tol, max_iter=a.max_iter, host_buffers=True)
         torch.cuda.synchronize()
+        link_before = pinned_copy_gbs(Ah, dev, stream, reps=1)   # the link's state as the steps start
         barrier()
         walls, gpus = [], []
         t0 = time.perf_counter()
@@ -367,7 +368,7 @@ def run_ours(a, rank, world, local_rank):
         # overlapped with the FP32 rounding and the sketch), and the link's rate for a plain copy
         prof = []
         rcp.rcp_profile(h, True)
-        for _ in range(max(1, a.e2e_steps)):
+        for _ in range(2):
             tp0 = time.perf_counter()
             rcp.rcp_sysv(h, Ah, Bh, Xh, opts, tol=a.tol, max_iter=a.max_iter, host_buffers=True)
             torch.cuda.synchronize()
@@ -381,7 +382,7 @@ def run_ours(a, rank, world, local_rank):
                                         "kernel_phases_ms": round(sum(v[0] for k, v in ph.items() if k != "h2d"), 3)}
                                        for w, ph in prof],
                     "phases_ms": {k: round(v[0], 3) for k, v in prof[-1][1].items()},
-                    "link_gbs": pinned_copy_gbs(Ah, dev, stream)})
+                    "link_gbs_before": link_before, "link_gbs": pinned_copy_gbs(Ah, dev, stream)})
         del Ah, Bh, Xh
 
     batched = (run_batched(a, dev, stream, rank, world, dist, fp64["dgemm_tflops"] if fp64 else None)

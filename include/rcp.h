@@ -340,7 +340,8 @@ rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, 
  *   batch (A64 required: every trial re-copies the originals into A) for every panel width b in
  *   {8, 12, 16, 24, 32, 48, 64} whose per-system state fits one CTA's shared memory, each with
  *   the CTA schedules of rcp_set_batched_schedule: (512, 0), (256, 0) where two 256-thread CTAs
- *   fit an SM, and (512, min(256, nmax / 2)), and keeps the fastest shape and schedule for
+ *   fit an SM, (128, 0) where three 128-thread CTAs do, and (512, min(256, nmax / 2)), and keeps
+ *   the fastest shape and schedule for
  *   (nmax, opts->d, FP64 or not) in the handle: later rcp_factor_batched calls with opts->b == 0
  *   and the same opts->d use them.  With opts->d > 0 the width changes only the
  *   blocking of the deferred trailing update (with q = 1 the pivot sequence is the same in exact
@@ -356,15 +357,17 @@ rcp_status rcp_tune_batched(rcp_handle *h, int batch, int nmax, const int *n, co
  *   over CTAs (a deployment choice; the paper, whose experiments factor one system at a time, has
  *   no counterpart).  Each CTA factors one system at a time and the factor is bound by the latency
  *   of each pivot step, so two resident CTAs per SM overlap two systems' waits.
- *   threads 512: one launch of 512-thread CTAs (one per SM);  threads 256: one launch of 256-thread
- *   CTAs, two per SM where two copies of the per-system shared state fit;  split > 0 (threads 0 or
- *   512): systems with n_i > split in a launch of 512-thread CTAs, then those with n_i <= split in
- *   a launch of 256-thread CTAs whose shared state is sized for order split.  The schedule changes
+ *   threads 512: one launch of 512-thread CTAs (one per SM);  threads 256 or 128: one launch of
+ *   256- or 128-thread CTAs, as many per SM as their shared state and registers allow (up to two
+ *   or four);  split > 0 (threads 0 or 512): systems with n_i > split in a launch of 512-thread
+ *   CTAs, then those with n_i <= split in a launch of 256-thread CTAs whose shared state is sized
+ *   for order split.  The schedule changes
  *   which thread does what, not the arithmetic of a system, except that an FP32 system whose
  *   launch keeps its sketch in registers (d <= 48 and the launch's order <= its CTA size) rounds
  *   the 2x2 steps' sketch update in another order than one that keeps it in shared memory.
  *   threads = split = 0 (the default): the schedule chosen by rcp_tune_batched, else (512, 0).
- *   RCP_EINVAL for other values (threads not 0, 256 or 512; split < 0; split > 0 with threads 256).
+ *   RCP_EINVAL for other values (threads not 0, 128, 256 or 512; split < 0; split > 0 with threads
+ *   128 or 256).
  * rcp_get_batched_schedule -- the shape (b, d) and schedule (threads, split) that rcp_factor_batched
  *   would use for (nmax, d, prec) with opts->b == 0 (d = 0 as in rcp_opts).  Host outputs may be
  *   NULL. */

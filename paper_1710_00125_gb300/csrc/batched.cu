@@ -170,6 +170,7 @@ template <typename T, int DR, int NT>
 __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared<T> &sh, int &cnt) {
     static_assert(DR == 0 || (sizeof(T) == 4 && DR % 4 == 0), "register sketch: FP32, whole float4s");
     constexpr int DR4 = DR > 0 ? DR / 4 : 1;
+    constexpr int RU = NT >= 512 ? 1 : 512 / NT;   // positions per thread whose loads go out together
     float4 b4[DR4];   // the register sketch column (DR > 0)
     const int n = a.n[sys], d = a.d, nmax = bt_stride(a.nmax), tid = threadIdx.x;
     const int lda = a.lda[sys];
@@ -290,33 +291,47 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
             // ---- phase A: k <-> P in the trailing part of A; Schur column k in the new labels
             //      (W, Lp and Bs are still in the old labels: position x came from sigma(x)) ----
             BtCand<T> lc{T(-1), INT_MAX};
-            for (int x = k + tid; x < n; x += NT) {
-                T av;
-                if (x == k) {
-                    av = A[(size_t)P + (size_t)P * lda];
-                    if (P != k) {
-                        A[(size_t)P + (size_t)P * lda] = A[(size_t)k + (size_t)k * lda];
-                        A[(size_t)k + (size_t)k * lda] = av;
-                    }
-                } else if (x == P) {
-                    av = A[(size_t)P + (size_t)k * lda];
-                } else {
-                    T *up = x > P ? A + (size_t)x + (size_t)P * lda : A + (size_t)P + (size_t)x * lda;
-                    av = *up;
-                    if (P != k) {
-                        T *uk = A + (size_t)x + (size_t)k * lda;
-                        *up = *uk;
-                        *uk = av;
+            // RU positions per thread at a time: all their loads of A are issued before any store
+            // (no two positions touch the same entry), so a thread waits for one round trip
+            for (int xb = k + tid; xb < n; xb += RU * NT) {
+                T av[RU], ak[RU];
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int x = xb + u * NT;
+                    if (x >= n) continue;
+                    if (x == k) {
+                        av[u] = A[(size_t)P + (size_t)P * lda];
+                        if (P != k) ak[u] = A[(size_t)k + (size_t)k * lda];
+                    } else if (x == P) {
+                        av[u] = A[(size_t)P + (size_t)k * lda];
+                    } else {
+                        av[u] = x > P ? A[(size_t)x + (size_t)P * lda] : A[(size_t)P + (size_t)x * lda];
+                        if (P != k) ak[u] = A[(size_t)x + (size_t)k * lda];
                     }
                 }
-                // the panel's correction does not wait for the load of A
-                const int sx = x == k ? P : (x == P ? k : x);
-                T cs = T(0);
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int x = xb + u * NT;
+                    if (x >= n) continue;
+                    if (P != k && x != P) {
+                        if (x == k) {
+                            A[(size_t)P + (size_t)P * lda] = ak[u];
+                            A[(size_t)k + (size_t)k * lda] = av[u];
+                        } else {
+                            T *up = x > P ? A + (size_t)x + (size_t)P * lda : A + (size_t)P + (size_t)x * lda;
+                            *up = ak[u];
+                            A[(size_t)x + (size_t)k * lda] = av[u];
+                        }
+                    }
+                    // the panel's correction does not wait for the load of A
+                    const int sx = x == k ? P : (x == P ? k : x);
+                    T cs = T(0);
 #pragma unroll 8
-                for (int t = 0; t < i; ++t) cs += W[(size_t)t * nmax + sx] * Lp[(size_t)t * nmax + P];
-                av -= cs;
-                c1[x] = av;
-                if (x > k && bt_better(bt_abs(av), x, lc.v, lc.j)) lc = BtCand<T>{bt_abs(av), x};
+                    for (int t = 0; t < i; ++t) cs += W[(size_t)t * nmax + sx] * Lp[(size_t)t * nmax + P];
+                    const T v = av[u] - cs;
+                    c1[x] = v;
+                    if (x > k && bt_better(bt_abs(v), x, lc.v, lc.j)) lc = BtCand<T>{bt_abs(v), x};
+                }
             }
             if constexpr (DR > 0) {
                 // the owners of positions k and P stage their columns
@@ -349,13 +364,22 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
             const int sR = R < 0 ? -1 : (R == P ? k : R);   // old label of R
             if (kase == 4) {
                 // ---- phase R: Schur column R (new labels), decision, 2x2 inverse, staging ----
-                for (int x = k + tid; x < n; x += NT) {
-                    T av = a_sym(A, lda, x, R);
+                for (int xb = k + tid; xb < n; xb += RU * NT) {
+                T avr[RU];
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int x = xb + u * NT;
+                    if (x < n) avr[u] = a_sym(A, lda, x, R);
+                }
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int x = xb + u * NT;
+                    if (x >= n) continue;
                     const int sx = x == k ? P : (x == P ? k : x);
                     T cs = T(0);
 #pragma unroll 8
                     for (int t = 0; t < i; ++t) cs += W[(size_t)t * nmax + sx] * Lp[(size_t)t * nmax + sR];
-                    av -= cs;
+                    const T av = avr[u] - cs;
                     c2[x] = av;
                     if (x == R) {
                         int kk;
@@ -377,6 +401,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                         }
                         sh.kase = kk;
                     }
+                }
                 }
                 if constexpr (DR > 0) {
                     if (tid == k + 1 || tid == sR) {
@@ -677,12 +702,13 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
     __syncthreads();
 }
 
-// NT threads per CTA: 512 (one CTA per SM) or 256 (two per SM where the shared memory allows).
+// NT threads per CTA: 512 (one CTA per SM), 256 or 128 (two, or up to four, per SM where the
+// shared memory allows).
 // The CTAs take the systems order[first .. last) (first and last read from device memory when
 // given, else 0 and batch).
 template <typename T, int DR, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) batched_factor_kernel(BtFactorArgs<T> a) {
-    static_assert(NT == 256 || NT == 512, "CTA size");
+    static_assert(NT == 128 || NT == 256 || NT == 512, "CTA size");
     extern __shared__ __align__(16) unsigned char bt_raw[];
     __shared__ BtShared<T> sh;
     int cnt = 0;
@@ -1111,16 +1137,18 @@ template <typename T>
 static void (*bt_factor_fn(int d, int nmax, int nt))(BtFactorArgs<T>) {
     if constexpr (sizeof(T) == 4) {
         if (bt_stride(d) <= BT_DR && nmax <= nt)
-            return nt == 256 ? batched_factor_kernel<T, BT_DR, 256> : batched_factor_kernel<T, BT_DR, 512>;
+            return nt == 128 ? batched_factor_kernel<T, BT_DR, 128>
+                 : nt == 256 ? batched_factor_kernel<T, BT_DR, 256> : batched_factor_kernel<T, BT_DR, 512>;
     }
     (void)d;
     (void)nmax;
-    return nt == 256 ? batched_factor_kernel<T, 0, 256> : batched_factor_kernel<T, 0, 512>;
+    return nt == 128 ? batched_factor_kernel<T, 0, 128>
+         : nt == 256 ? batched_factor_kernel<T, 0, 256> : batched_factor_kernel<T, 0, 512>;
 }
 
 template <typename T>
 int batched_factor_grid(int d, int b, int nmax, int nt) {
-    if (nt != 256 && nt != 512) return 0;
+    if (nt != 128 && nt != 256 && nt != 512) return 0;
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1140,7 +1168,7 @@ cudaError_t launch_batched_factor(int batch, int d, int b, int nmax, const int *
                                   int *const *perm, const T *om, double alpha, int *info, const int *order,
                                   int *ticket, int *pscr, int grid, int nt, const int *first, const int *last,
                                   cudaStream_t s) {
-    if (nt != 256 && nt != 512) return cudaErrorInvalidValue;
+    if (nt != 128 && nt != 256 && nt != 512) return cudaErrorInvalidValue;
     BtFactorArgs<T> a{batch, d, b, nmax, n, A64, lda64, A, lda, Dd, Ds, perm, om, alpha, info, order, ticket, pscr,
                       first, last};
     const size_t smem = batched_factor_smem<T>(d, b, nmax);

@@ -206,7 +206,7 @@ size_t batched_refine_smem(int nrhs, int nmax);
 // order: systems by decreasing n; above (nmax + 1 ints, may be NULL): above[v] = systems with n > v
 cudaError_t launch_batched_order(int batch, int nmax, const int *n, int *order, int *above, cudaStream_t s);
 size_t batched_factor_scratch_ints(int b, int nmax);   // per CTA
-// resident CTAs of the factor kernel with nt (256 or 512) threads per CTA (0: error)
+// resident CTAs of the factor kernel with nt (128, 256 or 512) threads per CTA (0: error)
 template <typename T>
 int batched_factor_grid(int d, int b, int nmax, int nt);
 // one launch over order[*first .. *last) (NULL: 0 and batch) with nt threads per CTA

@@ -1161,8 +1161,9 @@ rcp_status rcp_factor_batched(rcp_handle *h, int batch, int nmax, const int *n, 
 }
 
 rcp_status rcp_set_batched_schedule(rcp_handle *h, int threads, int split) {
-    if (!h || (threads != 0 && threads != 256 && threads != 512) || split < 0 || split > 65535) return RCP_EINVAL;
-    if (split > 0 && threads == 256) return RCP_EINVAL;   // a split runs the large systems with 512 threads
+    if (!h || (threads != 0 && threads != 128 && threads != 256 && threads != 512) || split < 0 || split > 65535)
+        return RCP_EINVAL;
+    if (split > 0 && threads != 0 && threads != 512) return RCP_EINVAL;   // a split runs the large systems with 512 threads
     h->bt_nt = threads;
     h->bt_split = split;
     return RCP_OK;
@@ -1202,10 +1203,11 @@ rcp_status rcp_tune_batched(rcp_handle *h, int batch, int nmax, const int *n, co
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // schedules: {threads, split}: one launch of 512-thread CTAs; one of 256-thread CTAs (tried
-    // where two fit an SM); the systems of order <= split in a second launch of 256-thread CTAs
+    // schedules: {threads, split}: one launch of 512-thread CTAs; one of 256- or 128-thread CTAs
+    // (tried where two, or three, fit an SM); the systems of order <= split in a second launch of
+    // 256-thread CTAs
     const int sp = std::min(256, nmax / 2) & ~3;
-    const int sched[3][2] = {{512, 0}, {256, 0}, {512, sp}};
+    const int sched[4][2] = {{512, 0}, {256, 0}, {128, 0}, {512, sp}};
     const int keep_nt = h->bt_nt, keep_split = h->bt_split;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CU_TRY(cudaEventCreate(&e0));
@@ -1218,9 +1220,9 @@ rcp_status rcp_tune_batched(rcp_handle *h, int batch, int nmax, const int *n, co
         const size_t smem = f64 ? batched_factor_smem<double>(d, b, nmax) : batched_factor_smem<float>(d, b, nmax);
         if (smem > batched_max_smem()) continue;
         for (const auto &sc : sched) {
-            if (sc[0] == 256 && sc[1] == 0) {
-                const int g = f64 ? batched_factor_grid<double>(d, b, nmax, 256) : batched_factor_grid<float>(d, b, nmax, 256);
-                if (g < 2 * sms) continue;
+            if (sc[0] < 512 && sc[1] == 0) {   // smaller CTAs only where more of them fit an SM
+                const int g = f64 ? batched_factor_grid<double>(d, b, nmax, sc[0]) : batched_factor_grid<float>(d, b, nmax, sc[0]);
+                if (g < (sc[0] == 256 ? 2 : 3) * sms) continue;
             }
             if (sc[1] > 0 && (sc[1] < 32 || sc[1] >= nmax)) continue;
             h->bt_nt = sc[0];

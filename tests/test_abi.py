@@ -187,7 +187,7 @@ def test_batched_schedule_setter_and_getter_on_the_host(clib):
     try:
         assert get(512) == (32, 40, 512, 0)              # default shape and schedule
         assert get(512, 24) == (32, 24, 512, 0)
-        for bad in ((128, 0), (-1, 0), (512, -1), (256, 100), (1024, 0)):
+        for bad in ((64, 0), (-1, 0), (512, -1), (256, 100), (128, 100), (1024, 0)):
             assert clib.rcp_set_batched_schedule(h, *bad) == -1, bad
         assert clib.rcp_set_batched_schedule(h, 256, 0) == 0
         assert get(512)[2:] == (256, 0)

@@ -266,7 +266,7 @@ def test_batched_autotuner(rcp, handle, d):
     assert b in (8, 12, 16, 24, 32, 48, 64) and ms > 0
     sch = rcp.rcp_get_batched_schedule(h, bt.nmax, d, "fp32")
     assert sch["b"] == b and sch["d"] == (d if d else b + 8)
-    assert (sch["threads"], sch["split"]) in ((512, 0), (256, 0), (512, min(256, bt.nmax // 2) & ~3))
+    assert (sch["threads"], sch["split"]) in ((512, 0), (256, 0), (128, 0), (512, min(256, bt.nmax // 2) & ~3))
     # the explicit shape and schedule the tuner chose give the same factorization as b = 0
     rcp.rcp_set_batched_schedule(h, sch["threads"], sch["split"])
     _load(bt, mats)
@@ -317,7 +317,7 @@ def _same(x, y):
     assert np.array_equal(x[4], y[4])
 
 
-@pytest.mark.parametrize("threads,split", [(256, 0), (512, 160), (0, 97)])
+@pytest.mark.parametrize("threads,split", [(256, 0), (128, 0), (512, 160), (0, 97)])
 def test_batched_fp64_schedules_give_identical_factors(rcp, threads, split):
     # FP64 has one code path for every CTA size: the schedule moves work between threads only
     sizes = [300, 0, 1, 2, 97, 98, 160, 161, 33, 250, 5, 64]
@@ -331,6 +331,19 @@ def test_batched_fp64_schedules_give_identical_factors(rcp, threads, split):
     for i, a in enumerate(mats):
         if a.shape[0]:
             _check_against_oracle(bt, i, a, 4, 24, 1e-11)
+
+
+@pytest.mark.parametrize("threads", [128, 256])
+def test_batched_fp32_small_ctas_with_register_sketch_give_identical_factors(rcp, threads):
+    # orders <= the CTA size with d <= 48: every schedule keeps the sketch in registers
+    sizes = inputs.batched_sizes(150, 1, threads, seed=threads).tolist() + [threads, 1, 0]
+    mats = inputs.batched_gaussian(sizes, seed=threads)
+    bt = rcp.Batch(sizes, 1, prec="fp32", device=DEV)
+    h = rcp.rcp_create()
+    opts = _opts(rcp, "fp32", 12, 20, seed=5)
+    ref = _factor_with(rcp, h, bt, mats, opts, 512, 0)
+    got = _factor_with(rcp, h, bt, mats, opts, threads, 0)
+    _same(ref, got)
 
 
 def test_batched_fp32_split_schedule_gives_identical_factors(rcp):
@@ -347,14 +360,14 @@ def test_batched_fp32_split_schedule_gives_identical_factors(rcp):
     assert (got[4] == 0).all()
 
 
-@pytest.mark.parametrize("b,d", [(8, 16), (16, 24), (32, 40)])
-def test_batched_fp32_256_thread_ctas_refine_to_fp64_backward_error(rcp, b, d):
-    # 256-thread CTAs over systems up to order 512: the sketch stays in shared memory
+@pytest.mark.parametrize("threads,b,d", [(256, 8, 16), (256, 16, 24), (256, 32, 40), (128, 8, 16), (128, 12, 20)])
+def test_batched_fp32_small_ctas_refine_to_fp64_backward_error(rcp, threads, b, d):
+    # 256- and 128-thread CTAs over systems up to order 512: the sketch stays in shared memory
     sizes = inputs.batched_sizes(200, 32, 512, seed=b).tolist()
     mats = inputs.batched_gaussian(sizes, seed=b)
     bt = rcp.Batch(sizes, 16, prec="fp32", device=DEV)
     h = rcp.rcp_create()
-    rcp.rcp_set_batched_schedule(h, 256, 0)
+    rcp.rcp_set_batched_schedule(h, threads, 0)
     try:
         rhs = _load(bt, mats, nrhs=16, seed=b)
         bt.factor(h, _opts(rcp, "fp32", b, d, seed=1))
