@@ -22,7 +22,7 @@
  *   Dd[i]    = D(i, i);  Ds[i] = D(i+1, i) (0 for a 1x1 block and for i = n-1)
  *   info     = 1 + position of the first exactly zero 1x1 pivot, 0 if none (LAPACK style)
  *
- * Readings of the paper where it is silent (listed again in the design notes):
+ * Readings of the paper where it is silent:
  *   - ties in every argmax go to the smallest current position;
  *   - the comparisons in the pivot rules are the non-strict ">=" printed in the figures;
  *   - SBKP case (0) (lambda = 0) takes a_kk as a 1x1 pivot with a zero multiplier
