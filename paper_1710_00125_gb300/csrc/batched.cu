@@ -814,12 +814,28 @@ __device__ __forceinline__ void bt_stage(int n, int j0, int nb, const TL *L, int
     }
 }
 
+// Bring the next block column of L (rows j0.. of columns j0 .. j0+31) towards L2 while the current
+// one is being used: one prefetch per 128-byte line, so that the next staging does not wait for DRAM.
+template <typename TL>
+__device__ __forceinline__ void bt_prefetch_block(int n, int j0, const TL *L, int lda) {
+    if (j0 < 0 || j0 >= n) return;
+    const int nb = min(32, n - j0), rows = n - j0;
+    constexpr int PER = 128 / (int)sizeof(TL);   // entries per line
+    const int lines = (rows + PER - 1) / PER;
+    for (int e = threadIdx.x; e < nb * lines; e += bt::THREADS) {
+        const int c = e / lines, l = e % lines;
+        const TL *a = L + (size_t)(j0 + l * PER) + (size_t)(j0 + c) * lda;
+        asm volatile("prefetch.global.L2 [%0];" :: "l"(a));
+    }
+}
+
 // y (n x rc, row stride BT_YS) <- (P L D L^T P^T)^{-1} y, by 32-column blocks of L staged in Ls.
 template <typename TL>
 __device__ void bt_solve(int n, int rc, const TL *L, int lda, const TL *de, const TL *df, const unsigned char *kind,
                          const int *perm, TL *y, TL *Ls, TL *part) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = (rc + 3) >> 2;
+    bt_prefetch_block<TL>(n, 0, L, lda);   // the forward pass's first block column
     // v = P^T y: perm comes from the factor kernel; an index outside [0, n) (a factor that
     // never ran) is replaced so that no access leaves the system's rows
     for (int e = tid; e < n * BT_RC; e += bt::THREADS) {
@@ -837,6 +853,7 @@ __device__ void bt_solve(int n, int rc, const TL *L, int lda, const TL *de, cons
         const int nb = min(32, n - j0), rows = n - j0;
         __syncthreads();
         bt_stage<TL>(n, j0, nb, L, lda, Ls);
+        bt_prefetch_block<TL>(n, j0 + 32, L, lda);
         __syncthreads();
         // the diagonal block, one warp per right-hand side, row = lane
         for (int c = warp; c < rc; c += bt::WARPS) {
@@ -869,6 +886,7 @@ __device__ void bt_solve(int n, int rc, const TL *L, int lda, const TL *de, cons
         }
     }
     __syncthreads();
+    bt_prefetch_block<TL>(n, ((n - 1) / 32) * 32, L, lda);   // the backward pass's first block column
     // ---- block diagonal: v <- D^{-1} v ----
     for (int e = tid; e < n * rc; e += bt::THREADS) {
         const int i = e / rc, c = e % rc;
@@ -886,6 +904,7 @@ __device__ void bt_solve(int n, int rc, const TL *L, int lda, const TL *de, cons
         const int nb = min(32, n - j0), rows = n - j0, R = rows - nb;
         __syncthreads();
         bt_stage<TL>(n, j0, nb, L, lda, Ls);
+        bt_prefetch_block<TL>(n, j0 - 32, L, lda);
         __syncthreads();
         if (R > 0) {
             // y(B, :) -= L(below, B)^T y(below, :): BT_SL row slices, reduced after
