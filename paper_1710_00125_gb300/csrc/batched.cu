@@ -171,6 +171,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
     static_assert(DR == 0 || (sizeof(T) == 4 && DR % 4 == 0), "register sketch: FP32, whole float4s");
     constexpr int DR4 = DR > 0 ? DR / 4 : 1;
     constexpr int RU = NT >= 512 ? 1 : 512 / NT;   // positions per thread whose loads go out together
+    constexpr int NW = NT / 32, MR = 128 / NW;     // warps; sketch rows per thread (d <= NW * MR = 128)
     float4 b4[DR4];   // the register sketch column (DR > 0)
     const int n = a.n[sys], d = a.d, nmax = bt_stride(a.nmax), tid = threadIdx.x;
     const int lda = a.lda[sys];
@@ -214,9 +215,9 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
         T *Os = W + bt::TILE * (bt::TILE + 1);         // [d][33]:  Os[r][i] = Omega(r, i0 + i)
         const int jj = tid & 31, r0 = tid >> 5;
         for (int j0 = 0; j0 < n; j0 += bt::TILE) {
-            T acc[(4096 / NT)];
+            T acc[MR];
 #pragma unroll
-            for (int m = 0; m < (4096 / NT); ++m) acc[m] = T(0);
+            for (int m = 0; m < MR; ++m) acc[m] = T(0);
             for (int i0 = 0; i0 < n; i0 += bt::TILE) {
                 for (int e = tid; e < bt::TILE * bt::TILE; e += NT) {
                     const int lo = e & 31, hi = e >> 5;
@@ -240,16 +241,16 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                 for (int i = 0; i < bt::TILE; ++i) {
                     const T av = As[i * (bt::TILE + 1) + jj];
 #pragma unroll
-                    for (int m = 0; m < (4096 / NT); ++m) {
-                        const int r = r0 + (NT / 32) * m;
+                    for (int m = 0; m < MR; ++m) {
+                        const int r = r0 + NW * m;
                         if (r < d) acc[m] += Os[r * (bt::TILE + 1) + i] * av;
                     }
                 }
                 __syncthreads();
             }
 #pragma unroll
-            for (int m = 0; m < (4096 / NT); ++m) {
-                const int r = r0 + (NT / 32) * m;
+            for (int m = 0; m < MR; ++m) {
+                const int r = r0 + NW * m;
                 if (r < dp && j0 + jj < n) Bs[(size_t)(j0 + jj) * dp + r] = r < d ? acc[m] : T(0);
             }
         }
@@ -277,7 +278,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
             if (bt_better(s, j, cand.v, cand.j)) cand = BtCand<T>{s, j};
         }
     }
-    cand = bt_argmax<NT / 32>(cand, sh, cnt);
+    cand = bt_argmax<NW>(cand, sh, cnt);
 
     int info = 0, k = 0, np = 0;
     bool bad = false;
@@ -351,7 +352,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                     stg[e < dp ? r : 2 * dp + r] = Bs[(size_t)(e < dp ? k : P) * dp + r];
                 }
             }
-            lc = bt_argmax<NT / 32>(lc, sh, cnt);
+            lc = bt_argmax<NW>(lc, sh, cnt);
             // ---- SBKP decision (every thread, in the factor's type) ----
             const int R = lc.j < n ? lc.j : -1;     // new label
             const T lam = R >= 0 ? lc.v : T(0);
@@ -596,7 +597,7 @@ __device__ void bt_factor_one(const BtFactorArgs<T> &a, int sys, T *sm, BtShared
                     else A[(size_t)Rm + (size_t)x * lda] = A[(size_t)x + (size_t)tgt * lda];
                 }
             }
-            cand = bt_argmax<NT / 32>(nc, sh, cnt);
+            cand = bt_argmax<NW>(nc, sh, cnt);
             k += s;
             i += s;
         }
