@@ -145,12 +145,16 @@ def test_batched_nonfinite_system_is_isolated(rcp, handle):
 # FP32 factor + FP64 refinement: the ragged workload of n ~ U{32..512}, 16 right-hand sides
 # ------------------------------------------------------------------------------------------
 
-def test_batched_fp32_factor_backward_error(rcp, handle):
+@pytest.mark.parametrize("threads", [512, 256, 128])
+def test_batched_fp32_factor_backward_error(rcp, threads):
+    # every CTA schedule: 512 threads keep the sketch in registers here, 256 and 128 in shared memory
     sizes = inputs.batched_sizes(24, 32, 512, seed=1).tolist() + [512, 32, 33]
     mats = inputs.batched_gaussian(sizes, seed=1)
     bt = rcp.Batch(sizes, 1, prec="fp32", device=DEV)
     _load(bt, mats)
-    bt.factor(handle, _opts(rcp, "fp32", seed=6))
+    h = rcp.rcp_create()
+    rcp.rcp_set_batched_schedule(h, threads, 0)
+    bt.factor(h, _opts(rcp, "fp32", seed=6))
     torch.cuda.synchronize()
     assert (bt.info == 0).all()
     for i, a in enumerate(mats):
