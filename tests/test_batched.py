@@ -416,3 +416,35 @@ def test_batched_schedule_graph_replay(rcp):
             _same(ref, got)
     finally:
         rcp.rcp_set_batched_schedule(h, 0, 0)
+
+
+# every oracle decision of these systems (one Omega, seed 0, d = 40) clears its threshold by more
+# than 2e-4 (checked below): the FP32 batched factor must take the oracle's decisions
+WELL_SEPARATED = [(40, 1000), (97, 1000), (130, 1000), (200, 1001), (257, 1001), (300, 1000), (400, 1000),
+                  (450, 1000), (512, 1002)]
+
+
+@pytest.mark.parametrize("threads,split", [(512, 0), (256, 0), (128, 0), (512, 256)])
+def test_batched_fp32_factor_matches_the_oracle_where_decisions_are_well_separated(rcp, threads, split):
+    mats = [inputs.gaussian_sym(n, seed=s) for n, s in WELL_SEPARATED]
+    refs = []
+    for a in mats:
+        ref = oracle.rcp(a, oracle.omega(0, 40, a.shape[0]), record=True)
+        assert min(m for _, m in oracle.decision_margins(ref["steps"])) > 2e-4
+        refs.append(ref)
+    bt = rcp.Batch([a.shape[0] for a in mats], 1, prec="fp32", device=DEV)
+    _load(bt, mats)
+    h = rcp.rcp_create()
+    rcp.rcp_set_batched_schedule(h, threads, split)
+    bt.factor(h, _opts(rcp, "fp32", 16, 40, seed=0))
+    torch.cuda.synchronize()
+    assert (bt.info == 0).all()
+    for i, (a, ref) in enumerate(zip(mats, refs)):
+        assert np.array_equal(bt.perm(i).cpu().numpy(), ref["perm"]), i
+        ds = bt.ds(i).cpu().numpy()
+        assert np.array_equal(ds != 0.0, ref["Ds"] != 0.0), i
+        rho = oracle.growth_d(ref["Dd"], ref["Ds"], a)
+        scale = np.abs(a).max() * max(1.0, rho)
+        assert np.abs(bt.dd(i).cpu().numpy() - ref["Dd"]).max() <= 1e-4 * scale, i
+        assert np.abs(ds - ref["Ds"]).max() <= 1e-4 * scale, i
+        assert np.abs(_unit_lower(bt.f(i)) - ref["L"]).max() <= 1e-4 * max(1.0, ref["max_abs_L"]), i
