@@ -159,18 +159,19 @@ __global__ void __launch_bounds__(256) tc_prep_kernel(FactorWork<float> w, float
 
 // ------------------------------------------------------------------------------------------
 // tcgen05 MMA kernel, warp-specialized.  Warp 0 (one elected thread) streams operand chunks
-// through the stage ring and issues the MMAs of each tile into one of two 128-column TMEM
-// accumulators; warps 1..8 drain the other accumulator (tcgen05.ld: lane quarter w % 4, a
-// 64-column half each) and update A, so the epilogue of tile t overlaps the MMAs of tile t + 1.
+// through the stage ring and issues the MMAs of each super-tile into one of two 256-column TMEM
+// accumulators; warps 1..16 drain the other accumulator (tcgen05.ld: lane quarter w % 4, a
+// 64-column quarter each) and update A, so the epilogue of super-tile t overlaps the MMAs of t + 1.
 // Each epilogue warp reads its 32 x 64 block of A in four 16-column chunks, two chunks ahead:
 // the first two are loaded before it waits for the accumulator, so the HBM latency of the
-// read-modify-write stays behind the tile's MMAs.
+// read-modify-write stays behind the MMAs.  Sixteen epilogue warps (not eight) keep twice the
+// bytes of A in flight per SM; 17 warps leave 96 registers per thread, which two chunks fit.
 //   full[s]  : operands of the chunk in stage s arrived (bulk-copy transaction count)
 //   free[s]  : the MMAs reading stage s completed (tcgen05.commit)
 //   accf[a]  : accumulator a holds a finished tile (tcgen05.commit)
 //   acce[a]  : the epilogue has read accumulator a (one arrival per epilogue warp)
 // ------------------------------------------------------------------------------------------
-constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_EPI_WARPS = 16;
 constexpr int TC_EPI_COLS = tc::TM * tc::NT * 4 / TC_EPI_WARPS;   // columns per epilogue warp
 constexpr int TC_THREADS = 32 * (1 + TC_EPI_WARPS);
 
