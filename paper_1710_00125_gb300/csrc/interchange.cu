@@ -118,27 +118,38 @@ __global__ void scatter_kernel(FactorWork<T> w) {
 }
 
 // Panel multipliers (already in position order, column-major) into A(:, k0:kend); clears the
-// position marks.  Grid: (row chunks of PS_ROWS, panel columns).
+// position marks.  Work items (column t, chunk x of PS_ROWS rows) over a fixed grid: the panel's
+// position is known only on the device, and a grid sized for the whole matrix would launch
+// thousands of empty blocks for the late panels.
 constexpr int PS_THREADS = 256, PS_ROWS = 4 * PS_THREADS;
 template <typename T>
-__global__ void panel_store_kernel(FactorWork<T> w, int *phi) {
+__global__ void __launch_bounds__(PS_THREADS) panel_store_kernel(FactorWork<T> w, int *phi) {
     if (ldcg(w.status) != 0) return;
     const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
     const int width = kend - k0;
     T *__restrict__ A = w.A;
-    // block (x, t): column k0 + t, rows k0 + t + 1 + [x, x + 1) * PS_ROWS
-    const int t = blockIdx.y;
-    if (t < width) {
-        const int p0 = k0 + t + 1 + blockIdx.x * PS_ROWS;
+    // item (t, x): column k0 + t, rows k0 + t + 1 + [x, x + 1) * PS_ROWS
+    const int chunks = (n - k0 + PS_ROWS - 1) / PS_ROWS;
+    const long long items = width > 0 ? (long long)width * chunks : 0;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int t = (int)(it / chunks), x = (int)(it - (long long)t * chunks);
+        const int p0 = k0 + t + 1 + x * PS_ROWS;
+        if (p0 >= n) continue;
         const T *__restrict__ src = w.Lc + (size_t)t * n;
         T *__restrict__ dst = A + (size_t)(k0 + t) * lda;
+        T v[PS_ROWS / PS_THREADS];
 #pragma unroll
         for (int u = 0; u < PS_ROWS / PS_THREADS; ++u) {
             const int p = p0 + u * PS_THREADS + threadIdx.x;
-            if (p < n) dst[p] = src[p];
+            v[u] = p < n ? src[p] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < PS_ROWS / PS_THREADS; ++u) {
+            const int p = p0 + u * PS_THREADS + threadIdx.x;
+            if (p < n) dst[p] = v[u];
         }
     }
-    if (blockIdx.x == 0 && blockIdx.y == 0) {
+    if (blockIdx.x == 0) {
         const int M = min(w.st->n_moved, w.maxmoved);
         for (int m = threadIdx.x; m < M; m += blockDim.x) {
             const int j = w.moved[m];
@@ -235,9 +246,7 @@ cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s, bool mark
     count_launches(1);
     scatter_kernel<T><<<g, IC_THREADS, 0, s>>>(w);
     count_launches(1);
-    // the panel width (device-side) is at most bw columns, each with fewer than n rows to store
-    const dim3 grid((unsigned)std::max(1, (w.n + PS_ROWS - 1) / PS_ROWS), (unsigned)w.bw);
-    panel_store_kernel<T><<<grid, PS_THREADS, 0, s>>>(w, phi);
+    panel_store_kernel<T><<<4 * sms, PS_THREADS, 0, s>>>(w, phi);
     count_launches(1);
     return cudaGetLastError();
 }
