@@ -19,6 +19,31 @@ enum : int {
 // Upper bound on a single device-side wait (nanoseconds of %globaltimer).
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s
 
+// Programmatic dependent launch between the kernels of one panel (gather, scatter, panel store,
+// panel record, tile preparation, trailing update): each of them is launched with the stream's
+// programmatic serialization allowed, and waits for its predecessor's completion (and memory) at
+// its first instruction, so only the launch itself overlaps the predecessor's last wave.  A
+// predecessor lets its successor's launch begin once all of its CTAs are running.  Both are
+// no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Device state of one factorization, kept in handle workspace.
 struct FactorState {
     int next;        // first column of the next panel

@@ -50,6 +50,8 @@ __device__ __forceinline__ bool moved_item(long long item, int M, int nt, int *m
 
 template <typename T>
 __global__ void gather_kernel(FactorWork<T> w, const int *phi) {
+    pdl_wait();
+    pdl_release();
     if (ldcg(w.status) != 0) return;
     const int M = min(ldcg(&w.st->n_moved), w.maxmoved);
     const int n = w.n, lda = w.lda, kend = w.st->kend;
@@ -87,6 +89,8 @@ __global__ void gather_kernel(FactorWork<T> w, const int *phi) {
 
 template <typename T>
 __global__ void scatter_kernel(FactorWork<T> w) {
+    pdl_wait();
+    pdl_release();
     if (ldcg(w.status) != 0) return;
     const int M = min(ldcg(&w.st->n_moved), w.maxmoved);
     const int n = w.n, lda = w.lda, kend = w.st->kend;
@@ -124,6 +128,8 @@ __global__ void scatter_kernel(FactorWork<T> w) {
 constexpr int PS_THREADS = 256, PS_ROWS = 4 * PS_THREADS;
 template <typename T>
 __global__ void __launch_bounds__(PS_THREADS) panel_store_kernel(FactorWork<T> w, int *phi) {
+    pdl_wait();
+    pdl_release();
     if (ldcg(w.status) != 0) return;
     const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
     const int width = kend - k0;
@@ -242,11 +248,14 @@ cudaError_t launch_interchange(const FactorWork<T> &w, cudaStream_t s, bool mark
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int g = 4 * sms;
-    gather_kernel<T><<<g, IC_THREADS, 0, s>>>(w, phi);
+    cudaError_t e = launch_pdl(gather_kernel<T>, dim3(g), dim3(IC_THREADS), 0, s, w, (const int *)phi);
+    if (e != cudaSuccess) return e;
     count_launches(1);
-    scatter_kernel<T><<<g, IC_THREADS, 0, s>>>(w);
+    e = launch_pdl(scatter_kernel<T>, dim3(g), dim3(IC_THREADS), 0, s, w);
+    if (e != cudaSuccess) return e;
     count_launches(1);
-    panel_store_kernel<T><<<4 * sms, PS_THREADS, 0, s>>>(w, phi);
+    e = launch_pdl(panel_store_kernel<T>, dim3(4 * sms), dim3(PS_THREADS), 0, s, w, phi);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     return cudaGetLastError();
 }
@@ -355,6 +364,8 @@ __global__ void guard_zero_kernel(int n, int k, T *A, int lda, double *Dd, doubl
 // perm and the panel bounds after panel blk (after its interchange kernels)
 template <typename T>
 __global__ void panel_record_kernel(FactorWork<T> w, int blk) {
+    pdl_wait();
+    pdl_release();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         w.pbounds[2 * blk] = w.st->k0;
         w.pbounds[2 * blk + 1] = w.st->kend;
@@ -461,7 +472,8 @@ cudaError_t launch_panel_record(const FactorWork<T> &w, int blk, cudaStream_t s)
     int blocks = (w.n + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (blocks > 1024) blocks = 1024;
-    panel_record_kernel<T><<<blocks, 256, 0, s>>>(w, blk);
+    cudaError_t e = launch_pdl(panel_record_kernel<T>, dim3(blocks), dim3(256), 0, s, w, blk);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     return cudaGetLastError();
 }

@@ -97,6 +97,8 @@ template <bool F16>
 __global__ void __launch_bounds__(256) tc_prep_kernel(FactorWork<float> w, float *ops, int nrb_cap, int nkc_cap) {
     constexpr int KC = tc::KC<F16>;
     __shared__ __align__(16) float t2[2][tc::TILE_FLOATS];   // hi, lo images of one operand tile (32 KB)
+    pdl_wait();
+    pdl_release();
     if (ldcg(w.status) != 0) return;
     const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
     const int K = kend - k0, N = n - kend;
@@ -233,6 +235,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_trailing_kernel(FactorWork<f
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    pdl_wait();
     if (ldcg(w.status) != 0) return;
     const int n = w.n, lda = w.lda, k0 = w.st->k0, kend = w.st->kend;
     const int K = kend - k0, N = n - kend;
@@ -448,11 +451,14 @@ static cudaError_t launch_trailing_tc_fmt(const FactorWork<float> &w, float *ops
     }
     const long long rows = (long long)w.n - kmin;
     const long long nrb = rows > 0 ? (rows + tc::TM - 1) / tc::TM : 1;
-    tc_prep_kernel<F16><<<8 * sms, 256, 0, s>>>(w, ops, nrb_cap, nkc_cap);
+    cudaError_t e = launch_pdl(tc_prep_kernel<F16>, dim3(8 * sms), dim3(256), 0, s, w, ops, nrb_cap, nkc_cap);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     const long long tiles = supertile_count(nrb);
     const int grid = (int)(tiles < sms ? tiles : sms);
-    tc_trailing_kernel<F16><<<grid > 0 ? grid : 1, TC_THREADS, smem, s>>>(w, ops, nrb_cap, nkc_cap);
+    e = launch_pdl(tc_trailing_kernel<F16>, dim3(grid > 0 ? grid : 1), dim3(TC_THREADS), smem, s, w, (const float *)ops,
+                   nrb_cap, nkc_cap);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     return cudaGetLastError();
 }
