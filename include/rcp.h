@@ -292,12 +292,13 @@ rcp_status rcp_profile_read(rcp_handle *h, double *ms, int *launches, int nphase
  * Batched ragged systems: many independent symmetric systems A_i x_i = b_i of small order
  * (n_i <= nmax, typically 32..512), each factored by Algorithm 1 (q = 1) exactly as rcp_factor
  * does, and solved or refined exactly as rcp_solve / rcp_refine do.  One persistent kernel per
- * phase covers the whole batch: one CTA works on one system at a time, taking systems from an
+ * phase covers the whole batch (the factor: two with a split schedule, see
+ * rcp_set_batched_schedule): one CTA works on one system at a time, taking systems from an
  * atomic ticket in decreasing order of n_i; the sketch and the current panel of a system live
  * in that CTA's shared memory, A_i in global memory.  No call allocates memory once the handle's
- * batch workspace (order array, ticket, Omega: about 4 * batch + 8 * d * nmax bytes) is large
- * enough, so after one warm-up call with the same batch and nmax the calls can be captured
- * into a CUDA graph.
+ * batch workspace (order array, ticket, Omega, per-CTA scratch: about 4 * (batch + nmax) +
+ * 8 * d * nmax bytes plus the scratch) is large enough, so after one warm-up call with the same
+ * batch, nmax and schedule the calls can be captured into a CUDA graph.
  *
  * Pointer arrays ("device array of device pointers") hold one pointer per system; every other
  * per-system array is a device array of length batch.  nmax (host) bounds every n_i; systems
