@@ -60,7 +60,6 @@ struct rcp_handle {
     Buf omt;                                       // Omega split into TF32 tiles (tensor-core sketch)
     Buf tcops;                                     // tensor-core operand tiles
     int trace_n = 0;
-    int y_words = -1;                              // solve work last used by: 1 FP32 (epoch words), 0 FP64
     Buf bord, bom, bticket, bscr;                  // batched path: order, Omega, ticket, per-CTA scratch
     const int *bord_n = nullptr;                   // (n, batch, nmax) the order was made for
     int bord_batch = -1, bord_nmax = -1;
@@ -500,21 +499,21 @@ rcp_status factor_impl(rcp_handle *h, int n, T *A, int lda, double *Dd, double *
 int solve_nb(int n) { return (n + 63) / 64; }
 
 // Workspace of the solves (work area and flags) for n x nrhs.
+// The solves' readers take a block as done when its flag (FP64) or its 64-bit words (FP32, the
+// value with the epoch in the high half) carry the current epoch.  The epoch is chosen on the host,
+// so a call replayed from a CUDA graph runs with the epoch of its capture and would find its own
+// previous replay's flags and words already "current": the flags and, for FP32 factors, the word
+// arrays are cleared on the stream before every solve (a few microseconds), which also removes
+// any doubles an FP64 solve left where FP32 words are read.
 template <typename T>
 rcp_status prepare_solve_ws(rcp_handle *h, int n, int nrhs, cudaStream_t s) {
     RCP_TRY(ensure_small(h));
     RCP_TRY(grow_zeroed(h->Y, solve_work_bytes<T>(n, nrhs), s, false));
-    // the FP32 solves take a 64-bit word of the work area as published once its high half is the
-    // current epoch: FP64 solves leave other bit patterns there, so the area is cleared on a switch
-    const int words = sizeof(T) == sizeof(float) ? 1 : 0;
-    if (h->y_words != words) {
-        if (h->y_words >= 0) CU_TRY(cudaMemsetAsync(h->Y.p, 0, h->Y.bytes, s));
-        h->y_words = words;
-    }
     const int nb = solve_nb(n);
-    bool fresh = h->flags.bytes < (size_t)(2 * nb + 2) * sizeof(int);
     RCP_TRY(grow(h->flags, (size_t)(2 * nb + 2) * sizeof(int)));
-    if (fresh) CU_TRY(cudaMemsetAsync(h->flags.p, 0, h->flags.bytes, s));
+    CU_TRY(cudaMemsetAsync(h->flags.p, 0, (size_t)(2 * nb) * sizeof(int), s));
+    if (sizeof(T) == sizeof(float))
+        CU_TRY(cudaMemsetAsync(h->Y.p, 0, 2 * (size_t)n * nrhs * sizeof(unsigned long long), s));
     return RCP_OK;
 }
 

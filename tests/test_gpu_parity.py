@@ -921,3 +921,51 @@ def test_fp32_factor_matches_the_oracle_where_decisions_are_well_separated(rcp, 
     assert np.abs(_unit_lower(A) - ref["L"]).max() <= 1e-4 * max(1.0, ref["max_abs_L"])
     rho = oracle.growth_d(ref["Dd"], ref["Ds"], a)
     assert abs(st.growth_D - rho) <= 0.01 * rho
+
+
+# ------------------------------------------------------------------------------------------
+# Graph capture: rcp_factor and rcp_solve (no host rcp_stats, workspace reserved first) replay
+# from a CUDA graph with the results of the eager calls, replay after replay
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x3"])
+def test_factor_and_solve_replay_from_a_cuda_graph(rcp, prec):
+    n, b, d, nrhs = 1500, 128, 80, 3
+    a = inputs.gaussian_sym(n, seed=31)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    A0 = torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(dt)
+    rhs = torch.from_numpy(inputs.x_true(n, nrhs, seed=4)).to(DEV)
+    h = rcp.rcp_create()
+    opts = rcp.make_opts(b=b, d=d, seed=2, prec=prec)
+    rcp.rcp_reserve(h, n, nrhs, opts)
+    A = A0.clone()
+    Dd = torch.zeros(n, dtype=torch.float64, device=DEV)
+    Ds = torch.zeros_like(Dd)
+    perm = torch.zeros(n, dtype=torch.int32, device=DEV)
+    X = rhs.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        rcp.rcp_factor(h, A, Dd, Ds, perm, opts, stream=s, stats=False)
+        rcp.rcp_solve(h, A, Dd, Ds, perm, prec, X, stream=s)
+    s.synchronize()
+    ref = [t.clone() for t in (A, Dd, Ds, perm, X)]
+    assert torch.isfinite(X).all()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        A.copy_(A0)
+        X.copy_(rhs)
+        rcp.rcp_factor(h, A, Dd, Ds, perm, opts, stream=s, stats=False)
+        rcp.rcp_solve(h, A, Dd, Ds, perm, prec, X, stream=s)
+    for _ in range(3):
+        A.fill_(float("nan"))      # the graph copies A and X in again
+        X.fill_(float("nan"))
+        for t in (Dd, Ds, perm):   # as before the eager call
+            t.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for got, want in zip((A, Dd, Ds, perm, X), ref):
+            assert torch.equal(got, want)
+    assert rcp.rcp_sync(h) == 0
+    be = oracle.berr(a, X.cpu().numpy().T, rhs.cpu().numpy().T)
+    assert be < (1e-13 if prec == "fp64" else 1e-5), be
