@@ -170,8 +170,11 @@ rcp_status rcp_solve(rcp_handle *h, int n, int nrhs, const void *LA, int lda, co
  * (||A||_inf ||x||_inf) (the experiments section's backward error), stop when berr <= tol,
  * else x += solve(r).  At most max_iter corrections; the loop also stops when a correction
  * fails to halve berr (the factor's error times the condition number is not small: the
- * iteration stagnates or diverges; rcp_refine_gmres is the remedy).  The loop control stays
- * on the device (no host round trip per iteration).
+ * iteration stagnates or diverges; rcp_refine_gmres is the remedy).  Without stats the loop
+ * control stays on the device (no host round trip per iteration: all max_iter iterations are
+ * launched and those after the stop skip their work, so the call can be captured); with stats
+ * (the call synchronizes anyway) the host reads the stop flag after each check and launches no
+ * further iterations.
  *   A64, lda     device double: the ORIGINAL matrix (lower triangle)
  *   LA, ldla     device factor; Dd, Ds, perm from rcp_factor; prec its precision
  *   Bv, ldb      device double n x nrhs right-hand sides

@@ -688,9 +688,27 @@ rcp_status rcp_solve(rcp_handle *h, int n, int nrhs, const void *LA, int lda, co
     return solve_impl<float>(h, n, nrhs, (const float *)LA, lda, Dd, Ds, perm, X, ldx, nullptr, s);
 }
 
+// host_checks: the caller synchronizes at the end anyway (it fills host statistics), so after each
+// iteration's convergence check the host reads the flag and stops launching: the iterations
+// after convergence are not launched at all (they would only skip their work on the device, at
+// the cost of their launches: ~0.4 ms for eight of them at n = 16384).  Without it (no host
+// statistics, e.g. inside a graph capture) all max_iter iterations are launched and skip.
+static rcp_status refine_run(rcp_handle *h, int n, int nrhs, const double *A64, int lda, const void *LA, int ldla,
+                             const double *Dd, const double *Ds, const int *perm, rcp_prec prec, const double *Bv,
+                             int ldb, double *X, int ldx, double tol, int max_iter, rcp_stream_t stream,
+                             rcp_stats *stats, bool host_checks);
+
 rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda, const void *LA, int ldla,
                       const double *Dd, const double *Ds, const int *perm, rcp_prec prec, const double *Bv, int ldb,
                       double *X, int ldx, double tol, int max_iter, rcp_stream_t stream, rcp_stats *stats) {
+    return refine_run(h, n, nrhs, A64, lda, LA, ldla, Dd, Ds, perm, prec, Bv, ldb, X, ldx, tol, max_iter, stream, stats,
+                      stats != nullptr);
+}
+
+static rcp_status refine_run(rcp_handle *h, int n, int nrhs, const double *A64, int lda, const void *LA, int ldla,
+                             const double *Dd, const double *Ds, const int *perm, rcp_prec prec, const double *Bv,
+                             int ldb, double *X, int ldx, double tol, int max_iter, rcp_stream_t stream,
+                             rcp_stats *stats, bool host_checks) {
     if (!h || n < 0 || nrhs < 0 || nrhs > kMaxRhs || !valid_prec(prec) || max_iter < 0) return RCP_EINVAL;
     if (stats) std::memset(stats, 0, sizeof *stats);
     if (n == 0 || nrhs == 0) return RCP_OK;
@@ -723,6 +741,12 @@ rcp_status rcp_refine(rcp_handle *h, int n, int nrhs, const double *A64, int lda
         CU_TRY(launch_refine_check(nrhs, sc->mx, &sc->anorm, tol, &sc->conv, &sc->berr, &sc->prev, &sc->iters,
                                    it < max_iter, s));
         if (it == max_iter) break;
+        if (host_checks) {
+            int conv = 0;
+            CU_TRY(cudaMemcpyAsync(&conv, &sc->conv, sizeof conv, cudaMemcpyDeviceToHost, s));
+            CU_TRY(cudaStreamSynchronize(s));
+            if (conv != 0) break;
+        }
         CU_TRY(cudaMemcpyAsync(Dc, R, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
         RCP_TRY(do_solve(Dc, &sc->conv, true));
         CU_TRY(launch_axpy_update(n, nrhs, X, ldx, Dc, n, &sc->conv, s));
@@ -1002,8 +1026,8 @@ rcp_status rcp_sysv(rcp_handle *h, int n, int nrhs, const double *A64, int lda, 
     if (fs != RCP_OK) return fs;
     (void)fst;
     rcp_stats rst;
-    rcp_status rs = rcp_refine(h, n, nrhs, dA, dlda, h->F.p, n, (double *)h->Dd.p, (double *)h->Ds.p, (int *)h->perm.p, r.prec,
-                               dB, dldb, dX, dldx, tol, max_iter, stream, nullptr);
+    rcp_status rs = refine_run(h, n, nrhs, dA, dlda, h->F.p, n, (double *)h->Dd.p, (double *)h->Ds.p, (int *)h->perm.p,
+                               r.prec, dB, dldb, dX, dldx, tol, max_iter, stream, nullptr, true);
     if (rs != RCP_OK) return rs;
     // classic refinement stopped short of the tolerance (the factor is too inaccurate for this
     // system): GMRES-based refinement from the current iterate
