@@ -67,6 +67,14 @@ def test_omega_is_standard_normal():
     assert not np.allclose(oracle.omega(3, 4, 8), oracle.omega(4, 4, 8))
 
 
+def test_omega_columns_and_rows_do_not_depend_on_the_draw_size():
+    # column j and row pair (2t, 2t+1) come from counter (j, t): a d x n draw is the leading
+    # block of any larger draw with the same seed (a ragged batch shares one d x nmax draw)
+    big = oracle.omega(7, 21, 300)
+    for d, n in ((21, 97), (20, 300), (5, 1), (1, 33)):
+        assert np.array_equal(oracle.omega(7, d, n), big[:d, :n]), (d, n)
+
+
 def test_sketch_is_the_matrix_product():
     a = inputs.gaussian_sym(37, seed=2)
     om = oracle.omega(5, 9, 37)
