@@ -17,15 +17,17 @@
 //
 // Data path per panel:
 //   prep kernel: rows kend..n of W (Wbuf) and of L21 (the panel columns of A) are rounded to
-//     hi/lo and written as K-major 128-row x 32-column tiles in the exact shared-memory image of
+//     hi/lo and written as K-major 128-row tiles of 128-byte rows (32 TF32 or 64 FP16 columns),
+//     in the exact shared-memory image of
 //     the 128-byte swizzle (16 KB per tile, contiguous), one tile per (row block, K chunk).
-//   MMA kernel: persistent CTAs walk the 128 x 128 tiles (I >= J) of the trailing lower
-//     triangle.  Per K chunk one thread issues four 16 KB bulk copies (W_hi, W_lo of row block
-//     I; L_hi, L_lo of row block J) into a 3-stage ring guarded by mbarriers, then 4 K-steps x 3
-//     tcgen05.mma (M = N = 128, K = 8 in TF32, 16 in FP16) into a 128-column TMEM accumulator,
-//     and commits the stage back to its "free" barrier.  After the last chunk the accumulator
-//     is drained by eight warps (tcgen05.ld 32x32b: TMEM lane quarter w % 4, 64 of the 128
-//     columns each) and subtracted from A in place.
+//   MMA kernel: persistent CTAs walk the 128 x 256 super-tiles (row block I, column tiles J0 and
+//     J0 + 1, I >= J0) of the trailing lower triangle.  Per K chunk one thread issues six 16 KB
+//     bulk copies (W_hi, W_lo of row block I; L_hi, L_lo of column tiles J0 and J0 + 1) into a
+//     2-stage ring of 96 KB guarded by mbarriers, then 4 K-steps x 3 tcgen05.mma (M = 128,
+//     N = 256, K = 8 in TF32, 16 in FP16) into one of two 256-column TMEM accumulators, and
+//     commits the stage back to its "free" barrier.  After the last chunk the accumulator is
+//     drained by sixteen warps (tcgen05.ld 32x32b: TMEM lane quarter w % 4, 64 of the 256 columns
+//     each) and subtracted from A in place, while the MMAs of the next super-tile fill the other.
 // Every wait is bounded (kWaitLimitNs); on expiry the status word is set, the CTA stops
 // issuing work, waits for its issued copies and MMAs (bounded), frees its tensor memory and
 // returns.
