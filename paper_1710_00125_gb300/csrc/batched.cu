@@ -4,7 +4,13 @@
 // Each CTA takes systems from an atomic ticket; the order puts the largest systems first
 // (longest-processing-time-first scheduling), so the tail of the launch is made of small
 // systems.  One CTA runs Algorithm 1 (q = 1) on one system, so every synchronization of the
-// method is a CTA barrier, and the per-system state (sketch, panel) lives in shared memory:
+// method is a CTA barrier, and the per-system state (sketch, panel) lives in shared memory.
+// The factor's CTAs have 512, 256 or 128 threads: a pivot step waits on a dependent load of A
+// and on CTA barriers, so two or more smaller CTAs per SM overlap several systems' waits (a
+// thread then owns several positions of a step and issues all their loads of A at once).  A
+// split schedule runs the systems above an order in one launch of 512-thread CTAs and the rest
+// in a second launch of 256-thread CTAs sized for the smaller order.
+//
 //
 //   Bs   nmax x dp     the sketch B = Omega A, one column per row ([j][r], dp = d rounded up to
 //                      a multiple of 4, padding zero), updated after every pivot
