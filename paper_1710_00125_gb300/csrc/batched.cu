@@ -9,8 +9,8 @@
 // and on CTA barriers, so two or more smaller CTAs per SM overlap several systems' waits (a
 // thread then owns several positions of a step and issues all their loads of A at once).  A
 // split schedule runs the systems above an order in one launch of 512-thread CTAs and the rest
-// in a second launch of 256-thread CTAs sized for the smaller order.
-//
+// in a second launch of 256-thread CTAs sized for the smaller order.  The shared state of one
+// system:
 //
 //   Bs   nmax x dp     the sketch B = Omega A, one column per row ([j][r], dp = d rounded up to
 //                      a multiple of 4, padding zero), updated after every pivot
